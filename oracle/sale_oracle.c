@@ -1,0 +1,719 @@
+/*
+ * sale_oracle.c -- plain serial FP64 reference of the SALE hydro cycle.
+ *
+ * TEST INFRASTRUCTURE (see sale_oracle.h).  Written for a reader checking
+ * it against the method by eye: one loop per step, no blocking, no fusion.
+ * Build with -O2 -ffp-contract=off so that no FMA contraction happens.
+ *
+ * The paper (ScalSALE, arXiv 2209.01983) names the physics steps -- ideal
+ * gas EoS (Sec. I-D), Update_acceleration (Sec. III-D), Calculate_density
+ * in Hydro (Sec. III-A), Lagrangian and Eulerian rezoning with an advection
+ * phase (Table I, Sec. IV) -- and the scheme (SALE) without printing its
+ * equations.  The formulas here are the standard ones:
+ *
+ *  Geometry:   V = (1/24) sum_f S_f . ((p2-p0) x (p3-p1)), S_f = p0+p1+p2+p3
+ *              over the 6 outward faces (p0..p3) of the hex.  This is the
+ *              divergence theorem over faces fanned from their node mean
+ *              and equals the exact volume of the trilinear hex.
+ *  EoS:        p = (g-1) rho e,  cs^2 = g (g-1) max(e,0).
+ *  Viscosity:  div = sum_a gradV_a . u_a / V;  if div < 0
+ *              q = rho (c_q (L div)^2 + c_l cs L |div|), else q = 0,
+ *              L = V / max_f |A_f|.
+ *  Lagrange:   sigma = p + q; F_a = sum_c sigma_c gradV_a(c);
+ *              u+ = u + dt F/m_n (normal part zeroed on walls);
+ *              ubar = (u + u+)/2; x+ = x + dt ubar;
+ *              e+ = e - dt/m_c sigma_c sum_a gradV_a(c).ubar_a
+ *              (compatible update: total energy conserved to roundoff).
+ *  dt:         dt = min(cfl min_c L/sqrt(cs^2 + 2 q/rho), growth * dt_last).
+ *  Remap:      rezone to the reference mesh; face swept volumes dV as hex
+ *              volumes; mass flux mu = rho_donor dV (upwind); energy flux
+ *              mu e_donor; node mass/momentum/KE fluxes on the dual mesh
+ *              psi = sum_{cells at edge} (mu_lo + mu_hi)/8, upwind by node;
+ *              KE lost by the momentum remap returned to the cells.
+ */
+#include "sale_oracle.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+/* ------------------------------------------------------------------ */
+/* Hex geometry                                                        */
+/* ------------------------------------------------------------------ */
+
+/* Outward-oriented faces of the hex, local node ids in cyclic order. */
+static const int FACE[6][4] = {
+    {0, 4, 6, 2}, /* x-lo */
+    {1, 3, 7, 5}, /* x-hi */
+    {0, 1, 5, 4}, /* y-lo */
+    {2, 6, 7, 3}, /* y-hi */
+    {0, 2, 3, 1}, /* z-lo */
+    {4, 5, 7, 6}, /* z-hi */
+};
+
+static void cross3(const double *a, const double *b, double *c) {
+  c[0] = a[1] * b[2] - a[2] * b[1];
+  c[1] = a[2] * b[0] - a[0] * b[2];
+  c[2] = a[0] * b[1] - a[1] * b[0];
+}
+
+static double dot3(const double *a, const double *b) {
+  return a[0] * b[0] + a[1] * b[1] + a[2] * b[2];
+}
+
+/* Coordinates relative to local node 0 (the volume and its gradient are
+ * translation invariant; the shift only reduces cancellation). */
+static void shift_to_node0(const double *X, double *Y) {
+  for (int a = 0; a < 8; ++a)
+    for (int d = 0; d < 3; ++d) Y[a * 3 + d] = X[a * 3 + d] - X[d];
+}
+
+double oracle_hex_volume(const double *X) {
+  double Y[24];
+  shift_to_node0(X, Y);
+  double sum = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    const double *p0 = &Y[FACE[f][0] * 3], *p1 = &Y[FACE[f][1] * 3];
+    const double *p2 = &Y[FACE[f][2] * 3], *p3 = &Y[FACE[f][3] * 3];
+    double d1[3], d2[3], D[3], S[3];
+    for (int d = 0; d < 3; ++d) {
+      d1[d] = p2[d] - p0[d];
+      d2[d] = p3[d] - p1[d];
+      S[d] = p0[d] + p1[d] + p2[d] + p3[d];
+    }
+    cross3(d1, d2, D);
+    sum += dot3(S, D);
+  }
+  return sum / 24.0;
+}
+
+/* dV/dp_k of one face term T = S.((p2-p0)x(p3-p1)) is
+ * (p_{k+1} + 2 p_{k+2} + p_{k+3}) x (p_{k+3} - p_{k+1})  (indices mod 4);
+ * V = (1/24) sum_f T_f, so dV/dx_a sums this over the 3 faces holding a. */
+void oracle_hex_volume_grad(const double *X, double *G) {
+  double Y[24];
+  shift_to_node0(X, Y);
+  for (int i = 0; i < 24; ++i) G[i] = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    for (int k = 0; k < 4; ++k) {
+      const double *pa = &Y[FACE[f][(k + 1) & 3] * 3];
+      const double *pb = &Y[FACE[f][(k + 2) & 3] * 3];
+      const double *pc = &Y[FACE[f][(k + 3) & 3] * 3];
+      double r[3], b[3], t[3];
+      for (int d = 0; d < 3; ++d) {
+        r[d] = pa[d] + 2.0 * pb[d] + pc[d];
+        b[d] = pc[d] - pa[d];
+      }
+      cross3(r, b, t);
+      double *g = &G[FACE[f][k] * 3];
+      for (int d = 0; d < 3; ++d) g[d] += t[d];
+    }
+  }
+  for (int i = 0; i < 24; ++i) G[i] /= 24.0;
+}
+
+/* Face vector area A_f = (1/2) (p2-p0) x (p3-p1), outward. */
+void oracle_hex_face_areas(const double *X, double *A) {
+  for (int f = 0; f < 6; ++f) {
+    const double *p0 = &X[FACE[f][0] * 3], *p1 = &X[FACE[f][1] * 3];
+    const double *p2 = &X[FACE[f][2] * 3], *p3 = &X[FACE[f][3] * 3];
+    double d1[3], d2[3], D[3];
+    for (int d = 0; d < 3; ++d) {
+      d1[d] = p2[d] - p0[d];
+      d2[d] = p3[d] - p1[d];
+    }
+    cross3(d1, d2, D);
+    for (int d = 0; d < 3; ++d) A[f * 3 + d] = 0.5 * D[d];
+  }
+}
+
+/* L = V / max_f |A_f|  (= min edge length on a box). */
+double oracle_hex_char_length(const double *X) {
+  double A[18];
+  oracle_hex_face_areas(X, A);
+  double amax2 = 0.0;
+  for (int f = 0; f < 6; ++f) {
+    double a2 = dot3(&A[f * 3], &A[f * 3]);
+    if (a2 > amax2) amax2 = a2;
+  }
+  return oracle_hex_volume(X) / sqrt(amax2);
+}
+
+/* ------------------------------------------------------------------ */
+/* Indexing                                                            */
+/* ------------------------------------------------------------------ */
+
+static long long cell_id(const oracle_state *s, int i, int j, int k) {
+  return (long long)i + (long long)s->nx * ((long long)j + (long long)s->ny * k);
+}
+
+static long long node_id(const oracle_state *s, int i, int j, int k) {
+  return (long long)i +
+         (long long)(s->nx + 1) * ((long long)j + (long long)(s->ny + 1) * k);
+}
+
+/* Gather the 8 node coordinates of cell (i,j,k) from arrays px,py,pz. */
+static void gather_hex(const oracle_state *s, int i, int j, int k,
+                       const double *px, const double *py, const double *pz,
+                       double *X) {
+  for (int a = 0; a < 8; ++a) {
+    long long n = node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a * 3 + 0] = px[n];
+    X[a * 3 + 1] = py[n];
+    X[a * 3 + 2] = pz[n];
+  }
+}
+
+/* Number of cells that contain node (i,j,k). */
+static int node_cell_count(const oracle_state *s, int i, int j, int k) {
+  int c = 1;
+  c *= (i == 0 || i == s->nx) ? 1 : 2;
+  c *= (j == 0 || j == s->ny) ? 1 : 2;
+  c *= (k == 0 || k == s->nz) ? 1 : 2;
+  return c;
+}
+
+/* Zero the velocity components normal to the reflecting walls the node
+ * lies on (all walls are axis-aligned planes). */
+static void apply_wall_bc(const oracle_state *s, int i, int j, int k,
+                          double *uu, double *vv, double *ww) {
+  if ((i == 0 && s->prm.reflect[0]) || (i == s->nx && s->prm.reflect[1])) *uu = 0.0;
+  if ((j == 0 && s->prm.reflect[2]) || (j == s->ny && s->prm.reflect[3])) *vv = 0.0;
+  if ((k == 0 && s->prm.reflect[4]) || (k == s->nz && s->prm.reflect[5])) *ww = 0.0;
+}
+
+/* ------------------------------------------------------------------ */
+/* State                                                               */
+/* ------------------------------------------------------------------ */
+
+static double *alloc_zero(long long n) {
+  return (double *)calloc((size_t)(n > 0 ? n : 1), sizeof(double));
+}
+
+oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,
+                            const double *yn, const double *zn,
+                            const oracle_params *prm) {
+  if (nx < 1 || ny < 1 || nz < 1 || !xn || !yn || !zn || !prm) return NULL;
+  oracle_state *s = (oracle_state *)calloc(1, sizeof(oracle_state));
+  if (!s) return NULL;
+  s->nx = nx;
+  s->ny = ny;
+  s->nz = nz;
+  s->nc = (long long)nx * ny * nz;
+  s->nn = (long long)(nx + 1) * (ny + 1) * (nz + 1);
+  s->prm = *prm;
+  double **node_arrays[] = {&s->x, &s->y, &s->z, &s->xr, &s->yr,
+                            &s->zr, &s->u, &s->v, &s->w, &s->mn};
+  for (size_t i = 0; i < sizeof(node_arrays) / sizeof(node_arrays[0]); ++i) {
+    *node_arrays[i] = alloc_zero(s->nn);
+    if (!*node_arrays[i]) { oracle_destroy(s); return NULL; }
+  }
+  double **cell_arrays[] = {&s->m, &s->e, &s->vol, &s->rho,
+                            &s->p, &s->q, &s->cs, &s->len};
+  for (size_t i = 0; i < sizeof(cell_arrays) / sizeof(cell_arrays[0]); ++i) {
+    *cell_arrays[i] = alloc_zero(s->nc);
+    if (!*cell_arrays[i]) { oracle_destroy(s); return NULL; }
+  }
+  memcpy(s->x, xn, sizeof(double) * s->nn);
+  memcpy(s->y, yn, sizeof(double) * s->nn);
+  memcpy(s->z, zn, sizeof(double) * s->nn);
+  memcpy(s->xr, xn, sizeof(double) * s->nn);
+  memcpy(s->yr, yn, sizeof(double) * s->nn);
+  memcpy(s->zr, zn, sizeof(double) * s->nn);
+  return s;
+}
+
+void oracle_destroy(oracle_state *s) {
+  if (!s) return;
+  double *arrays[] = {s->x, s->y, s->z, s->xr, s->yr, s->zr, s->u, s->v, s->w,
+                      s->mn, s->m, s->e, s->vol, s->rho, s->p, s->q, s->cs, s->len};
+  for (size_t i = 0; i < sizeof(arrays) / sizeof(arrays[0]); ++i) free(arrays[i]);
+  free(s);
+}
+
+/* Node mass m_n = sum over the cells holding the node of m_c / 8. */
+static void node_masses_from_cells(oracle_state *s) {
+  for (long long n = 0; n < s->nn; ++n) s->mn[n] = 0.0;
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        double share = s->m[cell_id(s, i, j, k)] / 8.0;
+        for (int a = 0; a < 8; ++a)
+          s->mn[node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))] += share;
+      }
+}
+
+/* EoS, sound speed, artificial viscosity and length scale at the current
+ * positions and velocities. */
+int oracle_eos(oracle_state *s) {
+  const double g = s->prm.gamma;
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double X[24], G[24], U[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        gather_hex(s, i, j, k, s->u, s->v, s->w, U);
+        double V = oracle_hex_volume(X);
+        if (!(V > 0.0)) {
+          s->status = isnan(V) ? ORACLE_ENAN : ORACLE_ENEGVOL;
+          return s->status;
+        }
+        double rho = s->m[c] / V;
+        double e = s->e[c];
+        double p = (g - 1.0) * rho * e;
+        double cs = sqrt(g * (g - 1.0) * (e > 0.0 ? e : 0.0));
+        oracle_hex_volume_grad(X, G);
+        double dvdt = 0.0;
+        for (int a = 0; a < 8; ++a) dvdt += dot3(&G[a * 3], &U[a * 3]);
+        double div = dvdt / V;
+        double L = oracle_hex_char_length(X);
+        double q = 0.0;
+        if (div < 0.0) {
+          double ld = L * div;
+          q = rho * (s->prm.c_q * ld * ld + s->prm.c_l * cs * L * fabs(div));
+        }
+        if (isnan(p) || isnan(q) || isnan(cs)) {
+          s->status = ORACLE_ENAN;
+          return s->status;
+        }
+        s->vol[c] = V;
+        s->rho[c] = rho;
+        s->p[c] = p;
+        s->cs[c] = cs;
+        s->q[c] = q;
+        s->len[c] = L;
+      }
+  return ORACLE_OK;
+}
+
+double oracle_cfl_dt(const oracle_state *s) {
+  double dt = INFINITY;
+  for (long long c = 0; c < s->nc; ++c) {
+    double ceff = sqrt(s->cs[c] * s->cs[c] + 2.0 * s->q[c] / s->rho[c]);
+    double dtc = s->prm.cfl * s->len[c] / ceff;
+    if (dtc < dt) dt = dtc;
+  }
+  return dt;
+}
+
+/* Proposed next dt: min(CFL limit, growth * last dt used). */
+static int propose_dt(oracle_state *s) {
+  double dt = oracle_cfl_dt(s);
+  double cap = s->prm.dt_growth * s->dt_last;
+  if (cap < dt) dt = cap;
+  if (!(dt > 0.0) || isinf(dt)) {
+    s->status = ORACLE_EDT;
+    return s->status;
+  }
+  s->dt = dt;
+  return ORACLE_OK;
+}
+
+int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
+                     long long deposit_cell, double deposit_energy) {
+  const double g = s->prm.gamma;
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double X[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        double V = oracle_hex_volume(X);
+        s->m[c] = rho0[c] * V;
+        s->e[c] = p0[c] / ((g - 1.0) * rho0[c]);
+      }
+  if (deposit_cell >= 0 && deposit_cell < s->nc)
+    s->e[deposit_cell] = deposit_energy / s->m[deposit_cell];
+  for (long long n = 0; n < s->nn; ++n) s->u[n] = s->v[n] = s->w[n] = 0.0;
+  node_masses_from_cells(s);
+  s->t = 0.0;
+  s->cycle = 0;
+  s->status = ORACLE_OK;
+  int rc = oracle_eos(s);
+  if (rc) return rc;
+  double dt = oracle_cfl_dt(s);
+  if (s->prm.dt_init > 0.0 && s->prm.dt_init < dt) dt = s->prm.dt_init;
+  if (!(dt > 0.0) || isinf(dt)) return s->status = ORACLE_EDT;
+  s->dt = dt;
+  s->dt_last = dt;
+  return ORACLE_OK;
+}
+
+int oracle_set_state(oracle_state *s, const double *x, const double *y,
+                     const double *z, const double *u, const double *v,
+                     const double *w, const double *mn, const double *m,
+                     const double *e, double t, double dt_last) {
+  size_t nb = sizeof(double) * (size_t)s->nn, cb = sizeof(double) * (size_t)s->nc;
+  memcpy(s->x, x, nb);
+  memcpy(s->y, y, nb);
+  memcpy(s->z, z, nb);
+  memcpy(s->u, u, nb);
+  memcpy(s->v, v, nb);
+  memcpy(s->w, w, nb);
+  memcpy(s->mn, mn, nb);
+  memcpy(s->m, m, cb);
+  memcpy(s->e, e, cb);
+  s->t = t;
+  s->dt_last = dt_last;
+  s->status = ORACLE_OK;
+  int rc = oracle_eos(s);
+  if (rc) return rc;
+  return propose_dt(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Lagrangian step                                                     */
+/* ------------------------------------------------------------------ */
+
+int oracle_lagrange_step(oracle_state *s, double dt) {
+  if (s->status) return s->status;
+  if (!(dt > 0.0)) return s->status = ORACLE_EDT;
+  const long long nn = s->nn, nc = s->nc;
+  double *fx = alloc_zero(nn), *fy = alloc_zero(nn), *fz = alloc_zero(nn);
+  double *ubx = alloc_zero(nn), *uby = alloc_zero(nn), *ubz = alloc_zero(nn);
+  double *e_new = alloc_zero(nc);
+  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new) {
+    free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new);
+    return s->status = ORACLE_ENOMEM;
+  }
+
+  /* Corner forces F_a += sigma_c dV_c/dx_a at x^n, gathered to nodes. */
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double sigma = s->p[c] + s->q[c];
+        double X[24], G[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        oracle_hex_volume_grad(X, G);
+        for (int a = 0; a < 8; ++a) {
+          long long n = node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+          fx[n] += sigma * G[a * 3 + 0];
+          fy[n] += sigma * G[a * 3 + 1];
+          fz[n] += sigma * G[a * 3 + 2];
+        }
+      }
+
+  /* Velocity update with wall conditions; time-centred velocity. */
+  for (int k = 0; k <= s->nz; ++k)
+    for (int j = 0; j <= s->ny; ++j)
+      for (int i = 0; i <= s->nx; ++i) {
+        long long n = node_id(s, i, j, k);
+        double un = s->u[n] + dt * fx[n] / s->mn[n];
+        double vn = s->v[n] + dt * fy[n] / s->mn[n];
+        double wn = s->w[n] + dt * fz[n] / s->mn[n];
+        apply_wall_bc(s, i, j, k, &un, &vn, &wn);
+        ubx[n] = 0.5 * (s->u[n] + un);
+        uby[n] = 0.5 * (s->v[n] + vn);
+        ubz[n] = 0.5 * (s->w[n] + wn);
+        s->u[n] = un;
+        s->v[n] = vn;
+        s->w[n] = wn;
+      }
+
+  /* Compatible internal-energy update, with gradients at x^n. */
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double sigma = s->p[c] + s->q[c];
+        double X[24], G[24], UB[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        gather_hex(s, i, j, k, ubx, uby, ubz, UB);
+        oracle_hex_volume_grad(X, G);
+        double work = 0.0;
+        for (int a = 0; a < 8; ++a) work += dot3(&G[a * 3], &UB[a * 3]);
+        e_new[c] = s->e[c] - dt / s->m[c] * sigma * work;
+      }
+
+  /* Move the mesh with the time-centred velocity. */
+  for (long long n = 0; n < nn; ++n) {
+    s->x[n] += dt * ubx[n];
+    s->y[n] += dt * uby[n];
+    s->z[n] += dt * ubz[n];
+  }
+  memcpy(s->e, e_new, sizeof(double) * (size_t)nc);
+  free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new);
+
+  s->t += dt;
+  s->dt_last = dt;
+  s->cycle += 1;
+  int rc = oracle_eos(s);
+  if (rc) return rc;
+  return propose_dt(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Remap                                                               */
+/* ------------------------------------------------------------------ */
+
+/* Swept hex of a face normal to axis `ax`: local node (di,dj,dk) of the
+ * hex takes the face node given by the two other bits, at the current
+ * (Lagrangian) position when the bit along `ax` is 0 and at the reference
+ * position when it is 1.  Its volume is positive when the reference face
+ * lies on the high-index side of the current face. */
+static double swept_volume(const oracle_state *s, int ax, int i, int j, int k) {
+  double X[24];
+  for (int a = 0; a < 8; ++a) {
+    int b[3] = {a & 1, (a >> 1) & 1, (a >> 2) & 1};
+    int ref = b[ax];
+    b[ax] = 0;
+    long long n = node_id(s, i + b[0], j + b[1], k + b[2]);
+    X[a * 3 + 0] = ref ? s->xr[n] : s->x[n];
+    X[a * 3 + 1] = ref ? s->yr[n] : s->y[n];
+    X[a * 3 + 2] = ref ? s->zr[n] : s->z[n];
+  }
+  return oracle_hex_volume(X);
+}
+
+void oracle_swept_volumes(const oracle_state *s, double *dvx, double *dvy,
+                          double *dvz) {
+  const int nx = s->nx, ny = s->ny, nz = s->nz;
+  /* Faces on the domain boundary are walls: no flux. */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i <= nx; ++i)
+        dvx[i + (long long)(nx + 1) * (j + (long long)ny * k)] =
+            (i == 0 || i == nx) ? 0.0 : swept_volume(s, 0, i, j, k);
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        dvy[i + (long long)nx * (j + (long long)(ny + 1) * k)] =
+            (j == 0 || j == ny) ? 0.0 : swept_volume(s, 1, i, j, k);
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i)
+        dvz[i + (long long)nx * (j + (long long)ny * k)] =
+            (k == 0 || k == nz) ? 0.0 : swept_volume(s, 2, i, j, k);
+}
+
+int oracle_remap_step(oracle_state *s) {
+  if (s->status) return s->status;
+  const int nx = s->nx, ny = s->ny, nz = s->nz;
+  const long long nc = s->nc, nn = s->nn;
+  const long long nfx = (long long)(nx + 1) * ny * nz;
+  const long long nfy = (long long)nx * (ny + 1) * nz;
+  const long long nfz = (long long)nx * ny * (nz + 1);
+  double *dvx = alloc_zero(nfx), *dvy = alloc_zero(nfy), *dvz = alloc_zero(nfz);
+  double *mux = alloc_zero(nfx), *muy = alloc_zero(nfy), *muz = alloc_zero(nfz);
+  double *rho_l = alloc_zero(nc), *m_new = alloc_zero(nc), *ie_new = alloc_zero(nc);
+  double *mn_new = alloc_zero(nn), *px = alloc_zero(nn), *py = alloc_zero(nn);
+  double *pz = alloc_zero(nn), *ke = alloc_zero(nn), *dke = alloc_zero(nn);
+  double *all[] = {dvx, dvy, dvz, mux, muy, muz, rho_l, m_new, ie_new,
+                   mn_new, px, py, pz, ke, dke};
+  const size_t nall = sizeof(all) / sizeof(all[0]);
+  for (size_t i = 0; i < nall; ++i)
+    if (!all[i]) {
+      for (size_t j = 0; j < nall; ++j) free(all[j]);
+      return s->status = ORACLE_ENOMEM;
+    }
+
+  /* Lagrangian density of every cell (donor density). */
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double X[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        rho_l[c] = s->m[c] / oracle_hex_volume(X);
+      }
+
+  /* 1. Swept volumes of every face. */
+  oracle_swept_volumes(s, dvx, dvy, dvz);
+
+  /* 2. Donor-cell mass and energy fluxes.  dV > 0: the swept region lies
+   *    in the high-index cell, which donates to the low-index one. */
+  for (long long c = 0; c < nc; ++c) {
+    m_new[c] = s->m[c];
+    ie_new[c] = s->m[c] * s->e[c];
+  }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 1; i < nx; ++i) {
+        long long f = i + (long long)(nx + 1) * (j + (long long)ny * k);
+        long long lo = cell_id(s, i - 1, j, k), hi = cell_id(s, i, j, k);
+        long long dn = dvx[f] > 0.0 ? hi : lo;
+        double mu = rho_l[dn] * dvx[f];
+        mux[f] = mu;
+        m_new[lo] += mu;
+        m_new[hi] -= mu;
+        ie_new[lo] += mu * s->e[dn];
+        ie_new[hi] -= mu * s->e[dn];
+      }
+  for (int k = 0; k < nz; ++k)
+    for (int j = 1; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long long f = i + (long long)nx * (j + (long long)(ny + 1) * k);
+        long long lo = cell_id(s, i, j - 1, k), hi = cell_id(s, i, j, k);
+        long long dn = dvy[f] > 0.0 ? hi : lo;
+        double mu = rho_l[dn] * dvy[f];
+        muy[f] = mu;
+        m_new[lo] += mu;
+        m_new[hi] -= mu;
+        ie_new[lo] += mu * s->e[dn];
+        ie_new[hi] -= mu * s->e[dn];
+      }
+  for (int k = 1; k < nz; ++k)
+    for (int j = 0; j < ny; ++j)
+      for (int i = 0; i < nx; ++i) {
+        long long f = i + (long long)nx * (j + (long long)ny * k);
+        long long lo = cell_id(s, i, j, k - 1), hi = cell_id(s, i, j, k);
+        long long dn = dvz[f] > 0.0 ? hi : lo;
+        double mu = rho_l[dn] * dvz[f];
+        muz[f] = mu;
+        m_new[lo] += mu;
+        m_new[hi] -= mu;
+        ie_new[lo] += mu * s->e[dn];
+        ie_new[hi] -= mu * s->e[dn];
+      }
+
+  /* 3. Node (dual-mesh) fluxes along every mesh edge (a -> b = a + e_ax).
+   *    psi = sum over the cells around the edge of (mu_lo + mu_hi)/8, the
+   *    quarter of the mass crossing the cell mid-plane normal to ax next
+   *    to the edge.  psi > 0 moves mass from b to a.  Momentum and kinetic
+   *    energy are carried with the donor node's velocity. */
+  for (long long n = 0; n < nn; ++n) {
+    double uu = s->u[n], vv = s->v[n], ww = s->w[n];
+    mn_new[n] = s->mn[n];
+    px[n] = s->mn[n] * uu;
+    py[n] = s->mn[n] * vv;
+    pz[n] = s->mn[n] * ww;
+    ke[n] = 0.5 * s->mn[n] * (uu * uu + vv * vv + ww * ww);
+  }
+  for (int ax = 0; ax < 3; ++ax) {
+    const int ex = ax == 0, ey = ax == 1, ez = ax == 2;
+    for (int k = 0; k <= nz - ez; ++k)
+      for (int j = 0; j <= ny - ey; ++j)
+        for (int i = 0; i <= nx - ex; ++i) {
+          /* the (up to) four cells around the edge */
+          double psi = 0.0;
+          for (int s1 = 0; s1 < 2; ++s1)
+            for (int s2 = 0; s2 < 2; ++s2) {
+              int ci = i, cj = j, ck = k;
+              if (ax == 0) { cj = j - 1 + s1; ck = k - 1 + s2; }
+              if (ax == 1) { ci = i - 1 + s1; ck = k - 1 + s2; }
+              if (ax == 2) { ci = i - 1 + s1; cj = j - 1 + s2; }
+              if (ci < 0 || ci >= nx || cj < 0 || cj >= ny || ck < 0 || ck >= nz)
+                continue;
+              double mu_lo, mu_hi;
+              if (ax == 0) {
+                mu_lo = mux[ci + (long long)(nx + 1) * (cj + (long long)ny * ck)];
+                mu_hi = mux[ci + 1 + (long long)(nx + 1) * (cj + (long long)ny * ck)];
+              } else if (ax == 1) {
+                mu_lo = muy[ci + (long long)nx * (cj + (long long)(ny + 1) * ck)];
+                mu_hi = muy[ci + (long long)nx * (cj + 1 + (long long)(ny + 1) * ck)];
+              } else {
+                mu_lo = muz[ci + (long long)nx * (cj + (long long)ny * ck)];
+                mu_hi = muz[ci + (long long)nx * (cj + (long long)ny * (ck + 1))];
+              }
+              psi += (mu_lo + mu_hi) / 8.0;
+            }
+          long long a = node_id(s, i, j, k);
+          long long b = node_id(s, i + ex, j + ey, k + ez);
+          long long dn = psi > 0.0 ? b : a;
+          double ud = s->u[dn], vd = s->v[dn], wd = s->w[dn];
+          double kd = 0.5 * (ud * ud + vd * vd + wd * wd);
+          mn_new[a] += psi;
+          mn_new[b] -= psi;
+          px[a] += psi * ud;
+          px[b] -= psi * ud;
+          py[a] += psi * vd;
+          py[b] -= psi * vd;
+          pz[a] += psi * wd;
+          pz[b] -= psi * wd;
+          ke[a] += psi * kd;
+          ke[b] -= psi * kd;
+        }
+  }
+
+  /* 4. New node velocity (walls reflect), and the kinetic energy that the
+   *    momentum remap did not keep. */
+  for (int k = 0; k <= nz; ++k)
+    for (int j = 0; j <= ny; ++j)
+      for (int i = 0; i <= nx; ++i) {
+        long long n = node_id(s, i, j, k);
+        double uu = px[n] / mn_new[n], vv = py[n] / mn_new[n], ww = pz[n] / mn_new[n];
+        apply_wall_bc(s, i, j, k, &uu, &vv, &ww);
+        dke[n] = ke[n] - 0.5 * mn_new[n] * (uu * uu + vv * vv + ww * ww);
+        s->u[n] = uu;
+        s->v[n] = vv;
+        s->w[n] = ww;
+        s->mn[n] = mn_new[n];
+      }
+
+  /* 5. Kinetic-energy fix: each node's lost KE goes in equal shares to
+   *    the internal energy of the cells around it. */
+  if (s->prm.ke_fix)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          long long c = cell_id(s, i, j, k);
+          for (int a = 0; a < 8; ++a) {
+            int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
+            ie_new[c] += dke[node_id(s, ni, nj, nk)] / node_cell_count(s, ni, nj, nk);
+          }
+        }
+
+  /* 6. New cell state on the reference mesh. */
+  for (long long c = 0; c < nc; ++c) {
+    s->m[c] = m_new[c];
+    s->e[c] = ie_new[c] / m_new[c];
+  }
+  memcpy(s->x, s->xr, sizeof(double) * (size_t)nn);
+  memcpy(s->y, s->yr, sizeof(double) * (size_t)nn);
+  memcpy(s->z, s->zr, sizeof(double) * (size_t)nn);
+  for (size_t i = 0; i < nall; ++i) free(all[i]);
+
+  int rc = oracle_eos(s);
+  if (rc) return rc;
+  return propose_dt(s);
+}
+
+/* ------------------------------------------------------------------ */
+/* Driver and diagnostics                                              */
+/* ------------------------------------------------------------------ */
+
+int oracle_run(oracle_state *s, double t_end, long long max_cycles,
+               int remap_every, long long *done) {
+  long long n = 0;
+  while (n < max_cycles && s->t < t_end && s->status == ORACLE_OK) {
+    double dt = s->dt;
+    int clamp = 0;
+    if (t_end - s->t < dt) {
+      dt = t_end - s->t;
+      clamp = 1;
+    }
+    int rc = oracle_lagrange_step(s, dt);
+    if (rc) break;
+    if (clamp) s->t = t_end;
+    if (remap_every > 0 && s->cycle % remap_every == 0) {
+      rc = oracle_remap_step(s);
+      if (rc) break;
+    }
+    ++n;
+  }
+  if (done) *done = n;
+  return s->status;
+}
+
+void oracle_diagnostics(const oracle_state *s, double *out) {
+  double mass = 0, mx = 0, my = 0, mz = 0, ie = 0, ke = 0;
+  for (long long c = 0; c < s->nc; ++c) {
+    mass += s->m[c];
+    ie += s->m[c] * s->e[c];
+  }
+  for (long long n = 0; n < s->nn; ++n) {
+    mx += s->mn[n] * s->u[n];
+    my += s->mn[n] * s->v[n];
+    mz += s->mn[n] * s->w[n];
+    ke += 0.5 * s->mn[n] * (s->u[n] * s->u[n] + s->v[n] * s->v[n] + s->w[n] * s->w[n]);
+  }
+  out[0] = mass;
+  out[1] = mx;
+  out[2] = my;
+  out[3] = mz;
+  out[4] = ie;
+  out[5] = ke;
+  out[6] = ie + ke;
+}

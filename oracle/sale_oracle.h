@@ -1,0 +1,113 @@
+/*
+ * sale_oracle.h -- plain serial FP64 reference of the SALE staggered-grid
+ * hydro cycle (ScalSALE, arXiv 2209.01983: SALE scheme of Sec. I-D, the
+ * Lagrangian/Eulerian rezoning + advection rows of Table I, Sec. IV).
+ *
+ * TEST INFRASTRUCTURE.  Only tests/, __graft_entry__.smoke() and the
+ * cpu_baseline leg of bench.py may load this library.  It shares no code
+ * with the CUDA library; it is slow on purpose and is never tuned.
+ *
+ * The paper names the scheme (SALE, Amsden-Ruppel-Hirt) but prints none of
+ * its formulas.  Every formula below is a standard published form, written
+ * out in full in sale_oracle.c next to the loop that evaluates it:
+ *   - hex volume: exact trilinear-hex volume, as the divergence-theorem sum
+ *     over the six faces, each face fanned into four triangles from its
+ *     node mean;
+ *   - compatible energy update (Caramana, Burton, Shashkov, Whalen 1998);
+ *   - donor-cell (upwind) remap of mass, energy, momentum (Amsden et al.
+ *     1980, "SALE"), with kinetic-energy fix-up.
+ *
+ * Layout: SoA, x index fastest.  Cell c = i + nx*(j + ny*k); node
+ * n = i + (nx+1)*(j + (ny+1)*k).  Local node a = di + 2*dj + 4*dk of cell
+ * (i,j,k) is node (i+di, j+dj, k+dk).
+ */
+#ifndef SALE_ORACLE_H
+#define SALE_ORACLE_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  ORACLE_OK = 0,
+  ORACLE_EINVAL = -1,
+  ORACLE_ENOMEM = -2,
+  ORACLE_ENEGVOL = -4,
+  ORACLE_EDT = -5,
+  ORACLE_ENAN = -6
+};
+
+typedef struct oracle_params {
+  double gamma;      /* ideal-gas ratio of specific heats                 */
+  double cfl;        /* Courant number                                    */
+  double c_q;        /* quadratic artificial-viscosity coefficient        */
+  double c_l;        /* linear artificial-viscosity coefficient           */
+  double dt_growth;  /* max ratio dt_{n+1}/dt_n                           */
+  double dt_init;    /* cap on the first dt (<=0 or inf: none)            */
+  int ke_fix;        /* 1: remap returns lost kinetic energy to cells     */
+  int reflect[6];    /* x-lo,x-hi,y-lo,y-hi,z-lo,z-hi: 1 = reflecting wall */
+} oracle_params;
+
+typedef struct oracle_state {
+  int nx, ny, nz;
+  long long nc, nn;
+  oracle_params prm;
+  double *x, *y, *z;       /* node position                                */
+  double *xr, *yr, *zr;    /* reference mesh = Eulerian rezone target      */
+  double *u, *v, *w;       /* node velocity                                */
+  double *mn;              /* node mass                                    */
+  double *m, *e;           /* cell mass, specific internal energy          */
+  double *vol, *rho, *p, *q, *cs, *len; /* derived cell quantities         */
+  double t, dt, dt_last;   /* time, proposed next dt, last dt used         */
+  long long cycle;
+  int status;
+} oracle_state;
+
+/* ---- single-hex geometry; X[a*3+d] = coordinate d of local node a ---- */
+double oracle_hex_volume(const double *X);
+void oracle_hex_volume_grad(const double *X, double *G); /* G[a*3+d] = dV/dX */
+/* face vector areas A[f*3+d], faces ordered x-lo,x-hi,y-lo,y-hi,z-lo,z-hi */
+void oracle_hex_face_areas(const double *X, double *A);
+double oracle_hex_char_length(const double *X);
+
+/* ---- state ---- */
+oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,
+                            const double *yn, const double *zn,
+                            const oracle_params *prm);
+void oracle_destroy(oracle_state *s);
+/* Initial state from per-cell primitive rho0, p0 (u = 0).  If
+ * deposit_cell >= 0 its specific energy is replaced by
+ * deposit_energy / m_cell.  Computes derived fields and the first dt. */
+int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
+                     long long deposit_cell, double deposit_energy);
+/* Overwrite the evolving fields (positions, velocities, node mass, cell
+ * mass, energy, time and last dt), then recompute derived fields and the
+ * proposed dt.  Used to restart the oracle from an arbitrary state. */
+int oracle_set_state(oracle_state *s, const double *x, const double *y,
+                     const double *z, const double *u, const double *v,
+                     const double *w, const double *mn, const double *m,
+                     const double *e, double t, double dt_last);
+int oracle_eos(oracle_state *s);            /* vol, rho, p, cs, q, len     */
+double oracle_cfl_dt(const oracle_state *s); /* min over cells (uses eos)  */
+
+/* One Lagrangian step with the given dt (> 0); then eos and dt proposal. */
+int oracle_lagrange_step(oracle_state *s, double dt);
+/* Eulerian rezone to the reference mesh + donor-cell advection; then eos
+ * and dt proposal. */
+int oracle_remap_step(oracle_state *s);
+/* Signed swept volumes of every face between the current and reference
+ * mesh.  dvx has (nx+1)*ny*nz entries (index i + (nx+1)*(j + ny*k)),
+ * dvy nx*(ny+1)*nz (i + nx*(j + (ny+1)*k)), dvz nx*ny*(nz+1). */
+void oracle_swept_volumes(const oracle_state *s, double *dvx, double *dvy,
+                          double *dvz);
+/* Cycles until t >= t_end or max_cycles; remap after every remap_every-th
+ * cycle (0 = never).  Returns status; *done = cycles run. */
+int oracle_run(oracle_state *s, double t_end, long long max_cycles,
+               int remap_every, long long *done);
+/* out: mass, mom_x, mom_y, mom_z, internal E, kinetic E, total E */
+void oracle_diagnostics(const oracle_state *s, double *out);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,193 @@
+"""Physics pins for the oracle: exact solutions, invariants, conservation.
+
+What fixes each expected value:
+  * Sod shock tube: the exact Riemann solution (textbook construction,
+    itself pinned to Toro's printed star state in tests/golden).
+  * Sedov-Taylor: the similarity shock radius R = (E/(alpha rho))^(1/5) t^(2/5)
+    with alpha from tests/golden/sedov_alpha.txt.
+  * Uniform state at rest, zero mesh motion, axis permutation: symmetries of
+    the equations.
+  * Mass, total energy: conserved exactly by the compatible Lagrange step
+    and the conservative remap (roundoff only).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+import exact_riemann as er
+from conftest import read_golden
+from paper_2209_01983_gb300 import inputs
+
+
+def test_exact_riemann_matches_textbook_star_state():
+    g = read_golden("sod_star_state.txt")
+    ps, us = er.star_state(1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    assert abs(ps - g["p_star"]) <= 6e-6
+    assert abs(us - g["u_star"]) <= 6e-6
+    rl, _, _ = er.sample(us - 1e-9, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    rr, _, _ = er.sample(us + 1e-9, 1.0, 0.0, 1.0, 0.125, 0.0, 0.1, 1.4)
+    assert abs(rl - g["rho_star_left"]) <= 6e-6
+    assert abs(rr - g["rho_star_right"]) <= 6e-6
+
+
+def sod_result(nx, t_end=0.2):
+    md, pd = inputs.sod_x(nx, 4, 4)
+    o = oracle.Oracle.from_problem(md, pd)
+    d0 = o.diagnostics()
+    rc, _ = o.run(t_end=t_end)
+    assert rc == 0
+    assert o.s.t == t_end
+    x = o.field("x").reshape(5, 5, nx + 1)
+    # cell centroid x = mean of the cell's 8 node x (motion is along x only)
+    xc = 0.25 * (x[:-1, :-1, :-1] + x[1:, :-1, :-1] + x[:-1, 1:, :-1] + x[1:, 1:, :-1]
+                 + x[:-1, :-1, 1:] + x[1:, :-1, 1:] + x[:-1, 1:, 1:] + x[1:, 1:, 1:]) / 2.0
+    rho = o.field("rho").reshape(4, 4, nx)
+    dx = np.diff(x, axis=2)[0, 0]
+    return o, d0, xc[0, 0], rho[0, 0], dx, rho
+
+
+@pytest.mark.parametrize("nx", [100])
+def test_sod_against_exact_riemann(nx):
+    o, d0, xc, rho, dx, rho3 = sod_result(nx)
+    left, right = (1.0, 0.0, 1.0), (0.125, 0.0, 0.1)
+    rex, _, _ = er.solution(xc, 0.2, 0.5, left, right, 1.4)
+    l1 = float(np.sum(np.abs(rho - rex) * dx))
+    assert l1 <= 2e-2
+    # shock position: last cell (from the right) above the mid density
+    g = read_golden("sod_star_state.txt")
+    mid = 0.5 * (g["rho_star_right"] + 0.125)
+    i_sh = np.max(np.nonzero(rho > mid)[0])
+    x_sim = 0.5 * (xc[i_sh] + xc[i_sh + 1])
+    x_ex = 0.5 + er.right_shock_speed(left, right, 1.4) * 0.2
+    assert abs(x_sim - x_ex) <= 2 * (1.0 / nx)
+    # the tube is uniform across y and z
+    assert np.max(np.abs(rho3 - rho3[:1, :1, :])) <= 1e-12
+    # mass is exactly constant in a Lagrangian run; total energy to roundoff
+    d = o.diagnostics()
+    assert d["mass"] == d0["mass"]
+    assert abs(d["etot"] - d0["etot"]) <= 1e-13 * d0["etot"]
+
+
+def test_sod_converges_with_resolution():
+    errs = []
+    for nx in (50, 100, 200):
+        _, _, xc, rho, dx, _ = sod_result(nx)
+        rex, _, _ = er.solution(xc, 0.2, 0.5, (1.0, 0.0, 1.0), (0.125, 0.0, 0.1), 1.4)
+        errs.append(float(np.sum(np.abs(rho - rex) * dx)))
+    assert errs[0] > errs[1] > errs[2]
+    assert errs[2] < 0.75 * errs[0] / 1.5  # at least ~first order over 4x
+
+
+def test_sod_axis_permutation():
+    """The same tube along y gives the x-tube's fields with axes swapped."""
+    md, pd = inputs.sod_x(40, 3, 3)
+    ox = oracle.Oracle.from_problem(md, pd)
+    ox.run(max_cycles=30)
+    # build the y-oriented tube from the x-oriented inputs with axes permuted
+    myd = inputs.MeshDesc(3, 40, 3, lo=(0.0, 0.0, 0.0), hi=(0.04, 1.0, 0.04))
+    xs, ys, zs = inputs.mesh_nodes(md)
+    perm = lambda a: a.reshape(4, 4, 41).transpose(0, 2, 1).ravel()
+    rho0, p0, _, _ = inputs.problem_prim(md, pd)
+    cperm = lambda a: a.reshape(3, 3, 40).transpose(0, 2, 1).ravel()
+    oy = oracle.Oracle(3, 40, 3, (perm(ys), perm(xs), perm(zs)), oracle.params_from(pd))
+    oy.check(oracle.lib().oracle_init_prim(oy._s, oracle._ptr(np.ascontiguousarray(cperm(rho0))),
+                                           oracle._ptr(np.ascontiguousarray(cperm(p0))), -1, 0.0))
+    oy.run(max_cycles=30)
+    cinv = lambda a: a.reshape(3, 40, 3).transpose(0, 2, 1).ravel()
+    ninv = lambda a: a.reshape(4, 41, 4).transpose(0, 2, 1).ravel()
+    for name in ("rho", "e", "p", "q"):
+        a, b = ox.field(name), cinv(oy.field(name))
+        assert np.max(np.abs(a - b)) <= 1e-12 * np.max(np.abs(a))
+    assert np.max(np.abs(ox.field("u") - ninv(oy.field("v")))) <= 1e-12
+    assert np.max(np.abs(ox.field("u"))) > 0.1
+
+
+def test_uniform_state_at_rest_stays_at_rest():
+    # power-of-two spacing: coordinate differences and volume gradients are
+    # exact, so only the summation order of equal forces leaves roundoff
+    md, pd = inputs.uniform_box(8, rho=1.3, p=0.7)
+    o = oracle.Oracle.from_problem(md, pd)
+    e0, r0 = o.field("e"), o.field("rho")
+    o.run(max_cycles=5, remap_every=0)
+    o.run(max_cycles=5, remap_every=1)
+    for name in "uvw":
+        assert np.max(np.abs(o.field(name))) <= 1e-15
+    assert np.max(np.abs(o.field("e") - e0)) <= 1e-15 * e0.max()
+    assert np.max(np.abs(o.field("rho") - r0)) <= 1e-15 * r0.max()
+
+
+def test_uniform_state_at_rest_on_jittered_mesh():
+    md, pd = inputs.uniform_box(6, rho=1.0, p=1.0, jitter=0.1, seed=5)
+    o = oracle.Oracle.from_problem(md, pd)
+    e0, r0 = o.field("e"), o.field("rho")
+    o.run(max_cycles=10, remap_every=1)
+    for name in "uvw":
+        assert np.max(np.abs(o.field(name))) <= 1e-13
+    assert np.max(np.abs(o.field("e") - e0)) <= 1e-13 * e0.max()
+    assert np.max(np.abs(o.field("rho") - r0)) <= 1e-13 * r0.max()
+
+
+def test_remap_without_mesh_motion_is_identity():
+    md, pd = inputs.sedov_octant(6, jitter=0.1)
+    o = oracle.Oracle.from_problem(md, pd)
+    before = {n: o.field(n) for n in ("m", "e", "mn", "u")}
+    o.check(o.remap_step())
+    assert np.array_equal(o.field("m"), before["m"])
+    assert np.array_equal(o.field("mn"), before["mn"])
+    assert np.max(np.abs(o.field("e") - before["e"]) / before["e"]) <= 4e-16
+
+
+@pytest.mark.parametrize("jitter", [0.0, 0.1])
+def test_sedov_ale_conservation_and_node_mass(jitter):
+    md, pd = inputs.sedov_octant(10, jitter=jitter)
+    o = oracle.Oracle.from_problem(md, pd)
+    d0 = o.diagnostics()
+    rc, n = o.run(max_cycles=60, remap_every=1)
+    assert rc == 0 and n == 60
+    d = o.diagnostics()
+    assert abs(d["mass"] - d0["mass"]) <= 1e-13 * d0["mass"]
+    assert abs(d["etot"] - d0["etot"]) <= 1e-12 * d0["etot"]
+    assert d["ke"] > 1e-3 * d0["etot"]  # the blast is moving
+    # node masses stay the cells' eighth-shares (dual-flux consistency)
+    m = o.field("m").reshape(10, 10, 10)
+    mn = o.field("mn").reshape(11, 11, 11)
+    share = np.zeros((11, 11, 11))
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                share[dk:dk + 10, dj:dj + 10, di:di + 10] += m / 8.0
+    assert np.max(np.abs(mn - share) / share) <= 1e-12
+
+
+def test_ke_fix_is_needed_for_energy_conservation():
+    md, pd = inputs.sedov_octant(8)
+    pd.ke_fix = 0
+    o = oracle.Oracle.from_problem(md, pd)
+    d0 = o.diagnostics()
+    o.run(max_cycles=40, remap_every=1)
+    d = o.diagnostics()
+    assert d["etot"] < d0["etot"] * (1 - 1e-8)  # upwind momentum remap dissipates KE
+
+
+def test_sedov_symmetry_and_shock_radius():
+    n, t_end = 24, 0.5
+    md, pd = inputs.sedov_octant(n)
+    o = oracle.Oracle.from_problem(md, pd)
+    rc, _ = o.run(t_end=t_end, remap_every=1)
+    assert rc == 0 and o.s.t == t_end
+    rho = o.field("rho").reshape(n, n, n)
+    for perm in ((0, 2, 1), (2, 1, 0), (1, 0, 2)):
+        assert np.max(np.abs(rho - rho.transpose(perm))) <= 1e-12 * rho.max()
+    h = 1.2 / n
+    c = (np.arange(n) + 0.5) * h
+    r = np.sqrt(c[None, None, :] ** 2 + c[None, :, None] ** 2 + c[:, None, None] ** 2).ravel()
+    shells = np.floor(r / h).astype(int)
+    prof = np.bincount(shells, weights=rho.ravel()) / np.maximum(np.bincount(shells), 1)
+    r_sim = (np.argmax(prof) + 0.5) * h
+    alpha = read_golden("sedov_alpha.txt")["alpha"]
+    e_full = 8.0 * pd.e_deposit
+    r_exact = (e_full / (alpha * 1.0)) ** 0.2 * t_end ** 0.4
+    assert abs(r_sim - r_exact) <= 3 * h
+    assert 1.5 < rho.max() < 6.0  # compressed shell, below the strong-shock limit 6
