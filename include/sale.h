@@ -1,0 +1,178 @@
+/*
+ * sale.h -- C ABI of the GB300 SALE hydro library (libsale_gb300.so).
+ *
+ * The library advances the staggered-grid hydrodynamics cycle of the SALE
+ * scheme on a structured hexahedral mesh, on one GPU, in hand-written
+ * sm_103a CUDA kernels.  ScalSALE (arXiv 2209.01983) defines the problem:
+ * 3D structured grid (Table I "Mesh: Structured"), ideal-gas equation of
+ * state (Sec. I-D), the SALE hydrodynamic scheme (Sec. I-D), Lagrangian and
+ * Eulerian rezoning with an advection phase (Table I "Numerical kernels";
+ * Sec. IV), slip (reflecting) cell boundary conditions per mesh edge
+ * (Sec. III-A, Polymorphism), and the Sod and Sedov-Taylor problems
+ * (Sec. I-D, Sec. IV).  The paper prints no equations; the library
+ * implements these standard forms:
+ *
+ *   EoS            p = (gamma-1) rho e,  cs^2 = gamma (gamma-1) max(e,0)
+ *   viscosity      q = rho (c_q (L div)^2 + c_l cs L |div|) when div < 0
+ *   corner force   F_a = sum_c (p_c + q_c) dV_c/dx_a   (node gather)
+ *   kinematics     u+ = u + dt F/m_n;  x+ = x + dt (u + u+)/2
+ *   energy         e+ = e - dt/m_c (p+q) sum_a dV_c/dx_a . (u_a + u+_a)/2
+ *   time step      dt = min(cfl min_c L_c / sqrt(cs^2 + 2q/rho), g dt_prev)
+ *   remap          donor-cell advection of mass, internal energy, node
+ *                  momentum and kinetic energy to the reference mesh
+ *
+ * Conventions
+ *  - Every call returns a sale_status (0 = OK, negative = error) and never
+ *    aborts the process.  sale_last_error() gives a message for the last
+ *    non-OK status of the calling thread.
+ *  - Device errors (non-positive volume, NaN, dt underflow, wait timeout)
+ *    are recorded in a status word on the GPU and reported by the next call
+ *    that synchronises (run_to_time, diagnostics, copy_field).  After that
+ *    the state refuses further steps (SALE_ESTATE).
+ *  - Field memory belongs to the caller: sale_state_bytes() says how much
+ *    device memory a state needs; sale_state_init() carves it out of the
+ *    caller's buffer, which must stay alive until sale_state_destroy().
+ *    Handles (mesh/state metadata) belong to the library.
+ *  - A state runs on the CUDA stream given at init; handles are not
+ *    thread-safe.
+ *  - Layout: structure of arrays, x index fastest.  Cell (i,j,k) is
+ *    c = i + nx*(j + ny*k); node (i,j,k) is n = i + (nx+1)*(j + (ny+1)*k).
+ */
+#ifndef SALE_H
+#define SALE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  SALE_OK = 0,
+  SALE_EINVAL = -1,   /* bad argument                                  */
+  SALE_ENOMEM = -2,   /* host allocation failed or device buffer small */
+  SALE_ECUDA = -3,    /* CUDA runtime error                            */
+  SALE_ENEGVOL = -4,  /* a cell volume became non-positive (tangling)  */
+  SALE_EDT = -5,      /* time step not positive / not finite           */
+  SALE_ENAN = -6,     /* NaN in a field                                */
+  SALE_ETIMEOUT = -7, /* a bounded device-side wait ran out            */
+  SALE_ESTATE = -8    /* state is in an error state or wrong mode      */
+} sale_status;
+
+typedef enum {
+  SALE_FP64 = 0,       /* FP64 storage and arithmetic                   */
+  SALE_FP32_MIXED = 1  /* FP32 storage, FP64 volumes/energy/sums        */
+} sale_precision;
+
+enum { SALE_PROB_SOD_X = 0, SALE_PROB_SEDOV = 1, SALE_PROB_UNIFORM = 2 };
+
+typedef struct sale_mesh sale_mesh;
+typedef struct sale_state sale_state;
+
+/* Structured mesh on the box [lo, hi].  Node (i,j,k) sits at
+ * lo + (i,j,k) * h with h = (hi - lo) / (nx,ny,nz), plus, when jitter > 0,
+ * an offset ((2u - 1) * jitter) * h per axis, u = top 53 bits of the
+ * SplitMix64 draw number 3*node + axis of stream `seed` divided by 2^53.
+ * Nodes get no offset normal to a boundary plane they lie on.
+ * reflect[6] (x-lo, x-hi, y-lo, y-hi, z-lo, z-hi) must all be 1: every wall
+ * is a reflecting (slip / symmetry) plane. */
+typedef struct {
+  int nx, ny, nz;
+  double lo[3], hi[3];
+  double jitter;
+  unsigned long long seed;
+  int reflect[6];
+} sale_mesh_desc;
+
+/* Initial state and scheme parameters.
+ *  SOD_X:   cell on the left state (rho_l, p_l) when its logical centre
+ *           lo_x + (i + 0.5) h_x < x_split, else (rho_r, p_r).
+ *  SEDOV:   background (rho_bg, p_bg); the origin cell (0,0,0) gets the
+ *           specific energy e_deposit / m_cell when e_deposit > 0, else the
+ *           primitive state (rho_blast, p_blast).
+ *  UNIFORM: (rho_bg, p_bg) everywhere.
+ * Velocities start at zero.  cfl: Courant number; c_q, c_l: quadratic and
+ * linear viscosity coefficients; dt_init: cap on the first step (<= 0 or
+ * inf: none); dt_growth: max ratio of successive steps; ke_fix: return the
+ * kinetic energy lost in the momentum remap to the cells (1) or not (0). */
+typedef struct {
+  int kind;
+  double gamma;
+  double rho_l, p_l, rho_r, p_r, x_split;
+  double rho_bg, p_bg, rho_blast, p_blast, e_deposit;
+  double cfl, c_q, c_l, dt_init, dt_growth;
+  int ke_fix;
+} sale_problem_desc;
+
+/* Diagnostics (FP64 sums in a fixed reduction order). */
+typedef struct {
+  double t;        /* simulated time                                    */
+  double dt;       /* proposed next time step                           */
+  long long cycle; /* Lagrangian steps taken                            */
+  double mass;     /* sum_c m_c                                         */
+  double mom[3];   /* sum_n m_n u_n                                     */
+  double ie;       /* sum_c m_c e_c                                     */
+  double ke;       /* sum_n m_n |u_n|^2 / 2                             */
+  double etot;     /* ie + ke                                           */
+  int status;      /* device status word (sale_status)                  */
+} sale_diag;
+
+/* Build the mesh (host coordinates, library-owned).  EINVAL for sizes < 1,
+ * hi <= lo, jitter outside [0, 0.45], non-reflecting walls. */
+int sale_mesh_create(const sale_mesh_desc *desc, sale_mesh **out);
+void sale_mesh_destroy(sale_mesh *mesh);
+/* Host copy of the mesh node coordinates: xyz holds 3 * nnodes doubles,
+ * all x, then all y, then all z. */
+int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n);
+
+/* Device bytes a state of this mesh and precision needs (0 on bad args). */
+size_t sale_state_bytes(const sale_mesh *mesh, int precision);
+/* Initialise a state in the caller's device buffer (>= sale_state_bytes,
+ * 256-byte aligned) on `cuda_stream` (a cudaStream_t; NULL = legacy
+ * default stream).  Computes volumes, masses, energies, node masses, the
+ * EoS/viscosity state and the first dt.  The mesh may be destroyed after. */
+int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *prob,
+                    int precision, void *device_buf, size_t bytes,
+                    void *cuda_stream, sale_state **out);
+void sale_state_destroy(sale_state *st);
+
+/* One Lagrangian step (force gather, velocity/position update, compatible
+ * energy update, new EoS/viscosity state, next dt).  dt > 0 uses that
+ * step; dt <= 0 uses the on-device CFL step.  Asynchronous. */
+int sale_lagrange_step(sale_state *st, double dt);
+/* Eulerian rezone to the initial mesh plus donor-cell advection of mass,
+ * energy, momentum and kinetic energy (Table I "Eulerian rezoning,
+ * Advection"); then EoS/viscosity state and next dt.  Asynchronous. */
+int sale_remap_step(sale_state *st);
+/* Cycle until t >= t_end or max_cycles cycles: each cycle is a Lagrangian
+ * step with the on-device dt (clamped to land on t_end) followed by a remap
+ * when remap_every > 0 and the cycle count is a multiple of it.  Runs as
+ * replays of a captured CUDA graph; synchronises; *cycles_done (may be
+ * NULL) gets the number of cycles run. */
+int sale_run_to_time(sale_state *st, double t_end, long long max_cycles,
+                     int remap_every, long long *cycles_done);
+/* Synchronising FP64 reductions of the conserved quantities. */
+int sale_diagnostics(const sale_state *st, sale_diag *out);
+
+/* Synchronising copy of a field to host FP64.  Names: node fields "x",
+ * "y", "z", "u", "v", "w", "mn", "xref", "yref", "zref" (n = nnodes); cell
+ * fields "m", "e", "rho", "p", "q", "cs", "vol" (n = ncells). */
+int sale_copy_field(const sale_state *st, const char *name, double *host_out,
+                    size_t n);
+/* Overwrite an evolving field from host FP64 (same names as copy_field for
+ * "x","y","z","u","v","w","mn","m","e"); call sale_refresh() after the last
+ * one to recompute derived fields and dt.  Asynchronous with respect to
+ * the host only when host_in is pinned memory. */
+int sale_set_field(sale_state *st, const char *name, const double *host_in,
+                   size_t n);
+int sale_refresh(sale_state *st);
+
+/* Sizes of a state: ncells, nnodes. */
+int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes);
+
+const char *sale_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SALE_H */

@@ -1,0 +1,190 @@
+// sale_internal.cuh -- device-side data structures and hex geometry of the
+// GB300 SALE library.  Shared by the kernel and host translation units of
+// the library only.
+//
+// Geometry (structured hex mesh, ScalSALE Table I "Mesh: Structured").
+// The hex volume is the divergence-theorem sum over the six outward faces,
+// each face fanned into four triangles from its node mean:
+//     V = (1/24) sum_f S_f . ((p2 - p0) x (p3 - p1)),  S_f = p0+p1+p2+p3,
+// which is the exact volume of the trilinear hex.  Its derivative with
+// respect to node p_k of face f is
+//     dT_f/dp_k = (p_{k+1} + 2 p_{k+2} + p_{k+3}) x (p_{k+3} - p_{k+1}),
+// and dV/dx_a = (1/24) sum over the three faces holding a.  Coordinates
+// are taken relative to local node 0 of the hex (translation invariance)
+// to limit cancellation.
+#pragma once
+
+#include <cstdint>
+
+#include "sale.h"
+
+namespace sale {
+
+constexpr int kBlock = 256;           // threads per block of the 1D kernels
+constexpr double kInvSixth24 = 1.0 / 24.0;
+
+// Device scalars of one state (one cache line group, device memory).
+struct DevScalars {
+  double t;          // simulated time
+  double dt;         // proposed next time step
+  double dt_last;    // last time step taken
+  double t_end;      // cycles stop once t >= t_end
+  long long cycle;   // Lagrangian steps taken
+  long long cycle_limit;  // cycles stop once cycle >= cycle_limit
+  unsigned long long dtmin_bits;  // running CFL minimum (bits of a double)
+  unsigned int blocks_done;       // last-block counter of the dt kernel
+  int status;        // first device error (sale_status), 0 = OK
+  double pad[8];
+};
+
+// Modes of the kernel that ends a step and proposes the next dt.
+enum DtMode : int {
+  kDtPropose = 0,  // dt = min(cfl, growth * dt_last)
+  kDtAdvance = 1,  // advance t and cycle by the step just taken, then propose
+  kDtInit = 2      // dt = min(cfl, dt_init); dt_last = dt
+};
+
+// Device pointers and constants of one state (passed by value).
+template <typename R>
+struct Fields {
+  int nx, ny, nz;
+  long long nc, nn;
+  const double *xr, *yr, *zr;  // reference mesh (Eulerian rezone target)
+  R *x, *y, *z;                // current node positions
+  R *xn, *yn, *zn;             // next node positions (written by the step)
+  R *u, *v, *w;                // node velocity
+  R *ub, *vb, *wb;             // time-centred / remapped node velocity
+  R *mn;                       // node mass
+  R *dke;                      // kinetic energy lost by the node remap
+  R *m, *e;                    // cell mass, specific internal energy
+  R *sig;                      // p + q
+  R *rho, *p, *q, *cs, *vol;   // derived cell fields
+  R *mux, *muy, *muz;          // mass flux through the low x/y/z face
+  R *epx, *epy, *epz;          // internal-energy flux through those faces
+  double gamma, cfl, c_q, c_l, growth, dt_init;
+  int ke_fix;
+  int reflect[6];
+};
+
+struct P3 {
+  double x, y, z;
+};
+
+__host__ __device__ __forceinline__ P3 operator+(P3 a, P3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
+__host__ __device__ __forceinline__ P3 operator-(P3 a, P3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
+__host__ __device__ __forceinline__ P3 operator*(double s, P3 a) { return {s * a.x, s * a.y, s * a.z}; }
+__host__ __device__ __forceinline__ P3 cross(P3 a, P3 b) {
+  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
+}
+__host__ __device__ __forceinline__ double dot(P3 a, P3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
+
+// Outward faces of the hex (local node a = di + 2 dj + 4 dk), cyclic order:
+// x-lo {0,4,6,2}, x-hi {1,3,7,5}, y-lo {0,1,5,4}, y-hi {2,6,7,3},
+// z-lo {0,2,3,1}, z-hi {4,5,7,6}.
+__host__ __device__ constexpr int face_node(int f, int k) {
+  return f == 0   ? (k == 0 ? 0 : k == 1 ? 4 : k == 2 ? 6 : 2)
+         : f == 1 ? (k == 0 ? 1 : k == 1 ? 3 : k == 2 ? 7 : 5)
+         : f == 2 ? (k == 0 ? 0 : k == 1 ? 1 : k == 2 ? 5 : 4)
+         : f == 3 ? (k == 0 ? 2 : k == 1 ? 6 : k == 2 ? 7 : 3)
+         : f == 4 ? (k == 0 ? 0 : k == 1 ? 2 : k == 2 ? 3 : 1)
+                  : (k == 0 ? 4 : k == 1 ? 5 : k == 2 ? 7 : 6);
+}
+
+// Position of local node a in the cycle of face f (f must hold a).
+__host__ __device__ constexpr int face_slot(int f, int a) {
+  return face_node(f, 0) == a ? 0 : face_node(f, 1) == a ? 1 : face_node(f, 2) == a ? 2 : 3;
+}
+
+// Shift hex coordinates so local node 0 is the origin.
+__device__ __forceinline__ void shift0(P3 (&X)[8]) {
+  const P3 o = X[0];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) X[a] = X[a] - o;
+}
+
+// Volume of a hex whose coordinates are already shifted (X[0] = 0).
+__device__ __forceinline__ double hex_volume_shifted(const P3 (&X)[8]) {
+  double s = 0.0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const P3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)];
+    const P3 p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
+    s += dot(p0 + p1 + p2 + p3, cross(p2 - p0, p3 - p1));
+  }
+  return s * kInvSixth24;
+}
+
+// Full volume gradient of a shifted hex: G[a] = dV/dx_a.
+__device__ __forceinline__ void hex_grad_shifted(const P3 (&X)[8], P3 (&G)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) G[a] = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const P3 pa = X[face_node(f, (k + 1) & 3)];
+      const P3 pb = X[face_node(f, (k + 2) & 3)];
+      const P3 pc = X[face_node(f, (k + 3) & 3)];
+      G[face_node(f, k)] = G[face_node(f, k)] + cross(pa + 2.0 * pb + pc, pc - pa);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) G[a] = kInvSixth24 * G[a];
+}
+
+// dV/dx_A for one compile-time corner A of a shifted hex.
+template <int A>
+__device__ __forceinline__ P3 hex_corner_grad_shifted(const P3 (&X)[8]) {
+  P3 g = {0.0, 0.0, 0.0};
+#pragma unroll
+  for (int t = 0; t < 3; ++t) {
+    const int f = 2 * t + ((A >> t) & 1);
+    const int k = face_slot(f, A);
+    const P3 pa = X[face_node(f, (k + 1) & 3)];
+    const P3 pb = X[face_node(f, (k + 2) & 3)];
+    const P3 pc = X[face_node(f, (k + 3) & 3)];
+    g = g + cross(pa + 2.0 * pb + pc, pc - pa);
+  }
+  return kInvSixth24 * g;
+}
+
+// max_f |A_f|^2 of the face vector areas A_f = (1/2)(p2-p0) x (p3-p1).
+__device__ __forceinline__ double hex_max_face_area2(const P3 (&X)[8]) {
+  double amax = 0.0;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const P3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)];
+    const P3 p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
+    const P3 D = cross(p2 - p0, p3 - p1);
+    amax = fmax(amax, 0.25 * dot(D, D));
+  }
+  return amax;
+}
+
+__device__ __forceinline__ long long node_index(int nx, int ny, int i, int j, int k) {
+  return (long long)i + (long long)(nx + 1) * ((long long)j + (long long)(ny + 1) * k);
+}
+
+__device__ __forceinline__ long long cell_index(int nx, int ny, int i, int j, int k) {
+  return (long long)i + (long long)nx * ((long long)j + (long long)ny * k);
+}
+
+// Record the first device error.
+__device__ __forceinline__ void set_status(DevScalars *S, int code) {
+  atomicCAS(&S->status, 0, code);
+}
+
+// True while the current cycle should run.
+__device__ __forceinline__ bool cycle_active(const DevScalars *S) {
+  return S->status == 0 && S->t < S->t_end && S->cycle < S->cycle_limit;
+}
+
+// The time step of the cycle in flight: an explicit dt > 0, else the
+// proposed dt clamped so the step lands on t_end.
+__device__ __forceinline__ double step_dt(const DevScalars *S, double dt_override) {
+  if (dt_override > 0.0) return dt_override;
+  const double rem = S->t_end - S->t;
+  return rem < S->dt ? rem : S->dt;
+}
+
+}  // namespace sale

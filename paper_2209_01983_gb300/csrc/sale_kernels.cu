@@ -1,0 +1,584 @@
+// sale_kernels.cu -- sm_103a kernels of the SALE hydro cycle (general path:
+// positions may be anywhere; geometry is recomputed from the node
+// coordinates every time it is needed).
+//
+// Cycle (ScalSALE Sec. IV: Lagrangian phase, then Eulerian rezoning with
+// an advection phase when the run is Eulerian):
+//   k_lagrange_nodes  corner forces gathered per node (no atomics), new
+//                     velocity (walls reflect), time-centred velocity,
+//                     new positions                  ("Update_acceleration")
+//   k_lagrange_cells  compatible internal-energy update, new density
+//                     ("Calculate_density")
+//   k_remap_faces     swept volumes of the three low faces of each cell,
+//                     donor-cell mass and energy fluxes
+//   k_remap_nodes     dual-mesh mass, momentum and kinetic-energy fluxes,
+//                     new node velocity and mass, lost kinetic energy
+//   k_remap_cells     new cell mass and energy (plus the kinetic-energy fix)
+//   k_eos_dt          EoS, sound speed, viscosity, p+q, CFL dt (warp-shuffle
+//                     min, one atomicMin per block on the bits of a positive
+//                     double, last block finalises time and dt)
+#include <cfloat>
+#include <cmath>
+
+#include "sale_internal.cuh"
+
+namespace sale {
+
+namespace {
+
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+template <typename R>
+__device__ __forceinline__ void load_hex(const R *px, const R *py, const R *pz, int nx, int ny, int i,
+                                         int j, int k, P3 (&X)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_index(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a] = {(double)px[n], (double)py[n], (double)pz[n]};
+  }
+}
+
+__device__ __forceinline__ void cell_ijk(long long c, int nx, int ny, int &i, int &j, int &k) {
+  const long long nxy = (long long)nx * ny;
+  k = (int)(c / nxy);
+  const long long r = c - (long long)k * nxy;
+  j = (int)(r / nx);
+  i = (int)(r - (long long)j * nx);
+}
+
+__device__ __forceinline__ void node_ijk(long long n, int nx, int ny, int &i, int &j, int &k) {
+  const long long sx = nx + 1, sxy = sx * (ny + 1);
+  k = (int)(n / sxy);
+  const long long r = n - (long long)k * sxy;
+  j = (int)(r / sx);
+  i = (int)(r - (long long)j * sx);
+}
+
+template <typename R>
+__device__ __forceinline__ void wall_bc(const Fields<R> &F, int i, int j, int k, double &u, double &v,
+                                        double &w) {
+  if ((i == 0 && F.reflect[0]) || (i == F.nx && F.reflect[1])) u = 0.0;
+  if ((j == 0 && F.reflect[2]) || (j == F.ny && F.reflect[3])) v = 0.0;
+  if ((k == 0 && F.reflect[4]) || (k == F.nz && F.reflect[5])) w = 0.0;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// Initialisation
+// ---------------------------------------------------------------------------
+
+// m = rho0 V, e = p0 / ((gamma-1) rho0); the deposit cell gets e = E / m.
+template <typename R>
+__global__ void k_init_cells(Fields<R> F, DevScalars *S, const double *rho0, const double *p0,
+                             long long dep_cell, double dep_e) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 X[8];
+  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  shift0(X);
+  const double V = hex_volume_shifted(X);
+  if (!(V > 0.0)) set_status(S, SALE_ENEGVOL);
+  const double r0 = rho0[c];
+  const double m = r0 * V;
+  double e = p0[c] / ((F.gamma - 1.0) * r0);
+  if (c == dep_cell) e = dep_e / m;
+  F.m[c] = (R)m;
+  F.e[c] = (R)e;
+}
+
+// Node mass = sum of m_c / 8 over the cells holding the node; u = 0.
+template <typename R>
+__global__ void k_init_nodes(Fields<R> F) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn) return;
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  double mn = 0.0;
+#pragma unroll
+  for (int s = 0; s < 8; ++s) {
+    const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
+    mn += (double)F.m[cell_index(F.nx, F.ny, ci, cj, ck)] / 8.0;
+  }
+  F.mn[n] = (R)mn;
+  F.u[n] = F.v[n] = F.w[n] = (R)0;
+}
+
+__global__ void k_set_limits(DevScalars *S, double t_end, long long cycle_limit) {
+  S->t_end = t_end;
+  S->cycle_limit = cycle_limit;
+}
+
+__global__ void k_reset_scalars(DevScalars *S) {
+  S->t = 0.0;
+  S->dt = 0.0;
+  S->dt_last = 0.0;
+  S->t_end = INFINITY;
+  S->cycle = 0;
+  S->cycle_limit = 0x7FFFFFFFFFFFFFFFll;
+  S->dtmin_bits = kInfBits;
+  S->blocks_done = 0;
+  S->status = 0;
+}
+
+// ---------------------------------------------------------------------------
+// EoS, viscosity, CFL dt
+// ---------------------------------------------------------------------------
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, int mode, double dt_override) {
+  const bool active = (mode == kDtAdvance) ? cycle_active(S) : (S->status == 0);
+  if (!active) return;  // uniform over the grid: S changes only in the last block
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double dtc = INFINITY;
+  if (c < F.nc) {
+    int i, j, k;
+    cell_ijk(c, F.nx, F.ny, i, j, k);
+    P3 X[8], U[8], G[8];
+    load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+    load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
+    shift0(X);
+    const double V = hex_volume_shifted(X);
+    if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
+    hex_grad_shifted(X, G);
+    double dvdt = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) dvdt += dot(G[a], U[a]);
+    const double div = dvdt / V;
+    const double L = V / sqrt(hex_max_face_area2(X));
+    const double m = (double)F.m[c], e = (double)F.e[c];
+    const double rho = m / V;
+    const double p = (F.gamma - 1.0) * rho * e;
+    const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+    double q = 0.0;
+    if (div < 0.0) {
+      const double ld = L * div;
+      q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
+    }
+    F.vol[c] = (R)V;
+    F.rho[c] = (R)rho;
+    F.p[c] = (R)p;
+    F.q[c] = (R)q;
+    F.cs[c] = (R)cs;
+    F.sig[c] = (R)(p + q);
+    dtc = F.cfl * L / sqrt(cs * cs + 2.0 * q / rho);
+    if (dtc != dtc) {
+      set_status(S, SALE_ENAN);
+      dtc = INFINITY;
+    }
+  }
+  __shared__ double smin[kBlock / 32];
+  __shared__ bool last;
+  dtc = warp_min(dtc);
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = dtc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kBlock / 32 ? smin[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) {
+      atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+      __threadfence();
+      const unsigned int done = atomicAdd(&S->blocks_done, 1u);
+      last = (done == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  // Last block: every other block has published its minimum.
+  __threadfence();
+  volatile DevScalars *VS = S;
+  const double dtcfl = __longlong_as_double((long long)atomicAdd(&S->dtmin_bits, 0ull));
+  double dt;
+  if (mode == kDtInit) {
+    dt = dtcfl;
+    if (F.dt_init > 0.0 && F.dt_init < dt) dt = F.dt_init;
+    VS->dt_last = dt;
+  } else {
+    if (mode == kDtAdvance) {
+      const double h = step_dt(S, dt_override);
+      const bool clamp = dt_override <= 0.0 && (VS->t_end - VS->t) < VS->dt;
+      VS->t = clamp ? VS->t_end : VS->t + h;
+      VS->dt_last = h;
+      VS->cycle = VS->cycle + 1;
+    }
+    dt = fmin(dtcfl, F.growth * VS->dt_last);
+  }
+  if (!(dt > 0.0) || dt == INFINITY) set_status(S, SALE_EDT);
+  else VS->dt = dt;
+  VS->dtmin_bits = kInfBits;
+  VS->blocks_done = 0;
+  __threadfence();
+}
+
+// ---------------------------------------------------------------------------
+// Lagrangian step
+// ---------------------------------------------------------------------------
+
+// One corner of the hex around a node: accumulate sigma_c dV_c/dx_node.
+template <int S8, typename R>
+__device__ __forceinline__ void add_corner_force(const Fields<R> &F, int i, int j, int k, P3 &f) {
+  const int ci = i - 1 + (S8 & 1), cj = j - 1 + ((S8 >> 1) & 1), ck = k - 1 + ((S8 >> 2) & 1);
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) return;
+  P3 X[8];
+  load_hex(F.x, F.y, F.z, F.nx, F.ny, ci, cj, ck, X);
+  shift0(X);
+  const P3 g = hex_corner_grad_shifted<7 - S8>(X);
+  const double sig = (double)F.sig[cell_index(F.nx, F.ny, ci, cj, ck)];
+  f = f + sig * g;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScalars *S, double dt_override) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn) return;
+  if (!cycle_active(S)) {  // inactive cycle: positions carry over unchanged
+    F.xn[n] = F.x[n];
+    F.yn[n] = F.y[n];
+    F.zn[n] = F.z[n];
+    return;
+  }
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  P3 f = {0.0, 0.0, 0.0};
+  add_corner_force<0>(F, i, j, k, f);
+  add_corner_force<1>(F, i, j, k, f);
+  add_corner_force<2>(F, i, j, k, f);
+  add_corner_force<3>(F, i, j, k, f);
+  add_corner_force<4>(F, i, j, k, f);
+  add_corner_force<5>(F, i, j, k, f);
+  add_corner_force<6>(F, i, j, k, f);
+  add_corner_force<7>(F, i, j, k, f);
+  const double mn = (double)F.mn[n];
+  const double u0 = (double)F.u[n], v0 = (double)F.v[n], w0 = (double)F.w[n];
+  double u1 = u0 + h * f.x / mn, v1 = v0 + h * f.y / mn, w1 = w0 + h * f.z / mn;
+  wall_bc(F, i, j, k, u1, v1, w1);
+  const double ub = 0.5 * (u0 + u1), vb = 0.5 * (v0 + v1), wb = 0.5 * (w0 + w1);
+  F.u[n] = (R)u1;
+  F.v[n] = (R)v1;
+  F.w[n] = (R)w1;
+  F.ub[n] = (R)ub;
+  F.vb[n] = (R)vb;
+  F.wb[n] = (R)wb;
+  F.xn[n] = (R)((double)F.x[n] + h * ub);
+  F.yn[n] = (R)((double)F.y[n] + h * vb);
+  F.zn[n] = (R)((double)F.z[n] + h * wb);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScalars *S, double dt_override) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 X[8], UB[8], G[8];
+  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  load_hex(F.ub, F.vb, F.wb, F.nx, F.ny, i, j, k, UB);
+  shift0(X);
+  hex_grad_shifted(X, G);
+  double work = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) work += dot(G[a], UB[a]);
+  const double m = (double)F.m[c];
+  const double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
+  load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+  shift0(X);
+  const double V1 = hex_volume_shifted(X);
+  if (!(V1 > 0.0)) set_status(S, V1 != V1 ? SALE_ENAN : SALE_ENEGVOL);
+  F.e[c] = (R)e1;
+  F.vol[c] = (R)V1;
+  F.rho[c] = (R)(m / V1);
+}
+
+// ---------------------------------------------------------------------------
+// Remap (Eulerian rezone to the reference mesh + donor-cell advection)
+// ---------------------------------------------------------------------------
+
+// Swept hex of the low face of cell (i,j,k) normal to axis AX: local node
+// with bit AX = 0 at the current position, = 1 at the reference position,
+// other bits picking the face node.  Positive volume: the reference face
+// lies on the high-index side, so the high cell donates.
+template <int AX, typename R>
+__device__ __forceinline__ double swept_volume(const Fields<R> &F, int i, int j, int k) {
+  P3 X[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int b0 = (AX == 0) ? 0 : (a & 1);
+    const int b1 = (AX == 1) ? 0 : ((a >> 1) & 1);
+    const int b2 = (AX == 2) ? 0 : ((a >> 2) & 1);
+    const long long n = node_index(F.nx, F.ny, i + b0, j + b1, k + b2);
+    const bool ref = (a >> AX) & 1;
+    X[a] = ref ? P3{F.xr[n], F.yr[n], F.zr[n]} : P3{(double)F.x[n], (double)F.y[n], (double)F.z[n]};
+  }
+  shift0(X);
+  return hex_volume_shifted(X);
+}
+
+template <int AX, typename R>
+__device__ __forceinline__ void face_flux(const Fields<R> &F, long long c, int i, int j, int k, R *mu,
+                                          R *ep) {
+  const int idx = AX == 0 ? i : AX == 1 ? j : k;
+  if (idx == 0) {
+    mu[c] = (R)0;
+    ep[c] = (R)0;
+    return;
+  }
+  const double dv = swept_volume<AX>(F, i, j, k);
+  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+  const long long dn = dv > 0.0 ? c : c - stride;
+  const double f = (double)F.rho[dn] * dv;
+  mu[c] = (R)f;
+  ep[c] = (R)(f * (double)F.e[dn]);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_remap_faces(Fields<R> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  face_flux<0>(F, c, i, j, k, F.mux, F.epx);
+  face_flux<1>(F, c, i, j, k, F.muy, F.epy);
+  face_flux<2>(F, c, i, j, k, F.muz, F.epz);
+}
+
+// Dual mass flux along the mesh edge from node (i,j,k) to its +AX
+// neighbour: sum over the (up to four) cells around the edge of
+// (mu_low_face + mu_high_face) / 8.  Positive: mass moves to the low node.
+template <int AX, typename R>
+__device__ __forceinline__ double edge_psi(const Fields<R> &F, int i, int j, int k) {
+  const R *mu = AX == 0 ? F.mux : AX == 1 ? F.muy : F.muz;
+  double psi = 0.0;
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int ci = i, cj = j, ck = k;
+    if (AX == 0) { cj = j - 1 + (s & 1); ck = k - 1 + (s >> 1); }
+    if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
+    if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
+    const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
+    const double lo = (double)mu[c];
+    const int hi_idx = (AX == 0 ? ci : AX == 1 ? cj : ck) + 1;
+    const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
+    const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+    const double hi = hi_idx < n_ax ? (double)mu[c + stride] : 0.0;
+    psi += (lo + hi) / 8.0;
+  }
+  return psi;
+}
+
+// Apply the flux of the edge along AX on the low (SIDE = 0: edge from this
+// node to +AX) or high (SIDE = 1: edge from the -AX neighbour) side.
+template <int AX, int SIDE, typename R>
+__device__ __forceinline__ void node_edge(const Fields<R> &F, int i, int j, int k, long long n, double &m,
+                                          P3 &p, double &ke) {
+  const int idx = AX == 0 ? i : AX == 1 ? j : k;
+  const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
+  if (SIDE == 0 && idx == n_ax) return;
+  if (SIDE == 1 && idx == 0) return;
+  const int li = (SIDE == 1 && AX == 0) ? i - 1 : i;
+  const int lj = (SIDE == 1 && AX == 1) ? j - 1 : j;
+  const int lk = (SIDE == 1 && AX == 2) ? k - 1 : k;
+  const double psi = edge_psi<AX>(F, li, lj, lk);
+  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)(F.nx + 1) : (long long)(F.nx + 1) * (F.ny + 1);
+  const long long lo = SIDE == 0 ? n : n - stride;
+  const long long dn = psi > 0.0 ? lo + stride : lo;
+  const double ud = (double)F.u[dn], vd = (double)F.v[dn], wd = (double)F.w[dn];
+  const double kd = 0.5 * (ud * ud + vd * vd + wd * wd);
+  const double sgn = SIDE == 0 ? 1.0 : -1.0;
+  m += sgn * psi;
+  p.x += sgn * psi * ud;
+  p.y += sgn * psi * vd;
+  p.z += sgn * psi * wd;
+  ke += sgn * psi * kd;
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_remap_nodes(Fields<R> F, DevScalars *S) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn) return;
+  if (!cycle_active(S)) {  // inactive cycle: velocity carries over unchanged
+    F.ub[n] = F.u[n];
+    F.vb[n] = F.v[n];
+    F.wb[n] = F.w[n];
+    return;
+  }
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  const double m0 = (double)F.mn[n];
+  const double u0 = (double)F.u[n], v0 = (double)F.v[n], w0 = (double)F.w[n];
+  double m = m0;
+  P3 p = {m0 * u0, m0 * v0, m0 * w0};
+  double ke = 0.5 * m0 * (u0 * u0 + v0 * v0 + w0 * w0);
+  node_edge<0, 0>(F, i, j, k, n, m, p, ke);
+  node_edge<0, 1>(F, i, j, k, n, m, p, ke);
+  node_edge<1, 0>(F, i, j, k, n, m, p, ke);
+  node_edge<1, 1>(F, i, j, k, n, m, p, ke);
+  node_edge<2, 0>(F, i, j, k, n, m, p, ke);
+  node_edge<2, 1>(F, i, j, k, n, m, p, ke);
+  if (!(m > 0.0)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
+  double u1 = p.x / m, v1 = p.y / m, w1 = p.z / m;
+  wall_bc(F, i, j, k, u1, v1, w1);
+  F.ub[n] = (R)u1;
+  F.vb[n] = (R)v1;
+  F.wb[n] = (R)w1;
+  F.mn[n] = (R)m;
+  F.dke[n] = (R)(ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1));
+  F.x[n] = (R)F.xr[n];
+  F.y[n] = (R)F.yr[n];
+  F.z[n] = (R)F.zr[n];
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_remap_cells(Fields<R> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+  double dm = -(double)F.mux[c] - (double)F.muy[c] - (double)F.muz[c];
+  double de = -(double)F.epx[c] - (double)F.epy[c] - (double)F.epz[c];
+  if (i + 1 < F.nx) { dm += (double)F.mux[c + 1]; de += (double)F.epx[c + 1]; }
+  if (j + 1 < F.ny) { dm += (double)F.muy[c + sy]; de += (double)F.epy[c + sy]; }
+  if (k + 1 < F.nz) { dm += (double)F.muz[c + sz]; de += (double)F.epz[c + sz]; }
+  const double m0 = (double)F.m[c];
+  const double m1 = m0 + dm;
+  double ie = m0 * (double)F.e[c] + de;
+  if (F.ke_fix) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
+      const int cnt = ((ni == 0 || ni == F.nx) ? 1 : 2) * ((nj == 0 || nj == F.ny) ? 1 : 2) *
+                      ((nk == 0 || nk == F.nz) ? 1 : 2);
+      ie += (double)F.dke[node_index(F.nx, F.ny, ni, nj, nk)] / (double)cnt;
+    }
+  }
+  if (!(m1 > 0.0)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
+  F.m[c] = (R)m1;
+  F.e[c] = (R)(ie / m1);
+}
+
+// ---------------------------------------------------------------------------
+// Diagnostics: fixed-order FP64 reduction (deterministic)
+// ---------------------------------------------------------------------------
+
+constexpr int kDiagBlocks = 512;
+constexpr int kDiagQ = 6;  // mass, mom x, mom y, mom z, ie, ke
+
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_diag_partial(Fields<R> F, double *partial) {
+  double acc[kDiagQ] = {0, 0, 0, 0, 0, 0};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < F.nc; c += stride) {
+    const double m = (double)F.m[c];
+    acc[0] += m;
+    acc[4] += m * (double)F.e[c];
+  }
+  for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < F.nn; n += stride) {
+    const double m = (double)F.mn[n], u = (double)F.u[n], v = (double)F.v[n], w = (double)F.w[n];
+    acc[1] += m * u;
+    acc[2] += m * v;
+    acc[3] += m * w;
+    acc[5] += 0.5 * m * (u * u + v * v + w * w);
+  }
+  __shared__ double sm[kDiagQ][kBlock / 32];
+#pragma unroll
+  for (int q = 0; q < kDiagQ; ++q) {
+    const double v = warp_sum(acc[q]);
+    if ((threadIdx.x & 31) == 0) sm[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagQ) {
+    double s = 0.0;
+    for (int w = 0; w < kBlock / 32; ++w) s += sm[threadIdx.x][w];
+    partial[threadIdx.x * kDiagBlocks + blockIdx.x] = s;
+  }
+}
+
+__global__ void k_diag_final(const double *partial, double *out) {
+  __shared__ double sm[kDiagQ][kDiagBlocks / 32];
+  for (int q = 0; q < kDiagQ; ++q) {
+    double v = partial[q * kDiagBlocks + threadIdx.x];
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0) sm[q][threadIdx.x >> 5] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < kDiagQ) {
+    double s = 0.0;
+    for (int w = 0; w < kDiagBlocks / 32; ++w) s += sm[threadIdx.x][w];
+    out[threadIdx.x] = s;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------
+
+static inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+template <typename R>
+void launch_init(const Fields<R> &F, DevScalars *S, const double *rho0, const double *p0, long long dep_cell,
+                 double dep_e, cudaStream_t st) {
+  k_reset_scalars<<<1, 1, 0, st>>>(S);
+  k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e);
+  k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F);
+  k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, kDtInit, 0.0);
+}
+
+void launch_set_limits(DevScalars *S, double t_end, long long cycle_limit, cudaStream_t st) {
+  k_set_limits<<<1, 1, 0, st>>>(S, t_end, cycle_limit);
+}
+
+template <typename R>
+void launch_eos(const Fields<R> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
+  k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+}
+
+template <typename R>
+void launch_lagrange(const Fields<R> &F, DevScalars *S, double dt_override, cudaStream_t st) {
+  k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override);
+  k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+}
+
+template <typename R>
+void launch_remap_a(const Fields<R> &F, DevScalars *S, cudaStream_t st) {
+  k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+  k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S);
+}
+
+template <typename R>
+void launch_remap_b(const Fields<R> &F, DevScalars *S, cudaStream_t st) {
+  k_remap_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+}
+
+template <typename R>
+void launch_diag(const Fields<R> &F, double *partial, double *out, cudaStream_t st) {
+  k_diag_partial<R><<<kDiagBlocks, kBlock, 0, st>>>(F, partial);
+  k_diag_final<<<1, kDiagBlocks, 0, st>>>(partial, out);
+}
+
+template void launch_init<double>(const Fields<double> &, DevScalars *, const double *, const double *,
+                                  long long, double, cudaStream_t);
+template void launch_eos<double>(const Fields<double> &, DevScalars *, int, double, cudaStream_t);
+template void launch_lagrange<double>(const Fields<double> &, DevScalars *, double, cudaStream_t);
+template void launch_remap_a<double>(const Fields<double> &, DevScalars *, cudaStream_t);
+template void launch_remap_b<double>(const Fields<double> &, DevScalars *, cudaStream_t);
+template void launch_diag<double>(const Fields<double> &, double *, double *, cudaStream_t);
+
+}  // namespace sale

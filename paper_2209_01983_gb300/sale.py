@@ -1,0 +1,198 @@
+"""Thin ctypes binding of libsale_gb300.so (include/sale.h), same names.
+
+Only argument marshalling happens here: every step of the hydro cycle runs
+in the library's CUDA kernels.  PyTorch supplies the device buffer and the
+CUDA stream.  If the library is not built the import of this module fails
+loudly; there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+import os
+
+import numpy as np
+
+from . import inputs
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libsale_gb300.so")
+
+SALE_OK, SALE_EINVAL, SALE_ENOMEM, SALE_ECUDA = 0, -1, -2, -3
+SALE_ENEGVOL, SALE_EDT, SALE_ENAN, SALE_ETIMEOUT, SALE_ESTATE = -4, -5, -6, -7, -8
+SALE_FP64, SALE_FP32_MIXED = 0, 1
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is not built: run `python -c 'import __graft_entry__ as g; g.build()'`")
+_lib = C.CDLL(LIB_PATH)
+
+
+class sale_mesh_desc(C.Structure):
+    _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
+                ("lo", C.c_double * 3), ("hi", C.c_double * 3), ("jitter", C.c_double),
+                ("seed", C.c_ulonglong), ("reflect", C.c_int * 6)]
+
+
+class sale_problem_desc(C.Structure):
+    _fields_ = [("kind", C.c_int), ("gamma", C.c_double),
+                ("rho_l", C.c_double), ("p_l", C.c_double), ("rho_r", C.c_double),
+                ("p_r", C.c_double), ("x_split", C.c_double),
+                ("rho_bg", C.c_double), ("p_bg", C.c_double), ("rho_blast", C.c_double),
+                ("p_blast", C.c_double), ("e_deposit", C.c_double),
+                ("cfl", C.c_double), ("c_q", C.c_double), ("c_l", C.c_double),
+                ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int)]
+
+
+class sale_diag(C.Structure):
+    _fields_ = [("t", C.c_double), ("dt", C.c_double), ("cycle", C.c_longlong),
+                ("mass", C.c_double), ("mom", C.c_double * 3), ("ie", C.c_double),
+                ("ke", C.c_double), ("etot", C.c_double), ("status", C.c_int)]
+
+
+_vp = C.c_void_p
+_dp = C.POINTER(C.c_double)
+
+
+def _sig(name, res, args):
+    f = getattr(_lib, name)
+    f.restype = res
+    f.argtypes = args
+    return f
+
+
+sale_mesh_create = _sig("sale_mesh_create", C.c_int, [C.POINTER(sale_mesh_desc), C.POINTER(_vp)])
+sale_mesh_destroy = _sig("sale_mesh_destroy", None, [_vp])
+sale_mesh_nodes = _sig("sale_mesh_nodes", C.c_int, [_vp, _dp, C.c_size_t])
+sale_state_bytes = _sig("sale_state_bytes", C.c_size_t, [_vp, C.c_int])
+sale_state_init = _sig("sale_state_init", C.c_int,
+                       [_vp, C.POINTER(sale_problem_desc), C.c_int, _vp, C.c_size_t, _vp, C.POINTER(_vp)])
+sale_state_destroy = _sig("sale_state_destroy", None, [_vp])
+sale_lagrange_step = _sig("sale_lagrange_step", C.c_int, [_vp, C.c_double])
+sale_remap_step = _sig("sale_remap_step", C.c_int, [_vp])
+sale_run_to_time = _sig("sale_run_to_time", C.c_int,
+                        [_vp, C.c_double, C.c_longlong, C.c_int, C.POINTER(C.c_longlong)])
+sale_diagnostics = _sig("sale_diagnostics", C.c_int, [_vp, C.POINTER(sale_diag)])
+sale_copy_field = _sig("sale_copy_field", C.c_int, [_vp, C.c_char_p, _dp, C.c_size_t])
+sale_set_field = _sig("sale_set_field", C.c_int, [_vp, C.c_char_p, _dp, C.c_size_t])
+sale_refresh = _sig("sale_refresh", C.c_int, [_vp])
+sale_state_dims = _sig("sale_state_dims", C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)])
+sale_last_error = _sig("sale_last_error", C.c_char_p, [])
+
+#: every symbol declared in include/sale.h
+EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes",
+           "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
+           "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
+           "sale_refresh", "sale_state_dims", "sale_last_error")
+
+
+class SaleError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"sale status {code}: {msg}")
+        self.code = code
+
+
+def check(rc):
+    if rc != SALE_OK:
+        raise SaleError(rc, sale_last_error().decode(errors="replace"))
+    return rc
+
+
+def mesh_desc(md: inputs.MeshDesc) -> sale_mesh_desc:
+    d = sale_mesh_desc()
+    d.nx, d.ny, d.nz = md.nx, md.ny, md.nz
+    for a in range(3):
+        d.lo[a], d.hi[a] = md.lo[a], md.hi[a]
+    d.jitter = md.jitter
+    d.seed = md.seed
+    for f in range(6):
+        d.reflect[f] = int(md.reflect[f])
+    return d
+
+
+def problem_desc(pd: inputs.ProblemDesc) -> sale_problem_desc:
+    p = sale_problem_desc()
+    for name, _ in sale_problem_desc._fields_:
+        v = getattr(pd, name)
+        setattr(p, name, int(v) if name in ("kind", "ke_fix") else float(v))
+    if not math.isfinite(p.dt_init):
+        p.dt_init = 0.0
+    return p
+
+
+class Mesh:
+    def __init__(self, md: inputs.MeshDesc):
+        self.md = md
+        self._h = _vp()
+        check(sale_mesh_create(C.byref(mesh_desc(md)), C.byref(self._h)))
+
+    def nodes(self):
+        n = 3 * self.md.nnode
+        out = np.empty(n)
+        check(sale_mesh_nodes(self._h, out.ctypes.data_as(_dp), n))
+        return out[: n // 3], out[n // 3: 2 * n // 3], out[2 * n // 3:]
+
+    def __del__(self):
+        if getattr(self, "_h", None):
+            sale_mesh_destroy(self._h)
+            self._h = None
+
+
+class State:
+    """A state on one GPU: torch owns the device buffer and the stream."""
+
+    NODE = ("x", "y", "z", "u", "v", "w", "mn", "xref", "yref", "zref")
+
+    def __init__(self, md: inputs.MeshDesc, pd: inputs.ProblemDesc, precision=SALE_FP64,
+                 device="cuda", stream=None):
+        import torch
+
+        self.md, self.pd = md, pd
+        self.mesh = Mesh(md)
+        nbytes = sale_state_bytes(self.mesh._h, precision)
+        if nbytes == 0:
+            raise SaleError(SALE_EINVAL, f"unsupported precision {precision}")
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self._h = _vp()
+        check(sale_state_init(self.mesh._h, C.byref(problem_desc(pd)), precision,
+                              _vp(self.buffer.data_ptr()), nbytes, _vp(self.stream.cuda_stream),
+                              C.byref(self._h)))
+        self.ncell, self.nnode = md.ncell, md.nnode
+
+    def close(self):
+        if getattr(self, "_h", None):
+            sale_state_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def lagrange_step(self, dt=0.0):
+        check(sale_lagrange_step(self._h, dt))
+
+    def remap_step(self):
+        check(sale_remap_step(self._h))
+
+    def run_to_time(self, t_end=math.inf, max_cycles=(1 << 62), remap_every=0):
+        done = C.c_longlong(0)
+        check(sale_run_to_time(self._h, t_end, max_cycles, remap_every, C.byref(done)))
+        return done.value
+
+    def diagnostics(self) -> dict:
+        d = sale_diag()
+        check(sale_diagnostics(self._h, C.byref(d)))
+        return dict(t=d.t, dt=d.dt, cycle=d.cycle, mass=d.mass, mom_x=d.mom[0], mom_y=d.mom[1],
+                    mom_z=d.mom[2], ie=d.ie, ke=d.ke, etot=d.etot, status=d.status)
+
+    def field(self, name) -> np.ndarray:
+        n = self.nnode if name in self.NODE else self.ncell
+        out = np.empty(n)
+        check(sale_copy_field(self._h, name.encode(), out.ctypes.data_as(_dp), n))
+        return out
+
+    def set_field(self, name, values):
+        a = np.ascontiguousarray(values, dtype=np.float64)
+        check(sale_set_field(self._h, name.encode(), a.ctypes.data_as(_dp), a.size))
+
+    def refresh(self):
+        check(sale_refresh(self._h))

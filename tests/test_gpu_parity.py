@@ -1,0 +1,176 @@
+"""GPU (FP64) vs CPU oracle, element by element, through the C ABI.
+
+Tolerance: relative L-infinity per field, max|gpu - oracle| / max|oracle|,
+<= 1e-10 after the whole run.  Both sides evaluate the same formulas in
+FP64; they differ only in rounding (the GPU fuses multiply-adds and sums in
+another order), which stays many orders below the bound.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2209_01983_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+NODE_FIELDS = ("x", "y", "z", "u", "v", "w", "mn")
+CELL_FIELDS = ("m", "e", "rho", "p", "q", "cs", "vol")
+
+
+@pytest.fixture(scope="module")
+def sale():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2209_01983_gb300 import sale as s
+    return s
+
+
+def rel_linf(a, b):
+    scale = np.max(np.abs(b))
+    if scale == 0.0:
+        return float(np.max(np.abs(a)))
+    return float(np.max(np.abs(a - b)) / scale)
+
+
+# Vector fields are compared normwise over their three components: a
+# component that is zero in exact arithmetic (v, w of the Sod tube) carries
+# only roundoff on both sides and has no scale of its own.
+GROUPS = {"x": ("x", "y", "z"), "y": ("x", "y", "z"), "z": ("x", "y", "z"),
+          "u": ("u", "v", "w"), "v": ("u", "v", "w"), "w": ("u", "v", "w")}
+
+
+def compare(st, o, fields=NODE_FIELDS + CELL_FIELDS, tol=TOL):
+    errs = {}
+    cache = {}
+
+    def get(src, name):
+        key = (id(src), name)
+        if key not in cache:
+            cache[key] = src.field(name)
+        return cache[key]
+
+    for name in fields:
+        a, b = get(st, name), get(o, name)
+        group = GROUPS.get(name, (name,))
+        scale = max(float(np.max(np.abs(get(o, g)))) for g in group)
+        diff = float(np.max(np.abs(a - b)))
+        errs[name] = diff / scale if scale > 0 else diff
+    bad = {k: v for k, v in errs.items() if not v <= tol}
+    assert not bad, f"fields over {tol}: {bad}"
+    return errs
+
+
+def test_initial_state(sale):
+    md, pd = inputs.sedov_octant(12, jitter=0.1)
+    st = sale.State(md, pd)
+    o = oracle.Oracle.from_problem(md, pd)
+    compare(st, o, tol=1e-13)
+    assert st.diagnostics()["dt"] == pytest.approx(o.s.dt, rel=1e-13)
+
+
+def test_sod_lagrange_to_t02(sale):
+    md, pd = inputs.sod_x(100, 4, 4)
+    st = sale.State(md, pd)
+    n = st.run_to_time(t_end=0.2)
+    o = oracle.Oracle.from_problem(md, pd)
+    rc, n_o = o.run(t_end=0.2)
+    assert rc == 0 and n == n_o
+    d = st.diagnostics()
+    assert d["t"] == 0.2 and d["cycle"] == n_o
+    compare(st, o)
+
+
+@pytest.mark.parametrize("dims,jitter", [((23, 17, 14), 0.0), ((16, 19, 13), 0.1)])
+def test_sedov_ale_100_cycles(sale, dims, jitter):
+    md, pd = inputs.sedov_octant(1, jitter=jitter)
+    md.nx, md.ny, md.nz = dims
+    st = sale.State(md, pd)
+    n = st.run_to_time(max_cycles=100, remap_every=1)
+    o = oracle.Oracle.from_problem(md, pd)
+    rc, n_o = o.run(max_cycles=100, remap_every=1)
+    assert rc == 0 and n == n_o == 100
+    compare(st, o)
+    d, do = st.diagnostics(), o.diagnostics()
+    assert d["dt"] == pytest.approx(do["dt"], rel=1e-10)
+    for k in ("mass", "ie", "ke", "etot"):
+        assert d[k] == pytest.approx(do[k], rel=1e-12, abs=1e-300)
+
+
+def test_remap_every_third_cycle(sale):
+    md, pd = inputs.sedov_octant(1, jitter=0.05)
+    md.nx, md.ny, md.nz = 14, 12, 10
+    st = sale.State(md, pd)
+    n = st.run_to_time(max_cycles=40, remap_every=3)
+    o = oracle.Oracle.from_problem(md, pd)
+    o.run(max_cycles=40, remap_every=3)
+    assert n == 40
+    compare(st, o)
+
+
+def test_explicit_calls_match(sale):
+    """lagrange_step(dt) / remap_step issued one by one."""
+    md, pd = inputs.sedov_octant(10, jitter=0.1)
+    st = sale.State(md, pd)
+    o = oracle.Oracle.from_problem(md, pd)
+    for it in range(6):
+        dt = 1e-4 * (1 + it)
+        st.lagrange_step(dt)
+        o.check(o.lagrange_step(dt))
+        if it % 2 == 1:
+            st.remap_step()
+            o.check(o.remap_step())
+    compare(st, o)
+    st.lagrange_step()  # on-device dt
+    o.check(o.lagrange_step(o.s.dt))
+    compare(st, o)
+
+
+def test_run_to_time_lands_on_t_end(sale):
+    md, pd = inputs.sedov_octant(8)
+    st = sale.State(md, pd)
+    n1 = st.run_to_time(t_end=0.01, remap_every=1)
+    n2 = st.run_to_time(t_end=0.02, remap_every=1)
+    d = st.diagnostics()
+    o = oracle.Oracle.from_problem(md, pd)
+    o.run(t_end=0.01, remap_every=1)
+    o.run(t_end=0.02, remap_every=1)
+    assert d["t"] == 0.02 and d["cycle"] == o.s.cycle == n1 + n2
+    compare(st, o)
+
+
+def test_deterministic(sale):
+    md, pd = inputs.sedov_octant(12, jitter=0.1)
+    outs = []
+    for _ in range(2):
+        st = sale.State(md, pd)
+        st.run_to_time(max_cycles=30, remap_every=1)
+        outs.append([st.field(f) for f in ("e", "u", "mn")])
+    for a, b in zip(*outs):
+        assert np.array_equal(a, b)
+
+
+def test_tangled_mesh_reports_negvol(sale):
+    md, pd = inputs.sedov_octant(6)
+    st = sale.State(md, pd)
+    st.lagrange_step(10.0)  # far beyond CFL: cells invert
+    with pytest.raises(sale.SaleError) as ei:
+        st.diagnostics()
+    assert ei.value.code in (sale.SALE_ENEGVOL, sale.SALE_ENAN, sale.SALE_EDT)
+    with pytest.raises(sale.SaleError) as ei:
+        st.lagrange_step()
+    assert ei.value.code == sale.SALE_ESTATE
+
+
+def test_set_field_and_refresh(sale):
+    md, pd = inputs.sedov_octant(8, jitter=0.1)
+    st = sale.State(md, pd)
+    st.run_to_time(max_cycles=5, remap_every=1)
+    e = st.field("e") * 1.5
+    st.set_field("e", e)
+    st.refresh()
+    assert np.array_equal(st.field("e"), e)
+    assert rel_linf(st.field("p"), 0.4 * st.field("rho") * e) <= 1e-15
