@@ -170,6 +170,19 @@ int sale_refresh(sale_state *st);
 /* Sizes of a state: ncells, nnodes. */
 int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes);
 
+/* Launch-time profile.  While on, every kernel launch of the state's steps
+ * is bracketed by CUDA events on the state's stream (inside captured
+ * graphs as event nodes); device times accumulate on the host at each
+ * synchronising call.  sale_profile_read() synchronises, copies the
+ * per-kernel totals (milliseconds, launches) for kernel ids [0, n) and
+ * optionally resets them.  Kernel ids name the kernels of the cycle in
+ * sale_kernel_name(id), 0 <= id < sale_kernel_count(). */
+int sale_profile(sale_state *st, int on);
+int sale_profile_read(sale_state *st, double *ms, long long *launches, int n,
+                      int reset);
+int sale_kernel_count(void);
+const char *sale_kernel_name(int id);
+
 const char *sale_last_error(void);
 
 #ifdef __cplusplus

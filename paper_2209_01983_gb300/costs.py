@@ -1,0 +1,45 @@
+"""Algorithmic cost of each kernel of the cycle, per unit (cell or node).
+
+bytes: compulsory HBM traffic of the kernel's data flow, every array it
+reads or writes counted once (N_nodes ~ N_cells, so node arrays count per
+cell too), in the storage precision.
+flops: floating-point operations of the formulas the kernel evaluates, each
+distinct quantity counted once per kernel (a multiply-add is 2, a divide or
+square root 1); recomputation inside the kernel (e.g. the node gather
+re-deriving corner gradients of its eight cells) is not counted.
+
+Formula counts used below (FP64 path):
+  hex volume            202  (6 faces x (9 adds node sum + 6 diagonal subs
+                              + 9 cross + 5 dot + 1 accumulate) + 21 shift + 1)
+  hex volume gradient   600  (24 face-corner terms x (9 weighted sum + 3 sub
+                              + 9 cross + 3 accumulate) + 24 scale)
+  face areas + L        122  (6 x (6 subs + 9 cross + 5 |A|^2) + max + sqrt + div)
+"""
+
+VOL, GRAD, LEN = 202, 600, 122
+
+# kernel: (unit, bytes per unit FP64, flops per unit)
+FP64 = {
+    # x, u, mn, sigma read; u, ubar, x+ written
+    "lagrange_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 3 + 3), GRAD + 48 + 20),
+    # x, ubar, x+, m, e, sigma read; e, vol, rho written
+    "lagrange_cells": ("cell", 8 * (3 + 3 + 3 + 3 + 3), GRAD + 40 + 5 + VOL + 1),
+    # x, x_ref, rho, e read; 3 mass + 3 energy fluxes written
+    "remap_faces": ("cell", 8 * (3 + 3 + 2 + 6), 3 * VOL + 6),
+    # 3 mass fluxes, u, mn, x_ref read; u', mn', dKE, x written
+    "remap_nodes": ("node", 8 * (3 + 3 + 1 + 3 + 3 + 1 + 1 + 3), 125),
+    # 6 fluxes, m, e, dKE read; m, e written
+    "remap_cells": ("cell", 8 * (6 + 2 + 1 + 2), 35),
+    # x, u, m, e read; vol, rho, p, q, cs, sigma written
+    "eos_dt": ("cell", 8 * (3 + 3 + 2 + 6), VOL + GRAD + 40 + LEN + 33),
+}
+
+# One full ALE cycle of the FP64 path, per cell.
+FP64_CYCLE_BYTES = sum(v[1] for v in FP64.values())
+FP64_CYCLE_FLOPS = sum(v[2] for v in FP64.values())
+
+
+def table(precision: str):
+    if precision == "fp64":
+        return FP64
+    raise KeyError(precision)

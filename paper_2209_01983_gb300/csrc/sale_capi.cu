@@ -19,20 +19,14 @@
 #include "sale_internal.cuh"
 
 namespace sale {
-template <typename R>
-void launch_init(const Fields<R> &, DevScalars *, const double *, const double *, long long, double,
-                 cudaStream_t);
+void launch_reset(DevScalars *, cudaStream_t);
 void launch_set_limits(DevScalars *, double, long long, cudaStream_t);
 template <typename R>
-void launch_eos(const Fields<R> &, DevScalars *, int, double, cudaStream_t);
+void launch_init_cells(const Fields<R> &, DevScalars *, const double *, const double *, long long, double,
+                       cudaStream_t);
 template <typename R>
-void launch_lagrange(const Fields<R> &, DevScalars *, double, cudaStream_t);
-template <typename R>
-void launch_remap_a(const Fields<R> &, DevScalars *, cudaStream_t);
-template <typename R>
-void launch_remap_b(const Fields<R> &, DevScalars *, cudaStream_t);
-template <typename R>
-void launch_diag(const Fields<R> &, double *, double *, cudaStream_t);
+void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt_override, double *partial,
+                   double *out, cudaStream_t);
 }  // namespace sale
 
 using namespace sale;
@@ -193,10 +187,15 @@ Layout make_layout(long long nc, long long nn, size_t elem) {
 }  // namespace
 
 struct GraphKey {
-  int k, remap_every, xpar, upar;
+  int k, remap_every, xpar, upar, prof;
   bool operator<(const GraphKey &o) const {
-    return std::tie(k, remap_every, xpar, upar) < std::tie(o.k, o.remap_every, o.xpar, o.upar);
+    return std::tie(k, remap_every, xpar, upar, prof) < std::tie(o.k, o.remap_every, o.xpar, o.upar, o.prof);
   }
+};
+
+struct ProfEvent {
+  int kid;
+  cudaEvent_t a, b;
 };
 
 struct sale_state {
@@ -220,6 +219,16 @@ struct sale_state {
   sale_problem_desc prob;
   int reflect[6];
   std::map<GraphKey, cudaGraphExec_t> graphs;
+  // launch-time profile: CUDA events around every kernel of the cycle
+  bool prof_on = false;
+  bool capturing = false;
+  std::vector<cudaEvent_t> ev_pool;                  // free events
+  std::vector<ProfEvent> pending;                    // direct launches not yet read
+  std::vector<ProfEvent> capture_events;             // events of the graph being captured
+  std::map<GraphKey, std::vector<ProfEvent>> graph_events;
+  std::vector<const std::vector<ProfEvent> *> pending_graphs;  // replays not yet read
+  double prof_ms[kNumKernels] = {};
+  long long prof_n[kNumKernels] = {};
 };
 
 static Fields<double> fields(const sale_state *st) {
@@ -320,9 +329,13 @@ static void host_primitives(const sale_mesh &mesh, const sale_problem_desc &p, s
   }
 }
 
-static int sync_scalars(const sale_state *st, DevScalars *h) {
+static void collect_profile(sale_state *st);
+
+static int sync_scalars(const sale_state *cst, DevScalars *h) {
+  sale_state *st = const_cast<sale_state *>(cst);
   CUDA_TRY(cudaMemcpyAsync(h, st->S, sizeof(DevScalars), cudaMemcpyDeviceToHost, st->stream));
   CUDA_TRY(cudaStreamSynchronize(st->stream));
+  if (!st->pending.empty() || !st->pending_graphs.empty()) collect_profile(st);
   return SALE_OK;
 }
 
@@ -422,7 +435,13 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     delete st;
     return cuda_fail(e, "sale_state_init: upload");
   }
-  launch_init(fields(st), st->S, st->p, st->q, dep_cell, dep_e, st->stream);
+  {
+    const Fields<double> F = fields(st);
+    launch_reset(st->S, st->stream);
+    launch_init_cells(F, st->S, st->p, st->q, dep_cell, dep_e, st->stream);
+    launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
+    launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
+  }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // host vectors die here
   if (e != cudaSuccess) {
@@ -442,8 +461,79 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
 
 extern "C" void sale_state_destroy(sale_state *st) {
   if (!st) return;
+  cudaStreamSynchronize(st->stream);
   for (auto &kv : st->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto &kv : st->graph_events)
+    for (auto &pe : kv.second) {
+      cudaEventDestroy(pe.a);
+      cudaEventDestroy(pe.b);
+    }
+  for (auto &pe : st->pending) {
+    cudaEventDestroy(pe.a);
+    cudaEventDestroy(pe.b);
+  }
+  for (auto ev : st->ev_pool) cudaEventDestroy(ev);
   delete st;
+}
+
+// ---------------------------------------------------------------------------
+// Launch with optional profiling events
+// ---------------------------------------------------------------------------
+
+static cudaEvent_t take_event(sale_state *st) {
+  if (!st->ev_pool.empty()) {
+    cudaEvent_t e = st->ev_pool.back();
+    st->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// During stream capture an event record becomes a graph node only with
+// cudaEventRecordExternal (a plain record is a capture-internal join point).
+static void record(sale_state *st, cudaEvent_t ev) {
+  if (st->capturing) cudaEventRecordWithFlags(ev, st->stream, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st->stream);
+}
+
+static void launch_k(sale_state *st, int kid, int mode = 0, double dt_override = 0.0) {
+  cudaEvent_t a = nullptr;
+  if (st->prof_on) {
+    a = take_event(st);
+    record(st, a);
+  }
+  launch_kernel(kid, fields(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
+  if (st->prof_on) {
+    cudaEvent_t b = take_event(st);
+    record(st, b);
+    (st->capturing ? st->capture_events : st->pending).push_back({kid, a, b});
+  }
+}
+
+// Accumulate the profile of launches that completed (stream synchronised).
+static void collect_profile(sale_state *st) {
+  for (auto &pe : st->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      st->prof_ms[pe.kid] += ms;
+      st->prof_n[pe.kid] += 1;
+    }
+    st->ev_pool.push_back(pe.a);
+    st->ev_pool.push_back(pe.b);
+  }
+  st->pending.clear();
+  for (auto *list : st->pending_graphs)
+    for (auto &pe : *list) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+        st->prof_ms[pe.kid] += ms;
+        st->prof_n[pe.kid] += 1;
+      }
+    }
+  st->pending_graphs.clear();
+  cudaGetLastError();  // a never-recorded event is not an error of the state
 }
 
 // ---------------------------------------------------------------------------
@@ -466,15 +556,19 @@ static void set_limits(sale_state *st, double t_end, long long cycles) {
 
 // Kernels of one cycle on the state's stream; toggles the host's record of
 // which buffers hold the current positions and velocities.
+static void launch_remap(sale_state *st) {
+  launch_k(st, kRemapFaces);
+  launch_k(st, kRemapNodes);
+  st->upar ^= 1;
+  launch_k(st, kRemapCells);
+}
+
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
-  launch_lagrange(fields(st), st->S, dt_override, st->stream);
+  launch_k(st, kLagNodes, 0, dt_override);
+  launch_k(st, kLagCells, 0, dt_override);
   st->xpar ^= 1;
-  if (remap) {
-    launch_remap_a(fields(st), st->S, st->stream);
-    st->upar ^= 1;
-    launch_remap_b(fields(st), st->S, st->stream);
-  }
-  launch_eos(fields(st), st->S, kDtAdvance, dt_override, st->stream);
+  if (remap) launch_remap(st);
+  launch_k(st, kEos, kDtAdvance, dt_override);
 }
 
 extern "C" int sale_lagrange_step(sale_state *st, double dt) {
@@ -491,10 +585,8 @@ extern "C" int sale_remap_step(sale_state *st) {
   int rc = ready(st, "sale_remap_step");
   if (rc) return rc;
   set_limits(st, INFINITY, 0x7FFFFFFFFFFFFFFFll);
-  launch_remap_a(fields(st), st->S, st->stream);
-  st->upar ^= 1;
-  launch_remap_b(fields(st), st->S, st->stream);
-  launch_eos(fields(st), st->S, kDtPropose, 0.0, st->stream);
+  launch_remap(st);
+  launch_k(st, kEos, kDtPropose);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SALE_OK : cuda_fail(e, "sale_remap_step");
 }
@@ -502,10 +594,11 @@ extern "C" int sale_remap_step(sale_state *st) {
 // Capture `k` cycles (remap after cycle j when (j+1) % remap_every == 0,
 // the first cycle being aligned to the remap cadence) as one graph.
 static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *out) {
-  GraphKey key{k, remap_every, st->xpar, st->upar};
+  GraphKey key{k, remap_every, st->xpar, st->upar, st->prof_on ? 1 : 0};
   auto it = st->graphs.find(key);
   if (it != st->graphs.end()) {
     *out = it->second;
+    if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
     for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles
       st->xpar ^= 1;
       if (remap_every > 0 && (j + 1) % remap_every == 0) st->upar ^= 1;
@@ -514,9 +607,17 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
   }
   cudaGraph_t g;
   CUDA_TRY(cudaStreamBeginCapture(st->stream, cudaStreamCaptureModeThreadLocal));
+  st->capturing = true;
+  st->capture_events.clear();
   for (int j = 0; j < k; ++j) launch_cycle(st, remap_every > 0 && (j + 1) % remap_every == 0, 0.0);
+  st->capturing = false;
   cudaError_t e = cudaStreamEndCapture(st->stream, &g);
   if (e != cudaSuccess) return cuda_fail(e, "graph capture");
+  if (st->prof_on) {
+    st->graph_events[key] = st->capture_events;
+    st->pending_graphs.push_back(&st->graph_events[key]);
+  }
+  st->capture_events.clear();
   cudaGraphExec_t ge;
   e = cudaGraphInstantiate(&ge, g, 0);
   cudaGraphDestroy(g);
@@ -545,7 +646,9 @@ extern "C" int sale_run_to_time(sale_state *st, double t_end, long long max_cycl
   if (chunk % 2) chunk *= 2;
   while (h.t < t_end && h.cycle < limit) {
     const bool aligned = remap_every == 0 || h.cycle % remap_every == 0;
-    if (graphs && aligned) {
+    // a graph only when a whole chunk of cycles is within the cycle budget
+    // (cycles past t_end inside a replay are cheap no-ops)
+    if (graphs && aligned && limit - h.cycle >= chunk) {
       cudaGraphExec_t ge;
       if ((rc = get_graph(st, chunk, remap_every, &ge))) return rc;
       CUDA_TRY(cudaGraphLaunch(ge, st->stream));
@@ -568,7 +671,7 @@ extern "C" int sale_run_to_time(sale_state *st, double t_end, long long max_cycl
 extern "C" int sale_diagnostics(const sale_state *cst, sale_diag *out) {
   sale_state *st = const_cast<sale_state *>(cst);
   if (!st || !out) return fail(SALE_EINVAL, "sale_diagnostics: null argument");
-  launch_diag(fields(st), st->diag_partial, st->diag_out, st->stream);
+  launch_kernel(kDiag, fields(st), st->S, 0, 0.0, st->diag_partial, st->diag_out, st->stream);
   CUDA_TRY(cudaGetLastError());
   double q[8];
   CUDA_TRY(cudaMemcpyAsync(q, st->diag_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, st->stream));
@@ -647,7 +750,7 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
 extern "C" int sale_refresh(sale_state *st) {
   int rc = ready(st, "sale_refresh");
   if (rc) return rc;
-  launch_eos(fields(st), st->S, kDtPropose, 0.0, st->stream);
+  launch_k(st, kEos, kDtPropose);
   CUDA_TRY(cudaGetLastError());
   return SALE_OK;
 }
@@ -656,6 +759,44 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
   if (!st) return fail(SALE_EINVAL, "sale_state_dims: null state");
   if (ncells) *ncells = st->nc;
   if (nnodes) *nnodes = st->nn;
+  return SALE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Launch-time profile
+// ---------------------------------------------------------------------------
+
+static const char *const kKernelNames[kNumKernels] = {
+    "init_nodes", "eos_dt", "lagrange_nodes", "lagrange_cells", "remap_faces", "remap_nodes", "remap_cells",
+    "diagnostics"};
+
+extern "C" int sale_kernel_count(void) { return kNumKernels; }
+
+extern "C" const char *sale_kernel_name(int id) {
+  return (id >= 0 && id < kNumKernels) ? kKernelNames[id] : nullptr;
+}
+
+extern "C" int sale_profile(sale_state *st, int on) {
+  if (!st) return fail(SALE_EINVAL, "sale_profile: null state");
+  st->prof_on = on != 0;
+  return SALE_OK;
+}
+
+extern "C" int sale_profile_read(sale_state *st, double *ms, long long *launches, int n, int reset) {
+  if (!st) return fail(SALE_EINVAL, "sale_profile_read: null state");
+  if (n < 0 || n > kNumKernels) return fail(SALE_EINVAL, "sale_profile_read: n must be in [0, %d]", kNumKernels);
+  DevScalars h;
+  int rc = sync_scalars(st, &h);
+  if (rc) return rc;
+  for (int i = 0; i < n; ++i) {
+    if (ms) ms[i] = st->prof_ms[i];
+    if (launches) launches[i] = st->prof_n[i];
+  }
+  if (reset)
+    for (int i = 0; i < kNumKernels; ++i) {
+      st->prof_ms[i] = 0.0;
+      st->prof_n[i] = 0;
+    }
   return SALE_OK;
 }
 

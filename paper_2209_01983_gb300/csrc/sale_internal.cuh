@@ -37,6 +37,19 @@ struct DevScalars {
   double pad[8];
 };
 
+// Kernels of the cycle, in the order of their launch-time profile slots.
+enum KernelId : int {
+  kInitNodes = 0,
+  kEos,
+  kLagNodes,
+  kLagCells,
+  kRemapFaces,
+  kRemapNodes,
+  kRemapCells,
+  kDiag,
+  kNumKernels
+};
+
 // Modes of the kernel that ends a step and proposes the next dt.
 enum DtMode : int {
   kDtPropose = 0,  // dt = min(cfl, growth * dt_last)

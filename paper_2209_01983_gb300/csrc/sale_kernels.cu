@@ -527,58 +527,45 @@ __global__ void k_diag_final(const double *partial, double *out) {
 }
 
 // ---------------------------------------------------------------------------
-// Host launchers
+// Host launchers (one per kernel, indexed by KernelId)
 // ---------------------------------------------------------------------------
 
 static inline unsigned grid_for(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
-template <typename R>
-void launch_init(const Fields<R> &F, DevScalars *S, const double *rho0, const double *p0, long long dep_cell,
-                 double dep_e, cudaStream_t st) {
-  k_reset_scalars<<<1, 1, 0, st>>>(S);
-  k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e);
-  k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F);
-  k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, kDtInit, 0.0);
-}
+void launch_reset(DevScalars *S, cudaStream_t st) { k_reset_scalars<<<1, 1, 0, st>>>(S); }
 
 void launch_set_limits(DevScalars *S, double t_end, long long cycle_limit, cudaStream_t st) {
   k_set_limits<<<1, 1, 0, st>>>(S, t_end, cycle_limit);
 }
 
 template <typename R>
-void launch_eos(const Fields<R> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
-  k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+void launch_init_cells(const Fields<R> &F, DevScalars *S, const double *rho0, const double *p0,
+                       long long dep_cell, double dep_e, cudaStream_t st) {
+  k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e);
 }
 
 template <typename R>
-void launch_lagrange(const Fields<R> &F, DevScalars *S, double dt_override, cudaStream_t st) {
-  k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override);
-  k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
+                   double *out, cudaStream_t st) {
+  switch (kid) {
+    case kInitNodes: k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F); break;
+    case kEos: k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override); break;
+    case kLagNodes: k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kLagCells: k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kRemapFaces: k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kRemapNodes: k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S); break;
+    case kRemapCells: k_remap_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kDiag:
+      k_diag_partial<R><<<kDiagBlocks, kBlock, 0, st>>>(F, partial);
+      k_diag_final<<<1, kDiagBlocks, 0, st>>>(partial, out);
+      break;
+    default: break;
+  }
 }
 
-template <typename R>
-void launch_remap_a(const Fields<R> &F, DevScalars *S, cudaStream_t st) {
-  k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
-  k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S);
-}
-
-template <typename R>
-void launch_remap_b(const Fields<R> &F, DevScalars *S, cudaStream_t st) {
-  k_remap_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
-}
-
-template <typename R>
-void launch_diag(const Fields<R> &F, double *partial, double *out, cudaStream_t st) {
-  k_diag_partial<R><<<kDiagBlocks, kBlock, 0, st>>>(F, partial);
-  k_diag_final<<<1, kDiagBlocks, 0, st>>>(partial, out);
-}
-
-template void launch_init<double>(const Fields<double> &, DevScalars *, const double *, const double *,
-                                  long long, double, cudaStream_t);
-template void launch_eos<double>(const Fields<double> &, DevScalars *, int, double, cudaStream_t);
-template void launch_lagrange<double>(const Fields<double> &, DevScalars *, double, cudaStream_t);
-template void launch_remap_a<double>(const Fields<double> &, DevScalars *, cudaStream_t);
-template void launch_remap_b<double>(const Fields<double> &, DevScalars *, cudaStream_t);
-template void launch_diag<double>(const Fields<double> &, double *, double *, cudaStream_t);
+template void launch_init_cells<double>(const Fields<double> &, DevScalars *, const double *, const double *,
+                                        long long, double, cudaStream_t);
+template void launch_kernel<double>(int, const Fields<double> &, DevScalars *, int, double, double *, double *,
+                                    cudaStream_t);
 
 }  // namespace sale

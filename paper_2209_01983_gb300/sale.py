@@ -76,13 +76,19 @@ sale_copy_field = _sig("sale_copy_field", C.c_int, [_vp, C.c_char_p, _dp, C.c_si
 sale_set_field = _sig("sale_set_field", C.c_int, [_vp, C.c_char_p, _dp, C.c_size_t])
 sale_refresh = _sig("sale_refresh", C.c_int, [_vp])
 sale_state_dims = _sig("sale_state_dims", C.c_int, [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong)])
+sale_profile = _sig("sale_profile", C.c_int, [_vp, C.c_int])
+sale_profile_read = _sig("sale_profile_read", C.c_int,
+                         [_vp, _dp, C.POINTER(C.c_longlong), C.c_int, C.c_int])
+sale_kernel_count = _sig("sale_kernel_count", C.c_int, [])
+sale_kernel_name = _sig("sale_kernel_name", C.c_char_p, [C.c_int])
 sale_last_error = _sig("sale_last_error", C.c_char_p, [])
 
 #: every symbol declared in include/sale.h
 EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes",
            "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
            "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
-           "sale_refresh", "sale_state_dims", "sale_last_error")
+           "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
+           "sale_kernel_count", "sale_kernel_name", "sale_last_error")
 
 
 class SaleError(RuntimeError):
@@ -196,3 +202,14 @@ class State:
 
     def refresh(self):
         check(sale_refresh(self._h))
+
+    def profile(self, on=True):
+        check(sale_profile(self._h, 1 if on else 0))
+
+    def profile_read(self, reset=True) -> dict:
+        """{kernel name: (total ms, launches)} since the last reset."""
+        n = sale_kernel_count()
+        ms = (C.c_double * n)()
+        cnt = (C.c_longlong * n)()
+        check(sale_profile_read(self._h, ms, cnt, n, 1 if reset else 0))
+        return {sale_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
