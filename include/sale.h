@@ -170,6 +170,44 @@ int sale_refresh(sale_state *st);
 /* Sizes of a state: ncells, nnodes. */
 int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes);
 
+/* Remap step without any device allocation.  The paper has no counterpart
+ * of this call; it serves callers that cannot allocate device memory
+ * (code running during CUDA stream capture, plug-ins whose host program
+ * owns every device allocation, loops that forbid allocator calls).  It
+ * does what sale_remap_step does -- face swept volumes, donor-cell mass and
+ * energy fluxes, dual-mesh node momentum and kinetic-energy fluxes, new
+ * node velocity and mass, cell mass and energy with the kinetic-energy
+ * fix -- on a mesh held entirely in the caller's device arrays (FP64, SoA,
+ * layout as above), without EoS or dt.  Arguments:
+ *   nx, ny, nz   cells per axis; at most SALE_STATIC_MAX_CELLS cells and
+ *                SALE_STATIC_MAX_NODES nodes, else SALE_EINVAL
+ *   reflect[6]   host array, 1 = reflecting wall (x-lo,x-hi,..,z-hi), 0 = none
+ *   ke_fix       return the remap's kinetic-energy loss to the cells (1)
+ *   xref         3*nnodes reference (rezone target) positions, x then y then z
+ *   x            3*nnodes Lagrangian positions in; the reference positions out
+ *   u_in         3*nnodes node velocity before the remap (not modified)
+ *   u_out        3*nnodes node velocity after the remap (must not alias u_in)
+ *   mn           nnodes node mass, in/out
+ *   m, e         ncells cell mass and specific internal energy, in/out
+ *   rho          ncells cell density on the Lagrangian mesh, m / V(x)
+ *   cuda_stream  stream to run on (NULL = legacy default stream)
+ * Scratch (status word, face fluxes, node energy losses) lives in one fixed
+ * static device array of the library (about 4 MB at the limits below),
+ * present on every GPU that loads the library until the process exits.
+ * Every call shares it and it keeps the last call's contents, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  The first call on a device looks up the array's device address
+ * (and may load the library's GPU code); make that first call before any
+ * stream capture.  Calls no device or host allocator.  Synchronises the
+ * stream and returns the device status (SALE_ENEGVOL when a node or cell
+ * mass is not positive). */
+#define SALE_STATIC_MAX_CELLS 65536
+#define SALE_STATIC_MAX_NODES 131072
+int sale_remap_static(int nx, int ny, int nz, const int *reflect, int ke_fix,
+                      const double *xref, double *x, const double *u_in,
+                      double *u_out, double *mn, double *m, double *e,
+                      const double *rho, void *cuda_stream);
+
 /* Launch-time profile.  While on, every kernel launch of the state's steps
  * is bracketed by CUDA events on the state's stream (inside captured
  * graphs as event nodes); device times accumulate on the host at each

@@ -47,6 +47,19 @@ static int fail(int code, const char *fmt, ...) {
   return code;
 }
 
+namespace sale {
+// Error reporting shared with the library's other host translation units.
+int report_error(int code, const char *fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return code;
+}
+}  // namespace sale
+
 static int cuda_fail(cudaError_t e, const char *where) {
   return fail(SALE_ECUDA, "%s: %s", where, cudaGetErrorString(e));
 }

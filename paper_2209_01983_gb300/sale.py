@@ -81,6 +81,11 @@ sale_profile_read = _sig("sale_profile_read", C.c_int,
                          [_vp, _dp, C.POINTER(C.c_longlong), C.c_int, C.c_int])
 sale_kernel_count = _sig("sale_kernel_count", C.c_int, [])
 sale_kernel_name = _sig("sale_kernel_name", C.c_char_p, [C.c_int])
+sale_remap_static = _sig("sale_remap_static", C.c_int,
+                         [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp, _vp,
+                          _vp, _vp, _vp, _vp, _vp])
+SALE_STATIC_MAX_CELLS = 65536
+SALE_STATIC_MAX_NODES = 131072
 sale_last_error = _sig("sale_last_error", C.c_char_p, [])
 
 #: every symbol declared in include/sale.h
@@ -88,7 +93,7 @@ EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_sta
            "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
            "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
            "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
-           "sale_kernel_count", "sale_kernel_name", "sale_last_error")
+           "sale_kernel_count", "sale_kernel_name", "sale_remap_static", "sale_last_error")
 
 
 class SaleError(RuntimeError):
