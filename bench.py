@@ -221,9 +221,12 @@ def gpu_arm(args):
     value = world * md.ncell * args.steps / (t_max * 1e-3)
 
     # ---- roofline of the dominant kernel
-    table = costs.table(precision)
+    table = costs.table(precision, "ale")
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     total_ms = sum(v[0] for v in kern.values())
+    missing = [k for k in kern if k not in table]
+    if missing:
+        raise RuntimeError(f"no cost entry for kernels {missing}")
     top = max(kern, key=lambda k: kern[k][0])
     unit, bytes_u, flops_u = table[top]
     units = md.ncell if unit == "cell" else md.nnode
@@ -236,11 +239,18 @@ def gpu_arm(args):
                 "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 vector pipe)",
                 "hbm_achieved_gbs": bytes_u * units / avg_s / 1e9,
                 "hbm_frac_of_measured": bytes_u * units / avg_s / 1e9 / peaks["hbm_gbs"]}
-    kernels = {k: {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms}
-               for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
+    def per_kernel(k, v):
+        u_, b_, f_ = table[k]
+        nunit = md.ncell if u_ == "cell" else md.nnode
+        sec = v[0] / v[1] * 1e-3
+        return {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms,
+                "alg_gbs": b_ * nunit / sec / 1e9, "alg_tflops": f_ * nunit / sec / 1e12}
+    kernels = {k: per_kernel(k, v) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
     launches = sum(v[1] for v in kern.values())
-    cycle_bytes = sum(table[k][1] * (md.ncell if table[k][0] == "cell" else md.nnode) for k in kern if k in table)
-    full = {"cycle_algorithmic_bytes": cycle_bytes,
+    cycle_bytes = sum(table[k][1] * (md.ncell if table[k][0] == "cell" else md.nnode) for k in kern)
+    cycle_flops = sum(table[k][2] * (md.ncell if table[k][0] == "cell" else md.nnode) for k in kern)
+    full = {"cycle_algorithmic_bytes": cycle_bytes, "cycle_algorithmic_flops": cycle_flops,
+            "cycle_tflops": cycle_flops * args.steps / (ms * 1e-3) / 1e12,
             "cycle_hbm_gbs": cycle_bytes * args.steps / (ms * 1e-3) / 1e9,
             "cycle_hbm_frac_of_measured": cycle_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
 

@@ -34,12 +34,32 @@ FP64 = {
     "eos_dt": ("cell", 8 * (3 + 3 + 2 + 6), VOL + GRAD + 40 + LEN + 33),
 }
 
-# One full ALE cycle of the FP64 path, per cell.
-FP64_CYCLE_BYTES = sum(v[1] for v in FP64.values())
-FP64_CYCLE_FLOPS = sum(v[2] for v in FP64.values())
+# FP64 Eulerian cycle (remap every cycle), cached reference geometry:
+# corner gradients G (24 doubles per cell), V_E, L_E read instead of recomputed.
+SWEPT3 = 3 * VOL + 7 * 3 * 3  # three swept hexes + Lagrangian coordinates of 7 nodes
+FP64_ALE = {
+    # sigma, G (24/cell), u, mn read; u, ubar written
+    "ale_nodes": ("node", 8 * (1 + 24 + 3 + 1 + 3 + 3), 48 + 20),
+    # G, ubar, m, e, sigma, x_ref read; e, 3 swept volumes written
+    "ale_cells": ("cell", 8 * (24 + 3 + 3 + 3 + 1 + 3), 48 + 5 + SWEPT3),
+    # 3 swept volumes, V_E, m read; V_L, rho_L written
+    "ale_density": ("cell", 8 * (3 + 2 + 2), 8),
+    # 3 swept volumes, rho_L, e read; 3 mass + 3 energy fluxes written
+    "ale_fluxes": ("cell", 8 * (3 + 2 + 6), 6),
+    # 3 mass fluxes, u, mn read; u', mn', dKE written
+    "remap_nodes": ("node", 8 * (3 + 3 + 1 + 3 + 1 + 1), 125),
+    # 6 fluxes, m, e, dKE, u', G, V_E, L_E read; m, e, vol, rho, p, q, cs, sigma written
+    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 2 + 8), 35 + 48 + 40),
+}
 
 
-def table(precision: str):
+def table(precision: str, path: str = "ale"):
     if precision == "fp64":
-        return FP64
+        return FP64_ALE if path == "ale" else FP64
     raise KeyError(precision)
+
+
+def cycle_cost(precision: str, path: str = "ale"):
+    """(bytes, flops) of one full cycle per cell."""
+    t = table(precision, path)
+    return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

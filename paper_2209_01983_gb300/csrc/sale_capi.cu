@@ -27,6 +27,8 @@ void launch_init_cells(const Fields<R> &, DevScalars *, const double *, const do
 template <typename R>
 void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t);
+void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
+                     cudaStream_t st);
 }  // namespace sale
 
 using namespace sale;
@@ -166,13 +168,14 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kNodeArrays = 17;  // xr,yr,zr, x(2x3), u(2x3), mn, dke
-constexpr int kCellArrays = 14;  // m,e,sig,rho,p,q,cs,vol, mu(3), ep(3)
+constexpr int kCellArrays = 17;  // m,e,sig,rho,p,q,cs,vol, mu(3), ep(3), dv(3)
+constexpr int kGeoPerCell = 29;  // cached reference geometry: 24 corner gradients, V_E, L_E, 3 face terms
 constexpr int kDiagBlocks = 512;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct Layout {
-  size_t scalars, diag_partial, diag_out, node[kNodeArrays], cell[kCellArrays], total;
+  size_t scalars, diag_partial, diag_out, node[kNodeArrays], cell[kCellArrays], geo, total;
 };
 
 Layout make_layout(long long nc, long long nn, size_t elem) {
@@ -193,6 +196,9 @@ Layout make_layout(long long nc, long long nn, size_t elem) {
     L.cell[a] = off;
     off = align_up(off + elem * (size_t)nc);
   }
+  // one contiguous block: the corner gradients are indexed with stride nc
+  L.geo = off;
+  off = align_up(off + elem * (size_t)kGeoPerCell * (size_t)nc);
   L.total = off;
   return L;
 }
@@ -223,8 +229,11 @@ struct sale_state {
   double *xs[2][3];  // two position buffers
   double *us[2][3];  // two velocity buffers
   double *mn, *dke;
-  double *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3];
+  double *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
+  double *geoG, *geoVE, *geoLE, *geoTE;  // cached reference geometry
   int xpar, upar;
+  bool x_is_ref;       // current positions are the reference mesh
+  int remap_sets_x;    // flag passed to the node remap kernel
   double lim_t_end;
   long long lim_cycles;
   bool failed;
@@ -282,6 +291,14 @@ static Fields<double> fields(const sale_state *st) {
   F.epx = st->ep[0];
   F.epy = st->ep[1];
   F.epz = st->ep[2];
+  F.dvx = st->dv[0];
+  F.dvy = st->dv[1];
+  F.dvz = st->dv[2];
+  F.G = st->geoG;
+  F.VE = st->geoVE;
+  F.LE = st->geoLE;
+  F.TE = st->geoTE;
+  F.remap_sets_x = st->remap_sets_x;
   F.gamma = st->prob.gamma;
   F.cfl = st->prob.cfl;
   F.c_q = st->prob.c_q;
@@ -423,7 +440,14 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
   for (int d = 0; d < 3; ++d) {
     st->mu[d] = ca[8 + d];
     st->ep[d] = ca[11 + d];
+    st->dv[d] = ca[14 + d];
   }
+  st->geoG = (double *)(b + L.geo);
+  st->geoVE = st->geoG + 24 * mesh->nc;
+  st->geoLE = st->geoVE + mesh->nc;
+  st->geoTE = st->geoLE + mesh->nc;
+  st->x_is_ref = true;
+  st->remap_sets_x = 1;
 
   std::vector<double> rho0, p0;
   long long dep_cell;
@@ -454,6 +478,7 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     launch_init_cells(F, st->S, st->p, st->q, dep_cell, dep_e, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
+    launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->stream);
   }
   e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // host vectors die here
@@ -576,12 +601,31 @@ static void launch_remap(sale_state *st) {
   launch_k(st, kRemapCells);
 }
 
+// Eulerian cycle starting on the reference mesh: cached geometry, the
+// Lagrangian positions stay implicit (x_ref + dt ubar), no position writes.
+static void launch_ale_cycle(sale_state *st, double dt_override) {
+  launch_k(st, kAleNodes, 0, dt_override);
+  launch_k(st, kAleCells, 0, dt_override);
+  launch_k(st, kAleDensity);
+  launch_k(st, kAleFluxes);
+  st->remap_sets_x = 0;
+  launch_k(st, kRemapNodes);
+  st->remap_sets_x = 1;
+  st->upar ^= 1;
+  launch_k(st, kAleRemapEos, kDtAdvance, dt_override);
+}
+
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
+  if (remap && st->x_is_ref) {
+    launch_ale_cycle(st, dt_override);
+    return;
+  }
   launch_k(st, kLagNodes, 0, dt_override);
   launch_k(st, kLagCells, 0, dt_override);
   st->xpar ^= 1;
   if (remap) launch_remap(st);
   launch_k(st, kEos, kDtAdvance, dt_override);
+  st->x_is_ref = remap;
 }
 
 extern "C" int sale_lagrange_step(sale_state *st, double dt) {
@@ -589,7 +633,7 @@ extern "C" int sale_lagrange_step(sale_state *st, double dt) {
   if (rc) return rc;
   if (!std::isfinite(dt)) return fail(SALE_EINVAL, "sale_lagrange_step: dt must be finite");
   set_limits(st, INFINITY, 0x7FFFFFFFFFFFFFFFll);
-  launch_cycle(st, false, dt > 0.0 ? dt : 0.0);
+  launch_cycle(st, false, dt > 0.0 ? dt : 0.0);  // leaves x off the reference mesh
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SALE_OK : cuda_fail(e, "sale_lagrange_step");
 }
@@ -599,6 +643,7 @@ extern "C" int sale_remap_step(sale_state *st) {
   if (rc) return rc;
   set_limits(st, INFINITY, 0x7FFFFFFFFFFFFFFFll);
   launch_remap(st);
+  st->x_is_ref = true;
   launch_k(st, kEos, kDtPropose);
   cudaError_t e = cudaGetLastError();
   return e == cudaSuccess ? SALE_OK : cuda_fail(e, "sale_remap_step");
@@ -607,14 +652,20 @@ extern "C" int sale_remap_step(sale_state *st) {
 // Capture `k` cycles (remap after cycle j when (j+1) % remap_every == 0,
 // the first cycle being aligned to the remap cadence) as one graph.
 static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *out) {
-  GraphKey key{k, remap_every, st->xpar, st->upar, st->prof_on ? 1 : 0};
+  GraphKey key{k, remap_every, st->xpar, st->upar, (st->prof_on ? 1 : 0) | (st->x_is_ref ? 2 : 0)};
   auto it = st->graphs.find(key);
   if (it != st->graphs.end()) {
     *out = it->second;
     if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
-    for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles
+    for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles of launch_cycle
+      const bool remap = remap_every > 0 && (j + 1) % remap_every == 0;
+      if (remap && st->x_is_ref) {
+        st->upar ^= 1;
+        continue;
+      }
       st->xpar ^= 1;
-      if (remap_every > 0 && (j + 1) % remap_every == 0) st->upar ^= 1;
+      if (remap) st->upar ^= 1;
+      st->x_is_ref = remap;
     }
     return SALE_OK;
   }
@@ -757,6 +808,7 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
   const size_t want = (size_t)(node ? st->nn : st->nc);
   if (n != want) return fail(SALE_EINVAL, "sale_set_field: '%s' has %zu values, got n = %zu", name, want, n);
   CUDA_TRY(cudaMemcpyAsync(p, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, st->stream));
+  if (!strcmp(name, "x") || !strcmp(name, "y") || !strcmp(name, "z")) st->x_is_ref = false;
   return SALE_OK;
 }
 
@@ -780,8 +832,8 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
 // ---------------------------------------------------------------------------
 
 static const char *const kKernelNames[kNumKernels] = {
-    "init_nodes", "eos_dt", "lagrange_nodes", "lagrange_cells", "remap_faces", "remap_nodes", "remap_cells",
-    "diagnostics"};
+    "init_nodes", "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",   "remap_nodes", "remap_cells",
+    "diagnostics", "ale_nodes", "ale_cells",      "ale_density",    "ale_fluxes", "ale_remap_eos", "geo_init"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

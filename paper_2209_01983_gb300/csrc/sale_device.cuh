@@ -1,0 +1,111 @@
+// sale_device.cuh -- device helpers shared by the kernel translation units
+// of the GB300 SALE library: index maps, hex gathers, wall conditions, warp
+// reductions and the end-of-step dt reduction.
+#pragma once
+
+#include <cmath>
+
+#include "sale_internal.cuh"
+
+namespace sale {
+
+constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
+
+template <typename R>
+__device__ __forceinline__ void load_hex(const R *px, const R *py, const R *pz, int nx, int ny, int i,
+                                         int j, int k, P3 (&X)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_index(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a] = {(double)px[n], (double)py[n], (double)pz[n]};
+  }
+}
+
+__device__ __forceinline__ void cell_ijk(long long c, int nx, int ny, int &i, int &j, int &k) {
+  const long long nxy = (long long)nx * ny;
+  k = (int)(c / nxy);
+  const long long r = c - (long long)k * nxy;
+  j = (int)(r / nx);
+  i = (int)(r - (long long)j * nx);
+}
+
+__device__ __forceinline__ void node_ijk(long long n, int nx, int ny, int &i, int &j, int &k) {
+  const long long sx = nx + 1, sxy = sx * (ny + 1);
+  k = (int)(n / sxy);
+  const long long r = n - (long long)k * sxy;
+  j = (int)(r / sx);
+  i = (int)(r - (long long)j * sx);
+}
+
+template <typename R>
+__device__ __forceinline__ void wall_bc(const Fields<R> &F, int i, int j, int k, double &u, double &v,
+                                        double &w) {
+  if ((i == 0 && F.reflect[0]) || (i == F.nx && F.reflect[1])) u = 0.0;
+  if ((j == 0 && F.reflect[2]) || (j == F.ny && F.reflect[3])) v = 0.0;
+  if ((k == 0 && F.reflect[4]) || (k == F.nz && F.reflect[5])) w = 0.0;
+}
+
+__device__ __forceinline__ double warp_min(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// End of a step: the block's minimum CFL step goes to one atomicMin on the
+// bits of a positive double (order of positive doubles = order of their
+// bits), then the last block to finish sets the next dt (and advances t by
+// the step just taken in kDtAdvance mode).  Every thread of the block must
+// call this; dtc = +inf for threads without a cell.
+template <typename R>
+__device__ __forceinline__ void block_min_dt_and_finalize(const Fields<R> &F, DevScalars *S, double dtc,
+                                                          int mode, double dt_override) {
+  __shared__ double smin[kBlock / 32];
+  __shared__ bool last;
+  dtc = warp_min(dtc);
+  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = dtc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    double v = threadIdx.x < kBlock / 32 ? smin[threadIdx.x] : INFINITY;
+    v = warp_min(v);
+    if (threadIdx.x == 0) {
+      atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong(v));
+      __threadfence();
+      const unsigned int done = atomicAdd(&S->blocks_done, 1u);
+      last = (done == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last || threadIdx.x != 0) return;
+  // Last block: every other block has published its minimum.
+  __threadfence();
+  volatile DevScalars *VS = S;
+  const double dtcfl = __longlong_as_double((long long)atomicAdd(&S->dtmin_bits, 0ull));
+  double dt;
+  if (mode == kDtInit) {
+    dt = dtcfl;
+    if (F.dt_init > 0.0 && F.dt_init < dt) dt = F.dt_init;
+    VS->dt_last = dt;
+  } else {
+    if (mode == kDtAdvance) {
+      const double h = step_dt(S, dt_override);
+      const bool clamp = dt_override <= 0.0 && (VS->t_end - VS->t) < VS->dt;
+      VS->t = clamp ? VS->t_end : VS->t + h;
+      VS->dt_last = h;
+      VS->cycle = VS->cycle + 1;
+    }
+    dt = fmin(dtcfl, F.growth * VS->dt_last);
+  }
+  if (!(dt > 0.0) || dt == INFINITY) set_status(S, SALE_EDT);
+  else VS->dt = dt;
+  VS->dtmin_bits = kInfBits;
+  VS->blocks_done = 0;
+  __threadfence();
+}
+
+}  // namespace sale

@@ -47,6 +47,12 @@ enum KernelId : int {
   kRemapNodes,
   kRemapCells,
   kDiag,
+  kAleNodes,     // ALE path (positions start each cycle on the reference mesh)
+  kAleCells,
+  kAleDensity,
+  kAleFluxes,
+  kAleRemapEos,
+  kGeoInit,
   kNumKernels
 };
 
@@ -74,8 +80,14 @@ struct Fields {
   R *rho, *p, *q, *cs, *vol;   // derived cell fields
   R *mux, *muy, *muz;          // mass flux through the low x/y/z face
   R *epx, *epy, *epz;          // internal-energy flux through those faces
+  // Cached reference-mesh geometry (ALE path): dV/dx of every cell corner,
+  // G[(corner*3 + axis) * nc + c], reference volume and length scale.
+  const R *G, *VE, *LE;
+  const R *TE;                 // reference-face terms of the low-face swept hexes (3 per cell)
+  R *dvx, *dvy, *dvz;          // swept volumes of the low x/y/z faces
   double gamma, cfl, c_q, c_l, growth, dt_init;
   int ke_fix;
+  int remap_sets_x;            // node remap writes the reference positions to x
   int reflect[6];
 };
 

@@ -19,62 +19,12 @@
 //                     double, last block finalises time and dt)
 #include <cfloat>
 #include <cmath>
+#include <type_traits>
 
-#include "sale_internal.cuh"
+#include "sale_device.cuh"
 
 namespace sale {
 
-namespace {
-
-constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
-
-template <typename R>
-__device__ __forceinline__ void load_hex(const R *px, const R *py, const R *pz, int nx, int ny, int i,
-                                         int j, int k, P3 (&X)[8]) {
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    const long long n = node_index(nx, ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-    X[a] = {(double)px[n], (double)py[n], (double)pz[n]};
-  }
-}
-
-__device__ __forceinline__ void cell_ijk(long long c, int nx, int ny, int &i, int &j, int &k) {
-  const long long nxy = (long long)nx * ny;
-  k = (int)(c / nxy);
-  const long long r = c - (long long)k * nxy;
-  j = (int)(r / nx);
-  i = (int)(r - (long long)j * nx);
-}
-
-__device__ __forceinline__ void node_ijk(long long n, int nx, int ny, int &i, int &j, int &k) {
-  const long long sx = nx + 1, sxy = sx * (ny + 1);
-  k = (int)(n / sxy);
-  const long long r = n - (long long)k * sxy;
-  j = (int)(r / sx);
-  i = (int)(r - (long long)j * sx);
-}
-
-template <typename R>
-__device__ __forceinline__ void wall_bc(const Fields<R> &F, int i, int j, int k, double &u, double &v,
-                                        double &w) {
-  if ((i == 0 && F.reflect[0]) || (i == F.nx && F.reflect[1])) u = 0.0;
-  if ((j == 0 && F.reflect[2]) || (j == F.ny && F.reflect[3])) v = 0.0;
-  if ((k == 0 && F.reflect[4]) || (k == F.nz && F.reflect[5])) w = 0.0;
-}
-
-__device__ __forceinline__ double warp_min(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v = fmin(v, __shfl_xor_sync(0xffffffffu, v, o));
-  return v;
-}
-
-__device__ __forceinline__ double warp_sum(double v) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  return v;
-}
-
-}  // namespace
 
 // ---------------------------------------------------------------------------
 // Initialisation
@@ -182,47 +132,7 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
       dtc = INFINITY;
     }
   }
-  __shared__ double smin[kBlock / 32];
-  __shared__ bool last;
-  dtc = warp_min(dtc);
-  if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = dtc;
-  __syncthreads();
-  if (threadIdx.x < 32) {
-    double v = threadIdx.x < kBlock / 32 ? smin[threadIdx.x] : INFINITY;
-    v = warp_min(v);
-    if (threadIdx.x == 0) {
-      atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong(v));
-      __threadfence();
-      const unsigned int done = atomicAdd(&S->blocks_done, 1u);
-      last = (done == gridDim.x - 1);
-    }
-  }
-  __syncthreads();
-  if (!last || threadIdx.x != 0) return;
-  // Last block: every other block has published its minimum.
-  __threadfence();
-  volatile DevScalars *VS = S;
-  const double dtcfl = __longlong_as_double((long long)atomicAdd(&S->dtmin_bits, 0ull));
-  double dt;
-  if (mode == kDtInit) {
-    dt = dtcfl;
-    if (F.dt_init > 0.0 && F.dt_init < dt) dt = F.dt_init;
-    VS->dt_last = dt;
-  } else {
-    if (mode == kDtAdvance) {
-      const double h = step_dt(S, dt_override);
-      const bool clamp = dt_override <= 0.0 && (VS->t_end - VS->t) < VS->dt;
-      VS->t = clamp ? VS->t_end : VS->t + h;
-      VS->dt_last = h;
-      VS->cycle = VS->cycle + 1;
-    }
-    dt = fmin(dtcfl, F.growth * VS->dt_last);
-  }
-  if (!(dt > 0.0) || dt == INFINITY) set_status(S, SALE_EDT);
-  else VS->dt = dt;
-  VS->dtmin_bits = kInfBits;
-  VS->blocks_done = 0;
-  __threadfence();
+  block_min_dt_and_finalize(F, S, dtc, mode, dt_override);
 }
 
 // ---------------------------------------------------------------------------
@@ -378,7 +288,7 @@ __device__ __forceinline__ double edge_psi(const Fields<R> &F, int i, int j, int
     const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
     const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
     const double hi = hi_idx < n_ax ? (double)mu[c + stride] : 0.0;
-    psi += (lo + hi) / 8.0;
+    psi += (lo + hi) * 0.125;
   }
   return psi;
 }
@@ -433,16 +343,19 @@ __global__ void __launch_bounds__(kBlock) k_remap_nodes(Fields<R> F, DevScalars 
   node_edge<2, 0>(F, i, j, k, n, m, p, ke);
   node_edge<2, 1>(F, i, j, k, n, m, p, ke);
   if (!(m > 0.0)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
-  double u1 = p.x / m, v1 = p.y / m, w1 = p.z / m;
+  const double inv_m = 1.0 / m;
+  double u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
   wall_bc(F, i, j, k, u1, v1, w1);
   F.ub[n] = (R)u1;
   F.vb[n] = (R)v1;
   F.wb[n] = (R)w1;
   F.mn[n] = (R)m;
   F.dke[n] = (R)(ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1));
-  F.x[n] = (R)F.xr[n];
-  F.y[n] = (R)F.yr[n];
-  F.z[n] = (R)F.zr[n];
+  if (F.remap_sets_x) {
+    F.x[n] = (R)F.xr[n];
+    F.y[n] = (R)F.yr[n];
+    F.z[n] = (R)F.zr[n];
+  }
 }
 
 template <typename R>
@@ -544,9 +457,15 @@ void launch_init_cells(const Fields<R> &F, DevScalars *S, const double *rho0, co
   k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e);
 }
 
+void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double dt_override, cudaStream_t st);
+
 template <typename R>
 void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t st) {
+  if (kid >= kAleNodes && kid <= kAleRemapEos) {
+    if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
+    return;
+  }
   switch (kid) {
     case kInitNodes: k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F); break;
     case kEos: k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override); break;

@@ -119,6 +119,7 @@ extern "C" int sale_remap_static(int nx, int ny, int nz, const int *reflect, int
   F.epz = flux + 5 * kMaxCells;
   F.dke = flux + 6 * kMaxCells;
   F.ke_fix = ke_fix ? 1 : 0;
+  F.remap_sets_x = 1;  // x leaves holding the reference positions
   for (int f = 0; f < 6; ++f) F.reflect[f] = reflect[f];
 
   // The status block starts from zero on every call (a previous call's
