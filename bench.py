@@ -41,7 +41,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
-    ap.add_argument("--precision", default="fp64", choices=("fp64",))
+    ap.add_argument("--precision", default="both", choices=("fp64", "fp32_mixed", "both"))
     ap.add_argument("--n", type=int, default=384, help="cells per axis")
     ap.add_argument("--jitter", type=float, default=0.1)
     ap.add_argument("--no-e2e", action="store_true")
@@ -165,28 +165,19 @@ def workload_config(args, precision):
 # GPU arm
 # ---------------------------------------------------------------------------
 
-def gpu_arm(args):
-    import numpy as np
+# FP32 vector peak: 128 lanes x 2 flop x 152 SMs x 2.07 GHz.
+FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
+
+
+def measure(args, precision, local, barrier):
+    """Time K full cycles of one precision; returns the numbers for the line."""
     import torch
 
     from paper_2209_01983_gb300 import costs, inputs, sale
 
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    dist = None
-    if world > 1:
-        import torch.distributed as dist
-        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
-
-    def barrier():
-        if dist is not None:
-            dist.barrier()
-
-    precision = args.precision
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
-    st = sale.State(md, pd, precision=sale.SALE_FP64, device=f"cuda:{local}")
+    code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
+    st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     st.run_to_time(max_cycles=args.warmup, remap_every=1)
 
     # ---- timed region: K full cycles, graph replays on the state's stream
@@ -211,72 +202,118 @@ def gpu_arm(args):
     if done != args.steps:
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
-    d = st.diagnostics()
 
-    t_max = ms
-    if dist is not None:
-        t = torch.tensor([ms], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_max = float(t.item())
-    value = world * md.ncell * args.steps / (t_max * 1e-3)
-
-    # ---- roofline of the dominant kernel
     table = costs.table(precision, "ale")
     kern = {k: v for k, v in prof.items() if v[1] > 0}
-    total_ms = sum(v[0] for v in kern.values())
     missing = [k for k in kern if k not in table]
     if missing:
         raise RuntimeError(f"no cost entry for kernels {missing}")
-    top = max(kern, key=lambda k: kern[k][0])
-    unit, bytes_u, flops_u = table[top]
-    units = md.ncell if unit == "cell" else md.nnode
-    avg_s = kern[top][0] / kern[top][1] * 1e-3
+    total_ms = sum(v[0] for v in kern.values())
     peaks, peak_src = load_peaks()
-    if precision == "fp64":
-        achieved = flops_u * units / avg_s / 1e12
-        roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                "frac": achieved / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top,
-                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 vector pipe)",
-                "hbm_achieved_gbs": bytes_u * units / avg_s / 1e9,
-                "hbm_frac_of_measured": bytes_u * units / avg_s / 1e9 / peaks["hbm_gbs"]}
+
+    def units(k):
+        return md.ncell if table[k][0] == "cell" else md.nnode
+
     def per_kernel(k, v):
-        u_, b_, f_ = table[k]
-        nunit = md.ncell if u_ == "cell" else md.nnode
         sec = v[0] / v[1] * 1e-3
         return {"ms_per_launch": v[0] / v[1], "launches": v[1], "share": v[0] / total_ms,
-                "alg_gbs": b_ * nunit / sec / 1e9, "alg_tflops": f_ * nunit / sec / 1e12}
-    kernels = {k: per_kernel(k, v) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
-    launches = sum(v[1] for v in kern.values())
-    cycle_bytes = sum(table[k][1] * (md.ncell if table[k][0] == "cell" else md.nnode) for k in kern)
-    cycle_flops = sum(table[k][2] * (md.ncell if table[k][0] == "cell" else md.nnode) for k in kern)
-    full = {"cycle_algorithmic_bytes": cycle_bytes, "cycle_algorithmic_flops": cycle_flops,
-            "cycle_tflops": cycle_flops * args.steps / (ms * 1e-3) / 1e12,
-            "cycle_hbm_gbs": cycle_bytes * args.steps / (ms * 1e-3) / 1e9,
-            "cycle_hbm_frac_of_measured": cycle_bytes * args.steps / (ms * 1e-3) / 1e9 / peaks["hbm_gbs"]}
+                "alg_gbs": table[k][1] * units(k) / sec / 1e9,
+                "alg_tflops": table[k][2] * units(k) / sec / 1e12}
 
-    # ---- end to end through the C ABI with host buffers
-    e2e = None
-    if not args.no_e2e:
-        names = ("u", "v", "w", "mn", "m", "e")
-        host = {nm: torch.from_numpy(st.field(nm)).pin_memory() for nm in names}
-        h2d = sum(t.numel() * 8 for t in host.values())
-        d2h = 8 * 8 + 128  # diagnostics sums + device scalars
-        e2e_steps = max(1, min(args.steps, 5))
-        dd = sale.sale_diag()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            for nm, t in host.items():
-                sale.check(sale.sale_set_field(st._h, nm.encode(),
-                                               sale.C.cast(t.data_ptr(), sale._dp), t.numel()))
-            sale.check(sale.sale_refresh(st._h))
-            sale.check(sale.sale_run_to_time(st._h, math.inf, 1, 1, None))
-            sale.check(sale.sale_diagnostics(st._h, sale.C.byref(dd)))
-        e2e_s = time.perf_counter() - t0
-        e2e = {"value": world * md.ncell * e2e_steps / e2e_s, "unit": UNIT,
-               "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h, "steps": e2e_steps}
+    kernels = {k: per_kernel(k, v) for k, v in sorted(kern.items(), key=lambda kv: -kv[1][0])}
+    top = next(iter(kernels))
+    kt = kernels[top]
+    if precision == "fp64":
+        roof = {"bound": "alu", "achieved": kt["alg_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                "frac": kt["alg_tflops"] / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top,
+                "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 vector pipe)",
+                "hbm_achieved_gbs": kt["alg_gbs"], "hbm_frac_of_measured": kt["alg_gbs"] / peaks["hbm_gbs"]}
+    else:
+        roof = {"bound": "hbm", "achieved": kt["alg_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": kt["alg_gbs"] / peaks["hbm_gbs"], "traffic": None, "kernel": top,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
+                "fp32_tflops": kt["alg_tflops"], "fp32_frac_of_derived": kt["alg_tflops"] / FP32_PEAK_TFLOPS}
+    cycle_bytes = sum(table[k][1] * units(k) for k in kern)
+    cycle_flops = sum(table[k][2] * units(k) for k in kern)
+    secs = ms * 1e-3
+    full = {"cycle_algorithmic_bytes": cycle_bytes, "cycle_algorithmic_flops": cycle_flops,
+            "cycle_tflops": cycle_flops * args.steps / secs / 1e12,
+            "cycle_hbm_gbs": cycle_bytes * args.steps / secs / 1e9,
+            "cycle_hbm_frac_of_measured": cycle_bytes * args.steps / secs / 1e9 / peaks["hbm_gbs"]}
+    launches = sum(v[1] for v in kern.values())
+    d = st.diagnostics()
+    return {"st": st, "md": md, "ms": ms, "roofline": roof, "kernels": kernels, "full_cycle": full,
+            "gpu_launches": launches, "clocks": clk, "check": {"t": d["t"], "cycle": d["cycle"], "status": d["status"]},
+            "peaks": {"hbm_gbs": peaks["hbm_gbs"], "source": peak_src}}
+
+
+def e2e_rate(args, res, world):
+    """The same cycle end to end through the C ABI: every step uploads the
+    evolving fields from pinned host memory (sale_set_field), refreshes, runs
+    one cycle and reads the diagnostics back."""
+    import torch
+
+    from paper_2209_01983_gb300 import sale
+
+    st, md = res["st"], res["md"]
+    names = ("u", "v", "w", "mn", "m", "e")
+    host = {nm: torch.from_numpy(st.field(nm)).pin_memory() for nm in names}
+    h2d = sum(t.numel() * 8 for t in host.values())
+    d2h = 8 * 6 + 128  # diagnostics sums + device scalars
+    steps = max(1, min(args.steps, 5))
+    dd = sale.sale_diag()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        for nm, t in host.items():
+            sale.check(sale.sale_set_field(st._h, nm.encode(), sale.C.cast(t.data_ptr(), sale._dp), t.numel()))
+        sale.check(sale.sale_refresh(st._h))
+        sale.check(sale.sale_run_to_time(st._h, math.inf, 1, 1, None))
+        sale.check(sale.sale_diagnostics(st._h, sale.C.byref(dd)))
+    secs = time.perf_counter() - t0
+    return {"value": world * md.ncell * steps / secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "steps": steps}
+
+
+def gpu_arm(args):
+    import torch
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def max_over_ranks(v):
+        if dist is None:
+            return v
+        t = torch.tensor([v], device=f"cuda:{local}")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    precisions = ["fp64", "fp32_mixed"] if args.precision == "both" else [args.precision]
+    results = {}
+    for prec in precisions:
+        res = measure(args, prec, local, barrier)
+        res["ms_max"] = max_over_ranks(res["ms"])
+        res["value"] = world * res["md"].ncell * args.steps / (res["ms_max"] * 1e-3)
+        if not args.no_e2e and prec == precisions[0]:
+            res["e2e"] = e2e_rate(args, res, world)
+        res["st"].close()
+        del res["st"]
+        torch.cuda.empty_cache()
+        results[prec] = res
 
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return 0
     cpu = None
     if not args.no_cpu_baseline:
@@ -285,16 +322,28 @@ def gpu_arm(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"same workload at {n}^3 ({ncell} cells), 40 cycles after 5, "
                          f"serial FP64 C oracle, {secs:.1f} s"}
+    main_p = precisions[0]
+    r = results[main_p]
+    dtypes = {"fp64": "f64", "fp32_mixed": "f32 (f64 islands)"}
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": t_max / args.steps, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-        "config": workload_config(args, precision),
-        "roofline": roof, "full_cycle": full, "cpu_baseline": cpu, "e2e": e2e,
-        "gpu_launches": launches, "clocks": clk, "kernels": kernels,
-        "check": {"t": d["t"], "cycle": d["cycle"], "status": d["status"]},
-        "peaks": {"hbm_gbs": peaks["hbm_gbs"], "source": peak_src},
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["ms_max"] / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": dtypes[main_p], "data": "synthetic",
+        "config": workload_config(args, main_p),
+        "roofline": r["roofline"], "full_cycle": r["full_cycle"], "cpu_baseline": cpu,
+        "e2e": r.get("e2e"), "gpu_launches": sum(x["gpu_launches"] for x in results.values()),
+        "clocks": r["clocks"], "kernels": r["kernels"], "check": r["check"], "peaks": r["peaks"],
     }
+    variants = {}
+    for prec, x in results.items():
+        if prec == main_p:
+            continue
+        variants[prec] = {"value": x["value"], "ms_per_step": x["ms_max"] / args.steps, "dtype": dtypes[prec],
+                          "speedup_vs_" + main_p: x["value"] / r["value"], "roofline": x["roofline"],
+                          "full_cycle": x["full_cycle"], "kernels": x["kernels"], "clocks": x["clocks"],
+                          "gpu_launches": x["gpu_launches"], "check": x["check"]}
+    if variants:
+        line["variants"] = variants
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()

@@ -53,9 +53,31 @@ FP64_ALE = {
 }
 
 
+# FP32-mixed Eulerian cycle: 4-byte fields, reference geometry recomputed
+# from the structured mesh + FP32 jitter offsets (12 bytes per node), V_E and
+# L_E stored.  Flops are FP32 (the FP64 islands are a few per cell).
+GRAD32 = GRAD + 42      # gradient + relative coordinates of the 8 nodes
+FORCE32 = 12 * 27 + 108 + 20  # 12 face terms + 18 relative node positions + update
+SWEPT32 = 6 * 30 + 3 * 12 + 3 * 60 + 24  # expanded side/pair terms + displacements
+MIXED_ALE = {
+    # offsets, sigma, u, mn read; u, ubar written
+    "mix_nodes": ("node", 4 * (3 + 1 + 3 + 1 + 3 + 3), FORCE32),
+    # offsets, ubar, sigma, m, e read; e, 3 swept volumes written
+    "mix_cells": ("cell", 4 * (3 + 3 + 3 + 1 + 3), GRAD32 + 40 + 6 + SWEPT32),
+    # swept volumes, V_E, m, e read; 3 mass + 3 energy fluxes written
+    "mix_fluxes": ("cell", 4 * (3 + 3 + 6), 30),
+    # 3 mass fluxes, u, mn read; u', mn', dKE written
+    "mix_remap_nodes": ("node", 4 * (3 + 3 + 1 + 3 + 1 + 1), 125),
+    # 6 fluxes, m, e, dKE, u', offsets, V_E, L_E read; m, e, rho, sigma written
+    "mix_remap_eos": ("cell", 4 * (6 + 2 + 1 + 3 + 3 + 2 + 4), 40 + GRAD32 + 40 + 30),
+}
+
+
 def table(precision: str, path: str = "ale"):
     if precision == "fp64":
         return FP64_ALE if path == "ale" else FP64
+    if precision == "fp32_mixed":
+        return MIXED_ALE
     raise KeyError(precision)
 
 

@@ -29,6 +29,9 @@ void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt
                    double *out, cudaStream_t);
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      cudaStream_t st);
+void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
+                         long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st);
+void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st);
 }  // namespace sale
 
 using namespace sale;
@@ -160,6 +163,7 @@ extern "C" int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n) {
   return SALE_OK;
 }
 
+
 // ---------------------------------------------------------------------------
 // State layout
 // ---------------------------------------------------------------------------
@@ -167,48 +171,29 @@ extern "C" int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n) {
 namespace {
 
 constexpr size_t kAlign = 256;
-constexpr int kNodeArrays = 17;  // xr,yr,zr, x(2x3), u(2x3), mn, dke
-constexpr int kCellArrays = 17;  // m,e,sig,rho,p,q,cs,vol, mu(3), ep(3), dv(3)
-constexpr int kGeoPerCell = 29;  // cached reference geometry: 24 corner gradients, V_E, L_E, 3 face terms
 constexpr int kDiagBlocks = 512;
 
 size_t align_up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
-struct Layout {
-  size_t scalars, diag_partial, diag_out, node[kNodeArrays], cell[kCellArrays], geo, total;
-};
-
-Layout make_layout(long long nc, long long nn, size_t elem) {
-  Layout L;
+// Hands out 256-byte aligned pieces of one buffer (or, with base == null,
+// only counts the bytes: the same code sizes and carves a state).
+struct Carver {
+  char *base;
   size_t off = 0;
-  L.scalars = off;
-  off = align_up(off + sizeof(DevScalars));
-  L.diag_partial = off;
-  off = align_up(off + sizeof(double) * 6 * kDiagBlocks);
-  L.diag_out = off;
-  off = align_up(off + sizeof(double) * 8);
-  for (int a = 0; a < kNodeArrays; ++a) {
-    L.node[a] = off;
-    // the reference mesh is FP64 in every precision
-    off = align_up(off + (a < 3 ? sizeof(double) : elem) * (size_t)nn);
+  void *take(size_t bytes) {
+    off = align_up(off);
+    void *p = base ? base + off : nullptr;
+    off += bytes;
+    return p;
   }
-  for (int a = 0; a < kCellArrays; ++a) {
-    L.cell[a] = off;
-    off = align_up(off + elem * (size_t)nc);
-  }
-  // one contiguous block: the corner gradients are indexed with stride nc
-  L.geo = off;
-  off = align_up(off + elem * (size_t)kGeoPerCell * (size_t)nc);
-  L.total = off;
-  return L;
-}
+};
 
 }  // namespace
 
 struct GraphKey {
-  int k, remap_every, xpar, upar, prof;
+  int k, remap_every, xpar, upar, flags;
   bool operator<(const GraphKey &o) const {
-    return std::tie(k, remap_every, xpar, upar, prof) < std::tie(o.k, o.remap_every, o.xpar, o.upar, o.prof);
+    return std::tie(k, remap_every, xpar, upar, flags) < std::tie(o.k, o.remap_every, o.xpar, o.upar, o.flags);
   }
 };
 
@@ -220,17 +205,20 @@ struct ProfEvent {
 struct sale_state {
   int nx, ny, nz;
   long long nc, nn;
-  int precision;
+  int precision;       // SALE_FP64 or SALE_FP32_MIXED
+  size_t elem;         // bytes of one stored value
   cudaStream_t stream;
-  char *base;
   DevScalars *S;
   double *diag_partial, *diag_out;
-  double *xr[3];
-  double *xs[2][3];  // two position buffers
-  double *us[2][3];  // two velocity buffers
-  double *mn, *dke;
-  double *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
-  double *geoG, *geoVE, *geoLE, *geoTE;  // cached reference geometry
+  double *xr[3];       // reference mesh, FP64 in every precision
+  void *xs[2][3];      // two position buffers (FP64 path)
+  void *us[2][3];      // two velocity buffers
+  void *mn, *dke;
+  void *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
+  double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
+  float4 *off4;                          // FP32-mixed path: jitter offsets
+  float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
+  float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
   int remap_sets_x;    // flag passed to the node remap kernel
@@ -253,8 +241,51 @@ struct sale_state {
   long long prof_n[kNumKernels] = {};
 };
 
-static Fields<double> fields(const sale_state *st) {
-  Fields<double> F;
+// Carve (or, with base == null, size) the device fields of a state.
+static size_t carve(sale_state *st, char *base) {
+  Carver cv{base};
+  const size_t E = st->elem, nn = (size_t)st->nn, nc = (size_t)st->nc;
+  const bool fp64 = st->precision == SALE_FP64;
+  st->S = (DevScalars *)cv.take(sizeof(DevScalars));
+  st->diag_partial = (double *)cv.take(sizeof(double) * 6 * kDiagBlocks);
+  st->diag_out = (double *)cv.take(sizeof(double) * 8);
+  for (int d = 0; d < 3; ++d) st->xr[d] = (double *)cv.take(sizeof(double) * nn);
+  for (int b = 0; b < 2; ++b)
+    for (int d = 0; d < 3; ++d) {
+      st->xs[b][d] = fp64 ? cv.take(E * nn) : nullptr;  // the mixed path keeps positions implicit
+      st->us[b][d] = cv.take(E * nn);
+    }
+  st->mn = cv.take(E * nn);
+  st->dke = cv.take(E * nn);
+  void **cells[] = {&st->m, &st->e, &st->sig, &st->rho, &st->p, &st->q, &st->cs, &st->vol};
+  for (void **c : cells) *c = cv.take(E * nc);
+  for (int d = 0; d < 3; ++d) {
+    st->mu[d] = cv.take(E * nc);
+    st->ep[d] = cv.take(E * nc);
+    st->dv[d] = cv.take(E * nc);
+  }
+  st->geoG = st->geoVE = st->geoLE = st->geoTE = nullptr;
+  st->off4 = nullptr;
+  st->VE32 = st->LE32 = nullptr;
+  if (fp64) {
+    // one block, the corner gradients indexed with stride nc
+    st->geoG = (double *)cv.take(sizeof(double) * 29 * nc);
+    if (base) {
+      st->geoVE = st->geoG + 24 * nc;
+      st->geoLE = st->geoVE + nc;
+      st->geoTE = st->geoLE + nc;
+    }
+  } else {
+    st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
+    st->VE32 = (float *)cv.take(sizeof(float) * nc);
+    st->LE32 = (float *)cv.take(sizeof(float) * nc);
+  }
+  return align_up(cv.off);
+}
+
+template <typename R>
+static Fields<R> fields_t(const sale_state *st) {
+  Fields<R> F = {};
   F.nx = st->nx;
   F.ny = st->ny;
   F.nz = st->nz;
@@ -263,41 +294,50 @@ static Fields<double> fields(const sale_state *st) {
   F.xr = st->xr[0];
   F.yr = st->xr[1];
   F.zr = st->xr[2];
-  F.x = st->xs[st->xpar][0];
-  F.y = st->xs[st->xpar][1];
-  F.z = st->xs[st->xpar][2];
-  F.xn = st->xs[st->xpar ^ 1][0];
-  F.yn = st->xs[st->xpar ^ 1][1];
-  F.zn = st->xs[st->xpar ^ 1][2];
-  F.u = st->us[st->upar][0];
-  F.v = st->us[st->upar][1];
-  F.w = st->us[st->upar][2];
-  F.ub = st->us[st->upar ^ 1][0];
-  F.vb = st->us[st->upar ^ 1][1];
-  F.wb = st->us[st->upar ^ 1][2];
-  F.mn = st->mn;
-  F.dke = st->dke;
-  F.m = st->m;
-  F.e = st->e;
-  F.sig = st->sig;
-  F.rho = st->rho;
-  F.p = st->p;
-  F.q = st->q;
-  F.cs = st->cs;
-  F.vol = st->vol;
-  F.mux = st->mu[0];
-  F.muy = st->mu[1];
-  F.muz = st->mu[2];
-  F.epx = st->ep[0];
-  F.epy = st->ep[1];
-  F.epz = st->ep[2];
-  F.dvx = st->dv[0];
-  F.dvy = st->dv[1];
-  F.dvz = st->dv[2];
-  F.G = st->geoG;
-  F.VE = st->geoVE;
-  F.LE = st->geoLE;
-  F.TE = st->geoTE;
+  F.x = (R *)st->xs[st->xpar][0];
+  F.y = (R *)st->xs[st->xpar][1];
+  F.z = (R *)st->xs[st->xpar][2];
+  F.xn = (R *)st->xs[st->xpar ^ 1][0];
+  F.yn = (R *)st->xs[st->xpar ^ 1][1];
+  F.zn = (R *)st->xs[st->xpar ^ 1][2];
+  F.u = (R *)st->us[st->upar][0];
+  F.v = (R *)st->us[st->upar][1];
+  F.w = (R *)st->us[st->upar][2];
+  F.ub = (R *)st->us[st->upar ^ 1][0];
+  F.vb = (R *)st->us[st->upar ^ 1][1];
+  F.wb = (R *)st->us[st->upar ^ 1][2];
+  F.mn = (R *)st->mn;
+  F.dke = (R *)st->dke;
+  F.m = (R *)st->m;
+  F.e = (R *)st->e;
+  F.sig = (R *)st->sig;
+  F.rho = (R *)st->rho;
+  F.p = (R *)st->p;
+  F.q = (R *)st->q;
+  F.cs = (R *)st->cs;
+  F.vol = (R *)st->vol;
+  F.mux = (R *)st->mu[0];
+  F.muy = (R *)st->mu[1];
+  F.muz = (R *)st->mu[2];
+  F.epx = (R *)st->ep[0];
+  F.epy = (R *)st->ep[1];
+  F.epz = (R *)st->ep[2];
+  F.dvx = (R *)st->dv[0];
+  F.dvy = (R *)st->dv[1];
+  F.dvz = (R *)st->dv[2];
+  if (st->precision == SALE_FP64) {
+    F.G = (const R *)st->geoG;
+    F.VE = (const R *)st->geoVE;
+    F.LE = (const R *)st->geoLE;
+    F.TE = (const R *)st->geoTE;
+  } else {
+    F.VE = (const R *)st->VE32;
+    F.LE = (const R *)st->LE32;
+  }
+  F.hx = st->h32[0];
+  F.hy = st->h32[1];
+  F.hz = st->h32[2];
+  F.off4 = st->off4;
   F.remap_sets_x = st->remap_sets_x;
   F.gamma = st->prob.gamma;
   F.cfl = st->prob.cfl;
@@ -305,14 +345,27 @@ static Fields<double> fields(const sale_state *st) {
   F.c_l = st->prob.c_l;
   F.growth = st->prob.dt_growth;
   F.dt_init = std::isfinite(st->prob.dt_init) ? st->prob.dt_init : 0.0;
+  F.gamma32 = (float)F.gamma;
+  F.cfl32 = (float)F.cfl;
+  F.c_q32 = (float)F.c_q;
+  F.c_l32 = (float)F.c_l;
   F.ke_fix = st->prob.ke_fix;
   for (int f = 0; f < 6; ++f) F.reflect[f] = st->reflect[f];
   return F;
 }
 
+static size_t state_bytes(long long nc, long long nn, int precision) {
+  sale_state tmp;
+  tmp.nc = nc;
+  tmp.nn = nn;
+  tmp.precision = precision;
+  tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
+  return carve(&tmp, nullptr);
+}
+
 extern "C" size_t sale_state_bytes(const sale_mesh *mesh, int precision) {
-  if (!mesh || precision != SALE_FP64) return 0;
-  return make_layout(mesh->nc, mesh->nn, sizeof(double)).total;
+  if (!mesh || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
+  return state_bytes(mesh->nc, mesh->nn, precision);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -379,17 +432,92 @@ static int check_device_status(sale_state *st, const DevScalars &h) {
   return SALE_OK;
 }
 
+// ---------------------------------------------------------------------------
+// Launch with optional profiling events
+// ---------------------------------------------------------------------------
+
+static cudaEvent_t take_event(sale_state *st) {
+  if (!st->ev_pool.empty()) {
+    cudaEvent_t e = st->ev_pool.back();
+    st->ev_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// During stream capture an event record becomes a graph node only with
+// cudaEventRecordExternal (a plain record is a capture-internal join point).
+static void record(sale_state *st, cudaEvent_t ev) {
+  if (st->capturing) cudaEventRecordWithFlags(ev, st->stream, cudaEventRecordExternal);
+  else cudaEventRecord(ev, st->stream);
+}
+
+static void dispatch(sale_state *st, int kid, int mode, double dt_override) {
+  if (st->precision == SALE_FP64) {
+    launch_kernel(kid, fields_t<double>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
+  } else if (kid >= kMixNodes && kid <= kMixEos) {
+    launch_m_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->stream);
+  } else {
+    launch_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
+  }
+}
+
+static void launch_k(sale_state *st, int kid, int mode = 0, double dt_override = 0.0) {
+  cudaEvent_t a = nullptr;
+  if (st->prof_on) {
+    a = take_event(st);
+    record(st, a);
+  }
+  dispatch(st, kid, mode, dt_override);
+  if (st->prof_on) {
+    cudaEvent_t b = take_event(st);
+    record(st, b);
+    (st->capturing ? st->capture_events : st->pending).push_back({kid, a, b});
+  }
+}
+
+// Accumulate the profile of launches that completed (stream synchronised).
+static void collect_profile(sale_state *st) {
+  for (auto &pe : st->pending) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+      st->prof_ms[pe.kid] += ms;
+      st->prof_n[pe.kid] += 1;
+    }
+    st->ev_pool.push_back(pe.a);
+    st->ev_pool.push_back(pe.b);
+  }
+  st->pending.clear();
+  for (auto *list : st->pending_graphs)
+    for (auto &pe : *list) {
+      float ms = 0.f;
+      if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
+        st->prof_ms[pe.kid] += ms;
+        st->prof_n[pe.kid] += 1;
+      }
+    }
+  st->pending_graphs.clear();
+  cudaGetLastError();  // a never-recorded event is not an error of the state
+}
+
+// ---------------------------------------------------------------------------
+// Initialisation
+// ---------------------------------------------------------------------------
+
 extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *prob, int precision,
                                void *device_buf, size_t bytes, void *cuda_stream, sale_state **out) {
   if (!mesh || !prob || !out) return fail(SALE_EINVAL, "sale_state_init: null argument");
   *out = nullptr;
-  if (precision != SALE_FP64) return fail(SALE_EINVAL, "sale_state_init: precision %d not supported", precision);
+  if (precision != SALE_FP64 && precision != SALE_FP32_MIXED)
+    return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
-  const Layout L = make_layout(mesh->nc, mesh->nn, sizeof(double));
+  const size_t need = state_bytes(mesh->nc, mesh->nn, precision);
   if (!device_buf) return fail(SALE_EINVAL, "sale_state_init: null device buffer");
   if ((uintptr_t)device_buf % kAlign) return fail(SALE_EINVAL, "sale_state_init: device buffer must be 256-byte aligned");
-  if (bytes < L.total) return fail(SALE_ENOMEM, "sale_state_init: buffer has %zu bytes, need %zu", bytes, L.total);
+  if (bytes < need) return fail(SALE_ENOMEM, "sale_state_init: buffer has %zu bytes, need %zu", bytes, need);
   cudaPointerAttributes attr;
   CUDA_TRY(cudaPointerGetAttributes(&attr, device_buf));
   if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
@@ -403,57 +531,44 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
   st->nc = mesh->nc;
   st->nn = mesh->nn;
   st->precision = precision;
+  st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
   for (int f = 0; f < 6; ++f) st->reflect[f] = mesh->d.reflect[f];
+  for (int a = 0; a < 3; ++a) {
+    const int n = a == 0 ? mesh->d.nx : a == 1 ? mesh->d.ny : mesh->d.nz;
+    st->h32[a] = (float)((mesh->d.hi[a] - mesh->d.lo[a]) / n);
+  }
   st->xpar = st->upar = 0;
+  st->x_is_ref = true;
+  st->remap_sets_x = 1;
   st->lim_t_end = INFINITY;
   st->lim_cycles = 0x7FFFFFFFFFFFFFFFll;
   st->failed = false;
   st->fail_code = 0;
-  char *b = (char *)device_buf;
-  st->base = b;
-  st->S = (DevScalars *)(b + L.scalars);
-  st->diag_partial = (double *)(b + L.diag_partial);
-  st->diag_out = (double *)(b + L.diag_out);
-  double *na[kNodeArrays];
-  for (int a = 0; a < kNodeArrays; ++a) na[a] = (double *)(b + L.node[a]);
-  double *ca[kCellArrays];
-  for (int a = 0; a < kCellArrays; ++a) ca[a] = (double *)(b + L.cell[a]);
-  for (int d = 0; d < 3; ++d) {
-    st->xr[d] = na[d];
-    st->xs[0][d] = na[3 + d];
-    st->xs[1][d] = na[6 + d];
-    st->us[0][d] = na[9 + d];
-    st->us[1][d] = na[12 + d];
-  }
-  st->mn = na[15];
-  st->dke = na[16];
-  st->m = ca[0];
-  st->e = ca[1];
-  st->sig = ca[2];
-  st->rho = ca[3];
-  st->p = ca[4];
-  st->q = ca[5];
-  st->cs = ca[6];
-  st->vol = ca[7];
-  for (int d = 0; d < 3; ++d) {
-    st->mu[d] = ca[8 + d];
-    st->ep[d] = ca[11 + d];
-    st->dv[d] = ca[14 + d];
-  }
-  st->geoG = (double *)(b + L.geo);
-  st->geoVE = st->geoG + 24 * mesh->nc;
-  st->geoLE = st->geoVE + mesh->nc;
-  st->geoTE = st->geoLE + mesh->nc;
-  st->x_is_ref = true;
-  st->remap_sets_x = 1;
+  carve(st, (char *)device_buf);
 
   std::vector<double> rho0, p0;
+  std::vector<float> offs;
   long long dep_cell;
   double dep_e;
+  const bool mixed = precision == SALE_FP32_MIXED;
   try {
     host_primitives(*mesh, *prob, rho0, p0, dep_cell, dep_e);
+    if (mixed && mesh->d.jitter > 0.0) {
+      // per-node offset from the structured position lo + i*h, as FP32
+      offs.assign(4 * (size_t)mesh->nn, 0.0f);
+      const int n[3] = {mesh->d.nx, mesh->d.ny, mesh->d.nz};
+      const std::vector<double> *src[3] = {&mesh->x, &mesh->y, &mesh->z};
+      for (int a = 0; a < 3; ++a) {
+        const double h = (mesh->d.hi[a] - mesh->d.lo[a]) / n[a];
+        for (long long nd = 0; nd < mesh->nn; ++nd) {
+          const long long sx = mesh->d.nx + 1, sxy = sx * (mesh->d.ny + 1);
+          const long long idx = a == 0 ? nd % sx : a == 1 ? (nd / sx) % (mesh->d.ny + 1) : nd / sxy;
+          offs[4 * nd + a] = (float)((*src[a])[nd] - (mesh->d.lo[a] + (double)idx * h));
+        }
+      }
+    }
   } catch (...) {
     delete st;
     return fail(SALE_ENOMEM, "sale_state_init: out of host memory");
@@ -463,24 +578,38 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
   const std::vector<double> *src[3] = {&mesh->x, &mesh->y, &mesh->z};
   for (int d = 0; d < 3 && e == cudaSuccess; ++d) {
     e = cudaMemcpyAsync(st->xr[d], src[d]->data(), nb, cudaMemcpyHostToDevice, st->stream);
-    if (e == cudaSuccess) e = cudaMemcpyAsync(st->xs[0][d], src[d]->data(), nb, cudaMemcpyHostToDevice, st->stream);
+    if (e == cudaSuccess && !mixed)
+      e = cudaMemcpyAsync(st->xs[0][d], src[d]->data(), nb, cudaMemcpyHostToDevice, st->stream);
   }
-  // primitives are staged in the p and q arrays, which the EoS overwrites
-  if (e == cudaSuccess) e = cudaMemcpyAsync(st->p, rho0.data(), cb, cudaMemcpyHostToDevice, st->stream);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(st->q, p0.data(), cb, cudaMemcpyHostToDevice, st->stream);
+  if (mixed && !offs.empty() && e == cudaSuccess)
+    e = cudaMemcpyAsync(st->off4, offs.data(), sizeof(float4) * mesh->nn, cudaMemcpyHostToDevice, st->stream);
+  if (mixed && offs.empty()) st->off4 = nullptr;  // unjittered: offsets are zero
+  // The per-cell FP64 primitives are staged in scratch that init does not
+  // otherwise touch: FP64 p and q arrays, or (mixed) the second-role
+  // velocity arrays (carved back to back: >= 12 bytes per node) and the
+  // flux / swept-volume arrays from mu[0] on (36 bytes per cell).
+  double *stage_rho = mixed ? (double *)st->us[1][0] : (double *)st->p;
+  double *stage_p = mixed ? (double *)st->mu[0] : (double *)st->q;
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage_rho, rho0.data(), cb, cudaMemcpyHostToDevice, st->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(stage_p, p0.data(), cb, cudaMemcpyHostToDevice, st->stream);
   if (e != cudaSuccess) {
     delete st;
     return cuda_fail(e, "sale_state_init: upload");
   }
-  {
-    const Fields<double> F = fields(st);
-    launch_reset(st->S, st->stream);
-    launch_init_cells(F, st->S, st->p, st->q, dep_cell, dep_e, st->stream);
+  launch_reset(st->S, st->stream);
+  if (!mixed) {
+    const Fields<double> F = fields_t<double>(st);
+    launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
     launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->stream);
+  } else {
+    const Fields<float> F = fields_t<float>(st);
+    launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->stream);
+    launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
+    launch_m_kernel(kMixEos, F, st->S, kDtInit, 0.0, st->stream);
   }
-  e = cudaGetLastError();
+  if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // host vectors die here
   if (e != cudaSuccess) {
     delete st;
@@ -515,72 +644,19 @@ extern "C" void sale_state_destroy(sale_state *st) {
 }
 
 // ---------------------------------------------------------------------------
-// Launch with optional profiling events
-// ---------------------------------------------------------------------------
-
-static cudaEvent_t take_event(sale_state *st) {
-  if (!st->ev_pool.empty()) {
-    cudaEvent_t e = st->ev_pool.back();
-    st->ev_pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  cudaEventCreate(&e);
-  return e;
-}
-
-// During stream capture an event record becomes a graph node only with
-// cudaEventRecordExternal (a plain record is a capture-internal join point).
-static void record(sale_state *st, cudaEvent_t ev) {
-  if (st->capturing) cudaEventRecordWithFlags(ev, st->stream, cudaEventRecordExternal);
-  else cudaEventRecord(ev, st->stream);
-}
-
-static void launch_k(sale_state *st, int kid, int mode = 0, double dt_override = 0.0) {
-  cudaEvent_t a = nullptr;
-  if (st->prof_on) {
-    a = take_event(st);
-    record(st, a);
-  }
-  launch_kernel(kid, fields(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
-  if (st->prof_on) {
-    cudaEvent_t b = take_event(st);
-    record(st, b);
-    (st->capturing ? st->capture_events : st->pending).push_back({kid, a, b});
-  }
-}
-
-// Accumulate the profile of launches that completed (stream synchronised).
-static void collect_profile(sale_state *st) {
-  for (auto &pe : st->pending) {
-    float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
-      st->prof_ms[pe.kid] += ms;
-      st->prof_n[pe.kid] += 1;
-    }
-    st->ev_pool.push_back(pe.a);
-    st->ev_pool.push_back(pe.b);
-  }
-  st->pending.clear();
-  for (auto *list : st->pending_graphs)
-    for (auto &pe : *list) {
-      float ms = 0.f;
-      if (cudaEventElapsedTime(&ms, pe.a, pe.b) == cudaSuccess) {
-        st->prof_ms[pe.kid] += ms;
-        st->prof_n[pe.kid] += 1;
-      }
-    }
-  st->pending_graphs.clear();
-  cudaGetLastError();  // a never-recorded event is not an error of the state
-}
-
-// ---------------------------------------------------------------------------
 // Stepping
 // ---------------------------------------------------------------------------
 
 static int ready(const sale_state *st, const char *who) {
   if (!st) return fail(SALE_EINVAL, "%s: null state", who);
   if (st->failed) return fail(SALE_ESTATE, "%s: state failed earlier (%s)", who, status_name(st->fail_code));
+  return SALE_OK;
+}
+
+static int fp64_only(const sale_state *st, const char *who) {
+  if (st->precision != SALE_FP64)
+    return fail(SALE_ESTATE,
+                "%s: FP32-mixed states run only Eulerian cycles (sale_run_to_time with remap_every = 1)", who);
   return SALE_OK;
 }
 
@@ -592,8 +668,6 @@ static void set_limits(sale_state *st, double t_end, long long cycles) {
   }
 }
 
-// Kernels of one cycle on the state's stream; toggles the host's record of
-// which buffers hold the current positions and velocities.
 static void launch_remap(sale_state *st) {
   launch_k(st, kRemapFaces);
   launch_k(st, kRemapNodes);
@@ -601,9 +675,18 @@ static void launch_remap(sale_state *st) {
   launch_k(st, kRemapCells);
 }
 
-// Eulerian cycle starting on the reference mesh: cached geometry, the
-// Lagrangian positions stay implicit (x_ref + dt ubar), no position writes.
+// Eulerian cycle starting on the reference mesh: the Lagrangian positions
+// stay implicit (x_ref + dt ubar) and are never written.
 static void launch_ale_cycle(sale_state *st, double dt_override) {
+  if (st->precision == SALE_FP32_MIXED) {
+    launch_k(st, kMixNodes, 0, dt_override);
+    launch_k(st, kMixCells, 0, dt_override);
+    launch_k(st, kMixFluxes);
+    launch_k(st, kMixRemapNodes);
+    st->upar ^= 1;
+    launch_k(st, kMixRemapEos, kDtAdvance, dt_override);
+    return;
+  }
   launch_k(st, kAleNodes, 0, dt_override);
   launch_k(st, kAleCells, 0, dt_override);
   launch_k(st, kAleDensity);
@@ -630,7 +713,7 @@ static void launch_cycle(sale_state *st, bool remap, double dt_override) {
 
 extern "C" int sale_lagrange_step(sale_state *st, double dt) {
   int rc = ready(st, "sale_lagrange_step");
-  if (rc) return rc;
+  if (rc || (rc = fp64_only(st, "sale_lagrange_step"))) return rc;
   if (!std::isfinite(dt)) return fail(SALE_EINVAL, "sale_lagrange_step: dt must be finite");
   set_limits(st, INFINITY, 0x7FFFFFFFFFFFFFFFll);
   launch_cycle(st, false, dt > 0.0 ? dt : 0.0);  // leaves x off the reference mesh
@@ -640,7 +723,7 @@ extern "C" int sale_lagrange_step(sale_state *st, double dt) {
 
 extern "C" int sale_remap_step(sale_state *st) {
   int rc = ready(st, "sale_remap_step");
-  if (rc) return rc;
+  if (rc || (rc = fp64_only(st, "sale_remap_step"))) return rc;
   set_limits(st, INFINITY, 0x7FFFFFFFFFFFFFFFll);
   launch_remap(st);
   st->x_is_ref = true;
@@ -698,6 +781,7 @@ extern "C" int sale_run_to_time(sale_state *st, double t_end, long long max_cycl
   if (cycles_done) *cycles_done = 0;
   if (std::isnan(t_end) || max_cycles < 0 || remap_every < 0)
     return fail(SALE_EINVAL, "sale_run_to_time: need t_end not NaN, max_cycles >= 0, remap_every >= 0");
+  if (st->precision == SALE_FP32_MIXED && remap_every != 1) return fp64_only(st, "sale_run_to_time");
   DevScalars h;
   if ((rc = sync_scalars(st, &h))) return rc;
   if ((rc = check_device_status(st, h))) return rc;
@@ -735,7 +819,7 @@ extern "C" int sale_run_to_time(sale_state *st, double t_end, long long max_cycl
 extern "C" int sale_diagnostics(const sale_state *cst, sale_diag *out) {
   sale_state *st = const_cast<sale_state *>(cst);
   if (!st || !out) return fail(SALE_EINVAL, "sale_diagnostics: null argument");
-  launch_kernel(kDiag, fields(st), st->S, 0, 0.0, st->diag_partial, st->diag_out, st->stream);
+  dispatch(st, kDiag, 0, 0.0);
   CUDA_TRY(cudaGetLastError());
   double q[8];
   CUDA_TRY(cudaMemcpyAsync(q, st->diag_out, sizeof(double) * 6, cudaMemcpyDeviceToHost, st->stream));
@@ -756,23 +840,34 @@ extern "C" int sale_diagnostics(const sale_state *cst, sale_diag *out) {
   return check_device_status(st, h);
 }
 
-static double *field_ptr(const sale_state *st, const char *name, bool *node, bool *writable) {
+// Device array of a named field; *elem = bytes per value (8 or 4).
+static void *field_ptr(const sale_state *st, const char *name, bool *node, bool *writable, size_t *elem) {
   *writable = true;
   *node = true;
+  *elem = st->elem;
   const int xp = st->xpar, up = st->upar;
-  if (!strcmp(name, "x")) return st->xs[xp][0];
-  if (!strcmp(name, "y")) return st->xs[xp][1];
-  if (!strcmp(name, "z")) return st->xs[xp][2];
+  const bool mixed = st->precision == SALE_FP32_MIXED;
+  if (!strcmp(name, "x") || !strcmp(name, "y") || !strcmp(name, "z")) {
+    const int d = name[0] - 'x';
+    if (mixed) {  // positions are always the reference mesh after a cycle
+      *writable = false;
+      *elem = sizeof(double);
+      return st->xr[d];
+    }
+    return st->xs[xp][d];
+  }
   if (!strcmp(name, "u")) return st->us[up][0];
   if (!strcmp(name, "v")) return st->us[up][1];
   if (!strcmp(name, "w")) return st->us[up][2];
   if (!strcmp(name, "mn")) return st->mn;
   *writable = false;
+  *elem = sizeof(double);
   if (!strcmp(name, "xref")) return st->xr[0];
   if (!strcmp(name, "yref")) return st->xr[1];
   if (!strcmp(name, "zref")) return st->xr[2];
   *node = false;
   *writable = true;
+  *elem = st->elem;
   if (!strcmp(name, "m")) return st->m;
   if (!strcmp(name, "e")) return st->e;
   *writable = false;
@@ -784,18 +879,31 @@ static double *field_ptr(const sale_state *st, const char *name, bool *node, boo
   return nullptr;
 }
 
-extern "C" int sale_copy_field(const sale_state *st, const char *name, double *host_out, size_t n) {
+extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *host_out, size_t n) {
+  sale_state *st = const_cast<sale_state *>(cst);
   if (!st || !name || !host_out) return fail(SALE_EINVAL, "sale_copy_field: null argument");
   bool node, wr;
-  double *p = field_ptr(st, name, &node, &wr);
+  size_t elem;
+  void *p = field_ptr(st, name, &node, &wr, &elem);
   if (!p) return fail(SALE_EINVAL, "sale_copy_field: unknown field '%s'", name);
   const size_t want = (size_t)(node ? st->nn : st->nc);
   if (n != want) return fail(SALE_EINVAL, "sale_copy_field: '%s' has %zu values, got n = %zu", name, want, n);
-  CUDA_TRY(cudaMemcpyAsync(host_out, p, sizeof(double) * n, cudaMemcpyDeviceToHost, st->stream));
+  if (st->precision == SALE_FP32_MIXED && !node && !st->failed &&
+      (!strcmp(name, "p") || !strcmp(name, "q") || !strcmp(name, "cs") || !strcmp(name, "vol")))
+    dispatch(st, kMixEos, -1, 0.0);  // the mixed cycle stores only rho and p+q
+  if (elem == sizeof(double)) {
+    CUDA_TRY(cudaMemcpyAsync(host_out, p, sizeof(double) * n, cudaMemcpyDeviceToHost, st->stream));
+  } else {
+    // FP32 field: copy into the tail half of the caller's buffer, widen in place
+    float *tmp = (float *)(host_out + n) - n;
+    CUDA_TRY(cudaMemcpyAsync(tmp, p, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    for (size_t i = 0; i < n; ++i) host_out[i] = (double)tmp[i];  // ascending: never overwrites unread floats
+  }
   DevScalars h;
   int rc = sync_scalars(st, &h);
   if (rc) return rc;
-  return check_device_status(const_cast<sale_state *>(st), h);
+  return check_device_status(st, h);
 }
 
 extern "C" int sale_set_field(sale_state *st, const char *name, const double *host_in, size_t n) {
@@ -803,11 +911,24 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
   if (rc) return rc;
   if (!name || !host_in) return fail(SALE_EINVAL, "sale_set_field: null argument");
   bool node, wr;
-  double *p = field_ptr(st, name, &node, &wr);
+  size_t elem;
+  void *p = field_ptr(st, name, &node, &wr, &elem);
   if (!p || !wr) return fail(SALE_EINVAL, "sale_set_field: '%s' is not a settable field", name);
   const size_t want = (size_t)(node ? st->nn : st->nc);
   if (n != want) return fail(SALE_EINVAL, "sale_set_field: '%s' has %zu values, got n = %zu", name, want, n);
-  CUDA_TRY(cudaMemcpyAsync(p, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, st->stream));
+  if (elem == sizeof(double)) {
+    CUDA_TRY(cudaMemcpyAsync(p, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, st->stream));
+  } else {
+    std::vector<float> tmp;
+    try {
+      tmp.resize(n);
+    } catch (...) {
+      return fail(SALE_ENOMEM, "sale_set_field: out of host memory");
+    }
+    for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_in[i];
+    CUDA_TRY(cudaMemcpyAsync(p, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp dies here
+  }
   if (!strcmp(name, "x") || !strcmp(name, "y") || !strcmp(name, "z")) st->x_is_ref = false;
   return SALE_OK;
 }
@@ -815,7 +936,7 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
 extern "C" int sale_refresh(sale_state *st) {
   int rc = ready(st, "sale_refresh");
   if (rc) return rc;
-  launch_k(st, kEos, kDtPropose);
+  launch_k(st, st->precision == SALE_FP64 ? kEos : kMixEos, kDtPropose);
   CUDA_TRY(cudaGetLastError());
   return SALE_OK;
 }
@@ -832,8 +953,10 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
 // ---------------------------------------------------------------------------
 
 static const char *const kKernelNames[kNumKernels] = {
-    "init_nodes", "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",   "remap_nodes", "remap_cells",
-    "diagnostics", "ale_nodes", "ale_cells",      "ale_density",    "ale_fluxes", "ale_remap_eos", "geo_init"};
+    "init_nodes",   "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",     "remap_nodes",
+    "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
+    "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
+    "mix_remap_eos", "mix_eos"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

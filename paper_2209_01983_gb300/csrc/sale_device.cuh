@@ -105,6 +105,61 @@ __device__ __forceinline__ void block_min_dt_and_finalize(const Fields<R> &F, De
   else VS->dt = dt;
   VS->dtmin_bits = kInfBits;
   VS->blocks_done = 0;
+  decide_next(VS);
+  __threadfence();
+}
+
+// FP32 variant: the block minimum is taken in FP32 and converted once per
+// block (the minimum of FP32 values is exact in either precision).
+__device__ __forceinline__ float warp_min_f32(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fminf(v, __shfl_xor_sync(0xffffffffu, v, o));
+  return v;
+}
+
+template <typename R>
+__device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, DevScalars *S, float dtc, int mode,
+                                                            double dt_override) {
+  __shared__ float smin32[kBlock / 32];
+  __shared__ bool last32;
+  dtc = warp_min_f32(dtc);
+  if ((threadIdx.x & 31) == 0) smin32[threadIdx.x >> 5] = dtc;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < kBlock / 32 ? smin32[threadIdx.x] : INFINITY;
+    v = warp_min_f32(v);
+    if (threadIdx.x == 0) {
+      atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong((double)v));
+      __threadfence();
+      const unsigned int done = atomicAdd(&S->blocks_done, 1u);
+      last32 = (done == gridDim.x - 1);
+    }
+  }
+  __syncthreads();
+  if (!last32 || threadIdx.x != 0) return;
+  __threadfence();
+  volatile DevScalars *VS = S;
+  const double dtcfl = __longlong_as_double((long long)atomicAdd(&S->dtmin_bits, 0ull));
+  double dt;
+  if (mode == kDtInit) {
+    dt = dtcfl;
+    if (F.dt_init > 0.0 && F.dt_init < dt) dt = F.dt_init;
+    VS->dt_last = dt;
+  } else {
+    if (mode == kDtAdvance) {
+      const double h = step_dt(S, dt_override);
+      const bool clamp = dt_override <= 0.0 && (VS->t_end - VS->t) < VS->dt;
+      VS->t = clamp ? VS->t_end : VS->t + h;
+      VS->dt_last = h;
+      VS->cycle = VS->cycle + 1;
+    }
+    dt = fmin(dtcfl, F.growth * VS->dt_last);
+  }
+  if (!(dt > 0.0) || dt == INFINITY) set_status(S, SALE_EDT);
+  else VS->dt = dt;
+  VS->dtmin_bits = kInfBits;
+  VS->blocks_done = 0;
+  decide_next(VS);
   __threadfence();
 }
 

@@ -34,7 +34,13 @@ struct DevScalars {
   unsigned long long dtmin_bits;  // running CFL minimum (bits of a double)
   unsigned int blocks_done;       // last-block counter of the dt kernel
   int status;        // first device error (sale_status), 0 = OK
-  double pad[8];
+  // The next cycle, decided whenever t, dt or the limits change, so that
+  // FP32 kernels read one flag and one step instead of comparing doubles
+  // per thread (FP64 runs at 1/64 rate on GB300).
+  int next_active;   // 1 while status == 0, t < t_end, cycle < cycle_limit
+  float next_h32;    // min(dt, t_end - t) as FP32
+  double next_h;     // min(dt, t_end - t)
+  double pad[6];
 };
 
 // Kernels of the cycle, in the order of their launch-time profile slots.
@@ -53,6 +59,12 @@ enum KernelId : int {
   kAleFluxes,
   kAleRemapEos,
   kGeoInit,
+  kMixNodes,     // FP32-mixed Eulerian path
+  kMixCells,
+  kMixFluxes,
+  kMixRemapNodes,
+  kMixRemapEos,
+  kMixEos,
   kNumKernels
 };
 
@@ -85,7 +97,13 @@ struct Fields {
   const R *G, *VE, *LE;
   const R *TE;                 // reference-face terms of the low-face swept hexes (3 per cell)
   R *dvx, *dvy, *dvz;          // swept volumes of the low x/y/z faces
+  // Structured reference mesh of the FP32-mixed path: node (i,j,k) sits at
+  // lo + (i,j,k) * h + off[node]; coordinate differences are formed as
+  // index difference * h + offset difference (no absolute coordinates).
+  float hx, hy, hz;
+  const float4 *off4;          // per-node jitter offsets x, y, z (w unused); null: none
   double gamma, cfl, c_q, c_l, growth, dt_init;
+  float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
   int ke_fix;
   int remap_sets_x;            // node remap writes the reference positions to x
   int reflect[6];
@@ -202,6 +220,16 @@ __device__ __forceinline__ void set_status(DevScalars *S, int code) {
 // True while the current cycle should run.
 __device__ __forceinline__ bool cycle_active(const DevScalars *S) {
   return S->status == 0 && S->t < S->t_end && S->cycle < S->cycle_limit;
+}
+
+// Refresh the next-cycle decision (single thread; after t/dt/limits change).
+__device__ __forceinline__ void decide_next(volatile DevScalars *S) {
+  const bool act = S->status == 0 && S->t < S->t_end && S->cycle < S->cycle_limit;
+  const double rem = S->t_end - S->t;
+  const double h = rem < S->dt ? rem : S->dt;
+  S->next_h = h;
+  S->next_h32 = (float)h;
+  S->next_active = act ? 1 : 0;
 }
 
 // The time step of the cycle in flight: an explicit dt > 0, else the

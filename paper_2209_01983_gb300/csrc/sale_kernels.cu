@@ -72,6 +72,7 @@ __global__ void k_init_nodes(Fields<R> F) {
 __global__ void k_set_limits(DevScalars *S, double t_end, long long cycle_limit) {
   S->t_end = t_end;
   S->cycle_limit = cycle_limit;
+  decide_next(S);
 }
 
 __global__ void k_reset_scalars(DevScalars *S) {
@@ -84,6 +85,7 @@ __global__ void k_reset_scalars(DevScalars *S) {
   S->dtmin_bits = kInfBits;
   S->blocks_done = 0;
   S->status = 0;
+  decide_next(S);
 }
 
 // ---------------------------------------------------------------------------
@@ -486,5 +488,7 @@ template void launch_init_cells<double>(const Fields<double> &, DevScalars *, co
                                         long long, double, cudaStream_t);
 template void launch_kernel<double>(int, const Fields<double> &, DevScalars *, int, double, double *, double *,
                                     cudaStream_t);
+template void launch_kernel<float>(int, const Fields<float> &, DevScalars *, int, double, double *, double *,
+                                   cudaStream_t);
 
 }  // namespace sale
