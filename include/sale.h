@@ -208,6 +208,31 @@ int sale_remap_static(int nx, int ny, int nz, const int *reflect, int ke_fix,
                       double *u_out, double *mn, double *m, double *e,
                       const double *rho, void *cuda_stream);
 
+/* Batches: n independent meshes (each its own problem, size and dt)
+ * advanced together.  Every cycle of every mesh runs in the same five
+ * kernel launches (a block-to-mesh table maps each block to its mesh), and
+ * a whole sale_batch_run is one CUDA-graph launch.  Batches run the
+ * FP32-mixed Eulerian cycle (precision SALE_FP32_MIXED, remap every
+ * cycle).  Memory: sale_batch_bytes() bytes of caller device memory
+ * (256-byte aligned), alive until sale_batch_destroy(); meshes[i] follow
+ * the sale_mesh_desc rules, probs[i] the sale_problem_desc rules; the
+ * stream must not be the legacy default stream. */
+typedef struct sale_batch sale_batch;
+size_t sale_batch_bytes(int n, const sale_mesh_desc *meshes, int precision);
+int sale_batch_create(int n, const sale_mesh_desc *meshes,
+                      const sale_problem_desc *probs, int precision,
+                      void *device_buf, size_t bytes, void *cuda_stream,
+                      sale_batch **out);
+/* Advance every mesh by `cycles` cycles, each with its own on-device dt;
+ * remap_every must be 1.  Synchronises; reports the first mesh with a
+ * device error.  *cycles_done (may be NULL) gets the cycles run. */
+int sale_batch_run(sale_batch *b, long long cycles, int remap_every,
+                   long long *cycles_done);
+/* Borrowed handle of mesh i (diagnostics, copy_field, set_field, refresh,
+ * run_to_time); valid until sale_batch_destroy().  NULL when out of range. */
+sale_state *sale_batch_state(sale_batch *b, int i);
+void sale_batch_destroy(sale_batch *b);
+
 /* Launch-time profile.  While on, every kernel launch of the state's steps
  * is bracketed by CUDA events on the state's stream (inside captured
  * graphs as event nodes); device times accumulate on the host at each

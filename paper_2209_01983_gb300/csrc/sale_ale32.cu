@@ -186,8 +186,11 @@ __device__ __forceinline__ void node_cell_faces(const Fields<float> &F, long lon
   node_face_force<SB, 2>(F, n, oa, i, j, k, sig, f);
 }
 
-__global__ void __launch_bounds__(kBlock) k_m_nodes(Fields<float> F, DevScalars *S, double dt_override) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// Kernel bodies: one thread's work for unit n (node) or c (cell) of the mesh
+// F.  The single-mesh kernels and the batched kernels wrap the same bodies,
+// so a mesh advanced inside a batch is bitwise equal to the mesh alone.
+
+__device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars *S, long long n) {
   if (n >= F.nn || !S->next_active) return;
   const float h = S->next_h32;
   int i, j, k;
@@ -220,8 +223,7 @@ __global__ void __launch_bounds__(kBlock) k_m_nodes(Fields<float> F, DevScalars 
   F.wb[n] = 0.5f * (w0 + w1);
 }
 
-__global__ void __launch_bounds__(kBlock) k_m_cells(Fields<float> F, DevScalars *S, double dt_override) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars *S, long long c) {
   if (c >= F.nc || !S->next_active) return;
   const float h = S->next_h32;
   int i, j, k;
@@ -285,8 +287,7 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, DevScalars *
 }
 
 // Lagrangian densities (closure) and donor-cell fluxes of the low faces.
-__global__ void __launch_bounds__(kBlock) k_m_fluxes(Fields<float> F, DevScalars *S) {
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars *S, long long c) {
   if (c >= F.nc || !S->next_active) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -341,8 +342,7 @@ __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j
   ke += flux * 0.5f * dotf(ud, ud);
 }
 
-__global__ void __launch_bounds__(kBlock) k_m_remap_nodes(Fields<float> F, DevScalars *S) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+__device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevScalars *S, long long n) {
   if (n >= F.nn) return;
   if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
     F.ub[n] = F.u[n];
@@ -415,9 +415,9 @@ __device__ __forceinline__ float m_eos_cell(const Fields<float> &F, long long c,
   return F.cfl32 * L / sqrtf(cs * cs + 2.f * q_rho);
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_m_remap_eos(Fields<float> F, DevScalars *S, double dt_override) {
-  if (!S->next_active) return;  // uniform over the grid: S changes only in the last block
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// Cell remap + EoS + dt; nblk = blocks of this mesh (last-block detection).
+__device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScalars *S, long long c, unsigned nblk) {
+  if (!S->next_active) return;  // uniform over the mesh's blocks: S changes only in its last block
   float dtc = INFINITY;
   if (c < F.nc) {
     int i, j, k;
@@ -447,7 +447,7 @@ __global__ void __launch_bounds__(kBlock, 4) k_m_remap_eos(Fields<float> F, DevS
     const float d = m_eos_cell(F, c, i, j, k, m1, e1, false);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
-  block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, dt_override);
+  block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, 0.0, nblk);
 }
 
 // EoS/viscosity/dt without a remap: kDtInit / kDtPropose, or no dt at all
@@ -462,10 +462,83 @@ __global__ void __launch_bounds__(kBlock, 4) k_m_eos(Fields<float> F, DevScalars
     const float d = m_eos_cell(F, c, i, j, k, F.m[c], F.e[c], true);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
-  if (mode >= 0) block_min_dt32_and_finalize(F, S, dtc, mode, 0.0);
+  if (mode >= 0) block_min_dt32_and_finalize(F, S, dtc, mode, 0.0, gridDim.x);
+}
+
+// Single-mesh kernels.
+__global__ void __launch_bounds__(kBlock) k_m_nodes(Fields<float> F, DevScalars *S) {
+  m_nodes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
+}
+__global__ void __launch_bounds__(kBlock) k_m_cells(Fields<float> F, DevScalars *S) {
+  m_cells_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
+}
+__global__ void __launch_bounds__(kBlock) k_m_fluxes(Fields<float> F, DevScalars *S) {
+  m_fluxes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
+}
+__global__ void __launch_bounds__(kBlock) k_m_remap_nodes(Fields<float> F, DevScalars *S) {
+  m_remap_nodes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
+}
+__global__ void __launch_bounds__(kBlock, 4) k_m_remap_eos(Fields<float> F, DevScalars *S) {
+  m_remap_eos_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x, gridDim.x);
+}
+
+// Batched kernels: one launch covers every mesh of a batch.  Block b works
+// on mesh tab[b].x, local block tab[b].y; the mesh's descriptor is staged in
+// shared memory once per block.
+template <int KID>
+__global__ void __launch_bounds__(kBlock, KID == kMixRemapEos ? 4 : 1) kb_m(const BatchItem *items, const int2 *tab) {
+  __shared__ BatchItem it;
+  const int2 t = tab[blockIdx.x];
+  const int *src = reinterpret_cast<const int *>(items + t.x);
+  int *dst = reinterpret_cast<int *>(&it);
+  for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += kBlock) dst[w] = src[w];
+  __syncthreads();
+  const long long u = (long long)t.y * kBlock + threadIdx.x;
+  if constexpr (KID == kMixNodes) m_nodes_body(it.F, it.S, u);
+  if constexpr (KID == kMixCells) m_cells_body(it.F, it.S, u);
+  if constexpr (KID == kMixFluxes) m_fluxes_body(it.F, it.S, u);
+  if constexpr (KID == kMixRemapNodes) m_remap_nodes_body(it.F, it.S, u);
+  if constexpr (KID == kMixRemapEos) m_remap_eos_body(it.F, it.S, u, it.nblk_cell);
+}
+
+// Per mesh of a batch: t_end = inf, cycle_limit = cycle + cycles, decide.
+__global__ void kb_set_limits(const BatchItem *items, int n, long long cycles) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  volatile DevScalars *S = items[i].S;
+  S->t_end = INFINITY;
+  S->cycle_limit = S->cycle + cycles;
+  decide_next(S);
+}
+
+// Gather (t, dt, cycle, status) of every mesh into one array for the host.
+__global__ void kb_gather(const BatchItem *items, int n, BatchStatus *out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const DevScalars *S = items[i].S;
+  out[i] = {S->t, S->dt, S->cycle, S->status};
 }
 
 static inline unsigned grid_m(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+void launch_m_batch(int kid, const BatchItem *items, const int2 *tab, unsigned nblocks, cudaStream_t st) {
+  switch (kid) {
+    case kMixNodes: kb_m<kMixNodes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    case kMixCells: kb_m<kMixCells><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    case kMixFluxes: kb_m<kMixFluxes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    case kMixRemapNodes: kb_m<kMixRemapNodes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    case kMixRemapEos: kb_m<kMixRemapEos><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    default: break;
+  }
+}
+
+void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st) {
+  kb_set_limits<<<(n + 127) / 128, 128, 0, st>>>(items, n, cycles);
+}
+
+void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st) {
+  kb_gather<<<(n + 127) / 128, 128, 0, st>>>(items, n, out);
+}
 
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
                          long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st) {
@@ -474,11 +547,11 @@ void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rh
 
 void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
   switch (kid) {
-    case kMixNodes: k_m_nodes<<<grid_m(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
-    case kMixCells: k_m_cells<<<grid_m(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kMixNodes: k_m_nodes<<<grid_m(F.nn), kBlock, 0, st>>>(F, S); break;
+    case kMixCells: k_m_cells<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
     case kMixFluxes: k_m_fluxes<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
     case kMixRemapNodes: k_m_remap_nodes<<<grid_m(F.nn), kBlock, 0, st>>>(F, S); break;
-    case kMixRemapEos: k_m_remap_eos<<<grid_m(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kMixRemapEos: k_m_remap_eos<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
     case kMixEos: k_m_eos<<<grid_m(F.nc), kBlock, 0, st>>>(F, S, mode); break;
     default: break;
   }

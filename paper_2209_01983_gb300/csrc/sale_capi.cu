@@ -506,6 +506,22 @@ static void collect_profile(sale_state *st) {
 // Initialisation
 // ---------------------------------------------------------------------------
 
+// Check a caller-provided device buffer: non-null, 256-byte aligned, large
+// enough, device (or managed) memory.
+static int check_device_buffer(const char *who, void *device_buf, size_t bytes, size_t need) {
+  if (!device_buf) return fail(SALE_EINVAL, "%s: null device buffer", who);
+  if ((uintptr_t)device_buf % kAlign) return fail(SALE_EINVAL, "%s: device buffer must be 256-byte aligned", who);
+  if (bytes < need) return fail(SALE_ENOMEM, "%s: buffer has %zu bytes, need %zu", who, bytes, need);
+  cudaPointerAttributes attr;
+  CUDA_TRY(cudaPointerGetAttributes(&attr, device_buf));
+  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
+    return fail(SALE_EINVAL, "%s: buffer is not device memory", who);
+  return SALE_OK;
+}
+
+static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, int precision, void *device_buf,
+                         void *cuda_stream, sale_state **out);
+
 extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *prob, int precision,
                                void *device_buf, size_t bytes, void *cuda_stream, sale_state **out) {
   if (!mesh || !prob || !out) return fail(SALE_EINVAL, "sale_state_init: null argument");
@@ -514,15 +530,15 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
-  const size_t need = state_bytes(mesh->nc, mesh->nn, precision);
-  if (!device_buf) return fail(SALE_EINVAL, "sale_state_init: null device buffer");
-  if ((uintptr_t)device_buf % kAlign) return fail(SALE_EINVAL, "sale_state_init: device buffer must be 256-byte aligned");
-  if (bytes < need) return fail(SALE_ENOMEM, "sale_state_init: buffer has %zu bytes, need %zu", bytes, need);
-  cudaPointerAttributes attr;
-  CUDA_TRY(cudaPointerGetAttributes(&attr, device_buf));
-  if (attr.type != cudaMemoryTypeDevice && attr.type != cudaMemoryTypeManaged)
-    return fail(SALE_EINVAL, "sale_state_init: buffer is not device memory");
+  rc = check_device_buffer("sale_state_init", device_buf, bytes, state_bytes(mesh->nc, mesh->nn, precision));
+  if (rc) return rc;
+  return state_init_at(mesh, prob, precision, device_buf, cuda_stream, out);
+}
 
+// Initialise a state in an already checked region of device memory.
+static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, int precision, void *device_buf,
+                         void *cuda_stream, sale_state **out) {
+  int rc = SALE_OK;
   sale_state *st = new (std::nothrow) sale_state;
   if (!st) return fail(SALE_ENOMEM, "sale_state_init: out of host memory");
   st->nx = mesh->d.nx;
@@ -945,6 +961,241 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
   if (!st) return fail(SALE_EINVAL, "sale_state_dims: null state");
   if (ncells) *ncells = st->nc;
   if (nnodes) *nnodes = st->nn;
+  return SALE_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Batches: many independent meshes advanced by one graph launch
+// ---------------------------------------------------------------------------
+
+namespace sale {
+void launch_m_batch(int kid, const BatchItem *items, const int2 *tab, unsigned nblocks, cudaStream_t st);
+void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st);
+void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st);
+}  // namespace sale
+
+struct sale_batch {
+  int n;
+  cudaStream_t stream;
+  std::vector<sale_state *> st;     // one state per mesh, carved from the batch buffer
+  BatchItem *items[2];              // per velocity-buffer parity
+  int2 *tab_cell, *tab_node;        // block -> (mesh, local block)
+  unsigned nb_cell, nb_node;
+  BatchStatus *status;              // device gather area
+  std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
+  std::map<long long, cudaGraphExec_t> graphs;
+};
+
+static unsigned blocks_of(long long units) { return (unsigned)((units + kBlock - 1) / kBlock); }
+
+// Layout of a batch buffer: header (descriptors, block tables, status
+// gather area) then one state region per mesh.
+static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, size_t *state_off, size_t *hdr_parts) {
+  long long nbc = 0, nbn = 0;
+  for (int i = 0; i < n; ++i) {
+    const sale_mesh_desc &d = meshes[i];
+    nbc += blocks_of((long long)d.nx * d.ny * d.nz);
+    nbn += blocks_of((long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1));
+  }
+  size_t off = 0;
+  hdr_parts[0] = off;  // descriptors, two parities
+  off = align_up(off + 2 * sizeof(BatchItem) * n);
+  hdr_parts[1] = off;  // cell block table
+  off = align_up(off + sizeof(int2) * nbc);
+  hdr_parts[2] = off;  // node block table
+  off = align_up(off + sizeof(int2) * nbn);
+  hdr_parts[3] = off;  // status gather
+  off = align_up(off + sizeof(BatchStatus) * n);
+  for (int i = 0; i < n; ++i) {
+    const sale_mesh_desc &d = meshes[i];
+    const long long nc = (long long)d.nx * d.ny * d.nz, nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
+    if (state_off) state_off[i] = off;
+    off = align_up(off + state_bytes(nc, nn, precision));
+  }
+  return off;
+}
+
+extern "C" size_t sale_batch_bytes(int n, const sale_mesh_desc *meshes, int precision) {
+  if (n < 1 || !meshes || precision != SALE_FP32_MIXED) return 0;
+  for (int i = 0; i < n; ++i)
+    if (meshes[i].nx < 1 || meshes[i].ny < 1 || meshes[i].nz < 1) return 0;
+  size_t parts[4];
+  return batch_layout(n, meshes, precision, nullptr, parts);
+}
+
+extern "C" void sale_batch_destroy(sale_batch *b) {
+  if (!b) return;
+  cudaStreamSynchronize(b->stream);
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);
+  for (auto *st : b->st) sale_state_destroy(st);
+  delete b;
+}
+
+// Descriptors relative to each mesh's current velocity-buffer parity:
+// items[0] as the buffers are now, items[1] with the two roles swapped.
+static int upload_batch_items(sale_batch *b) {
+  std::vector<BatchItem> h((size_t)b->n);
+  for (int rel = 0; rel < 2; ++rel) {
+    for (int i = 0; i < b->n; ++i) {
+      sale_state *st = b->st[i];
+      const int keep = st->upar;
+      st->upar = keep ^ rel;
+      h[i].F = fields_t<float>(st);
+      st->upar = keep;
+      h[i].S = st->S;
+      h[i].nblk_cell = blocks_of(st->nc);
+      h[i].pad = 0;
+    }
+    CUDA_TRY(cudaMemcpyAsync(b->items[rel], h.data(), sizeof(BatchItem) * b->n, cudaMemcpyHostToDevice, b->stream));
+    CUDA_TRY(cudaStreamSynchronize(b->stream));  // h is rewritten next
+  }
+  b->item_upar.resize(b->n);
+  for (int i = 0; i < b->n; ++i) b->item_upar[i] = b->st[i]->upar;
+  return SALE_OK;
+}
+
+extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale_problem_desc *probs,
+                                 int precision, void *device_buf, size_t bytes, void *cuda_stream,
+                                 sale_batch **out) {
+  if (!out) return fail(SALE_EINVAL, "sale_batch_create: null out");
+  *out = nullptr;
+  if (n < 1 || !meshes || !probs) return fail(SALE_EINVAL, "sale_batch_create: need n >= 1, meshes, problems");
+  if (precision != SALE_FP32_MIXED)
+    return fail(SALE_EINVAL, "sale_batch_create: batches run the FP32-mixed Eulerian cycle (precision %d)",
+                SALE_FP32_MIXED);
+  if (!cuda_stream) return fail(SALE_EINVAL, "sale_batch_create: a non-default stream is required (graph capture)");
+  for (int i = 0; i < n; ++i) {
+    int rc = validate_problem(probs[i]);
+    if (rc) return fail(rc, "sale_batch_create: mesh %d: %s", i, sale_last_error());
+  }
+  std::vector<size_t> soff((size_t)n);
+  size_t parts[4];
+  const size_t need = batch_layout(n, meshes, precision, soff.data(), parts);
+  int rc = check_device_buffer("sale_batch_create", device_buf, bytes, need);
+  if (rc) return rc;
+  sale_batch *b = new (std::nothrow) sale_batch;
+  if (!b) return fail(SALE_ENOMEM, "sale_batch_create: out of host memory");
+  char *base = (char *)device_buf;
+  b->n = n;
+  b->stream = (cudaStream_t)cuda_stream;
+  b->items[0] = (BatchItem *)(base + parts[0]);
+  b->items[1] = b->items[0] + n;
+  b->tab_cell = (int2 *)(base + parts[1]);
+  b->tab_node = (int2 *)(base + parts[2]);
+  b->status = (BatchStatus *)(base + parts[3]);
+  for (int i = 0; i < n; ++i) {
+    sale_mesh *m = nullptr;
+    sale_state *sti = nullptr;
+    rc = sale_mesh_create(&meshes[i], &m);
+    if (rc == SALE_OK) rc = state_init_at(m, &probs[i], precision, base + soff[i], cuda_stream, &sti);
+    sale_mesh_destroy(m);
+    if (rc) {
+      const std::string msg = sale_last_error();
+      sale_batch_destroy(b);
+      return fail(rc, "sale_batch_create: mesh %d: %s", i, msg.c_str());
+    }
+    b->st.push_back(sti);
+  }
+  // block tables (meshes in order) and descriptors for both parities
+  std::vector<int2> tc, tn;
+  try {
+    for (int i = 0; i < n; ++i) {
+      for (unsigned k = 0; k < blocks_of(b->st[i]->nc); ++k) tc.push_back(make_int2(i, (int)k));
+      for (unsigned k = 0; k < blocks_of(b->st[i]->nn); ++k) tn.push_back(make_int2(i, (int)k));
+    }
+  } catch (...) {
+    sale_batch_destroy(b);
+    return fail(SALE_ENOMEM, "sale_batch_create: out of host memory");
+  }
+  b->nb_cell = (unsigned)tc.size();
+  b->nb_node = (unsigned)tn.size();
+  cudaError_t e = cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int2) * tc.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int2) * tn.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e != cudaSuccess) {
+    sale_batch_destroy(b);
+    return cuda_fail(e, "sale_batch_create: upload");
+  }
+  rc = upload_batch_items(b);
+  if (rc) {
+    sale_batch_destroy(b);
+    return rc;
+  }
+  *out = b;
+  return SALE_OK;
+}
+
+extern "C" sale_state *sale_batch_state(sale_batch *b, int i) {
+  if (!b || i < 0 || i >= b->n) return nullptr;
+  return b->st[i];
+}
+
+// One cycle of every mesh: the four kernels before the velocity-buffer
+// toggle read descriptors of parity p, the fused remap/EoS/dt one p ^ 1.
+static void launch_batch_cycle(sale_batch *b, int p) {
+  launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->stream);
+  launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->stream);
+  launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->stream);
+  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_node, b->nb_node, b->stream);
+  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->stream);
+}
+
+extern "C" int sale_batch_run(sale_batch *b, long long cycles, int remap_every, long long *cycles_done) {
+  if (!b) return fail(SALE_EINVAL, "sale_batch_run: null batch");
+  if (cycles_done) *cycles_done = 0;
+  if (cycles < 0 || cycles > (1ll << 20)) return fail(SALE_EINVAL, "sale_batch_run: cycles must be in [0, 2^20]");
+  if (remap_every != 1)
+    return fail(SALE_EINVAL, "sale_batch_run: batches run Eulerian cycles (remap_every = 1)");
+  for (auto *st : b->st) {
+    int rc = ready(st, "sale_batch_run");
+    if (rc) return rc;
+    st->lim_t_end = NAN;  // the batch sets the device limits; force a reset on the next single-mesh call
+  }
+  if (cycles == 0) return SALE_OK;
+  for (int i = 0; i < b->n; ++i)
+    if (b->st[i]->upar != b->item_upar[i]) {  // a mesh was advanced on its own since
+      int rc = upload_batch_items(b);
+      if (rc) return rc;
+      break;
+    }
+  launch_batch_limits(b->items[0], b->n, cycles, b->stream);
+  // the whole run is one graph: `cycles` cycles of every mesh
+  auto it = b->graphs.find(cycles);
+  cudaGraphExec_t ge;
+  if (it == b->graphs.end()) {
+    cudaGraph_t g;
+    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+    int p = 0;
+    for (long long j = 0; j < cycles; ++j, p ^= 1) launch_batch_cycle(b, p);
+    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+    if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph capture");
+    e = cudaGraphInstantiate(&ge, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph instantiate");
+    b->graphs[cycles] = ge;
+  } else {
+    ge = it->second;
+  }
+  CUDA_TRY(cudaGraphLaunch(ge, b->stream));
+  if (cycles & 1)  // odd run: every mesh's velocity roles swapped
+    for (auto *st : b->st) st->upar ^= 1;
+  launch_batch_gather(b->items[0], b->n, b->status, b->stream);
+  std::vector<BatchStatus> hs((size_t)b->n);
+  CUDA_TRY(cudaMemcpyAsync(hs.data(), b->status, sizeof(BatchStatus) * b->n, cudaMemcpyDeviceToHost, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  if (cycles & 1) {  // descriptors follow the swapped roles (graphs keep their array pointers)
+    int rc = upload_batch_items(b);
+    if (rc) return rc;
+  }
+  for (int i = 0; i < b->n; ++i) {
+    if (hs[i].status != 0) {
+      b->st[i]->failed = true;
+      b->st[i]->fail_code = (int)hs[i].status;
+      return fail((int)hs[i].status, "sale_batch_run: mesh %d: %s (t = %.17g, cycle %lld)", i,
+                  status_name((int)hs[i].status), hs[i].t, hs[i].cycle);
+    }
+  }
+  if (cycles_done) *cycles_done = cycles;
   return SALE_OK;
 }
 

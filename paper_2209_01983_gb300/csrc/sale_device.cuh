@@ -119,7 +119,7 @@ __device__ __forceinline__ float warp_min_f32(float v) {
 
 template <typename R>
 __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, DevScalars *S, float dtc, int mode,
-                                                            double dt_override) {
+                                                            double dt_override, unsigned nblk) {
   __shared__ float smin32[kBlock / 32];
   __shared__ bool last32;
   dtc = warp_min_f32(dtc);
@@ -132,7 +132,7 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
       atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong((double)v));
       __threadfence();
       const unsigned int done = atomicAdd(&S->blocks_done, 1u);
-      last32 = (done == gridDim.x - 1);
+      last32 = (done == nblk - 1);
     }
   }
   __syncthreads();

@@ -109,6 +109,21 @@ struct Fields {
   int reflect[6];
 };
 
+// One mesh of a batch, as seen by the batched kernels.
+struct BatchItem {
+  Fields<float> F;
+  DevScalars *S;
+  unsigned nblk_cell;  // blocks of this mesh in a cell kernel
+  unsigned pad;
+};
+
+// Per-mesh summary the host reads after a batched run.
+struct BatchStatus {
+  double t, dt;
+  long long cycle;
+  long long status;
+};
+
 struct P3 {
   double x, y, z;
 };

@@ -81,6 +81,13 @@ sale_profile_read = _sig("sale_profile_read", C.c_int,
                          [_vp, _dp, C.POINTER(C.c_longlong), C.c_int, C.c_int])
 sale_kernel_count = _sig("sale_kernel_count", C.c_int, [])
 sale_kernel_name = _sig("sale_kernel_name", C.c_char_p, [C.c_int])
+sale_batch_bytes = _sig("sale_batch_bytes", C.c_size_t, [C.c_int, C.POINTER(sale_mesh_desc), C.c_int])
+sale_batch_create = _sig("sale_batch_create", C.c_int,
+                         [C.c_int, C.POINTER(sale_mesh_desc), C.POINTER(sale_problem_desc), C.c_int, _vp,
+                          C.c_size_t, _vp, C.POINTER(_vp)])
+sale_batch_run = _sig("sale_batch_run", C.c_int, [_vp, C.c_longlong, C.c_int, C.POINTER(C.c_longlong)])
+sale_batch_state = _sig("sale_batch_state", _vp, [_vp, C.c_int])
+sale_batch_destroy = _sig("sale_batch_destroy", None, [_vp])
 sale_remap_static = _sig("sale_remap_static", C.c_int,
                          [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp, _vp,
                           _vp, _vp, _vp, _vp, _vp])
@@ -93,7 +100,9 @@ EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_sta
            "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
            "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
            "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
-           "sale_kernel_count", "sale_kernel_name", "sale_remap_static", "sale_last_error")
+           "sale_kernel_count", "sale_kernel_name", "sale_remap_static", "sale_batch_bytes",
+           "sale_batch_create", "sale_batch_run", "sale_batch_state", "sale_batch_destroy",
+           "sale_last_error")
 
 
 class SaleError(RuntimeError):
@@ -218,3 +227,53 @@ class State:
         cnt = (C.c_longlong * n)()
         check(sale_profile_read(self._h, ms, cnt, n, 1 if reset else 0))
         return {sale_kernel_name(i).decode(): (ms[i], cnt[i]) for i in range(n)}
+
+
+class _Borrowed(State):
+    """A mesh of a batch (the batch owns the handle and the memory)."""
+
+    def __init__(self, handle, md, pd, stream):
+        self._h = _vp(handle)
+        self.md, self.pd, self.stream = md, pd, stream
+        self.ncell, self.nnode = md.ncell, md.nnode
+
+    def close(self):
+        self._h = None
+
+
+class Batch:
+    """Independent meshes advanced together (FP32-mixed Eulerian cycle)."""
+
+    def __init__(self, instances, device="cuda", stream=None):
+        import torch
+
+        self.instances = list(instances)
+        n = len(self.instances)
+        self._meshes = (sale_mesh_desc * n)(*[mesh_desc(md) for md, _ in self.instances])
+        self._probs = (sale_problem_desc * n)(*[problem_desc(pd) for _, pd in self.instances])
+        nbytes = sale_batch_bytes(n, self._meshes, SALE_FP32_MIXED)
+        if nbytes == 0:
+            raise SaleError(SALE_EINVAL, "bad batch description")
+        self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=device)
+        self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
+        self._h = _vp()
+        check(sale_batch_create(n, self._meshes, self._probs, SALE_FP32_MIXED, _vp(self.buffer.data_ptr()),
+                                nbytes, _vp(self.stream.cuda_stream), C.byref(self._h)))
+        self.ncell_total = sum(md.ncell for md, _ in self.instances)
+
+    def run(self, cycles):
+        done = C.c_longlong(0)
+        check(sale_batch_run(self._h, cycles, 1, C.byref(done)))
+        return done.value
+
+    def state(self, i) -> State:
+        md, pd = self.instances[i]
+        return _Borrowed(sale_batch_state(self._h, i), md, pd, self.stream)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            sale_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
