@@ -43,24 +43,32 @@ __device__ __forceinline__ F3 crossf(F3 a, F3 b) {
 }
 __device__ __forceinline__ float dotf(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
-// Jitter offset of a node (one 16-byte load: x, y, z, unused).
-__device__ __forceinline__ float4 node_off(const Fields<float> &F, long long n) {
-  return F.off4 ? __ldg(F.off4 + n) : make_float4(0.f, 0.f, 0.f, 0.f);
+// Jitter offset of a node (one 16-byte load: x, y, z, unused); on an
+// unjittered mesh (JIT = false) the offsets are zero and the geometry below
+// folds to constants.
+template <bool JIT>
+__device__ __forceinline__ float4 off_at(const Fields<float> &F, int n) {
+  if constexpr (JIT) return __ldg(F.off4 + n);
+  return make_float4(0.f, 0.f, 0.f, 0.f);
 }
 
-// Position of a node relative to a base node with offset oa, the two
+// Position of node nb relative to a base node with offset oa, the two
 // differing by the index offset (ox, oy, oz): o * h + (offset - oa).
-__device__ __forceinline__ F3 rel_pos(const Fields<float> &F, float4 oa, long long nb, int ox, int oy, int oz) {
-  const float4 ob = node_off(F, nb);
+template <bool JIT>
+__device__ __forceinline__ F3 relp(const Fields<float> &F, float4 oa, int nb, int ox, int oy, int oz) {
+  const float4 ob = off_at<JIT>(F, nb);
   return {(float)ox * F.hx + (ob.x - oa.x), (float)oy * F.hy + (ob.y - oa.y), (float)oz * F.hz + (ob.z - oa.z)};
 }
 
-// Reference nodes of cell (i,j,k) relative to its node 0.
-__device__ __forceinline__ void ref_hex(const Fields<float> &F, const long long (&nid)[8], F3 (&E)[8]) {
-  const float4 o0 = node_off(F, nid[0]);
+// Reference nodes of the cell whose node 0 is n0 (node strides sy, sz),
+// relative to that node.
+template <bool JIT>
+__device__ __forceinline__ void ref_hex2(const Fields<float> &F, int n0, int sy, int sz, F3 (&E)[8]) {
+  const float4 o0 = off_at<JIT>(F, n0);
   E[0] = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int a = 1; a < 8; ++a) E[a] = rel_pos(F, o0, nid[a], a & 1, (a >> 1) & 1, (a >> 2) & 1);
+  for (int a = 1; a < 8; ++a)
+    E[a] = relp<JIT>(F, o0, n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz, a & 1, (a >> 1) & 1, (a >> 2) & 1);
 }
 
 // sum_a dV/dx_a . U_a for a hex given relative to its node 0, accumulated
@@ -145,72 +153,79 @@ __global__ void __launch_bounds__(kBlock) k_m_init_cells(Fields<float> F, DevSca
 // ---------------------------------------------------------------------------
 // Lagrangian phase
 // ---------------------------------------------------------------------------
+//
+// Thread layout: blocks of 32 x 8 threads over (i, j) of one k plane; the
+// grid is (ceil(n_i / 32), ceil(n_j / 8), n_k) over nodes or cells, so a
+// thread's (i, j, k) comes from its block and thread indices (no division)
+// and indices stay 32-bit.
 
 // Face term of one mesh face through node (i,j,k): the lower cell across
-// the face is s (bits: cell = node - 1 + bit), the face is normal to D.
-template <int SB, int D>
-__device__ __forceinline__ void node_face_force(const Fields<float> &F, long long n, float4 oa, int i, int j, int k,
-                                                const float (&sig)[8], F3 &f) {
+// the face is SB (bits: cell = node - 1 + bit), the face is normal to D.
+template <bool JIT, int SB, int D>
+__device__ __forceinline__ void node_face2(const Fields<float> &F, int n, int sy, int sz, float4 oa,
+                                           const bool (&lo_ok)[3], const bool (&hi_ok)[3], const float (&sig)[8],
+                                           F3 &f) {
   if ((SB >> D) & 1) return;  // the cell must be the lower one across the plane
-  const int c0 = i - 1 + (SB & 1), c1 = j - 1 + ((SB >> 1) & 1), c2 = k - 1 + ((SB >> 2) & 1);
-  const int cc[3] = {c0, c1, c2};
-  const int nn[3] = {F.nx, F.ny, F.nz};
   constexpr int D1 = (D + 1) % 3, D2 = (D + 2) % 3;
-  if (cc[D1] < 0 || cc[D1] >= nn[D1] || cc[D2] < 0 || cc[D2] >= nn[D2]) return;  // face outside the mesh
-  const float slo = sig[SB];
-  const float shi = sig[SB | (1 << D)];
-  constexpr int A = 7 - SB;          // local corner of the node in the lower cell
-  constexpr int FACE = 2 * D + 1;    // the lower cell's high face normal to D
-  constexpr int K = face_slot(FACE, A);
-  constexpr int B1 = face_node(FACE, (K + 1) & 3), B2 = face_node(FACE, (K + 2) & 3),
-                B3 = face_node(FACE, (K + 3) & 3);
-  const long long sx = 1, sy = F.nx + 1, sz = (long long)(F.nx + 1) * (F.ny + 1);
-  // node offsets from (i,j,k): cell offset (bit - 1) plus the local node bits
-  constexpr int O1x = (SB & 1) + (B1 & 1) - 1, O1y = ((SB >> 1) & 1) + ((B1 >> 1) & 1) - 1,
-                O1z = ((SB >> 2) & 1) + ((B1 >> 2) & 1) - 1;
-  constexpr int O2x = (SB & 1) + (B2 & 1) - 1, O2y = ((SB >> 1) & 1) + ((B2 >> 1) & 1) - 1,
-                O2z = ((SB >> 2) & 1) + ((B2 >> 2) & 1) - 1;
-  constexpr int O3x = (SB & 1) + (B3 & 1) - 1, O3y = ((SB >> 1) & 1) + ((B3 >> 1) & 1) - 1,
-                O3z = ((SB >> 2) & 1) + ((B3 >> 2) & 1) - 1;
-  const F3 p1 = rel_pos(F, oa, n + O1x * sx + O1y * sy + O1z * sz, O1x, O1y, O1z);
-  const F3 p2 = rel_pos(F, oa, n + O2x * sx + O2y * sy + O2z * sz, O2x, O2y, O2z);
-  const F3 p3 = rel_pos(F, oa, n + O3x * sx + O3y * sy + O3z * sz, O3x, O3y, O3z);
-  f = f + (slo - shi) * crossf(p1 + 2.f * p2 + p3, p3 - p1);
+  const bool v1 = ((SB >> D1) & 1) ? hi_ok[D1] : lo_ok[D1];
+  const bool v2 = ((SB >> D2) & 1) ? hi_ok[D2] : lo_ok[D2];
+  if (!(v1 && v2)) return;  // face outside the mesh
+  const float ds = sig[SB] - sig[SB | (1 << D)];
+  constexpr int A = 7 - SB;        // local corner of the node in the lower cell
+  constexpr int FC = 2 * D + 1;    // the lower cell's high face normal to D
+  constexpr int K = face_slot(FC, A);
+  constexpr int B1 = face_node(FC, (K + 1) & 3), B2 = face_node(FC, (K + 2) & 3), B3 = face_node(FC, (K + 3) & 3);
+  constexpr int X1 = (SB & 1) + (B1 & 1) - 1, Y1 = ((SB >> 1) & 1) + ((B1 >> 1) & 1) - 1,
+                Z1 = ((SB >> 2) & 1) + ((B1 >> 2) & 1) - 1;
+  constexpr int X2 = (SB & 1) + (B2 & 1) - 1, Y2 = ((SB >> 1) & 1) + ((B2 >> 1) & 1) - 1,
+                Z2 = ((SB >> 2) & 1) + ((B2 >> 2) & 1) - 1;
+  constexpr int X3 = (SB & 1) + (B3 & 1) - 1, Y3 = ((SB >> 1) & 1) + ((B3 >> 1) & 1) - 1,
+                Z3 = ((SB >> 2) & 1) + ((B3 >> 2) & 1) - 1;
+  const F3 p1 = relp<JIT>(F, oa, n + X1 + Y1 * sy + Z1 * sz, X1, Y1, Z1);
+  const F3 p2 = relp<JIT>(F, oa, n + X2 + Y2 * sy + Z2 * sz, X2, Y2, Z2);
+  const F3 p3 = relp<JIT>(F, oa, n + X3 + Y3 * sy + Z3 * sz, X3, Y3, Z3);
+  f = f + ds * crossf(p1 + 2.f * p2 + p3, p3 - p1);
 }
 
-template <int SB>
-__device__ __forceinline__ void node_cell_faces(const Fields<float> &F, long long n, float4 oa, int i, int j, int k,
-                                                const float (&sig)[8], F3 &f) {
-  node_face_force<SB, 0>(F, n, oa, i, j, k, sig, f);
-  node_face_force<SB, 1>(F, n, oa, i, j, k, sig, f);
-  node_face_force<SB, 2>(F, n, oa, i, j, k, sig, f);
+template <bool JIT, int SB>
+__device__ __forceinline__ void node_faces2(const Fields<float> &F, int n, int sy, int sz, float4 oa,
+                                            const bool (&lo_ok)[3], const bool (&hi_ok)[3], const float (&sig)[8],
+                                            F3 &f) {
+  node_face2<JIT, SB, 0>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_face2<JIT, SB, 1>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_face2<JIT, SB, 2>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
 }
 
-// Kernel bodies: one thread's work for unit n (node) or c (cell) of the mesh
-// F.  The single-mesh kernels and the batched kernels wrap the same bodies,
-// so a mesh advanced inside a batch is bitwise equal to the mesh alone.
+// Kernel bodies: one thread's work for node or cell (i, j, k) of the mesh F.
+// The single-mesh kernels and the batched kernels wrap the same bodies, so
+// a mesh advanced inside a batch is bitwise equal to the mesh alone.
 
-__device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars *S, long long n) {
-  if (n >= F.nn || !S->next_active) return;
+template <bool JIT>
+__device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if (i > F.nx || j > F.ny || k > F.nz || !S->next_active) return;
   const float h = S->next_h32;
-  int i, j, k;
-  node_ijk(n, F.nx, F.ny, i, j, k);
+  const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
+  const int n = i + sy * j + sz * k;
+  const int csy = F.nx, csz = F.nx * F.ny;
+  const int c0 = (i - 1) + csy * (j - 1) + csz * (k - 1);  // cell (i-1, j-1, k-1)
+  const bool lo_ok[3] = {i > 0, j > 0, k > 0};
+  const bool hi_ok[3] = {i < F.nx, j < F.ny, k < F.nz};
   float sig[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
-    const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
-    const bool ok = ci >= 0 && cj >= 0 && ck >= 0 && ci < F.nx && cj < F.ny && ck < F.nz;
-    sig[s] = ok ? F.sig[cell_index(F.nx, F.ny, ci, cj, ck)] : 0.f;
+    const bool ok = ((s & 1) ? hi_ok[0] : lo_ok[0]) && ((s & 2) ? hi_ok[1] : lo_ok[1]) &&
+                    ((s & 4) ? hi_ok[2] : lo_ok[2]);
+    sig[s] = ok ? F.sig[c0 + (s & 1) + ((s >> 1) & 1) * csy + ((s >> 2) & 1) * csz] : 0.f;
   }
+  const float4 oa = off_at<JIT>(F, n);
   F3 f = {0.f, 0.f, 0.f};
-  const float4 oa = node_off(F, n);
-  node_cell_faces<0>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<1>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<2>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<3>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<4>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<5>(F, n, oa, i, j, k, sig, f);
-  node_cell_faces<6>(F, n, oa, i, j, k, sig, f);
+  node_faces2<JIT, 0>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 1>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 2>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 3>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 4>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 5>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+  node_faces2<JIT, 6>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
   const float hm = h / (24.f * F.mn[n]);
   const float u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
   float u1 = u0 + hm * f.x, v1 = v0 + hm * f.y, w1 = w0 + hm * f.z;
@@ -223,18 +238,20 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   F.wb[n] = 0.5f * (w0 + w1);
 }
 
-__device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars *S, long long c) {
-  if (c >= F.nc || !S->next_active) return;
+template <bool JIT>
+__device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if (i >= F.nx || j >= F.ny || k >= F.nz || !S->next_active) return;
   const float h = S->next_h32;
-  int i, j, k;
-  cell_ijk(c, F.nx, F.ny, i, j, k);
-  long long nid[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) nid[a] = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+  const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
+  const int n0 = i + sy * j + sz * k;
+  const int c = i + F.nx * (j + F.ny * k);
   F3 E[8], ub[8];
-  ref_hex(F, nid, E);
+  ref_hex2<JIT>(F, n0, sy, sz, E);
 #pragma unroll
-  for (int a = 0; a < 8; ++a) ub[a] = {F.ub[nid[a]], F.vb[nid[a]], F.wb[nid[a]]};
+  for (int a = 0; a < 8; ++a) {
+    const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    ub[a] = {F.ub[na], F.vb[na], F.wb[na]};
+  }
   const float work = grad_dot_f(E, ub);
   // compatible energy update; the increment is FP32, the accumulation FP64
   const float de = h * F.sig[c] * work / F.m[c];
@@ -250,8 +267,8 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
 }
 
 // Lagrangian volume of a cell by closure: V_E minus its net swept volume.
-__device__ __forceinline__ float lag_volume(const Fields<float> &F, long long c, int i, int j, int k) {
-  const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+__device__ __forceinline__ float lag_volume(const Fields<float> &F, int c, int i, int j, int k) {
+  const int sy = F.nx, sz = F.nx * F.ny;
   float net = -F.dvx[c] - F.dvy[c] - F.dvz[c];
   if (i + 1 < F.nx) net += F.dvx[c + 1];
   if (j + 1 < F.ny) net += F.dvy[c + sy];
@@ -260,8 +277,8 @@ __device__ __forceinline__ float lag_volume(const Fields<float> &F, long long c,
 }
 
 template <int AX>
-__device__ __forceinline__ void m_face_flux(const Fields<float> &F, DevScalars *S, long long c, int i, int j, int k,
-                                            float rho_c, float *mu, float *ep) {
+__device__ __forceinline__ void m_face_flux(const Fields<float> &F, int c, int i, int j, int k, float rho_c, float *mu,
+                                            float *ep) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const float *dv = AX == 0 ? F.dvx : AX == 1 ? F.dvy : F.dvz;
   if (idx == 0) {
@@ -275,8 +292,8 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, DevScalars *
     rho_d = rho_c;
     e_d = F.e[c];
   } else {
-    const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
-    const long long d = c - stride;
+    const int stride = AX == 0 ? 1 : AX == 1 ? F.nx : F.nx * F.ny;
+    const int d = c - stride;
     const float VL = lag_volume(F, d, AX == 0 ? i - 1 : i, AX == 1 ? j - 1 : j, AX == 2 ? k - 1 : k);
     rho_d = F.m[d] / VL;
     e_d = F.e[d];
@@ -287,27 +304,29 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, DevScalars *
 }
 
 // Lagrangian densities (closure) and donor-cell fluxes of the low faces.
-__device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars *S, long long c) {
-  if (c >= F.nc || !S->next_active) return;
-  int i, j, k;
-  cell_ijk(c, F.nx, F.ny, i, j, k);
+__device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if (i >= F.nx || j >= F.ny || k >= F.nz || !S->next_active) return;
+  const int c = i + F.nx * (j + F.ny * k);
   const float VL = lag_volume(F, c, i, j, k);
   if (!(VL > 0.f)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
   const float rho_c = F.m[c] / VL;
-  m_face_flux<0>(F, S, c, i, j, k, rho_c, F.mux, F.epx);
-  m_face_flux<1>(F, S, c, i, j, k, rho_c, F.muy, F.epy);
-  m_face_flux<2>(F, S, c, i, j, k, rho_c, F.muz, F.epz);
+  m_face_flux<0>(F, c, i, j, k, rho_c, F.mux, F.epx);
+  m_face_flux<1>(F, c, i, j, k, rho_c, F.muy, F.epy);
+  m_face_flux<2>(F, c, i, j, k, rho_c, F.muz, F.epz);
 }
 
 // ---------------------------------------------------------------------------
 // Node remap (FP32)
 // ---------------------------------------------------------------------------
 
+// Dual mass flux along the mesh edge from node (i,j,k) to its +AX
+// neighbour: sum over the (up to four) cells around the edge of
+// (mu_low_face + mu_high_face) / 8.
 template <int AX>
 __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j, int k) {
   const float *mu = AX == 0 ? F.mux : AX == 1 ? F.muy : F.muz;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
-  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+  const int stride = AX == 0 ? 1 : AX == 1 ? F.nx : F.nx * F.ny;
   float psi = 0.f;
 #pragma unroll
   for (int s = 0; s < 4; ++s) {
@@ -316,7 +335,7 @@ __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j
     if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
     if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
     if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
-    const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
+    const int c = ci + F.nx * (cj + F.ny * ck);
     const int hi_idx = (AX == 0 ? ci : AX == 1 ? cj : ck) + 1;
     psi += mu[c] + (hi_idx < n_ax ? mu[c + stride] : 0.f);
   }
@@ -324,17 +343,17 @@ __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j
 }
 
 template <int AX, int SIDE>
-__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, long long n, float &m,
-                                            F3 &p, float &ke) {
+__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, float &m, F3 &p,
+                                            float &ke) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
   if (SIDE == 0 && idx == n_ax) return;
   if (SIDE == 1 && idx == 0) return;
   const float psi = m_edge_psi<AX>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
                                    (SIDE == 1 && AX == 2) ? k - 1 : k);
-  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)(F.nx + 1) : (long long)(F.nx + 1) * (F.ny + 1);
-  const long long lo = SIDE == 0 ? n : n - stride;
-  const long long dn = psi > 0.f ? lo + stride : lo;
+  const int stride = AX == 0 ? 1 : AX == 1 ? (F.nx + 1) : (F.nx + 1) * (F.ny + 1);
+  const int lo = SIDE == 0 ? n : n - stride;
+  const int dn = psi > 0.f ? lo + stride : lo;
   const F3 ud = {F.u[dn], F.v[dn], F.w[dn]};
   const float flux = SIDE == 0 ? psi : -psi;
   m += flux;
@@ -342,16 +361,15 @@ __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j
   ke += flux * 0.5f * dotf(ud, ud);
 }
 
-__device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevScalars *S, long long n) {
-  if (n >= F.nn) return;
+__device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if (i > F.nx || j > F.ny || k > F.nz) return;
+  const int n = i + (F.nx + 1) * (j + (F.ny + 1) * k);
   if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
     F.ub[n] = F.u[n];
     F.vb[n] = F.v[n];
     F.wb[n] = F.w[n];
     return;
   }
-  int i, j, k;
-  node_ijk(n, F.nx, F.ny, i, j, k);
   const float m0 = F.mn[n];
   const F3 u0 = {F.u[n], F.v[n], F.w[n]};
   float m = m0;
@@ -378,17 +396,20 @@ __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevSc
 // Cell remap, EoS, viscosity, CFL dt (FP32; dt reduced as a double)
 // ---------------------------------------------------------------------------
 
-// EoS and viscosity of a cell on the reference mesh; returns its CFL step.
-__device__ __forceinline__ float m_eos_cell(const Fields<float> &F, long long c, int i, int j, int k, float m,
-                                            float e, bool store_all) {
-  long long nid[8];
+// EoS and viscosity of cell (i,j,k) on the reference mesh; returns its CFL
+// step.
+template <bool JIT>
+__device__ __forceinline__ float m_eos_cell(const Fields<float> &F, int c, int i, int j, int k, float m, float e,
+                                            bool store_all) {
+  const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
+  const int n0 = i + sy * j + sz * k;
+  F3 E[8], U[8];
+  ref_hex2<JIT>(F, n0, sy, sz, E);
 #pragma unroll
-  for (int a = 0; a < 8; ++a) nid[a] = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-  F3 E[8];
-  ref_hex(F, nid, E);
-  F3 U[8];
-#pragma unroll
-  for (int a = 0; a < 8; ++a) U[a] = {F.u[nid[a]], F.v[nid[a]], F.w[nid[a]]};
+  for (int a = 0; a < 8; ++a) {
+    const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    U[a] = {F.u[na], F.v[na], F.w[na]};
+  }
   const float dvdt = grad_dot_f(E, U);
   const float V = F.VE[c];
   const float inv_v = 1.f / V;
@@ -416,13 +437,14 @@ __device__ __forceinline__ float m_eos_cell(const Fields<float> &F, long long c,
 }
 
 // Cell remap + EoS + dt; nblk = blocks of this mesh (last-block detection).
-__device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScalars *S, long long c, unsigned nblk) {
+template <bool JIT>
+__device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScalars *S, int i, int j, int k,
+                                                 unsigned nblk) {
   if (!S->next_active) return;  // uniform over the mesh's blocks: S changes only in its last block
   float dtc = INFINITY;
-  if (c < F.nc) {
-    int i, j, k;
-    cell_ijk(c, F.nx, F.ny, i, j, k);
-    const long long sy = F.nx, sz = (long long)F.nx * F.ny;
+  if (i < F.nx && j < F.ny && k < F.nz) {
+    const int sy = F.nx, sz = F.nx * F.ny;
+    const int c = i + sy * j + sz * k;
     float dm = -F.mux[c] - F.muy[c] - F.muz[c];
     float de = -F.epx[c] - F.epy[c] - F.epz[c];
     if (i + 1 < F.nx) { dm += F.mux[c + 1]; de += F.epx[c + 1]; }
@@ -432,19 +454,21 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
     const float m1 = m0 + dm;
     float ie = m0 * F.e[c] + de;
     if (F.ke_fix) {
+      const int nsy = F.nx + 1, nsz = (F.nx + 1) * (F.ny + 1);
+      const int n0 = i + nsy * j + nsz * k;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
         const float share = ((ni == 0 || ni == F.nx) ? 1.f : 0.5f) * ((nj == 0 || nj == F.ny) ? 1.f : 0.5f) *
                             ((nk == 0 || nk == F.nz) ? 1.f : 0.5f);
-        ie += F.dke[node_index(F.nx, F.ny, ni, nj, nk)] * share;
+        ie += F.dke[n0 + (a & 1) + ((a >> 1) & 1) * nsy + ((a >> 2) & 1) * nsz] * share;
       }
     }
     if (!(m1 > 0.f)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
     const float e1 = ie / m1;
     F.m[c] = m1;
     F.e[c] = e1;
-    const float d = m_eos_cell(F, c, i, j, k, m1, e1, false);
+    const float d = m_eos_cell<JIT>(F, c, i, j, k, m1, e1, false);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
   block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, 0.0, nblk);
@@ -452,53 +476,66 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
 
 // EoS/viscosity/dt without a remap: kDtInit / kDtPropose, or no dt at all
 // (mode < 0: only refresh the derived fields p, q, cs, vol, rho).
-__global__ void __launch_bounds__(kBlock, 4) k_m_eos(Fields<float> F, DevScalars *S, int mode) {
+template <bool JIT>
+__device__ __forceinline__ void m_eos_body(const Fields<float> &F, DevScalars *S, int i, int j, int k, int mode,
+                                           unsigned nblk) {
   if (mode >= 0 && S->status != 0) return;
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   float dtc = INFINITY;
-  if (c < F.nc) {
-    int i, j, k;
-    cell_ijk(c, F.nx, F.ny, i, j, k);
-    const float d = m_eos_cell(F, c, i, j, k, F.m[c], F.e[c], true);
+  if (i < F.nx && j < F.ny && k < F.nz) {
+    const int c = i + F.nx * (j + F.ny * k);
+    const float d = m_eos_cell<JIT>(F, c, i, j, k, F.m[c], F.e[c], true);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
-  if (mode >= 0) block_min_dt32_and_finalize(F, S, dtc, mode, 0.0, gridDim.x);
+  if (mode >= 0) block_min_dt32_and_finalize(F, S, dtc, mode, 0.0, nblk);
 }
 
-// Single-mesh kernels.
-__global__ void __launch_bounds__(kBlock) k_m_nodes(Fields<float> F, DevScalars *S) {
-  m_nodes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
-}
-__global__ void __launch_bounds__(kBlock) k_m_cells(Fields<float> F, DevScalars *S) {
-  m_cells_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
-}
-__global__ void __launch_bounds__(kBlock) k_m_fluxes(Fields<float> F, DevScalars *S) {
-  m_fluxes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
-}
-__global__ void __launch_bounds__(kBlock) k_m_remap_nodes(Fields<float> F, DevScalars *S) {
-  m_remap_nodes_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x);
-}
-__global__ void __launch_bounds__(kBlock, 4) k_m_remap_eos(Fields<float> F, DevScalars *S) {
-  m_remap_eos_body(F, S, blockIdx.x * (long long)kBlock + threadIdx.x, gridDim.x);
+// ---------------------------------------------------------------------------
+// Kernels: 32 x 8 thread blocks; single mesh (3D grid) and batched (table)
+// ---------------------------------------------------------------------------
+
+constexpr int kTileX = 32, kTileY = 8;
+static_assert(kTileX * kTileY == kBlock, "tile must match the block size");
+
+template <bool JIT>
+__device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevScalars *S, int i, int j, int k,
+                                         unsigned nblk, int mode) {
+  switch (kid) {
+    case kMixNodes: m_nodes_body<JIT>(F, S, i, j, k); break;
+    case kMixCells: m_cells_body<JIT>(F, S, i, j, k); break;
+    case kMixFluxes: m_fluxes_body(F, S, i, j, k); break;
+    case kMixRemapNodes: m_remap_nodes_body(F, S, i, j, k); break;
+    case kMixRemapEos: m_remap_eos_body<JIT>(F, S, i, j, k, nblk); break;
+    case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
+    default: break;
+  }
 }
 
-// Batched kernels: one launch covers every mesh of a batch.  Block b works
-// on mesh tab[b].x, local block tab[b].y; the mesh's descriptor is staged in
-// shared memory once per block.
+// Blocks per SM the register budget is held to, per kernel.
+__host__ __device__ constexpr int min_blocks(int kid) {
+  return (kid == kMixRemapEos || kid == kMixEos) ? 4 : kid == kMixCells ? 3 : 1;
+}
+
+template <int KID, bool JIT>
+__global__ void __launch_bounds__(kBlock, min_blocks(KID)) k_m(Fields<float> F, DevScalars *S, int mode) {
+  const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
+  run_body<JIT>(KID, F, S, blockIdx.x * kTileX + threadIdx.x, blockIdx.y * kTileY + threadIdx.y, blockIdx.z, nblk,
+                mode);
+}
+
+// Batched: block b works on mesh tab[b].x, tile (tab[b].y, tab[b].z) of
+// plane tab[b].w; the mesh's descriptor is staged in shared memory.
 template <int KID>
-__global__ void __launch_bounds__(kBlock, KID == kMixRemapEos ? 4 : 1) kb_m(const BatchItem *items, const int2 *tab) {
+__global__ void __launch_bounds__(kBlock, min_blocks(KID)) kb_m(const BatchItem *items, const int4 *tab) {
   __shared__ BatchItem it;
-  const int2 t = tab[blockIdx.x];
+  const int4 t = tab[blockIdx.x];
+  const int tid = threadIdx.x + kTileX * threadIdx.y;
   const int *src = reinterpret_cast<const int *>(items + t.x);
   int *dst = reinterpret_cast<int *>(&it);
-  for (int w = threadIdx.x; w < (int)(sizeof(BatchItem) / sizeof(int)); w += kBlock) dst[w] = src[w];
+  for (int w = tid; w < (int)(sizeof(BatchItem) / sizeof(int)); w += kBlock) dst[w] = src[w];
   __syncthreads();
-  const long long u = (long long)t.y * kBlock + threadIdx.x;
-  if constexpr (KID == kMixNodes) m_nodes_body(it.F, it.S, u);
-  if constexpr (KID == kMixCells) m_cells_body(it.F, it.S, u);
-  if constexpr (KID == kMixFluxes) m_fluxes_body(it.F, it.S, u);
-  if constexpr (KID == kMixRemapNodes) m_remap_nodes_body(it.F, it.S, u);
-  if constexpr (KID == kMixRemapEos) m_remap_eos_body(it.F, it.S, u, it.nblk_cell);
+  const int i = t.y * kTileX + threadIdx.x, j = t.z * kTileY + threadIdx.y, k = t.w;
+  if (it.F.off4) run_body<true>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
+  else run_body<false>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
 }
 
 // Per mesh of a batch: t_end = inf, cycle_limit = cycle + cycles, decide.
@@ -519,15 +556,47 @@ __global__ void kb_gather(const BatchItem *items, int n, BatchStatus *out) {
   out[i] = {S->t, S->dt, S->cycle, S->status};
 }
 
-static inline unsigned grid_m(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+// Grid of 32 x 8 tiles over an (ni, nj, nk) box of nodes or cells.
+dim3 tile_grid(int ni, int nj, int nk) {
+  return dim3((unsigned)((ni + kTileX - 1) / kTileX), (unsigned)((nj + kTileY - 1) / kTileY), (unsigned)nk);
+}
 
-void launch_m_batch(int kid, const BatchItem *items, const int2 *tab, unsigned nblocks, cudaStream_t st) {
+void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
+                         long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st) {
+  k_m_init_cells<<<(unsigned)((F.nc + kBlock - 1) / kBlock), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e, VE,
+                                                                              LE);
+}
+
+template <int KID>
+static void launch_one(const Fields<float> &F, DevScalars *S, int mode, cudaStream_t st) {
+  const bool node = KID == kMixNodes || KID == kMixRemapNodes;
+  const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1) : tile_grid(F.nx, F.ny, F.nz);
+  const dim3 b(kTileX, kTileY);
+  if (F.off4) k_m<KID, true><<<g, b, 0, st>>>(F, S, mode);
+  else k_m<KID, false><<<g, b, 0, st>>>(F, S, mode);
+}
+
+void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
+  (void)dt_override;  // the mixed path always steps with the on-device dt
   switch (kid) {
-    case kMixNodes: kb_m<kMixNodes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
-    case kMixCells: kb_m<kMixCells><<<nblocks, kBlock, 0, st>>>(items, tab); break;
-    case kMixFluxes: kb_m<kMixFluxes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
-    case kMixRemapNodes: kb_m<kMixRemapNodes><<<nblocks, kBlock, 0, st>>>(items, tab); break;
-    case kMixRemapEos: kb_m<kMixRemapEos><<<nblocks, kBlock, 0, st>>>(items, tab); break;
+    case kMixNodes: launch_one<kMixNodes>(F, S, mode, st); break;
+    case kMixCells: launch_one<kMixCells>(F, S, mode, st); break;
+    case kMixFluxes: launch_one<kMixFluxes>(F, S, mode, st); break;
+    case kMixRemapNodes: launch_one<kMixRemapNodes>(F, S, mode, st); break;
+    case kMixRemapEos: launch_one<kMixRemapEos>(F, S, mode, st); break;
+    case kMixEos: launch_one<kMixEos>(F, S, mode, st); break;
+    default: break;
+  }
+}
+
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st) {
+  const dim3 b(kTileX, kTileY);
+  switch (kid) {
+    case kMixNodes: kb_m<kMixNodes><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixCells: kb_m<kMixCells><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixFluxes: kb_m<kMixFluxes><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapNodes: kb_m<kMixRemapNodes><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapEos: kb_m<kMixRemapEos><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;
   }
 }
@@ -538,23 +607,6 @@ void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaSt
 
 void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st) {
   kb_gather<<<(n + 127) / 128, 128, 0, st>>>(items, n, out);
-}
-
-void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
-                         long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st) {
-  k_m_init_cells<<<grid_m(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e, VE, LE);
-}
-
-void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
-  switch (kid) {
-    case kMixNodes: k_m_nodes<<<grid_m(F.nn), kBlock, 0, st>>>(F, S); break;
-    case kMixCells: k_m_cells<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kMixFluxes: k_m_fluxes<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kMixRemapNodes: k_m_remap_nodes<<<grid_m(F.nn), kBlock, 0, st>>>(F, S); break;
-    case kMixRemapEos: k_m_remap_eos<<<grid_m(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kMixEos: k_m_eos<<<grid_m(F.nc), kBlock, 0, st>>>(F, S, mode); break;
-    default: break;
-  }
 }
 
 }  // namespace sale

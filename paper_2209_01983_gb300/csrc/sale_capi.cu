@@ -969,7 +969,7 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
 // ---------------------------------------------------------------------------
 
 namespace sale {
-void launch_m_batch(int kid, const BatchItem *items, const int2 *tab, unsigned nblocks, cudaStream_t st);
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st);
 void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st);
 void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st);
 }  // namespace sale
@@ -979,31 +979,40 @@ struct sale_batch {
   cudaStream_t stream;
   std::vector<sale_state *> st;     // one state per mesh, carved from the batch buffer
   BatchItem *items[2];              // per velocity-buffer parity
-  int2 *tab_cell, *tab_node;        // block -> (mesh, local block)
+  int4 *tab_cell, *tab_node;        // block -> (mesh, tile x, tile y, plane)
   unsigned nb_cell, nb_node;
   BatchStatus *status;              // device gather area
   std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
   std::map<long long, cudaGraphExec_t> graphs;
 };
 
-static unsigned blocks_of(long long units) { return (unsigned)((units + kBlock - 1) / kBlock); }
+// 32 x 8 tiles per plane, as the mixed kernels lay threads out.
+static unsigned tiles_of(int ni, int nj, int nk) {
+  return (unsigned)(((ni + 31) / 32) * ((nj + 7) / 8) * nk);
+}
+static unsigned cell_tiles(const sale_mesh_desc &d) { return tiles_of(d.nx, d.ny, d.nz); }
+static unsigned node_tiles(const sale_mesh_desc &d) { return tiles_of(d.nx + 1, d.ny + 1, d.nz + 1); }
+static void append_tiles(std::vector<int4> &tab, int mesh, int ni, int nj, int nk) {
+  for (int k = 0; k < nk; ++k)
+    for (int by = 0; by < (nj + 7) / 8; ++by)
+      for (int bx = 0; bx < (ni + 31) / 32; ++bx) tab.push_back(make_int4(mesh, bx, by, k));
+}
 
 // Layout of a batch buffer: header (descriptors, block tables, status
 // gather area) then one state region per mesh.
 static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, size_t *state_off, size_t *hdr_parts) {
   long long nbc = 0, nbn = 0;
   for (int i = 0; i < n; ++i) {
-    const sale_mesh_desc &d = meshes[i];
-    nbc += blocks_of((long long)d.nx * d.ny * d.nz);
-    nbn += blocks_of((long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1));
+    nbc += cell_tiles(meshes[i]);
+    nbn += node_tiles(meshes[i]);
   }
   size_t off = 0;
   hdr_parts[0] = off;  // descriptors, two parities
   off = align_up(off + 2 * sizeof(BatchItem) * n);
   hdr_parts[1] = off;  // cell block table
-  off = align_up(off + sizeof(int2) * nbc);
+  off = align_up(off + sizeof(int4) * nbc);
   hdr_parts[2] = off;  // node block table
-  off = align_up(off + sizeof(int2) * nbn);
+  off = align_up(off + sizeof(int4) * nbn);
   hdr_parts[3] = off;  // status gather
   off = align_up(off + sizeof(BatchStatus) * n);
   for (int i = 0; i < n; ++i) {
@@ -1043,7 +1052,7 @@ static int upload_batch_items(sale_batch *b) {
       h[i].F = fields_t<float>(st);
       st->upar = keep;
       h[i].S = st->S;
-      h[i].nblk_cell = blocks_of(st->nc);
+      h[i].nblk_cell = tiles_of(st->nx, st->ny, st->nz);
       h[i].pad = 0;
     }
     CUDA_TRY(cudaMemcpyAsync(b->items[rel], h.data(), sizeof(BatchItem) * b->n, cudaMemcpyHostToDevice, b->stream));
@@ -1080,8 +1089,8 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   b->stream = (cudaStream_t)cuda_stream;
   b->items[0] = (BatchItem *)(base + parts[0]);
   b->items[1] = b->items[0] + n;
-  b->tab_cell = (int2 *)(base + parts[1]);
-  b->tab_node = (int2 *)(base + parts[2]);
+  b->tab_cell = (int4 *)(base + parts[1]);
+  b->tab_node = (int4 *)(base + parts[2]);
   b->status = (BatchStatus *)(base + parts[3]);
   for (int i = 0; i < n; ++i) {
     sale_mesh *m = nullptr;
@@ -1097,11 +1106,12 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
     b->st.push_back(sti);
   }
   // block tables (meshes in order) and descriptors for both parities
-  std::vector<int2> tc, tn;
+  std::vector<int4> tc, tn;
   try {
     for (int i = 0; i < n; ++i) {
-      for (unsigned k = 0; k < blocks_of(b->st[i]->nc); ++k) tc.push_back(make_int2(i, (int)k));
-      for (unsigned k = 0; k < blocks_of(b->st[i]->nn); ++k) tn.push_back(make_int2(i, (int)k));
+      const sale_mesh_desc &d = meshes[i];
+      append_tiles(tc, i, d.nx, d.ny, d.nz);
+      append_tiles(tn, i, d.nx + 1, d.ny + 1, d.nz + 1);
     }
   } catch (...) {
     sale_batch_destroy(b);
@@ -1109,9 +1119,10 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   }
   b->nb_cell = (unsigned)tc.size();
   b->nb_node = (unsigned)tn.size();
-  cudaError_t e = cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int2) * tc.size(), cudaMemcpyHostToDevice, b->stream);
+  cudaError_t e = cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, b->stream);
   if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int2) * tn.size(), cudaMemcpyHostToDevice, b->stream);
+    e = cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, b->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // tc, tn die here
   if (e != cudaSuccess) {
     sale_batch_destroy(b);
     return cuda_fail(e, "sale_batch_create: upload");

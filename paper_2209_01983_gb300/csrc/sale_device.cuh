@@ -122,13 +122,14 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
                                                             double dt_override, unsigned nblk) {
   __shared__ float smin32[kBlock / 32];
   __shared__ bool last32;
+  const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   dtc = warp_min_f32(dtc);
-  if ((threadIdx.x & 31) == 0) smin32[threadIdx.x >> 5] = dtc;
+  if ((tid & 31) == 0) smin32[tid >> 5] = dtc;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float v = threadIdx.x < kBlock / 32 ? smin32[threadIdx.x] : INFINITY;
+  if (tid < 32) {
+    float v = tid < kBlock / 32 ? smin32[tid] : INFINITY;
     v = warp_min_f32(v);
-    if (threadIdx.x == 0) {
+    if (tid == 0) {
       atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong((double)v));
       __threadfence();
       const unsigned int done = atomicAdd(&S->blocks_done, 1u);
@@ -136,7 +137,7 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
     }
   }
   __syncthreads();
-  if (!last32 || threadIdx.x != 0) return;
+  if (!last32 || tid != 0) return;
   __threadfence();
   volatile DevScalars *VS = S;
   const double dtcfl = __longlong_as_double((long long)atomicAdd(&S->dtmin_bits, 0ull));
