@@ -47,7 +47,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
-    ap.add_argument("--config", default="large", choices=("large", "batch"))
+    ap.add_argument("--config", default="large", choices=("large", "batch", "precision"))
+    ap.add_argument("--t-end", type=float, default=0.5)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--unbatched-steps", type=int, default=16)
     return ap.parse_args()
@@ -420,12 +421,80 @@ def batch_arm(args):
     return 0
 
 
+def precision_arm(args):
+    """Sedov octant at 256^3 to t = 0.5 in FP32-mixed and FP64: throughput of
+    both, the mixed run's relative L1 error in density and energy against
+    FP64, conservation drift, and both downsampled (conservative 4^3 block
+    averages) against the CPU oracle at 64^3."""
+    import numpy as np
+    import torch
+
+    from paper_2209_01983_gb300 import inputs, sale
+
+    n, t_end = args.n, args.t_end
+    md, pd = inputs.sedov_octant(n)
+    out = {}
+    for prec, code in (("fp32_mixed", sale.SALE_FP32_MIXED), ("fp64", sale.SALE_FP64)):
+        st = sale.State(md, pd, precision=code)
+        d0 = st.diagnostics()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(st.stream)
+        cycles = st.run_to_time(t_end=t_end, remap_every=1)
+        ev1.record(st.stream)
+        ev1.synchronize()
+        d = st.diagnostics()
+        ms = ev0.elapsed_time(ev1)
+        out[prec] = {"cycles": cycles, "ms": ms, "value": md.ncell * cycles / (ms * 1e-3),
+                     "mass_drift": (d["mass"] - d0["mass"]) / d0["mass"],
+                     "energy_drift": (d["etot"] - d0["etot"]) / d0["etot"],
+                     "fields": {f: st.field(f) for f in ("m", "e", "rho", "vol")}}
+        st.close()
+        del st
+        torch.cuda.empty_cache()
+    a, b = out["fp32_mixed"]["fields"], out["fp64"]["fields"]
+    w = b["vol"]
+    l1 = {f: float(np.sum(np.abs(a[f] - b[f]) * w) / np.sum(np.abs(b[f]) * w)) for f in ("rho", "e")}
+
+    def down(fl, k=4):  # conservative block averages: rho = sum m / sum V, e = sum m e / sum m
+        nn = n // k
+        sh = (nn, k, nn, k, nn, k)
+        m = fl["m"].reshape(n, n, n).reshape(sh).sum(axis=(1, 3, 5))
+        me = (fl["m"] * fl["e"]).reshape(n, n, n).reshape(sh).sum(axis=(1, 3, 5))
+        v = fl["vol"].reshape(n, n, n).reshape(sh).sum(axis=(1, 3, 5))
+        return {"rho": (m / v).ravel(), "e": (me / m).ravel()}
+
+    line = {"metric": METRIC, "config": {"workload": f"sedov-octant-{n}^3-to-t{t_end}-ale-every-cycle",
+                                         "cells": md.ncell},
+            "fp32_mixed": {k: v for k, v in out["fp32_mixed"].items() if k != "fields"},
+            "fp64": {k: v for k, v in out["fp64"].items() if k != "fields"},
+            "mixed_vs_fp64_l1_rel": l1,
+            "speedup_mixed_vs_fp64": out["fp32_mixed"]["value"] / out["fp64"]["value"]}
+    if not args.no_cpu_baseline and n % 4 == 0:
+        import oracle
+        oracle.build()
+        mo, po = inputs.sedov_octant(n // 4)
+        o = oracle.Oracle.from_problem(mo, po)
+        t0 = time.perf_counter()
+        rc, oc = o.run(t_end=t_end, remap_every=1)
+        secs = time.perf_counter() - t0
+        ref = {"rho": o.field("rho"), "e": o.field("e")}
+        wo = o.field("vol")
+        line["downsampled_vs_oracle"] = {
+            "oracle": f"{n // 4}^3 to t={t_end}, {oc} cycles, {secs:.1f} s on one core",
+            **{prec: {f: float(np.sum(np.abs(down(out[prec]["fields"])[f] - ref[f]) * wo) / np.sum(np.abs(ref[f]) * wo))
+                      for f in ("rho", "e")} for prec in ("fp32_mixed", "fp64")}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return reference_arm(args)
     if args.config == "batch":
         return batch_arm(args)
+    if args.config == "precision":
+        return precision_arm(args)
     return gpu_arm(args)
 
 

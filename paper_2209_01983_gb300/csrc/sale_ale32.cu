@@ -43,6 +43,63 @@ __device__ __forceinline__ F3 crossf(F3 a, F3 b) {
 }
 __device__ __forceinline__ float dotf(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// ---------------------------------------------------------------------------
+// Float-float arithmetic for the conserved cell quantities
+// ---------------------------------------------------------------------------
+// Cell mass and specific internal energy are held as unevaluated sums
+// hi + lo of two FP32 numbers (about 48 significant bits).  Plain FP32
+// accumulation of the small per-cycle increments these quantities receive
+// drifts systematically (round-to-nearest of a slowly varying increment is
+// biased); FP64 hardware runs at 1/64 of the FP32 rate on GB300, so the
+// extra precision comes from error-free transformations on the FP32 pipe:
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2), FastTwoSum and TwoProduct via FMA
+// (Dekker, "A floating-point technique for extending the available
+// precision", Numer. Math. 18, 1971).  The _rn intrinsics keep the compiler
+// from contracting or reordering these sequences.
+struct DF {
+  float hi, lo;
+};
+
+__device__ __forceinline__ DF two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bp = __fsub_rn(s, a);
+  const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bp)), __fsub_rn(b, bp));
+  return {s, e};
+}
+
+// Requires |a| >= |b| (or a = 0).
+__device__ __forceinline__ DF fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ DF df_add_f(DF a, float b) {
+  const DF s = two_sum(a.hi, b);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, a.lo));
+}
+
+__device__ __forceinline__ DF df_add(DF a, DF b) {
+  const DF s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ DF df_mul(DF a, DF b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ DF df_div(DF a, DF b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const DF p = df_mul(b, DF{q1, 0.f});
+  const DF r = df_add(a, DF{-p.hi, -p.lo});
+  return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
+__device__ __forceinline__ DF load_df(const float *hi, const float *lo, int c) { return {hi[c], lo[c]}; }
+
 // Jitter offset of a node (one 16-byte load: x, y, z, unused); on an
 // unjittered mesh (JIT = false) the offsets are zero and the geometry below
 // folds to constants.
@@ -144,8 +201,11 @@ __global__ void __launch_bounds__(kBlock) k_m_init_cells(Fields<float> F, DevSca
   const double m = rho0[c] * V;
   double e = p0[c] / ((F.gamma - 1.0) * rho0[c]);
   if (c == dep_cell) e = dep_e / m;
+  // float-float split: hi = nearest FP32, lo = nearest FP32 to the rest
   F.m[c] = (float)m;
+  F.mlo[c] = (float)(m - (double)(float)m);
   F.e[c] = (float)e;
+  F.elo[c] = (float)(e - (double)(float)e);
   VE[c] = (float)V;
   LE[c] = (float)(V / sqrt(hex_max_face_area2(X)));
 }
@@ -253,9 +313,12 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
     ub[a] = {F.ub[na], F.vb[na], F.wb[na]};
   }
   const float work = grad_dot_f(E, ub);
-  // compatible energy update; the increment is FP32, the accumulation FP64
+  // compatible energy update; the increment is FP32, the accumulation
+  // float-float
   const float de = h * F.sig[c] * work / F.m[c];
-  F.e[c] = (float)((double)F.e[c] - (double)de);
+  const DF e1 = df_add_f(load_df(F.e, F.elo, c), -de);
+  F.e[c] = e1.hi;
+  F.elo[c] = e1.lo;
   F3 Dd[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) Dd[a] = h * ub[a];
@@ -445,14 +508,19 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
   if (i < F.nx && j < F.ny && k < F.nz) {
     const int sy = F.nx, sz = F.nx * F.ny;
     const int c = i + sy * j + sz * k;
-    float dm = -F.mux[c] - F.muy[c] - F.muz[c];
-    float de = -F.epx[c] - F.epy[c] - F.epz[c];
-    if (i + 1 < F.nx) { dm += F.mux[c + 1]; de += F.epx[c + 1]; }
-    if (j + 1 < F.ny) { dm += F.muy[c + sy]; de += F.epy[c + sy]; }
-    if (k + 1 < F.nz) { dm += F.muz[c + sz]; de += F.epz[c + sz]; }
-    const float m0 = F.m[c];
-    const float m1 = m0 + dm;
-    float ie = m0 * F.e[c] + de;
+    // float-float: every flux is added to the conserved quantities on its
+    // own, so what leaves one cell is exactly what the next one receives
+    const DF m0 = load_df(F.m, F.mlo, c);
+    DF m1 = df_add_f(m0, -F.mux[c]);
+    m1 = df_add_f(m1, -F.muy[c]);
+    m1 = df_add_f(m1, -F.muz[c]);
+    DF ie = df_mul(m0, load_df(F.e, F.elo, c));
+    ie = df_add_f(ie, -F.epx[c]);
+    ie = df_add_f(ie, -F.epy[c]);
+    ie = df_add_f(ie, -F.epz[c]);
+    if (i + 1 < F.nx) { m1 = df_add_f(m1, F.mux[c + 1]); ie = df_add_f(ie, F.epx[c + 1]); }
+    if (j + 1 < F.ny) { m1 = df_add_f(m1, F.muy[c + sy]); ie = df_add_f(ie, F.epy[c + sy]); }
+    if (k + 1 < F.nz) { m1 = df_add_f(m1, F.muz[c + sz]); ie = df_add_f(ie, F.epz[c + sz]); }
     if (F.ke_fix) {
       const int nsy = F.nx + 1, nsz = (F.nx + 1) * (F.ny + 1);
       const int n0 = i + nsy * j + nsz * k;
@@ -461,14 +529,16 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
         const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
         const float share = ((ni == 0 || ni == F.nx) ? 1.f : 0.5f) * ((nj == 0 || nj == F.ny) ? 1.f : 0.5f) *
                             ((nk == 0 || nk == F.nz) ? 1.f : 0.5f);
-        ie += F.dke[n0 + (a & 1) + ((a >> 1) & 1) * nsy + ((a >> 2) & 1) * nsz] * share;
+        ie = df_add_f(ie, F.dke[n0 + (a & 1) + ((a >> 1) & 1) * nsy + ((a >> 2) & 1) * nsz] * share);
       }
     }
-    if (!(m1 > 0.f)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
-    const float e1 = ie / m1;
-    F.m[c] = m1;
-    F.e[c] = e1;
-    const float d = m_eos_cell<JIT>(F, c, i, j, k, m1, e1, false);
+    if (!(m1.hi > 0.f)) set_status(S, m1.hi != m1.hi ? SALE_ENAN : SALE_ENEGVOL);
+    const DF e1 = df_div(ie, m1);
+    F.m[c] = m1.hi;
+    F.mlo[c] = m1.lo;
+    F.e[c] = e1.hi;
+    F.elo[c] = e1.lo;
+    const float d = m_eos_cell<JIT>(F, c, i, j, k, m1.hi, e1.hi, false);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
   block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, 0.0, nblk);

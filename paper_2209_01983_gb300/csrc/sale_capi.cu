@@ -217,6 +217,7 @@ struct sale_state {
   void *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
   double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
   float4 *off4;                          // FP32-mixed path: jitter offsets
+  float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
   float h32[3];
   int xpar, upar;
@@ -266,7 +267,7 @@ static size_t carve(sale_state *st, char *base) {
   }
   st->geoG = st->geoVE = st->geoLE = st->geoTE = nullptr;
   st->off4 = nullptr;
-  st->VE32 = st->LE32 = nullptr;
+  st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
     st->geoG = (double *)cv.take(sizeof(double) * 29 * nc);
@@ -279,6 +280,8 @@ static size_t carve(sale_state *st, char *base) {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
     st->LE32 = (float *)cv.take(sizeof(float) * nc);
+    st->mlo = (float *)cv.take(sizeof(float) * nc);
+    st->elo = (float *)cv.take(sizeof(float) * nc);
   }
   return align_up(cv.off);
 }
@@ -334,6 +337,8 @@ static Fields<R> fields_t(const sale_state *st) {
     F.VE = (const R *)st->VE32;
     F.LE = (const R *)st->LE32;
   }
+  F.mlo = (R *)st->mlo;
+  F.elo = (R *)st->elo;
   F.hx = st->h32[0];
   F.hy = st->h32[1];
   F.hz = st->h32[2];
@@ -915,6 +920,18 @@ extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *
     CUDA_TRY(cudaMemcpyAsync(tmp, p, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));
     for (size_t i = 0; i < n; ++i) host_out[i] = (double)tmp[i];  // ascending: never overwrites unread floats
+    const float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : nullptr;
+    if (lo) {  // float-float cell quantity: add the low part
+      std::vector<float> low;
+      try {
+        low.resize(n);
+      } catch (...) {
+        return fail(SALE_ENOMEM, "sale_copy_field: out of host memory");
+      }
+      CUDA_TRY(cudaMemcpyAsync(low.data(), lo, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
+      CUDA_TRY(cudaStreamSynchronize(st->stream));
+      for (size_t i = 0; i < n; ++i) host_out[i] += (double)low[i];
+    }
   }
   DevScalars h;
   int rc = sync_scalars(st, &h);
@@ -943,7 +960,13 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
     }
     for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_in[i];
     CUDA_TRY(cudaMemcpyAsync(p, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
-    CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp dies here
+    CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp is rewritten next
+    float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : nullptr;
+    if (lo) {  // float-float cell quantity: low part = rest after the FP32 high part
+      for (size_t i = 0; i < n; ++i) tmp[i] = (float)(host_in[i] - (double)(float)host_in[i]);
+      CUDA_TRY(cudaMemcpyAsync(lo, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
+      CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp dies here
+    }
   }
   if (!strcmp(name, "x") || !strcmp(name, "y") || !strcmp(name, "z")) st->x_is_ref = false;
   return SALE_OK;

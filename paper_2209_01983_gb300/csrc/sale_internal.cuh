@@ -88,6 +88,7 @@ struct Fields {
   R *mn;                       // node mass
   R *dke;                      // kinetic energy lost by the node remap
   R *m, *e;                    // cell mass, specific internal energy
+  R *mlo, *elo;                // FP32-mixed path: low parts of m and e (float-float); null otherwise
   R *sig;                      // p + q
   R *rho, *p, *q, *cs, *vol;   // derived cell fields
   R *mux, *muy, *muz;          // mass flux through the low x/y/z face

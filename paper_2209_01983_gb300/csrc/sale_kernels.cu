@@ -401,9 +401,13 @@ __global__ void __launch_bounds__(kBlock) k_diag_partial(Fields<R> F, double *pa
   double acc[kDiagQ] = {0, 0, 0, 0, 0, 0};
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < F.nc; c += stride) {
-    const double m = (double)F.m[c];
+    double m = (double)F.m[c], e = (double)F.e[c];
+    if (F.mlo) {  // float-float cell quantities of the mixed path
+      m += (double)F.mlo[c];
+      e += (double)F.elo[c];
+    }
     acc[0] += m;
-    acc[4] += m * (double)F.e[c];
+    acc[4] += m * e;
   }
   for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < F.nn; n += stride) {
     const double m = (double)F.mn[n], u = (double)F.u[n], v = (double)F.v[n], w = (double)F.w[n];

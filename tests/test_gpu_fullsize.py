@@ -1,0 +1,143 @@
+"""Parity at full size, in the launch configuration bench.py times.
+
+The benchmark workload is the 384^3 jittered Sedov octant advanced with
+Eulerian cycles (FP64 path, CUDA-graph replays).  The oracle cannot run
+that mesh, but one cycle of a cell depends only on a few cells around it:
+the oracle is restarted on an 11^3-cell sub-box cut from the GPU state
+around each sampled cell, advanced one cycle with the GPU's time step, and
+the centre cell and its eight nodes are compared with the GPU's next state.
+The cut faces of the sub-box are free (their error stays within 4 cells of
+the cut in one cycle; the centre is 5 cells in), domain walls stay walls.
+
+The Sedov 64^3 configuration (energy 0.851/8 in the origin cell, to t = 1)
+is checked for parity with the oracle after 100 cycles and for its physics
+at t = 1: shock radius, conservation, axis symmetry.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from conftest import read_golden
+from paper_2209_01983_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+TOL = 1e-10
+R = 5  # sub-box half width in cells
+
+
+@pytest.fixture(scope="module")
+def sale():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2209_01983_gb300 import sale as s
+    return s
+
+
+def node_box(a, n, lo, hi):
+    """Sub-array of a node field (flat, x fastest) over node ranges."""
+    return np.ascontiguousarray(a.reshape(n[2] + 1, n[1] + 1, n[0] + 1)[lo[2]:hi[2] + 1, lo[1]:hi[1] + 1,
+                                                                        lo[0]:hi[0] + 1]).ravel()
+
+
+def cell_box(a, n, lo, hi):
+    return np.ascontiguousarray(a.reshape(n[2], n[1], n[0])[lo[2]:hi[2], lo[1]:hi[1], lo[0]:hi[0]]).ravel()
+
+
+@pytest.mark.slow
+def test_sampled_parity_at_384_cubed(sale):
+    md, pd = inputs.sedov_octant(384, jitter=0.1)
+    n = (md.nx, md.ny, md.nz)
+    st = sale.State(md, pd, precision=sale.SALE_FP64)
+    st.run_to_time(max_cycles=40, remap_every=1)  # graph replays, as in bench.py
+    d0 = st.diagnostics()
+    names = ("u", "v", "w", "mn", "m", "e")
+    before = {f: st.field(f) for f in names}
+    xr, yr, zr = inputs.mesh_nodes(md)
+    assert np.array_equal(xr, st.field("xref"))
+    dt = d0["dt"]
+    st.run_to_time(max_cycles=1, remap_every=1)
+    after = {f: st.field(f) for f in names + ("rho", "p", "q")}
+    scales = {f: float(np.max(np.abs(after[f]))) for f in ("m", "e", "rho", "p", "q")}
+    scales["vel"] = max(float(np.max(np.abs(after[f]))) for f in "uvw")
+    # the blast is active near the origin: sample it densely, elsewhere sparsely
+    rng = np.random.default_rng(2209)
+    cells = [(0, 0, 0), (1, 0, 0), (0, 1, 2), (3, 3, 3)]
+    cells += [tuple(rng.integers(0, 14, 3)) for _ in range(14)]
+    cells += [tuple(rng.integers(0, 384, 3)) for _ in range(6)]
+    cells += [(383, 383, 383), (200, 0, 383)]
+    moved = 0
+    for c in cells:
+        lo = [max(0, c[d] - R) for d in range(3)]
+        hi = [min(n[d], c[d] + R + 1) for d in range(3)]
+        sub = tuple(hi[d] - lo[d] for d in range(3))
+        reflect = [1 if lo[d] == 0 else 0 for d in range(3)], [1 if hi[d] == n[d] else 0 for d in range(3)]
+        flags = (reflect[0][0], reflect[1][0], reflect[0][1], reflect[1][1], reflect[0][2], reflect[1][2])
+        nodes = tuple(node_box(a, n, lo, hi) for a in (xr, yr, zr))
+        o = oracle.Oracle(sub[0], sub[1], sub[2], nodes, oracle.params_from(pd, flags))
+        o.check(o.set_state(nodes[0], nodes[1], nodes[2],
+                            *(node_box(before[f], n, lo, hi) for f in ("u", "v", "w", "mn")),
+                            cell_box(before["m"], n, lo, hi), cell_box(before["e"], n, lo, hi),
+                            t=d0["t"], dt_last=dt))
+        o.check(o.lagrange_step(dt))
+        o.check(o.remap_step())
+        lc = tuple(c[d] - lo[d] for d in range(3))
+        ci = lc[0] + sub[0] * (lc[1] + sub[1] * lc[2])
+        gi = c[0] + n[0] * (c[1] + n[1] * c[2])
+        # relative L-infinity: differences against each field's largest value
+        for f in ("m", "e", "rho", "p", "q"):
+            a, b = after[f][gi], o.field(f)[ci]
+            assert abs(a - b) <= TOL * scales[f], (c, f, a, b)
+        vel_scale = scales["vel"]
+        for a8 in range(8):
+            nl = (lc[0] + (a8 & 1), lc[1] + ((a8 >> 1) & 1), lc[2] + ((a8 >> 2) & 1))
+            ng = (c[0] + (a8 & 1), c[1] + ((a8 >> 1) & 1), c[2] + ((a8 >> 2) & 1))
+            li = nl[0] + (sub[0] + 1) * (nl[1] + (sub[1] + 1) * nl[2])
+            gn = ng[0] + (n[0] + 1) * (ng[1] + (n[1] + 1) * ng[2])
+            for f in ("u", "v", "w"):
+                assert abs(after[f][gn] - o.field(f)[li]) <= TOL * max(vel_scale, 1e-300), (c, a8, f)
+            assert abs(after["mn"][gn] - o.field("mn")[li]) <= TOL * o.field("mn")[li], (c, a8)
+        moved += float(np.max(np.abs(o.field("u")))) > 0
+    assert moved >= 10  # most samples sit in the moving region
+
+
+@pytest.mark.slow
+def test_sedov64_parity_100_cycles(sale):
+    md, pd = inputs.sedov_octant(64)
+    st = sale.State(md, pd, precision=sale.SALE_FP64)
+    assert st.run_to_time(max_cycles=100, remap_every=1) == 100
+    o = oracle.Oracle.from_problem(md, pd)
+    rc, n_o = o.run(max_cycles=100, remap_every=1)
+    assert rc == 0 and n_o == 100
+    for f in ("m", "e", "rho", "p", "q", "cs", "mn"):
+        a, b = st.field(f), o.field(f)
+        assert float(np.max(np.abs(a - b)) / np.max(np.abs(b))) <= TOL, f
+    vel = max(float(np.max(np.abs(o.field(f)))) for f in "uvw")
+    for f in "uvw":
+        assert float(np.max(np.abs(st.field(f) - o.field(f)))) <= TOL * vel, f
+
+
+def test_sedov64_to_t1_physics(sale):
+    md, pd = inputs.sedov_octant(64)
+    st = sale.State(md, pd, precision=sale.SALE_FP64)
+    d0 = st.diagnostics()
+    n = st.run_to_time(t_end=1.0, remap_every=1)
+    d = st.diagnostics()
+    assert d["t"] == 1.0 and d["cycle"] == n
+    assert abs(d["mass"] - d0["mass"]) <= 1e-12 * d0["mass"]
+    assert abs(d["etot"] - d0["etot"]) <= 1e-11 * d0["etot"]
+    rho = st.field("rho").reshape(64, 64, 64)
+    for perm in ((0, 2, 1), (2, 1, 0), (1, 0, 2)):
+        assert np.max(np.abs(rho - rho.transpose(perm))) <= 1e-11 * rho.max()
+    h = 1.2 / 64
+    c = (np.arange(64) + 0.5) * h
+    r = np.sqrt(c[None, None, :] ** 2 + c[None, :, None] ** 2 + c[:, None, None] ** 2).ravel()
+    shells = np.floor(r / h).astype(int)
+    prof = np.bincount(shells, weights=rho.ravel()) / np.maximum(np.bincount(shells), 1)
+    r_sim = (np.argmax(prof) + 0.5) * h
+    alpha = read_golden("sedov_alpha.txt")["alpha"]
+    r_exact = (8.0 * pd.e_deposit / alpha) ** 0.2 * 1.0 ** 0.4
+    assert abs(r_sim - r_exact) <= 3 * h, (r_sim, r_exact)
