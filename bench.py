@@ -45,6 +45,7 @@ def parse():
     ap.add_argument("--n", type=int, default=384, help="cells per axis")
     ap.add_argument("--jitter", type=float, default=0.1)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="keep the default 32x8 tiles of the FP32-mixed kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision"))
@@ -169,6 +170,23 @@ def workload_config(args, precision):
 # GPU arm
 # ---------------------------------------------------------------------------
 
+def max_over_ranks(v, dist=None, device="cpu"):
+    """The largest value over all ranks (the slowest rank's time)."""
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([float(v)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replica_rate(ms_local, cells_per_rank, steps, world, dist=None, device="cpu"):
+    """Whole-job rate of N independent replicas: every rank's cells over the
+    slowest rank's time (weak scaling).  Returns (rate, max ms)."""
+    ms = max_over_ranks(ms_local, dist, device)
+    return world * cells_per_rank * steps / (ms * 1e-3), ms
+
+
 # FP32 vector peak: 128 lanes x 2 flop x 152 SMs x 2.07 GHz.
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 
@@ -182,6 +200,11 @@ def measure(args, precision, local, barrier):
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
+    tuning = None
+    if precision == "fp32_mixed" and not args.no_tune:
+        # warm-up part 1: pick the tile shape (ordinary cycles, results unchanged)
+        from paper_2209_01983_gb300 import autotune
+        tuning = autotune.tune_state(st, cycles=16, repeats=2)
     st.run_to_time(max_cycles=args.warmup, remap_every=1)
 
     # ---- timed region: K full cycles, graph replays on the state's stream
@@ -248,7 +271,7 @@ def measure(args, precision, local, barrier):
     d = st.diagnostics()
     return {"st": st, "md": md, "ms": ms, "roofline": roof, "kernels": kernels, "full_cycle": full,
             "gpu_launches": launches, "clocks": clk, "check": {"t": d["t"], "cycle": d["cycle"], "status": d["status"]},
-            "peaks": {"hbm_gbs": peaks["hbm_gbs"], "source": peak_src}}
+            "peaks": {"hbm_gbs": peaks["hbm_gbs"], "source": peak_src}, "tuning": tuning}
 
 
 def e2e_rate(args, res, world):
@@ -295,19 +318,12 @@ def gpu_arm(args):
         if dist is not None:
             dist.barrier()
 
-    def max_over_ranks(v):
-        if dist is None:
-            return v
-        t = torch.tensor([v], device=f"cuda:{local}")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
-
     precisions = ["fp64", "fp32_mixed"] if args.precision == "both" else [args.precision]
     results = {}
     for prec in precisions:
         res = measure(args, prec, local, barrier)
-        res["ms_max"] = max_over_ranks(res["ms"])
-        res["value"] = world * res["md"].ncell * args.steps / (res["ms_max"] * 1e-3)
+        res["value"], res["ms_max"] = replica_rate(res["ms"], res["md"].ncell, args.steps, world, dist,
+                                                   f"cuda:{local}")
         if not args.no_e2e and prec == precisions[0]:
             res["e2e"] = e2e_rate(args, res, world)
         res["st"].close()
@@ -337,6 +353,7 @@ def gpu_arm(args):
         "roofline": r["roofline"], "full_cycle": r["full_cycle"], "cpu_baseline": cpu,
         "e2e": r.get("e2e"), "gpu_launches": sum(x["gpu_launches"] for x in results.values()),
         "clocks": r["clocks"], "kernels": r["kernels"], "check": r["check"], "peaks": r["peaks"],
+        "tuning": r["tuning"],
     }
     variants = {}
     for prec, x in results.items():
@@ -345,7 +362,7 @@ def gpu_arm(args):
         variants[prec] = {"value": x["value"], "ms_per_step": x["ms_max"] / args.steps, "dtype": dtypes[prec],
                           "speedup_vs_" + main_p: x["value"] / r["value"], "roofline": x["roofline"],
                           "full_cycle": x["full_cycle"], "kernels": x["kernels"], "clocks": x["clocks"],
-                          "gpu_launches": x["gpu_launches"], "check": x["check"]}
+                          "gpu_launches": x["gpu_launches"], "check": x["check"], "tuning": x["tuning"]}
     if variants:
         line["variants"] = variants
     print(json.dumps(line), flush=True)
@@ -367,6 +384,10 @@ def batch_arm(args):
     inst = inputs.batch_instances(args.batch_count, seed=2209)
     cells = sum(md.ncell for md, _ in inst)
     b = sale.Batch(inst, device=f"cuda:{local}")
+    tuning = None
+    if not args.no_tune:
+        from paper_2209_01983_gb300 import autotune
+        tuning = autotune.tune_batch(b, cycles=4, repeats=2)
     b.run(args.steps)  # untimed: captures and instantiates the graph of K cycles
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
@@ -415,7 +436,7 @@ def batch_arm(args):
                     "speedup_vs_one_by_one_fp32_mixed": value / rate_single_mixed,
                     "speedup_vs_one_by_one_fp64": value / rate_single_fp64,
                     "one_by_one_cycles": k1},
-        "gpu_launches": 5 * args.steps + 2, "clocks": clk, "check": {"t_samples": ts},
+        "gpu_launches": 5 * args.steps + 2, "clocks": clk, "check": {"t_samples": ts}, "tuning": tuning,
     }
     print(json.dumps(line), flush=True)
     return 0

@@ -233,6 +233,18 @@ int sale_batch_run(sale_batch *b, long long cycles, int remap_every,
 sale_state *sale_batch_state(sale_batch *b, int i);
 void sale_batch_destroy(sale_batch *b);
 
+/* Tuning knobs of the FP32-mixed kernels (no effect on results: every
+ * thread's work is independent of the tiling and the dt minimum is exact).
+ * Shapes 0..3 are thread tiles of tx x ty threads over one k plane:
+ * (32,8), (32,4), (64,4), (128,2).  sale_set_tiling applies to an
+ * FP32-mixed state (EINVAL otherwise); sale_batch_set_schedule sets the
+ * shape of a batch and the order of its meshes' tiles in a launch
+ * (0: input order, 1: largest mesh first).  Both synchronise and drop
+ * captured graphs. */
+int sale_tile_shape(int shape, int *tx, int *ty);
+int sale_set_tiling(sale_state *st, int shape);
+int sale_batch_set_schedule(sale_batch *b, int shape, int order);
+
 /* Launch-time profile.  While on, every kernel launch of the state's steps
  * is bracketed by CUDA events on the state's stream (inside captured
  * graphs as event nodes); device times accumulate on the host at each

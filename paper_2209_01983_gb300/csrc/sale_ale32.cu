@@ -560,11 +560,9 @@ __device__ __forceinline__ void m_eos_body(const Fields<float> &F, DevScalars *S
 }
 
 // ---------------------------------------------------------------------------
-// Kernels: 32 x 8 thread blocks; single mesh (3D grid) and batched (table)
+// Kernels: tiles of TX x TY threads over one k plane; single mesh (3D grid)
+// and batched (table)
 // ---------------------------------------------------------------------------
-
-constexpr int kTileX = 32, kTileY = 8;
-static_assert(kTileX * kTileY == kBlock, "tile must match the block size");
 
 template <bool JIT>
 __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevScalars *S, int i, int j, int k,
@@ -580,30 +578,33 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
   }
 }
 
-// Blocks per SM the register budget is held to, per kernel.
-__host__ __device__ constexpr int min_blocks(int kid) {
-  return (kid == kMixRemapEos || kid == kMixEos) ? 4 : kid == kMixCells ? 3 : 1;
+// Blocks per SM the register budget is held to, per kernel and block size
+// (the heavy cell kernels keep 768 / 1024 threads resident per SM).
+__host__ __device__ constexpr int min_blocks(int kid, int threads) {
+  return kid == kMixCells ? 768 / threads : (kid == kMixRemapEos || kid == kMixEos) ? 1024 / threads : 1;
 }
 
-template <int KID, bool JIT>
-__global__ void __launch_bounds__(kBlock, min_blocks(KID)) k_m(Fields<float> F, DevScalars *S, int mode) {
+template <int KID, bool JIT, int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
+    k_m(Fields<float> F, DevScalars *S, int mode) {
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  run_body<JIT>(KID, F, S, blockIdx.x * kTileX + threadIdx.x, blockIdx.y * kTileY + threadIdx.y, blockIdx.z, nblk,
-                mode);
+  run_body<JIT>(KID, F, S, blockIdx.x * tile_x(SH) + threadIdx.x, blockIdx.y * tile_y(SH) + threadIdx.y, blockIdx.z,
+                nblk, mode);
 }
 
 // Batched: block b works on mesh tab[b].x, tile (tab[b].y, tab[b].z) of
 // plane tab[b].w; the mesh's descriptor is staged in shared memory.
-template <int KID>
-__global__ void __launch_bounds__(kBlock, min_blocks(KID)) kb_m(const BatchItem *items, const int4 *tab) {
+template <int KID, int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
+    kb_m(const BatchItem *items, const int4 *tab) {
   __shared__ BatchItem it;
   const int4 t = tab[blockIdx.x];
-  const int tid = threadIdx.x + kTileX * threadIdx.y;
+  const int tid = threadIdx.x + tile_x(SH) * threadIdx.y;
   const int *src = reinterpret_cast<const int *>(items + t.x);
   int *dst = reinterpret_cast<int *>(&it);
-  for (int w = tid; w < (int)(sizeof(BatchItem) / sizeof(int)); w += kBlock) dst[w] = src[w];
+  for (int w = tid; w < (int)(sizeof(BatchItem) / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
   __syncthreads();
-  const int i = t.y * kTileX + threadIdx.x, j = t.z * kTileY + threadIdx.y, k = t.w;
+  const int i = t.y * tile_x(SH) + threadIdx.x, j = t.z * tile_y(SH) + threadIdx.y, k = t.w;
   if (it.F.off4) run_body<true>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
   else run_body<false>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
 }
@@ -626,9 +627,10 @@ __global__ void kb_gather(const BatchItem *items, int n, BatchStatus *out) {
   out[i] = {S->t, S->dt, S->cycle, S->status};
 }
 
-// Grid of 32 x 8 tiles over an (ni, nj, nk) box of nodes or cells.
-dim3 tile_grid(int ni, int nj, int nk) {
-  return dim3((unsigned)((ni + kTileX - 1) / kTileX), (unsigned)((nj + kTileY - 1) / kTileY), (unsigned)nk);
+// Grid of tiles of a shape over an (ni, nj, nk) box of nodes or cells.
+dim3 tile_grid(int ni, int nj, int nk, int shape) {
+  return dim3((unsigned)((ni + tile_x(shape) - 1) / tile_x(shape)),
+              (unsigned)((nj + tile_y(shape) - 1) / tile_y(shape)), (unsigned)nk);
 }
 
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
@@ -637,37 +639,56 @@ void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rh
                                                                               LE);
 }
 
-template <int KID>
-static void launch_one(const Fields<float> &F, DevScalars *S, int mode, cudaStream_t st) {
+template <int KID, int SH>
+static void launch_shaped(const Fields<float> &F, DevScalars *S, int mode, cudaStream_t st) {
   const bool node = KID == kMixNodes || KID == kMixRemapNodes;
-  const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1) : tile_grid(F.nx, F.ny, F.nz);
-  const dim3 b(kTileX, kTileY);
-  if (F.off4) k_m<KID, true><<<g, b, 0, st>>>(F, S, mode);
-  else k_m<KID, false><<<g, b, 0, st>>>(F, S, mode);
+  const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1, SH) : tile_grid(F.nx, F.ny, F.nz, SH);
+  const dim3 b(tile_x(SH), tile_y(SH));
+  if (F.off4) k_m<KID, true, SH><<<g, b, 0, st>>>(F, S, mode);
+  else k_m<KID, false, SH><<<g, b, 0, st>>>(F, S, mode);
 }
 
-void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st) {
-  (void)dt_override;  // the mixed path always steps with the on-device dt
+template <int KID>
+static void launch_one(const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st) {
+  switch (shape) {
+    case 1: launch_shaped<KID, 1>(F, S, mode, st); break;
+    case 2: launch_shaped<KID, 2>(F, S, mode, st); break;
+    case 3: launch_shaped<KID, 3>(F, S, mode, st); break;
+    default: launch_shaped<KID, 0>(F, S, mode, st); break;
+  }
+}
+
+void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st) {
   switch (kid) {
-    case kMixNodes: launch_one<kMixNodes>(F, S, mode, st); break;
-    case kMixCells: launch_one<kMixCells>(F, S, mode, st); break;
-    case kMixFluxes: launch_one<kMixFluxes>(F, S, mode, st); break;
-    case kMixRemapNodes: launch_one<kMixRemapNodes>(F, S, mode, st); break;
-    case kMixRemapEos: launch_one<kMixRemapEos>(F, S, mode, st); break;
-    case kMixEos: launch_one<kMixEos>(F, S, mode, st); break;
+    case kMixNodes: launch_one<kMixNodes>(F, S, mode, shape, st); break;
+    case kMixCells: launch_one<kMixCells>(F, S, mode, shape, st); break;
+    case kMixFluxes: launch_one<kMixFluxes>(F, S, mode, shape, st); break;
+    case kMixRemapNodes: launch_one<kMixRemapNodes>(F, S, mode, shape, st); break;
+    case kMixRemapEos: launch_one<kMixRemapEos>(F, S, mode, shape, st); break;
+    case kMixEos: launch_one<kMixEos>(F, S, mode, shape, st); break;
     default: break;
   }
 }
 
-void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st) {
-  const dim3 b(kTileX, kTileY);
+template <int SH>
+static void launch_batch_shaped(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st) {
+  const dim3 b(tile_x(SH), tile_y(SH));
   switch (kid) {
-    case kMixNodes: kb_m<kMixNodes><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixCells: kb_m<kMixCells><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixFluxes: kb_m<kMixFluxes><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixRemapNodes: kb_m<kMixRemapNodes><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixRemapEos: kb_m<kMixRemapEos><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixNodes: kb_m<kMixNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixCells: kb_m<kMixCells, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixFluxes: kb_m<kMixFluxes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapNodes: kb_m<kMixRemapNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapEos: kb_m<kMixRemapEos, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;
+  }
+}
+
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, cudaStream_t st) {
+  switch (shape) {
+    case 1: launch_batch_shaped<1>(kid, items, tab, nblocks, st); break;
+    case 2: launch_batch_shaped<2>(kid, items, tab, nblocks, st); break;
+    case 3: launch_batch_shaped<3>(kid, items, tab, nblocks, st); break;
+    default: launch_batch_shaped<0>(kid, items, tab, nblocks, st); break;
   }
 }
 

@@ -10,6 +10,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <algorithm>
 #include <map>
 #include <new>
 #include <string>
@@ -31,7 +32,7 @@ void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *
                      cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
                          long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st);
-void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, double dt_override, cudaStream_t st);
+void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st);
 }  // namespace sale
 
 using namespace sale;
@@ -222,6 +223,7 @@ struct sale_state {
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
+  int tile_shape = 0;  // thread-tile shape of the FP32-mixed kernels
   int remap_sets_x;    // flag passed to the node remap kernel
   double lim_t_end;
   long long lim_cycles;
@@ -463,7 +465,7 @@ static void dispatch(sale_state *st, int kid, int mode, double dt_override) {
   if (st->precision == SALE_FP64) {
     launch_kernel(kid, fields_t<double>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
   } else if (kid >= kMixNodes && kid <= kMixEos) {
-    launch_m_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->stream);
+    launch_m_kernel(kid, fields_t<float>(st), st->S, mode, st->tile_shape, st->stream);
   } else {
     launch_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
   }
@@ -628,7 +630,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     const Fields<float> F = fields_t<float>(st);
     launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
-    launch_m_kernel(kMixEos, F, st->S, kDtInit, 0.0, st->stream);
+    launch_m_kernel(kMixEos, F, st->S, kDtInit, st->tile_shape, st->stream);
   }
   if (e == cudaSuccess) e = cudaGetLastError();
   if (e == cudaSuccess) e = cudaStreamSynchronize(st->stream);  // host vectors die here
@@ -980,6 +982,27 @@ extern "C" int sale_refresh(sale_state *st) {
   return SALE_OK;
 }
 
+extern "C" int sale_tile_shape(int shape, int *tx, int *ty) {
+  if (shape < 0 || shape >= kNumTileShapes) return fail(SALE_EINVAL, "sale_tile_shape: shape in [0, %d)", kNumTileShapes);
+  if (tx) *tx = tile_x(shape);
+  if (ty) *ty = tile_y(shape);
+  return SALE_OK;
+}
+
+extern "C" int sale_set_tiling(sale_state *st, int shape) {
+  if (!st) return fail(SALE_EINVAL, "sale_set_tiling: null state");
+  if (st->precision != SALE_FP32_MIXED) return fail(SALE_EINVAL, "sale_set_tiling: applies to FP32-mixed states");
+  if (shape < 0 || shape >= kNumTileShapes) return fail(SALE_EINVAL, "sale_set_tiling: shape in [0, %d)", kNumTileShapes);
+  if (shape == st->tile_shape) return SALE_OK;
+  CUDA_TRY(cudaStreamSynchronize(st->stream));
+  for (auto &kv : st->graphs) cudaGraphExecDestroy(kv.second);  // captured with the old launch shapes
+  st->graphs.clear();
+  st->graph_events.clear();
+  st->pending_graphs.clear();
+  st->tile_shape = shape;
+  return SALE_OK;
+}
+
 extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes) {
   if (!st) return fail(SALE_EINVAL, "sale_state_dims: null state");
   if (ncells) *ncells = st->nc;
@@ -992,7 +1015,7 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
 // ---------------------------------------------------------------------------
 
 namespace sale {
-void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st);
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, cudaStream_t st);
 void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st);
 void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st);
 }  // namespace sale
@@ -1006,28 +1029,38 @@ struct sale_batch {
   unsigned nb_cell, nb_node;
   BatchStatus *status;              // device gather area
   std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
+  std::vector<sale_mesh_desc> meshes;
+  int shape = 0;                    // thread-tile shape
+  int order = 0;                    // 0: meshes in input order, 1: largest mesh first
   std::map<long long, cudaGraphExec_t> graphs;
 };
 
-// 32 x 8 tiles per plane, as the mixed kernels lay threads out.
-static unsigned tiles_of(int ni, int nj, int nk) {
-  return (unsigned)(((ni + 31) / 32) * ((nj + 7) / 8) * nk);
+// Tiles of a thread-tile shape per plane, as the mixed kernels lay threads out.
+static unsigned tiles_of(int ni, int nj, int nk, int shape) {
+  const int tx = tile_x(shape), ty = tile_y(shape);
+  return (unsigned)(((ni + tx - 1) / tx) * ((nj + ty - 1) / ty) * nk);
 }
-static unsigned cell_tiles(const sale_mesh_desc &d) { return tiles_of(d.nx, d.ny, d.nz); }
-static unsigned node_tiles(const sale_mesh_desc &d) { return tiles_of(d.nx + 1, d.ny + 1, d.nz + 1); }
-static void append_tiles(std::vector<int4> &tab, int mesh, int ni, int nj, int nk) {
+static unsigned cell_tiles(const sale_mesh_desc &d, int shape) { return tiles_of(d.nx, d.ny, d.nz, shape); }
+static unsigned node_tiles(const sale_mesh_desc &d, int shape) { return tiles_of(d.nx + 1, d.ny + 1, d.nz + 1, shape); }
+static void append_tiles(std::vector<int4> &tab, int mesh, int ni, int nj, int nk, int shape) {
+  const int tx = tile_x(shape), ty = tile_y(shape);
   for (int k = 0; k < nk; ++k)
-    for (int by = 0; by < (nj + 7) / 8; ++by)
-      for (int bx = 0; bx < (ni + 31) / 32; ++bx) tab.push_back(make_int4(mesh, bx, by, k));
+    for (int by = 0; by < (nj + ty - 1) / ty; ++by)
+      for (int bx = 0; bx < (ni + tx - 1) / tx; ++bx) tab.push_back(make_int4(mesh, bx, by, k));
 }
 
 // Layout of a batch buffer: header (descriptors, block tables, status
 // gather area) then one state region per mesh.
 static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, size_t *state_off, size_t *hdr_parts) {
-  long long nbc = 0, nbn = 0;
-  for (int i = 0; i < n; ++i) {
-    nbc += cell_tiles(meshes[i]);
-    nbn += node_tiles(meshes[i]);
+  long long nbc = 0, nbn = 0;  // the largest tables over the tile shapes
+  for (int sh = 0; sh < kNumTileShapes; ++sh) {
+    long long c = 0, nd = 0;
+    for (int i = 0; i < n; ++i) {
+      c += cell_tiles(meshes[i], sh);
+      nd += node_tiles(meshes[i], sh);
+    }
+    nbc = std::max(nbc, c);
+    nbn = std::max(nbn, nd);
   }
   size_t off = 0;
   hdr_parts[0] = off;  // descriptors, two parities
@@ -1075,7 +1108,7 @@ static int upload_batch_items(sale_batch *b) {
       h[i].F = fields_t<float>(st);
       st->upar = keep;
       h[i].S = st->S;
-      h[i].nblk_cell = tiles_of(st->nx, st->ny, st->nz);
+      h[i].nblk_cell = tiles_of(st->nx, st->ny, st->nz, b->shape);
       h[i].pad = 0;
     }
     CUDA_TRY(cudaMemcpyAsync(b->items[rel], h.data(), sizeof(BatchItem) * b->n, cudaMemcpyHostToDevice, b->stream));
@@ -1083,6 +1116,30 @@ static int upload_batch_items(sale_batch *b) {
   }
   b->item_upar.resize(b->n);
   for (int i = 0; i < b->n; ++i) b->item_upar[i] = b->st[i]->upar;
+  return SALE_OK;
+}
+
+// Block tables for the batch's tile shape and mesh order.
+static int upload_batch_tables(sale_batch *b) {
+  std::vector<int> ord((size_t)b->n);
+  for (int i = 0; i < b->n; ++i) ord[i] = i;
+  if (b->order == 1)  // largest meshes first: their blocks start early, the short tail is small meshes
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return b->st[a]->nc > b->st[c]->nc; });
+  std::vector<int4> tc, tn;
+  try {
+    for (int i : ord) {
+      const sale_mesh_desc &d = b->meshes[i];
+      append_tiles(tc, i, d.nx, d.ny, d.nz, b->shape);
+      append_tiles(tn, i, d.nx + 1, d.ny + 1, d.nz + 1, b->shape);
+    }
+  } catch (...) {
+    return fail(SALE_ENOMEM, "batch: out of host memory");
+  }
+  b->nb_cell = (unsigned)tc.size();
+  b->nb_node = (unsigned)tn.size();
+  CUDA_TRY(cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));  // tc, tn die here
   return SALE_OK;
 }
 
@@ -1128,29 +1185,9 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
     }
     b->st.push_back(sti);
   }
-  // block tables (meshes in order) and descriptors for both parities
-  std::vector<int4> tc, tn;
-  try {
-    for (int i = 0; i < n; ++i) {
-      const sale_mesh_desc &d = meshes[i];
-      append_tiles(tc, i, d.nx, d.ny, d.nz);
-      append_tiles(tn, i, d.nx + 1, d.ny + 1, d.nz + 1);
-    }
-  } catch (...) {
-    sale_batch_destroy(b);
-    return fail(SALE_ENOMEM, "sale_batch_create: out of host memory");
-  }
-  b->nb_cell = (unsigned)tc.size();
-  b->nb_node = (unsigned)tn.size();
-  cudaError_t e = cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess)
-    e = cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, b->stream);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(b->stream);  // tc, tn die here
-  if (e != cudaSuccess) {
-    sale_batch_destroy(b);
-    return cuda_fail(e, "sale_batch_create: upload");
-  }
-  rc = upload_batch_items(b);
+  b->meshes.assign(meshes, meshes + n);
+  rc = upload_batch_tables(b);
+  if (rc == SALE_OK) rc = upload_batch_items(b);
   if (rc) {
     sale_batch_destroy(b);
     return rc;
@@ -1167,11 +1204,27 @@ extern "C" sale_state *sale_batch_state(sale_batch *b, int i) {
 // One cycle of every mesh: the four kernels before the velocity-buffer
 // toggle read descriptors of parity p, the fused remap/EoS/dt one p ^ 1.
 static void launch_batch_cycle(sale_batch *b, int p) {
-  launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->stream);
-  launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->stream);
-  launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->stream);
-  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_node, b->nb_node, b->stream);
-  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->stream);
+  launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
+  launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
+  launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
+  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
+  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->shape, b->stream);
+}
+
+extern "C" int sale_batch_set_schedule(sale_batch *b, int shape, int order) {
+  if (!b) return fail(SALE_EINVAL, "sale_batch_set_schedule: null batch");
+  if (shape < 0 || shape >= kNumTileShapes || (order != 0 && order != 1))
+    return fail(SALE_EINVAL, "sale_batch_set_schedule: shape in [0, %d), order 0 or 1", kNumTileShapes);
+  if (shape == b->shape && order == b->order) return SALE_OK;
+  CUDA_TRY(cudaStreamSynchronize(b->stream));
+  for (auto &kv : b->graphs) cudaGraphExecDestroy(kv.second);  // they bake in the old tables
+  b->graphs.clear();
+  b->shape = shape;
+  b->order = order;
+  for (auto *st : b->st) st->tile_shape = shape;
+  int rc = upload_batch_tables(b);
+  if (rc == SALE_OK) rc = upload_batch_items(b);
+  return rc;
 }
 
 extern "C" int sale_batch_run(sale_batch *b, long long cycles, int remap_every, long long *cycles_done) {

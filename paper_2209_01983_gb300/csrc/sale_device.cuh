@@ -120,14 +120,15 @@ __device__ __forceinline__ float warp_min_f32(float v) {
 template <typename R>
 __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, DevScalars *S, float dtc, int mode,
                                                             double dt_override, unsigned nblk) {
-  __shared__ float smin32[kBlock / 32];
+  __shared__ float smin32[kMaxWarpsPerBlock];
   __shared__ bool last32;
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
+  const int nwarps = (int)((blockDim.x * blockDim.y * blockDim.z + 31) / 32);
   dtc = warp_min_f32(dtc);
   if ((tid & 31) == 0) smin32[tid >> 5] = dtc;
   __syncthreads();
   if (tid < 32) {
-    float v = tid < kBlock / 32 ? smin32[tid] : INFINITY;
+    float v = tid < nwarps ? smin32[tid] : INFINITY;
     v = warp_min_f32(v);
     if (tid == 0) {
       atomicMin(&S->dtmin_bits, (unsigned long long)__double_as_longlong((double)v));

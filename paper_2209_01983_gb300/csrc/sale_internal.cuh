@@ -110,6 +110,13 @@ struct Fields {
   int reflect[6];
 };
 
+// Thread-tile shapes of the FP32-mixed kernels (x by y threads over one k
+// plane); the autotuner picks one per state or batch.
+constexpr int kNumTileShapes = 4;
+__host__ __device__ constexpr int tile_x(int shape) { return shape == 0 ? 32 : shape == 1 ? 32 : shape == 2 ? 64 : 128; }
+__host__ __device__ constexpr int tile_y(int shape) { return shape == 0 ? 8 : shape == 1 ? 4 : shape == 2 ? 4 : 2; }
+constexpr int kMaxWarpsPerBlock = 16;
+
 // One mesh of a batch, as seen by the batched kernels.
 struct BatchItem {
   Fields<float> F;

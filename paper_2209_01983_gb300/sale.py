@@ -88,6 +88,9 @@ sale_batch_create = _sig("sale_batch_create", C.c_int,
 sale_batch_run = _sig("sale_batch_run", C.c_int, [_vp, C.c_longlong, C.c_int, C.POINTER(C.c_longlong)])
 sale_batch_state = _sig("sale_batch_state", _vp, [_vp, C.c_int])
 sale_batch_destroy = _sig("sale_batch_destroy", None, [_vp])
+sale_tile_shape = _sig("sale_tile_shape", C.c_int, [C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int)])
+sale_set_tiling = _sig("sale_set_tiling", C.c_int, [_vp, C.c_int])
+sale_batch_set_schedule = _sig("sale_batch_set_schedule", C.c_int, [_vp, C.c_int, C.c_int])
 sale_remap_static = _sig("sale_remap_static", C.c_int,
                          [C.c_int, C.c_int, C.c_int, C.POINTER(C.c_int), C.c_int, _vp, _vp, _vp, _vp,
                           _vp, _vp, _vp, _vp, _vp])
@@ -102,7 +105,7 @@ EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_sta
            "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
            "sale_kernel_count", "sale_kernel_name", "sale_remap_static", "sale_batch_bytes",
            "sale_batch_create", "sale_batch_run", "sale_batch_state", "sale_batch_destroy",
-           "sale_last_error")
+           "sale_tile_shape", "sale_set_tiling", "sale_batch_set_schedule", "sale_last_error")
 
 
 class SaleError(RuntimeError):
@@ -217,6 +220,9 @@ class State:
     def refresh(self):
         check(sale_refresh(self._h))
 
+    def set_tiling(self, shape):
+        check(sale_set_tiling(self._h, shape))
+
     def profile(self, on=True):
         check(sale_profile(self._h, 1 if on else 0))
 
@@ -265,6 +271,9 @@ class Batch:
         done = C.c_longlong(0)
         check(sale_batch_run(self._h, cycles, 1, C.byref(done)))
         return done.value
+
+    def set_schedule(self, shape, order):
+        check(sale_batch_set_schedule(self._h, shape, order))
 
     def state(self, i) -> State:
         md, pd = self.instances[i]

@@ -1,0 +1,102 @@
+"""Launch schedules of the FP32-mixed kernels change no bit of the result.
+
+Every tile shape, switched between runs, and every batch schedule (shape,
+mesh order) must give the fields the default 32x8 schedule gives; the
+autotuner picks one of them and caches the choice.
+"""
+import numpy as np
+import pytest
+
+from paper_2209_01983_gb300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+FIELDS = ("m", "e", "rho", "p", "q", "u", "v", "w", "mn")
+
+
+@pytest.fixture(scope="module")
+def sale():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2209_01983_gb300 import sale as s
+    return s
+
+
+def ragged_sedov():
+    # ragged against every tile width (32..128) and height (2..8)
+    md, pd = inputs.sedov_octant(9, jitter=0.1)
+    md = inputs.MeshDesc(37, 21, 9, lo=md.lo, hi=(1.2 * 37 / 9, 1.2 * 21 / 9, 1.2), jitter=0.1,
+                         seed=md.seed, reflect=md.reflect)
+    return md, pd
+
+
+def test_state_tile_shapes_bitwise(sale):
+    from paper_2209_01983_gb300 import autotune
+    md, pd = ragged_sedov()
+    ref = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+    assert ref.run_to_time(max_cycles=24, remap_every=1) == 24
+    want = {f: ref.field(f) for f in FIELDS}
+    for shape, _, _ in autotune.tile_shapes():
+        st = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+        st.set_tiling(shape)
+        assert st.run_to_time(max_cycles=24, remap_every=1) == 24
+        for f in FIELDS:
+            assert np.array_equal(st.field(f), want[f]), (shape, f)
+        assert st.diagnostics()["t"] == ref.diagnostics()["t"]
+    # shapes switched between runs (graphs re-captured) and one Lagrange step pair
+    st = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+    for shape, cyc in ((3, 5), (1, 7), (2, 4), (0, 8)):
+        st.set_tiling(shape)
+        st.run_to_time(max_cycles=cyc, remap_every=1)
+    for f in FIELDS:
+        assert np.array_equal(st.field(f), want[f]), f
+
+
+def test_tiling_rejected_for_fp64(sale):
+    md, pd = inputs.sedov_octant(6)
+    st = sale.State(md, pd, precision=sale.SALE_FP64)
+    with pytest.raises(sale.SaleError) as ei:
+        st.set_tiling(1)
+    assert ei.value.code == sale.SALE_EINVAL
+
+
+def test_batch_schedules_bitwise(sale):
+    inst = inputs.batch_instances(6, seed=31, nmin=5, nmax=40)
+    ref = sale.Batch(inst)
+    ref.run(12)
+    want = [{f: ref.state(i).field(f) for f in ("m", "e", "u")} for i in range(len(inst))]
+    b = sale.Batch(inst)
+    done = 0
+    for shape, order, cyc in ((2, 1, 3), (0, 1, 2), (3, 0, 4), (1, 1, 3)):
+        b.set_schedule(shape, order)
+        done += b.run(cyc)
+    assert done == 12
+    for i in range(len(inst)):
+        for f in ("m", "e", "u"):
+            assert np.array_equal(b.state(i).field(f), want[i][f]), (i, f)
+    with pytest.raises(sale.SaleError):
+        b.set_schedule(9, 0)
+    with pytest.raises(sale.SaleError):
+        b.set_schedule(0, 2)
+
+
+def test_autotune_state_and_batch(sale, tmp_path):
+    from paper_2209_01983_gb300 import autotune
+    cache = str(tmp_path / "tune.json")
+    md, pd = ragged_sedov()
+    st = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+    r = autotune.tune_state(st, cycles=4, repeats=1, cache=cache)
+    assert not r["cached"] and 0 <= r["shape"] < len(autotune.tile_shapes())
+    assert len(r["ms_per_cycle"]) == len(autotune.tile_shapes())
+    r2 = autotune.tune_state(st, cache=cache)
+    assert r2["cached"] and r2["shape"] == r["shape"]
+    # tuning advanced the state with ordinary cycles: same bits as a plain run
+    cyc = st.diagnostics()["cycle"]
+    ref = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+    ref.run_to_time(max_cycles=cyc, remap_every=1)
+    assert np.array_equal(st.field("e"), ref.field("e"))
+    b = sale.Batch(inputs.batch_instances(4, seed=5, nmin=5, nmax=20))
+    rb = autotune.tune_batch(b, cycles=2, repeats=1, cache=cache)
+    assert rb["order"] in (0, 1) and len(rb["ms_per_cycle"]) == 2 * len(autotune.tile_shapes())
+    assert autotune.tune_batch(b, cache=cache)["cached"]
