@@ -35,41 +35,52 @@ FP64 = {
 }
 
 # FP64 Eulerian cycle (remap every cycle), cached reference geometry:
-# corner gradients G (24 doubles per cell), V_E, L_E read instead of recomputed.
-SWEPT3 = 3 * VOL + 7 * 3 * 3  # three swept hexes + Lagrangian coordinates of 7 nodes
+# corner gradients G (24 doubles per cell), V_E, L_E, 1/V_E, 1/(cfl L_E)^2
+# and the reference-face terms read instead of recomputed; the side quads of
+# the swept hexes computed once per mesh edge (k_ale_edges) instead of once
+# per cell that uses them.
+QUAD = 29  # fan term of one quad: 4-point sum 9, diagonals 6, cross 9, dot 5
+EDGES = 3 * QUAD + 9 + 3 + 18 + 9 + 6 * 7  # 3 side quads, relative positions, L, shifts
+SWEPT3 = 3 * QUAD + 18 + 21 + 3 + 12 + 3  # Lagrangian faces + assembly of 9 side terms
 FP64_ALE = {
-    # sigma, G (24/cell), u, mn read; u, ubar written
-    "ale_nodes": ("node", 8 * (1 + 24 + 3 + 1 + 3 + 3), 48 + 20),
-    # G, ubar, m, e, sigma, x_ref read; e, 3 swept volumes written
-    "ale_cells": ("cell", 8 * (24 + 3 + 3 + 3 + 1 + 3), 48 + 5 + SWEPT3),
+    # sigma, G (24/cell), u, mn read; u, ubar, 0.5|u|^2 written
+    "ale_nodes": ("node", 8 * (1 + 24 + 3 + 1 + 3 + 3 + 1), 48 + 20 + 5),
+    # x_ref, ubar read; 9 side-quad terms written
+    "ale_edges": ("node", 8 * (3 + 3 + 9), EDGES),
+    # G, ubar, m, e, sigma, x_ref, 3 reference-face terms, 9 side terms read;
+    # e, 3 swept volumes written
+    "ale_cells": ("cell", 8 * (24 + 3 + 3 + 3 + 3 + 9 + 1 + 3), 48 + 5 + SWEPT3),
     # 3 swept volumes, V_E, m read; V_L, rho_L written
     "ale_density": ("cell", 8 * (3 + 2 + 2), 8),
-    # 3 swept volumes, rho_L, e read; 3 mass + 3 energy fluxes written
-    "ale_fluxes": ("cell", 8 * (3 + 2 + 6), 6),
-    # 3 mass fluxes, u, mn read; u', mn', dKE written
-    "remap_nodes": ("node", 8 * (3 + 3 + 1 + 3 + 1 + 1), 125),
-    # 6 fluxes, m, e, dKE, u', G, V_E, L_E read; m, e, vol, rho, p, q, cs, sigma written
-    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 2 + 8), 35 + 48 + 40),
+    # 3 swept volumes, rho_L, e read; 3 mass + 3 energy fluxes + 3 dual-flux parts written
+    "ale_fluxes": ("cell", 8 * (3 + 2 + 6 + 3), 15),
+    # 3 dual-flux parts (per cell), u, mn, 0.5|u|^2 read; u', mn', dKE written
+    "ale_remap_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 1 + 1), 6 * 12 + 20),
+    # 6 fluxes, m, e, dKE, u', G, V_E, L_E, 1/V_E, 1/(cfl L_E)^2 read;
+    # m, e, vol, rho, p, q, cs, sigma written
+    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 4 + 8), 35 + 48 + 30),
 }
 
 
 # FP32-mixed Eulerian cycle: 4-byte fields, reference geometry recomputed
-# from the structured mesh + FP32 jitter offsets (12 bytes per node), V_E and
-# L_E stored.  Flops are FP32 (the FP64 islands are a few per cell).
+# from the structured mesh + FP32 jitter offsets (one 16-byte float4 per
+# node), V_E and L_E stored; cell mass and energy are float-float (hi and lo
+# arrays).  Flops are FP32.
 GRAD32 = GRAD + 42      # gradient + relative coordinates of the 8 nodes
 FORCE32 = 12 * 27 + 108 + 20  # 12 face terms + 18 relative node positions + update
 SWEPT32 = 6 * 30 + 3 * 12 + 3 * 60 + 24  # expanded side/pair terms + displacements
 MIXED_ALE = {
-    # offsets, sigma, u, mn read; u, ubar written
-    "mix_nodes": ("node", 4 * (3 + 1 + 3 + 1 + 3 + 3), FORCE32),
-    # offsets, ubar, sigma, m, e read; e, 3 swept volumes written
-    "mix_cells": ("cell", 4 * (3 + 3 + 3 + 1 + 3), GRAD32 + 40 + 6 + SWEPT32),
+    # offsets (float4), sigma, u, mn read; u, ubar written
+    "mix_nodes": ("node", 4 * (4 + 1 + 3 + 1 + 3 + 3), FORCE32),
+    # offsets (float4), ubar, sigma, m, e (hi, lo) read; e (hi, lo), 3 swept volumes written
+    "mix_cells": ("cell", 4 * (4 + 3 + 1 + 1 + 2 + 2 + 3), GRAD32 + 40 + 6 + SWEPT32),
     # swept volumes, V_E, m, e read; 3 mass + 3 energy fluxes written
     "mix_fluxes": ("cell", 4 * (3 + 3 + 6), 30),
     # 3 mass fluxes, u, mn read; u', mn', dKE written
     "mix_remap_nodes": ("node", 4 * (3 + 3 + 1 + 3 + 1 + 1), 125),
-    # 6 fluxes, m, e, dKE, u', offsets, V_E, L_E read; m, e, rho, sigma written
-    "mix_remap_eos": ("cell", 4 * (6 + 2 + 1 + 3 + 3 + 2 + 4), 40 + GRAD32 + 40 + 30),
+    # 6 fluxes, m, e (hi, lo), dKE, u', offsets (float4), V_E, L_E read;
+    # m, e (hi, lo), rho, sigma written
+    "mix_remap_eos": ("cell", 4 * (6 + 4 + 1 + 3 + 4 + 2 + 6), 40 + GRAD32 + 40 + 30),
 }
 
 

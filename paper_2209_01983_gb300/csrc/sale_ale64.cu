@@ -11,16 +11,25 @@
 //
 // Cycle (ScalSALE Sec. IV, Eulerian rezoning with an advection phase):
 //   k_ale_nodes      F_a = sum_c (p+q)_c G_c(a) gathered per node, new
-//                    velocity with walls, time-centred velocity ubar
+//                    velocity with walls, time-centred velocity ubar, and
+//                    0.5 |u|^2 for the node remap
+//   k_ale_edges      side quads of the swept hexes, one per mesh edge (each
+//                    is shared by three cells' swept hexes), with the origin
+//                    shifts those cells need
 //   k_ale_cells      compatible energy e_L = e - dt/m (p+q) sum_a G(a).ubar_a;
 //                    swept volumes of the three low faces between the
 //                    Lagrangian face (x_ref + dt ubar) and the reference face
 //   k_ale_density    V_L = V_E - (net swept volume): the Lagrangian volume by
 //                    closure; rho_L = m / V_L
-//   k_ale_fluxes     donor-cell mass and energy fluxes of the low faces
-//   k_remap_nodes    (shared with the general path) dual-mesh node remap
+//   k_ale_fluxes     donor-cell mass and energy fluxes of the low faces, and
+//                    each cell's dual-mesh flux parts (mu_low + mu_high) / 8
+//   k_ale_remap_nodes  dual-mesh node remap from those parts
 //   k_ale_remap_eos  new cell mass/energy + kinetic-energy fix, then EoS,
 //                    viscosity, p+q and the CFL dt on the reference mesh
+//
+// Every FP64 operation counts on GB300 (one FP64 FMA per 62 FP32 ones), so
+// work shared between cells or nodes is done once and passed through HBM,
+// which this path leaves mostly idle.
 #include "sale_device.cuh"
 
 namespace sale {
@@ -34,41 +43,19 @@ __device__ __forceinline__ P3 corner_g(const double *G, long long nc, long long 
 }
 
 // Face term of the fan volume formula for the quad (p0,p1,p2,p3):
-// T = (p0+p1+p2+p3) . ((p2-p0) x (p3-p1)); a hex volume is (1/24) times the
-// sum of the terms of its six outward faces (same origin for all six).
+// T = (p0+p1+p2+p3) . (d1 x d2), d1 = p2 - p0, d2 = p3 - p1; a hex volume is
+// (1/24) times the sum of the terms of its six outward faces (same origin
+// for all six).  With p2 + p3 = p0 + p1 + d1 + d2 and (d1 + d2) . (d1 x d2)
+// = 0 this is T = 2 (p0 + p1) . (d1 x d2), five FP64 operations fewer.
 __device__ __forceinline__ double quad_term(P3 p0, P3 p1, P3 p2, P3 p3) {
-  return dot(p0 + p1 + p2 + p3, cross(p2 - p0, p3 - p1));
-}
-
-// Swept volumes of the three low faces of a cell (each the volume of the
-// hex between the face at its Lagrangian position L and at its reference
-// position E; positive when E lies on the high-index side).  All three hexes
-// use the cell's reference node 0 as origin, so the side quad along each of
-// the three mesh edges at node 0 is shared by two hexes (with opposite
-// orientation) and computed once; the three reference-face terms are time
-// invariant and come from the cache (TE).  L[a], E[a]: local node a of the
-// cell relative to its reference node 0 (E[0] = 0).
-__device__ __forceinline__ void swept_low_faces(const P3 (&L)[8], const P3 (&E)[8], const double (&TE)[3],
-                                                double &vx, double &vy, double &vz) {
-  const double tz0 = quad_term(L[0], E[0], E[4], L[4]);  // edge 0-4
-  const double ty0 = quad_term(L[0], L[2], E[2], E[0]);  // edge 0-2
-  const double tx0 = quad_term(L[0], E[0], E[1], L[1]);  // edge 0-1
-  const double sx = quad_term(L[0], L[4], L[6], L[2]) + TE[0] + tz0 + quad_term(L[2], L[6], E[6], E[2]) + ty0 +
-                    quad_term(L[4], E[4], E[6], L[6]);
-  const double sy = -tz0 + quad_term(L[1], E[1], E[5], L[5]) + quad_term(L[0], L[1], L[5], L[4]) + TE[1] + tx0 +
-                    quad_term(L[4], L[5], E[5], E[4]);
-  const double sz = -ty0 + quad_term(L[1], L[3], E[3], E[1]) - tx0 + quad_term(L[2], E[2], E[3], L[3]) +
-                    quad_term(L[0], L[2], L[3], L[1]) + TE[2];
-  vx = sx * kInvSixth24;
-  vy = sy * kInvSixth24;
-  vz = sz * kInvSixth24;
+  return 2.0 * dot(p0 + p1, cross(p2 - p0, p3 - p1));
 }
 
 }  // namespace
 
 // Reference geometry of every cell: corner gradients, volume, length scale.
 __global__ void __launch_bounds__(kBlock) k_geo_init(Fields<double> F, DevScalars *S, double *G, double *VE,
-                                                     double *LE, double *TE) {
+                                                     double *LE, double *TE, double *iVE, double *iL2) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc) return;
   int i, j, k;
@@ -86,7 +73,11 @@ __global__ void __launch_bounds__(kBlock) k_geo_init(Fields<double> F, DevScalar
     G[(3ll * a + 2) * F.nc + c] = g[a].z;
   }
   VE[c] = V;
-  LE[c] = V / sqrt(hex_max_face_area2(X));
+  const double L = V / sqrt(hex_max_face_area2(X));
+  LE[c] = L;
+  iVE[c] = 1.0 / V;
+  const double cl = F.cfl * L;
+  iL2[c] = 1.0 / (cl * cl);
   // reference faces of the swept hexes of the low x/y/z faces, origin node 0
   TE[c] = quad_term(X[0], X[2], X[6], X[4]);
   TE[F.nc + c] = quad_term(X[0], X[4], X[5], X[1]);
@@ -117,6 +108,50 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
   F.ub[n] = 0.5 * (u0 + u1);
   F.vb[n] = 0.5 * (v0 + v1);
   F.wb[n] = 0.5 * (w0 + w1);
+  F.kd[n] = 0.5 * (u1 * u1 + v1 * v1 + w1 * w1);
+}
+
+// Side quad (L_a, E_a, E_b, L_b) of the swept hexes along the mesh edge from
+// node a = n to b = n + e_AX: its fan term with node n as origin, and the
+// same term for origin n - e_Q of each other axis Q (the node 0 of the other
+// cells whose low faces hold the edge): T(o) = T(n) + 4 (x_n - x_o) . A, A
+// the quad's diagonal cross product.  ste[(3 AX + v) nn + n], v = 0 for
+// origin n, v = 1, 2 for the other two axes in increasing order.
+template <int AX>
+__device__ __forceinline__ void edge_side_terms(const Fields<double> &F, long long n, const int (&ijk)[3],
+                                                const int (&nmax)[3], const long long (&stride)[3], P3 xa, P3 La,
+                                                double h) {
+  if (ijk[AX] == nmax[AX]) return;  // no edge along AX from this node
+  const long long b = n + stride[AX];
+  const P3 Eb = P3{F.xr[b], F.yr[b], F.zr[b]} - xa;
+  const P3 Lb = Eb + h * P3{F.ub[b], F.vb[b], F.wb[b]};
+  const P3 A = cross(Eb - La, Lb);  // diagonals (E_b - L_a) and (L_b - E_a), E_a = 0
+  const double T = 2.0 * dot(La, A);  // 2 (L_a + E_a) . A
+  F.ste[(3 * AX) * F.nn + n] = T;
+  constexpr int Q1 = AX == 0 ? 1 : 0, Q2 = AX == 2 ? 1 : 2;
+  if (ijk[Q1] > 0) {
+    const long long o = n - stride[Q1];
+    F.ste[(3 * AX + 1) * F.nn + n] = T + 4.0 * dot(xa - P3{F.xr[o], F.yr[o], F.zr[o]}, A);
+  }
+  if (ijk[Q2] > 0) {
+    const long long o = n - stride[Q2];
+    F.ste[(3 * AX + 2) * F.nn + n] = T + 4.0 * dot(xa - P3{F.xr[o], F.yr[o], F.zr[o]}, A);
+  }
+}
+
+__global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScalars *S, double dt_override) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  const int ijk[3] = {i, j, k}, nmax[3] = {F.nx, F.ny, F.nz};
+  const long long stride[3] = {1, F.nx + 1, (long long)(F.nx + 1) * (F.ny + 1)};
+  const P3 xa = {F.xr[n], F.yr[n], F.zr[n]};
+  const P3 La = h * P3{F.ub[n], F.vb[n], F.wb[n]};
+  edge_side_terms<0>(F, n, ijk, nmax, stride, xa, La, h);
+  edge_side_terms<1>(F, n, ijk, nmax, stride, xa, La, h);
+  edge_side_terms<2>(F, n, ijk, nmax, stride, xa, La, h);
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
@@ -138,23 +173,26 @@ __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScala
   }
   const double m = F.m[c];
   F.e[c] = F.e[c] - h / m * F.sig[c] * work;
-  // swept volumes of the three low faces (nodes relative to reference node 0)
-  P3 Er[8], Lr[8];
+  // swept volumes of the three low faces: the Lagrangian face terms here
+  // (nodes relative to reference node 0), the reference faces from the
+  // cache, the side quads from k_ale_edges (a side quad traversed the other
+  // way round changes sign)
+  P3 Lr[7];
   const P3 o = {F.xr[nid[0]], F.yr[nid[0]], F.zr[nid[0]]};
-  Er[0] = {0.0, 0.0, 0.0};
   Lr[0] = h * ub[0];
 #pragma unroll
-  for (int a = 1; a < 7; ++a) {
-    Er[a] = P3{F.xr[nid[a]], F.yr[nid[a]], F.zr[nid[a]]} - o;
-    Lr[a] = Er[a] + h * ub[a];
-  }
-  Er[7] = Lr[7] = {0.0, 0.0, 0.0};  // node 7 is on no low face
-  const double TE[3] = {F.TE[c], F.TE[F.nc + c], F.TE[2 * F.nc + c]};
-  double vx, vy, vz;
-  swept_low_faces(Lr, Er, TE, vx, vy, vz);
-  F.dvx[c] = i > 0 ? vx : 0.0;
-  F.dvy[c] = j > 0 ? vy : 0.0;
-  F.dvz[c] = k > 0 ? vz : 0.0;
+  for (int a = 1; a < 7; ++a) Lr[a] = (P3{F.xr[nid[a]], F.yr[nid[a]], F.zr[nid[a]]} - o) + h * ub[a];
+  const long long nn = F.nn, n0 = nid[0], n1 = nid[1], n2 = nid[2], n4 = nid[4];
+  const double *ste = F.ste;
+  const double cx0 = ste[n0], cxy = ste[nn + n2], cxz = ste[2 * nn + n4];
+  const double cy0 = ste[3 * nn + n0], cyx = ste[4 * nn + n1], cyz = ste[5 * nn + n4];
+  const double cz0 = ste[6 * nn + n0], czx = ste[7 * nn + n1], czy = ste[8 * nn + n2];
+  const double sx = quad_term(Lr[0], Lr[4], Lr[6], Lr[2]) + F.TE[c] + cz0 - czy - cy0 + cyz;
+  const double sy = quad_term(Lr[0], Lr[1], Lr[5], Lr[4]) + F.TE[F.nc + c] - cz0 + czx + cx0 - cxz;
+  const double sz = quad_term(Lr[0], Lr[2], Lr[3], Lr[1]) + F.TE[2 * F.nc + c] + cy0 - cyx - cx0 + cxy;
+  F.dvx[c] = i > 0 ? sx * kInvSixth24 : 0.0;
+  F.dvy[c] = j > 0 ? sy * kInvSixth24 : 0.0;
+  F.dvz[c] = k > 0 ? sz * kInvSixth24 : 0.0;
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevScalars *S) {
@@ -174,20 +212,31 @@ __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevSca
   F.rho[c] = F.m[c] / VL;
 }
 
+// Donor-cell fluxes of the low face normal to AX; also the cell's part of
+// the dual-mesh mass flux along AX, (mu_low + mu_high) / 8, mu_high being
+// the low-face flux of the +AX neighbour (0 on the high wall).  The node
+// remap sums four such parts per mesh edge instead of eight fluxes.
 template <int AX>
-__device__ __forceinline__ void ale_face_flux(const Fields<double> &F, long long c, int idx, const double *dv,
-                                              double *mu, double *ep) {
+__device__ __forceinline__ void ale_face_flux(const Fields<double> &F, long long c, int idx, int n_ax,
+                                              const double *dv, double *mu, double *ep, double *mq) {
+  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+  double lo = 0.0;
   if (idx == 0) {
     mu[c] = 0.0;
     ep[c] = 0.0;
-    return;
+  } else {
+    const double v = dv[c];
+    const long long dn = v > 0.0 ? c : c - stride;
+    lo = F.rho[dn] * v;
+    mu[c] = lo;
+    ep[c] = lo * F.e[dn];
   }
-  const double v = dv[c];
-  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
-  const long long dn = v > 0.0 ? c : c - stride;
-  const double f = F.rho[dn] * v;
-  mu[c] = f;
-  ep[c] = f * F.e[dn];
+  double hi = 0.0;
+  if (idx + 1 < n_ax) {
+    const double v = dv[c + stride];
+    hi = F.rho[v > 0.0 ? c + stride : c] * v;
+  }
+  mq[c] = (lo + hi) * 0.125;
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_fluxes(Fields<double> F, DevScalars *S) {
@@ -195,15 +244,88 @@ __global__ void __launch_bounds__(kBlock) k_ale_fluxes(Fields<double> F, DevScal
   if (c >= F.nc || !cycle_active(S)) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
-  ale_face_flux<0>(F, c, i, F.dvx, F.mux, F.epx);
-  ale_face_flux<1>(F, c, j, F.dvy, F.muy, F.epy);
-  ale_face_flux<2>(F, c, k, F.dvz, F.muz, F.epz);
+  ale_face_flux<0>(F, c, i, F.nx, F.dvx, F.mux, F.epx, F.mqx);
+  ale_face_flux<1>(F, c, j, F.ny, F.dvy, F.muy, F.epy, F.mqy);
+  ale_face_flux<2>(F, c, k, F.nz, F.dvz, F.muz, F.epz, F.mqz);
+}
+
+// Dual mass flux of the mesh edge from node (i,j,k) to its +AX neighbour:
+// the sum of the dual-flux parts of the (up to four) cells around the edge.
+template <int AX>
+__device__ __forceinline__ double ale_edge_psi(const Fields<double> &F, int i, int j, int k) {
+  const double *mq = AX == 0 ? F.mqx : AX == 1 ? F.mqy : F.mqz;
+  double psi = -0.0;  // -0 + x = x for every x: the first addition folds away
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    int ci = i, cj = j, ck = k;
+    if (AX == 0) { cj = j - 1 + (s & 1); ck = k - 1 + (s >> 1); }
+    if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
+    if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
+    if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
+    psi += mq[cell_index(F.nx, F.ny, ci, cj, ck)];
+  }
+  return psi;
+}
+
+// Upwind transport of mass, momentum and kinetic energy across one edge on
+// the low (SIDE = 0: edge from this node to +AX) or high (SIDE = 1: from
+// the -AX neighbour) side of the node.
+template <int AX, int SIDE>
+__device__ __forceinline__ void ale_node_edge(const Fields<double> &F, int i, int j, int k, long long n, double &m,
+                                              P3 &p, double &ke) {
+  const int idx = AX == 0 ? i : AX == 1 ? j : k;
+  const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
+  if (SIDE == 0 && idx == n_ax) return;
+  if (SIDE == 1 && idx == 0) return;
+  const double psi = ale_edge_psi<AX>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
+                                      (SIDE == 1 && AX == 2) ? k - 1 : k);
+  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)(F.nx + 1) : (long long)(F.nx + 1) * (F.ny + 1);
+  const long long lo = SIDE == 0 ? n : n - stride;
+  const long long dn = psi > 0.0 ? lo + stride : lo;
+  const double sgn = SIDE == 0 ? 1.0 : -1.0;
+  m += sgn * psi;
+  p.x += sgn * psi * F.u[dn];
+  p.y += sgn * psi * F.v[dn];
+  p.z += sgn * psi * F.w[dn];
+  ke += sgn * psi * F.kd[dn];
+}
+
+__global__ void __launch_bounds__(kBlock) k_ale_remap_nodes(Fields<double> F, DevScalars *S) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn) return;
+  if (!cycle_active(S)) {  // inactive cycle: velocity carries over unchanged
+    F.ub[n] = F.u[n];
+    F.vb[n] = F.v[n];
+    F.wb[n] = F.w[n];
+    return;
+  }
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  const double m0 = F.mn[n];
+  double m = m0;
+  P3 p = {m0 * F.u[n], m0 * F.v[n], m0 * F.w[n]};
+  double ke = m0 * F.kd[n];
+  ale_node_edge<0, 0>(F, i, j, k, n, m, p, ke);
+  ale_node_edge<0, 1>(F, i, j, k, n, m, p, ke);
+  ale_node_edge<1, 0>(F, i, j, k, n, m, p, ke);
+  ale_node_edge<1, 1>(F, i, j, k, n, m, p, ke);
+  ale_node_edge<2, 0>(F, i, j, k, n, m, p, ke);
+  ale_node_edge<2, 1>(F, i, j, k, n, m, p, ke);
+  if (!(m > 0.0)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
+  const double inv_m = 1.0 / m;
+  double u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
+  wall_bc(F, i, j, k, u1, v1, w1);
+  F.ub[n] = u1;
+  F.vb[n] = v1;
+  F.wb[n] = w1;
+  F.mn[n] = m;
+  F.dke[n] = ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1);
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
   if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double dtc = INFINITY;
+  double rate = 0.0;  // CFL rate 1 / dt_c^2
   if (c < F.nc) {
     int i, j, k;
     cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -222,9 +344,9 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
       const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
       const long long n = node_index(F.nx, F.ny, ni, nj, nk);
       U[a] = {F.u[n], F.v[n], F.w[n]};
-      if (F.ke_fix) {  // share 1/(cells at the node): a power of two, exact
-        const double share = ((ni == 0 || ni == F.nx) ? 1.0 : 0.5) * ((nj == 0 || nj == F.ny) ? 1.0 : 0.5) *
-                             ((nk == 0 || nk == F.nz) ? 1.0 : 0.5);
+      if (F.ke_fix) {  // share 1/(cells at the node) = 2^-(interior axes), built from its bits
+        const int interior = (ni != 0 && ni != F.nx) + (nj != 0 && nj != F.ny) + (nk != 0 && nk != F.nz);
+        const double share = __longlong_as_double((long long)(1023 - interior) << 52);
         ie += F.dke[n] * share;
       }
     }
@@ -232,7 +354,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
     const double e = ie / m1;
     // EoS and viscosity on the reference mesh
     const double V = F.VE[c];
-    const double inv_v = 1.0 / V;
+    const double inv_v = F.iVE[c];
     double dvdt = 0.0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) dvdt += dot(corner_g(F.G, F.nc, c, a), U[a]);
@@ -240,7 +362,8 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
     const double L = F.LE[c];
     const double rho = m1 * inv_v;
     const double p = (F.gamma - 1.0) * rho * e;
-    const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+    const double cs2 = F.gamma * (F.gamma - 1.0) * fmax(e, 0.0);
+    const double cs = sqrt(cs2);
     double q_rho = 0.0;  // q / rho
     if (div < 0.0) {
       const double ld = L * div;
@@ -255,28 +378,31 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
     F.q[c] = q;
     F.cs[c] = cs;
     F.sig[c] = p + q;
-    dtc = F.cfl * L / sqrt(cs * cs + 2.0 * q_rho);
-    if (dtc != dtc) {
+    // dt_c = cfl L / sqrt(cs^2 + 2 q / rho), as the rate (cs^2 + 2 q / rho) / (cfl L)^2
+    rate = (cs2 + 2.0 * q_rho) * F.iL2[c];
+    if (rate != rate) {
       set_status(S, SALE_ENAN);
-      dtc = INFINITY;
+      rate = 0.0;
     }
   }
-  block_min_dt_and_finalize(F, S, dtc, kDtAdvance, dt_override);
+  block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
 }
 
 static inline unsigned grid_ale(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
 
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
-                     cudaStream_t st) {
-  k_geo_init<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, G, VE, LE, TE);
+                     double *iVE, double *iL2, cudaStream_t st) {
+  k_geo_init<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, G, VE, LE, TE, iVE, iL2);
 }
 
 void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double dt_override, cudaStream_t st) {
   switch (kid) {
     case kAleNodes: k_ale_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleCells: k_ale_cells<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleFluxes: k_ale_fluxes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kAleRemapNodes: k_ale_remap_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S); break;
     case kAleRemapEos: k_ale_remap_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     default: break;
   }

@@ -29,7 +29,7 @@ template <typename R>
 void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t);
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
-                     cudaStream_t st);
+                     double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
                          long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st);
 void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st);
@@ -217,6 +217,8 @@ struct sale_state {
   void *mn, *dke;
   void *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
   double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
+  double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
+  double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   float4 *off4;                          // FP32-mixed path: jitter offsets
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
@@ -267,17 +269,23 @@ static size_t carve(sale_state *st, char *base) {
     st->ep[d] = cv.take(E * nc);
     st->dv[d] = cv.take(E * nc);
   }
-  st->geoG = st->geoVE = st->geoLE = st->geoTE = nullptr;
+  st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = nullptr;
+  st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->off4 = nullptr;
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
-    st->geoG = (double *)cv.take(sizeof(double) * 29 * nc);
+    st->geoG = (double *)cv.take(sizeof(double) * 31 * nc);
     if (base) {
       st->geoVE = st->geoG + 24 * nc;
       st->geoLE = st->geoVE + nc;
       st->geoTE = st->geoLE + nc;
+      st->geoIVE = st->geoTE + 3 * nc;
+      st->geoIL2 = st->geoIVE + nc;
     }
+    st->ste = (double *)cv.take(sizeof(double) * 9 * nn);
+    for (int d = 0; d < 3; ++d) st->mq[d] = (double *)cv.take(sizeof(double) * nc);
+    st->kd = (double *)cv.take(sizeof(double) * nn);
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
@@ -335,6 +343,13 @@ static Fields<R> fields_t(const sale_state *st) {
     F.VE = (const R *)st->geoVE;
     F.LE = (const R *)st->geoLE;
     F.TE = (const R *)st->geoTE;
+    F.iVE = (const R *)st->geoIVE;
+    F.iL2 = (const R *)st->geoIL2;
+    F.ste = (R *)st->ste;
+    F.mqx = (R *)st->mq[0];
+    F.mqy = (R *)st->mq[1];
+    F.mqz = (R *)st->mq[2];
+    F.kd = (R *)st->kd;
   } else {
     F.VE = (const R *)st->VE32;
     F.LE = (const R *)st->LE32;
@@ -625,7 +640,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
-    launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->stream);
+    launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->geoIVE, st->geoIL2, st->stream);
   } else {
     const Fields<float> F = fields_t<float>(st);
     launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->stream);
@@ -711,12 +726,11 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
     return;
   }
   launch_k(st, kAleNodes, 0, dt_override);
+  launch_k(st, kAleEdges, 0, dt_override);
   launch_k(st, kAleCells, 0, dt_override);
   launch_k(st, kAleDensity);
   launch_k(st, kAleFluxes);
-  st->remap_sets_x = 0;
-  launch_k(st, kRemapNodes);
-  st->remap_sets_x = 1;
+  launch_k(st, kAleRemapNodes);
   st->upar ^= 1;
   launch_k(st, kAleRemapEos, kDtAdvance, dt_override);
 }
@@ -1294,7 +1308,7 @@ static const char *const kKernelNames[kNumKernels] = {
     "init_nodes",   "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",     "remap_nodes",
     "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
     "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
-    "mix_remap_eos", "mix_eos"};
+    "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

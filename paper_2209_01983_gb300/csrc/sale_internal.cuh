@@ -65,6 +65,8 @@ enum KernelId : int {
   kMixRemapNodes,
   kMixRemapEos,
   kMixEos,
+  kAleEdges,     // ALE path: side-quad terms of the swept hexes, per mesh edge
+  kAleRemapNodes,
   kNumKernels
 };
 
@@ -98,6 +100,15 @@ struct Fields {
   const R *G, *VE, *LE;
   const R *TE;                 // reference-face terms of the low-face swept hexes (3 per cell)
   R *dvx, *dvy, *dvz;          // swept volumes of the low x/y/z faces
+  // FP64 Eulerian path: 1 / V_E and 1 / (cfl L_E)^2 of the reference mesh,
+  // the side-quad terms of the swept hexes along every mesh edge (nine node
+  // arrays, ste[slot * nn + n], slot = 3 * axis + origin variant), each
+  // cell's dual-mesh flux part (mu_low + mu_high) / 8 along x/y/z, and the
+  // node kinetic energy per unit mass 0.5 |u|^2 after the Lagrangian step.
+  const R *iVE, *iL2;
+  R *ste;
+  R *mqx, *mqy, *mqz;
+  R *kd;
   // Structured reference mesh of the FP32-mixed path: node (i,j,k) sits at
   // lo + (i,j,k) * h + off[node]; coordinate differences are formed as
   // index difference * h + offset difference (no absolute coordinates).
