@@ -31,7 +31,7 @@ void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
-                         long long dep_cell, double dep_e, float *VE, float *LE, cudaStream_t st);
+                         long long dep_cell, double dep_e, float *VE, float *LE, float4 *G4, cudaStream_t st);
 void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st);
 }  // namespace sale
 
@@ -222,6 +222,8 @@ struct sale_state {
   float4 *off4;                          // FP32-mixed path: jitter offsets
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
+  float4 *G4;                            // FP32-mixed path, jittered mesh: corner gradients
+  bool jit = false;                      // the mesh is jittered
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
@@ -273,6 +275,7 @@ static size_t carve(sale_state *st, char *base) {
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->off4 = nullptr;
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
+  st->G4 = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
     st->geoG = (double *)cv.take(sizeof(double) * 31 * nc);
@@ -292,6 +295,7 @@ static size_t carve(sale_state *st, char *base) {
     st->LE32 = (float *)cv.take(sizeof(float) * nc);
     st->mlo = (float *)cv.take(sizeof(float) * nc);
     st->elo = (float *)cv.take(sizeof(float) * nc);
+    if (st->jit) st->G4 = (float4 *)cv.take(sizeof(float4) * 6 * nc);
   }
   return align_up(cv.off);
 }
@@ -360,6 +364,7 @@ static Fields<R> fields_t(const sale_state *st) {
   F.hy = st->h32[1];
   F.hz = st->h32[2];
   F.off4 = st->off4;
+  F.G4 = st->G4;
   F.remap_sets_x = st->remap_sets_x;
   F.gamma = st->prob.gamma;
   F.cfl = st->prob.cfl;
@@ -376,18 +381,19 @@ static Fields<R> fields_t(const sale_state *st) {
   return F;
 }
 
-static size_t state_bytes(long long nc, long long nn, int precision) {
+static size_t state_bytes(long long nc, long long nn, int precision, bool jit) {
   sale_state tmp;
   tmp.nc = nc;
   tmp.nn = nn;
   tmp.precision = precision;
+  tmp.jit = jit;
   tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   return carve(&tmp, nullptr);
 }
 
 extern "C" size_t sale_state_bytes(const sale_mesh *mesh, int precision) {
   if (!mesh || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
-  return state_bytes(mesh->nc, mesh->nn, precision);
+  return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -552,7 +558,8 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
-  rc = check_device_buffer("sale_state_init", device_buf, bytes, state_bytes(mesh->nc, mesh->nn, precision));
+  rc = check_device_buffer("sale_state_init", device_buf, bytes,
+                           state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0));
   if (rc) return rc;
   return state_init_at(mesh, prob, precision, device_buf, cuda_stream, out);
 }
@@ -569,6 +576,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   st->nc = mesh->nc;
   st->nn = mesh->nn;
   st->precision = precision;
+  st->jit = mesh->d.jitter > 0.0;
   st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
@@ -643,7 +651,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->geoIVE, st->geoIL2, st->stream);
   } else {
     const Fields<float> F = fields_t<float>(st);
-    launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->stream);
+    launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->G4, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_m_kernel(kMixEos, F, st->S, kDtInit, st->tile_shape, st->stream);
   }
@@ -1089,7 +1097,7 @@ static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, s
     const sale_mesh_desc &d = meshes[i];
     const long long nc = (long long)d.nx * d.ny * d.nz, nn = (long long)(d.nx + 1) * (d.ny + 1) * (d.nz + 1);
     if (state_off) state_off[i] = off;
-    off = align_up(off + state_bytes(nc, nn, precision));
+    off = align_up(off + state_bytes(nc, nn, precision, d.jitter > 0.0));
   }
   return off;
 }

@@ -114,6 +114,10 @@ struct Fields {
   // index difference * h + offset difference (no absolute coordinates).
   float hx, hy, hz;
   const float4 *off4;          // per-node jitter offsets x, y, z (w unused); null: none
+  // Jittered FP32-mixed meshes: dV/dx of the 8 corners of every reference
+  // cell, 24 floats per cell (corner-major, then axis) as 6 float4; null on
+  // unjittered meshes, where the gradient folds to constants.
+  const float4 *G4;
   double gamma, cfl, c_q, c_l, growth, dt_init;
   float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
   int ke_fix;
