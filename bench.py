@@ -42,17 +42,23 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--precision", default="both", choices=("fp64", "fp32_mixed", "both"))
-    ap.add_argument("--n", type=int, default=384, help="cells per axis")
+    ap.add_argument("--n", type=int, default=None,
+                    help="cells per axis (default 384; 256 for --config precision)")
     ap.add_argument("--jitter", type=float, default=0.1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default 32x8 tiles of the FP32-mixed kernels")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
-    ap.add_argument("--config", default="large", choices=("large", "batch", "precision"))
+    ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
+    ap.add_argument("--save-fields", default=None,
+                    help="precision: write 4^3 block averages of both runs (.npz); precision-oracle: read them")
     ap.add_argument("--t-end", type=float, default=0.5)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--unbatched-steps", type=int, default=16)
-    return ap.parse_args()
+    args = ap.parse_args()
+    if args.n is None:
+        args.n = 256 if args.config == "precision" else 384
+    return args
 
 
 def load_peaks():
@@ -500,21 +506,44 @@ def precision_arm(args):
             "mixed_vs_fp64_l1_rel_outside_core": l1_core_out,
             "core_volume_fraction": float(np.sum(w * ~keep) / np.sum(w)),
             "speedup_mixed_vs_fp64": out["fp32_mixed"]["value"] / out["fp64"]["value"]}
-    if not args.no_cpu_baseline and n % 4 == 0:
-        import oracle
-        oracle.build()
-        mo, po = inputs.sedov_octant(n // 4)
-        o = oracle.Oracle.from_problem(mo, po)
-        t0 = time.perf_counter()
-        rc, oc = o.run(t_end=t_end, remap_every=1)
-        secs = time.perf_counter() - t0
-        ref = {"rho": o.field("rho"), "e": o.field("e")}
-        wo = o.field("vol")
-        line["downsampled_vs_oracle"] = {
-            "oracle": f"{n // 4}^3 to t={t_end}, {oc} cycles, {secs:.1f} s on one core",
-            **{prec: {f: float(np.sum(np.abs(down(out[prec]["fields"])[f] - ref[f]) * wo) / np.sum(np.abs(ref[f]) * wo))
-                      for f in ("rho", "e")} for prec in ("fp32_mixed", "fp64")}}
+    if args.save_fields and n % 4 == 0:
+        # 4^3 block averages of both runs, for the oracle comparison that
+        # runs on the host afterwards (--config precision-oracle)
+        np.savez_compressed(args.save_fields, n=n, t_end=t_end,
+                            **{f"{prec}_{f}": v for prec in ("fp32_mixed", "fp64")
+                               for f, v in down(out[prec]["fields"]).items()})
+        line["saved_fields"] = args.save_fields
     print(json.dumps(line), flush=True)
+    return 0
+
+
+def precision_oracle_arm(args):
+    """Host only: the oracle at n/4 cells per axis to t_end, against the 4^3
+    block averages that --config precision --save-fields stored; relative L1
+    (volume-weighted) of density and specific internal energy."""
+    import numpy as np
+
+    import oracle
+    from paper_2209_01983_gb300 import inputs
+
+    saved = np.load(args.save_fields)
+    n, t_end = int(saved["n"]), float(saved["t_end"])
+    oracle.build()
+    mo, po = inputs.sedov_octant(n // 4)
+    o = oracle.Oracle.from_problem(mo, po)
+    t0 = time.perf_counter()
+    rc, oc = o.run(t_end=t_end, remap_every=1)
+    secs = time.perf_counter() - t0
+    if rc != 0:
+        raise RuntimeError(f"oracle stopped with status {rc}")
+    ref = {"rho": o.field("rho"), "e": o.field("e")}
+    wo = o.field("vol")
+    res = {prec: {f: float(np.sum(np.abs(saved[f"{prec}_{f}"] - ref[f]) * wo) / np.sum(np.abs(ref[f]) * wo))
+                  for f in ("rho", "e")} for prec in ("fp32_mixed", "fp64")}
+    print(json.dumps({"config": {"workload": f"sedov-octant-{n}^3-to-t{t_end}, 4^3 block averages vs "
+                                             f"the oracle at {n // 4}^3"},
+                      "oracle": f"{n // 4}^3 to t={t_end}, {oc} cycles, {secs:.1f} s on one core",
+                      "downsampled_vs_oracle_l1_rel": res}), flush=True)
     return 0
 
 
@@ -526,6 +555,8 @@ def main():
         return batch_arm(args)
     if args.config == "precision":
         return precision_arm(args)
+    if args.config == "precision-oracle":
+        return precision_oracle_arm(args)
     return gpu_arm(args)
 
 

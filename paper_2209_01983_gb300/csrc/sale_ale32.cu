@@ -295,16 +295,16 @@ __device__ __forceinline__ void node_faces2(const Fields<float> &F, int n, int s
 // The single-mesh kernels and the batched kernels wrap the same bodies, so
 // a mesh advanced inside a batch is bitwise equal to the mesh alone.
 
-template <bool JIT>
+template <bool JIT, bool IN>
 __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
-  if (i > F.nx || j > F.ny || k > F.nz || !S->next_active) return;
+  if ((!IN && (i > F.nx || j > F.ny || k > F.nz)) || !S->next_active) return;
   const float h = S->next_h32;
   const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
   const int n = i + sy * j + sz * k;
   const int csy = F.nx, csz = F.nx * F.ny;
   const int c0 = (i - 1) + csy * (j - 1) + csz * (k - 1);  // cell (i-1, j-1, k-1)
-  const bool lo_ok[3] = {i > 0, j > 0, k > 0};
-  const bool hi_ok[3] = {i < F.nx, j < F.ny, k < F.nz};
+  const bool lo_ok[3] = {IN || i > 0, IN || j > 0, IN || k > 0};
+  const bool hi_ok[3] = {IN || i < F.nx, IN || j < F.ny, IN || k < F.nz};
   float sig[8];
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
@@ -324,7 +324,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   const float hm = h / (24.f * F.mn[n]);
   const float u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
   float u1 = u0 + hm * f.x, v1 = v0 + hm * f.y, w1 = w0 + hm * f.z;
-  wall_bc_f(F, i, j, k, u1, v1, w1);
+  if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
   F.u[n] = u1;
   F.v[n] = v1;
   F.w[n] = w1;
@@ -333,9 +333,9 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   F.wb[n] = 0.5f * (w0 + w1);
 }
 
-template <bool JIT>
+template <bool JIT, bool IN>
 __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
-  if (i >= F.nx || j >= F.ny || k >= F.nz || !S->next_active) return;
+  if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
   const float h = S->next_h32;
   const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
   const int n0 = i + sy * j + sz * k;
@@ -359,27 +359,28 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
   for (int a = 0; a < 8; ++a) Dd[a] = h * ub[a];
   float vx, vy, vz;
   swept_low_faces_f(E, Dd, vx, vy, vz);
-  F.dvx[c] = i > 0 ? vx : 0.f;
-  F.dvy[c] = j > 0 ? vy : 0.f;
-  F.dvz[c] = k > 0 ? vz : 0.f;
+  F.dvx[c] = IN || i > 0 ? vx : 0.f;
+  F.dvy[c] = IN || j > 0 ? vy : 0.f;
+  F.dvz[c] = IN || k > 0 ? vz : 0.f;
 }
 
 // Lagrangian volume of a cell by closure: V_E minus its net swept volume.
+template <bool IN>
 __device__ __forceinline__ float lag_volume(const Fields<float> &F, int c, int i, int j, int k) {
   const int sy = F.nx, sz = F.nx * F.ny;
   float net = -F.dvx[c] - F.dvy[c] - F.dvz[c];
-  if (i + 1 < F.nx) net += F.dvx[c + 1];
-  if (j + 1 < F.ny) net += F.dvy[c + sy];
-  if (k + 1 < F.nz) net += F.dvz[c + sz];
+  if (IN || i + 1 < F.nx) net += F.dvx[c + 1];
+  if (IN || j + 1 < F.ny) net += F.dvy[c + sy];
+  if (IN || k + 1 < F.nz) net += F.dvz[c + sz];
   return F.VE[c] - net;
 }
 
-template <int AX>
+template <int AX, bool IN>
 __device__ __forceinline__ void m_face_flux(const Fields<float> &F, int c, int i, int j, int k, float rho_c, float *mu,
                                             float *ep) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const float *dv = AX == 0 ? F.dvx : AX == 1 ? F.dvy : F.dvz;
-  if (idx == 0) {
+  if (!IN && idx == 0) {
     mu[c] = 0.f;
     ep[c] = 0.f;
     return;
@@ -392,7 +393,7 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, int c, int i
   } else {
     const int stride = AX == 0 ? 1 : AX == 1 ? F.nx : F.nx * F.ny;
     const int d = c - stride;
-    const float VL = lag_volume(F, d, AX == 0 ? i - 1 : i, AX == 1 ? j - 1 : j, AX == 2 ? k - 1 : k);
+    const float VL = lag_volume<IN>(F, d, AX == 0 ? i - 1 : i, AX == 1 ? j - 1 : j, AX == 2 ? k - 1 : k);
     rho_d = F.m[d] / VL;
     e_d = F.e[d];
   }
@@ -402,15 +403,16 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, int c, int i
 }
 
 // Lagrangian densities (closure) and donor-cell fluxes of the low faces.
+template <bool IN>
 __device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
-  if (i >= F.nx || j >= F.ny || k >= F.nz || !S->next_active) return;
+  if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
   const int c = i + F.nx * (j + F.ny * k);
-  const float VL = lag_volume(F, c, i, j, k);
+  const float VL = lag_volume<IN>(F, c, i, j, k);
   if (!(VL > 0.f)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
   const float rho_c = F.m[c] / VL;
-  m_face_flux<0>(F, c, i, j, k, rho_c, F.mux, F.epx);
-  m_face_flux<1>(F, c, i, j, k, rho_c, F.muy, F.epy);
-  m_face_flux<2>(F, c, i, j, k, rho_c, F.muz, F.epz);
+  m_face_flux<0, IN>(F, c, i, j, k, rho_c, F.mux, F.epx);
+  m_face_flux<1, IN>(F, c, i, j, k, rho_c, F.muy, F.epy);
+  m_face_flux<2, IN>(F, c, i, j, k, rho_c, F.muz, F.epz);
 }
 
 // ---------------------------------------------------------------------------
@@ -420,7 +422,7 @@ __device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars
 // Dual mass flux along the mesh edge from node (i,j,k) to its +AX
 // neighbour: sum over the (up to four) cells around the edge of
 // (mu_low_face + mu_high_face) / 8.
-template <int AX>
+template <int AX, bool IN>
 __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j, int k) {
   const float *mu = AX == 0 ? F.mux : AX == 1 ? F.muy : F.muz;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
@@ -432,22 +434,22 @@ __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j
     if (AX == 0) { cj = j - 1 + (s & 1); ck = k - 1 + (s >> 1); }
     if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
     if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
-    if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
+    if (!IN && (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz)) continue;
     const int c = ci + F.nx * (cj + F.ny * ck);
     const int hi_idx = (AX == 0 ? ci : AX == 1 ? cj : ck) + 1;
-    psi += mu[c] + (hi_idx < n_ax ? mu[c + stride] : 0.f);
+    psi += mu[c] + (IN || hi_idx < n_ax ? mu[c + stride] : 0.f);
   }
   return 0.125f * psi;
 }
 
-template <int AX, int SIDE>
+template <int AX, int SIDE, bool IN>
 __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, float &m, F3 &p,
                                             float &ke) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
-  if (SIDE == 0 && idx == n_ax) return;
-  if (SIDE == 1 && idx == 0) return;
-  const float psi = m_edge_psi<AX>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
+  if (!IN && SIDE == 0 && idx == n_ax) return;
+  if (!IN && SIDE == 1 && idx == 0) return;
+  const float psi = m_edge_psi<AX, IN>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
                                    (SIDE == 1 && AX == 2) ? k - 1 : k);
   const int stride = AX == 0 ? 1 : AX == 1 ? (F.nx + 1) : (F.nx + 1) * (F.ny + 1);
   const int lo = SIDE == 0 ? n : n - stride;
@@ -459,8 +461,9 @@ __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j
   ke += flux * 0.5f * dotf(ud, ud);
 }
 
+template <bool IN>
 __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
-  if (i > F.nx || j > F.ny || k > F.nz) return;
+  if (!IN && (i > F.nx || j > F.ny || k > F.nz)) return;
   const int n = i + (F.nx + 1) * (j + (F.ny + 1) * k);
   if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
     F.ub[n] = F.u[n];
@@ -473,16 +476,16 @@ __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevSc
   float m = m0;
   F3 p = m0 * u0;
   float ke = 0.5f * m0 * dotf(u0, u0);
-  m_node_edge<0, 0>(F, i, j, k, n, m, p, ke);
-  m_node_edge<0, 1>(F, i, j, k, n, m, p, ke);
-  m_node_edge<1, 0>(F, i, j, k, n, m, p, ke);
-  m_node_edge<1, 1>(F, i, j, k, n, m, p, ke);
-  m_node_edge<2, 0>(F, i, j, k, n, m, p, ke);
-  m_node_edge<2, 1>(F, i, j, k, n, m, p, ke);
+  m_node_edge<0, 0, IN>(F, i, j, k, n, m, p, ke);
+  m_node_edge<0, 1, IN>(F, i, j, k, n, m, p, ke);
+  m_node_edge<1, 0, IN>(F, i, j, k, n, m, p, ke);
+  m_node_edge<1, 1, IN>(F, i, j, k, n, m, p, ke);
+  m_node_edge<2, 0, IN>(F, i, j, k, n, m, p, ke);
+  m_node_edge<2, 1, IN>(F, i, j, k, n, m, p, ke);
   if (!(m > 0.f)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
   const float inv_m = 1.f / m;
   float u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
-  wall_bc_f(F, i, j, k, u1, v1, w1);
+  if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
   F.ub[n] = u1;
   F.vb[n] = v1;
   F.wb[n] = w1;
@@ -541,12 +544,12 @@ __device__ __forceinline__ float m_eos_cell(const Fields<float> &F, int c, int i
 }
 
 // Cell remap + EoS + dt; nblk = blocks of this mesh (last-block detection).
-template <bool JIT>
+template <bool JIT, bool IN>
 __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScalars *S, int i, int j, int k,
                                                  unsigned nblk) {
   if (!S->next_active) return;  // uniform over the mesh's blocks: S changes only in its last block
   float dtc = INFINITY;
-  if (i < F.nx && j < F.ny && k < F.nz) {
+  if (IN || (i < F.nx && j < F.ny && k < F.nz)) {
     const int sy = F.nx, sz = F.nx * F.ny;
     const int c = i + sy * j + sz * k;
     // float-float: every flux is added to the conserved quantities on its
@@ -559,17 +562,18 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
     ie = df_add_f(ie, -F.epx[c]);
     ie = df_add_f(ie, -F.epy[c]);
     ie = df_add_f(ie, -F.epz[c]);
-    if (i + 1 < F.nx) { m1 = df_add_f(m1, F.mux[c + 1]); ie = df_add_f(ie, F.epx[c + 1]); }
-    if (j + 1 < F.ny) { m1 = df_add_f(m1, F.muy[c + sy]); ie = df_add_f(ie, F.epy[c + sy]); }
-    if (k + 1 < F.nz) { m1 = df_add_f(m1, F.muz[c + sz]); ie = df_add_f(ie, F.epz[c + sz]); }
+    if (IN || i + 1 < F.nx) { m1 = df_add_f(m1, F.mux[c + 1]); ie = df_add_f(ie, F.epx[c + 1]); }
+    if (IN || j + 1 < F.ny) { m1 = df_add_f(m1, F.muy[c + sy]); ie = df_add_f(ie, F.epy[c + sy]); }
+    if (IN || k + 1 < F.nz) { m1 = df_add_f(m1, F.muz[c + sz]); ie = df_add_f(ie, F.epz[c + sz]); }
     if (F.ke_fix) {
       const int nsy = F.nx + 1, nsz = (F.nx + 1) * (F.ny + 1);
       const int n0 = i + nsy * j + nsz * k;
 #pragma unroll
       for (int a = 0; a < 8; ++a) {
         const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
-        const float share = ((ni == 0 || ni == F.nx) ? 1.f : 0.5f) * ((nj == 0 || nj == F.ny) ? 1.f : 0.5f) *
-                            ((nk == 0 || nk == F.nz) ? 1.f : 0.5f);
+        const float share = IN ? 0.125f
+                               : ((ni == 0 || ni == F.nx) ? 1.f : 0.5f) * ((nj == 0 || nj == F.ny) ? 1.f : 0.5f) *
+                                     ((nk == 0 || nk == F.nz) ? 1.f : 0.5f);
         ie = df_add_f(ie, F.dke[n0 + (a & 1) + ((a >> 1) & 1) * nsy + ((a >> 2) & 1) * nsz] * share);
       }
     }
@@ -605,32 +609,52 @@ __device__ __forceinline__ void m_eos_body(const Fields<float> &F, DevScalars *S
 // and batched (table)
 // ---------------------------------------------------------------------------
 
-template <bool JIT>
+// IN: the block's whole tile lies in 1 <= index <= n - 2 on every axis
+// (cells and nodes alike), so every neighbour a body reads exists, no node
+// is on a wall and every node is shared by eight cells: the bodies drop
+// those tests, with bitwise the same results.
+template <bool JIT, bool IN>
 __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevScalars *S, int i, int j, int k,
                                          unsigned nblk, int mode) {
   switch (kid) {
-    case kMixNodes: m_nodes_body<JIT>(F, S, i, j, k); break;
-    case kMixCells: m_cells_body<JIT>(F, S, i, j, k); break;
-    case kMixFluxes: m_fluxes_body(F, S, i, j, k); break;
-    case kMixRemapNodes: m_remap_nodes_body(F, S, i, j, k); break;
-    case kMixRemapEos: m_remap_eos_body<JIT>(F, S, i, j, k, nblk); break;
+    case kMixNodes: m_nodes_body<JIT, IN>(F, S, i, j, k); break;
+    case kMixCells: m_cells_body<JIT, IN>(F, S, i, j, k); break;
+    case kMixFluxes: m_fluxes_body<IN>(F, S, i, j, k); break;
+    case kMixRemapNodes: m_remap_nodes_body<IN>(F, S, i, j, k); break;
+    case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
     default: break;
   }
 }
 
-// Blocks per SM the register budget is held to, per kernel and block size
-// (the heavy cell kernels keep 768 / 1024 threads resident per SM).
+template <int SH>
+__device__ __forceinline__ bool tile_interior(const Fields<float> &F, int bx, int by, int k) {
+  const int i0 = bx * tile_x(SH), j0 = by * tile_y(SH);
+  return i0 >= 1 && i0 + tile_x(SH) <= F.nx - 1 && j0 >= 1 && j0 + tile_y(SH) <= F.ny - 1 && k >= 1 &&
+         k <= F.nz - 2;
+}
+
+template <int KID, bool JIT, int SH>
+__device__ __forceinline__ void run_tile(const Fields<float> &F, DevScalars *S, int bx, int by, int k, unsigned nblk,
+                                         int mode) {
+  const int i = bx * tile_x(SH) + threadIdx.x, j = by * tile_y(SH) + threadIdx.y;
+  if (KID != kMixEos && tile_interior<SH>(F, bx, by, k)) run_body<JIT, true>(KID, F, S, i, j, k, nblk, mode);
+  else run_body<JIT, false>(KID, F, S, i, j, k, nblk, mode);
+}
+
+// Blocks per SM the register budget is held to, per kernel and block size:
+// 768 resident threads per SM for the cell pass, 1024 (64 registers) for
+// the others; the node gathers lose more to occupancy than they gain from
+// the extra loads in flight of an uncapped build.
 __host__ __device__ constexpr int min_blocks(int kid, int threads) {
-  return kid == kMixCells ? 768 / threads : (kid == kMixRemapEos || kid == kMixEos) ? 1024 / threads : 1;
+  return kid == kMixCells ? 768 / threads : (kid == kMixRemapEos || kid == kMixEos || kid == kMixNodes || kid == kMixRemapNodes) ? 1024 / threads : 1;
 }
 
 template <int KID, bool JIT, int SH>
 __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
     k_m(Fields<float> F, DevScalars *S, int mode) {
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  run_body<JIT>(KID, F, S, blockIdx.x * tile_x(SH) + threadIdx.x, blockIdx.y * tile_y(SH) + threadIdx.y, blockIdx.z,
-                nblk, mode);
+  run_tile<KID, JIT, SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z, nblk, mode);
 }
 
 // Batched: block b works on mesh tab[b].x, tile (tab[b].y, tab[b].z) of
@@ -645,9 +669,8 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   int *dst = reinterpret_cast<int *>(&it);
   for (int w = tid; w < (int)(sizeof(BatchItem) / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
   __syncthreads();
-  const int i = t.y * tile_x(SH) + threadIdx.x, j = t.z * tile_y(SH) + threadIdx.y, k = t.w;
-  if (it.F.off4) run_body<true>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
-  else run_body<false>(KID, it.F, it.S, i, j, k, it.nblk_cell, 0);
+  if (it.F.off4) run_tile<KID, true, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
+  else run_tile<KID, false, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
 }
 
 // Per mesh of a batch: t_end = inf, cycle_limit = cycle + cycles, decide.
