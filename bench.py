@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--jitter", type=float, default=0.1)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default 32x8 tiles of the FP32-mixed kernels")
+    ap.add_argument("--tile", type=int, default=None, help="FP32-mixed tile shape to use instead of tuning")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
@@ -193,6 +194,44 @@ def replica_rate(ms_local, cells_per_rank, steps, world, dist=None, device="cpu"
     return world * cells_per_rank * steps / (ms * 1e-3), ms
 
 
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_per_unit_sedov160.txt")
+
+
+def source_digest():
+    """Digest of the kernel sources: the ncu traffic figures hold only for
+    the kernels they were taken on."""
+    import glob
+    import hashlib
+
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2209_01983_gb300", "csrc")
+    for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
+        h.update(os.path.basename(f).encode())
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def load_traffic():
+    """({(precision, kernel): DRAM bytes per unit}, note) from the committed
+    ncu summary; empty when the kernels changed since it was taken."""
+    try:
+        with open(TRAFFIC_FILE) as f:
+            lines = f.read().splitlines()
+    except OSError:
+        return {}, "no ncu traffic summary"
+    digest, table = None, {}
+    for ln in lines:
+        if ln.startswith("# source-digest:"):
+            digest = ln.split(":", 1)[1].strip()
+        elif ln.strip() and not ln.startswith("#"):
+            prec, kern, _unit, per_unit = ln.split()[:4]
+            table[(prec, kern)] = float(per_unit)
+    if digest != source_digest():
+        return {}, "kernels changed since the ncu traffic capture"
+    return table, f"ncu dram__bytes_read.sum + dram__bytes_write.sum per unit at 160^3, scaled ({TRAFFIC_FILE[len(ROOT) + 1:]})"
+
+
 # FP32 vector peak: 128 lanes x 2 flop x 152 SMs x 2.07 GHz.
 FP32_PEAK_TFLOPS = 128 * 2 * 152 * 2.07e9 / 1e12
 
@@ -207,7 +246,10 @@ def measure(args, precision, local, barrier):
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     tuning = None
-    if precision == "fp32_mixed" and not args.no_tune:
+    if precision == "fp32_mixed" and args.tile is not None:
+        st.set_tiling(args.tile)
+        tuning = {"shape": args.tile, "forced": True}
+    elif precision == "fp32_mixed" and not args.no_tune:
         # warm-up part 1: pick the tile shape (ordinary cycles, results unchanged)
         from paper_2209_01983_gb300 import autotune
         tuning = autotune.tune_state(st, cycles=16, repeats=2)
@@ -236,7 +278,7 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    table = costs.table(precision, "ale")
+    table = costs.table(precision, "ale", jitter=args.jitter > 0)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
     if missing:
@@ -266,6 +308,12 @@ def measure(args, precision, local, barrier):
                 "frac": kt["alg_gbs"] / peaks["hbm_gbs"], "traffic": None, "kernel": top,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
                 "fp32_tflops": kt["alg_tflops"], "fp32_frac_of_derived": kt["alg_tflops"] / FP32_PEAK_TFLOPS}
+    traffic, note = load_traffic()
+    per_unit = traffic.get((precision, top))
+    roof["traffic"] = per_unit * units(top) if per_unit is not None else None
+    roof["traffic_note"] = note
+    if per_unit is not None:
+        roof["traffic_over_algorithmic"] = per_unit / table[top][1]
     cycle_bytes = sum(table[k][1] * units(k) for k in kern)
     cycle_flops = sum(table[k][2] * units(k) for k in kern)
     secs = ms * 1e-3

@@ -84,15 +84,24 @@ MIXED_ALE = {
 }
 
 
-def table(precision: str, path: str = "ale"):
+# Jittered meshes: the reference corner gradients (24 floats per cell) are
+# cached, so the cell pass and the remap+EoS pass read them instead of
+# evaluating the gradient (and the remap+EoS pass no longer needs the
+# offsets).
+MIXED_ALE_JIT = dict(MIXED_ALE)
+MIXED_ALE_JIT["mix_cells"] = ("cell", 4 * (4 + 24 + 3 + 1 + 1 + 2 + 2 + 3), 48 + 40 + 6 + SWEPT32)
+MIXED_ALE_JIT["mix_remap_eos"] = ("cell", 4 * (6 + 4 + 1 + 3 + 24 + 2 + 6), 40 + 48 + 40 + 30)
+
+
+def table(precision: str, path: str = "ale", jitter: bool = True):
     if precision == "fp64":
         return FP64_ALE if path == "ale" else FP64
     if precision == "fp32_mixed":
-        return MIXED_ALE
+        return MIXED_ALE_JIT if jitter else MIXED_ALE
     raise KeyError(precision)
 
 
-def cycle_cost(precision: str, path: str = "ale"):
+def cycle_cost(precision: str, path: str = "ale", jitter: bool = True):
     """(bytes, flops) of one full cycle per cell."""
-    t = table(precision, path)
+    t = table(precision, path, jitter)
     return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

@@ -322,6 +322,46 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_nodes(Fields<double> F, De
   F.dke[n] = ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1);
 }
 
+// EoS and viscosity of cell c on the reference mesh (cached gradient,
+// 1/V_E, L_E) from its mass, specific energy and node velocities U; writes
+// the derived fields and returns the CFL rate (cs^2 + 2 q / rho) / (cfl L)^2
+// = 1 / dt_c^2.
+__device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long long c, const P3 (&U)[8], double m,
+                                               double e) {
+  const double V = F.VE[c];
+  const double inv_v = F.iVE[c];
+  double dvdt = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) dvdt += dot(corner_g(F.G, F.nc, c, a), U[a]);
+  const double div = dvdt * inv_v;
+  const double L = F.LE[c];
+  const double rho = m * inv_v;
+  const double p = (F.gamma - 1.0) * rho * e;
+  const double cs2 = F.gamma * (F.gamma - 1.0) * fmax(e, 0.0);
+  const double cs = sqrt(cs2);
+  double q_rho = 0.0;  // q / rho
+  if (div < 0.0) {
+    const double ld = L * div;
+    q_rho = F.c_q * ld * ld + F.c_l * cs * L * fabs(div);
+  }
+  const double q = rho * q_rho;
+  F.vol[c] = V;
+  F.rho[c] = rho;
+  F.p[c] = p;
+  F.q[c] = q;
+  F.cs[c] = cs;
+  F.sig[c] = p + q;
+  return (cs2 + 2.0 * q_rho) * F.iL2[c];
+}
+
+__device__ __forceinline__ void ale_cell_velocities(const Fields<double> &F, int i, int j, int k, P3 (&U)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    U[a] = {F.u[n], F.v[n], F.w[n]};
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
   if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -339,53 +379,48 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
     const double m1 = m0 + dm;
     double ie = m0 * F.e[c] + de;
     P3 U[8];
+    ale_cell_velocities(F, i, j, k, U);
+    if (F.ke_fix) {
 #pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
-      const long long n = node_index(F.nx, F.ny, ni, nj, nk);
-      U[a] = {F.u[n], F.v[n], F.w[n]};
-      if (F.ke_fix) {  // share 1/(cells at the node) = 2^-(interior axes), built from its bits
+      for (int a = 0; a < 8; ++a) {
+        // share 1/(cells at the node) = 2^-(interior axes), built from its bits
+        const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
         const int interior = (ni != 0 && ni != F.nx) + (nj != 0 && nj != F.ny) + (nk != 0 && nk != F.nz);
         const double share = __longlong_as_double((long long)(1023 - interior) << 52);
-        ie += F.dke[n] * share;
+        ie += F.dke[node_index(F.nx, F.ny, ni, nj, nk)] * share;
       }
     }
     if (!(m1 > 0.0)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
     const double e = ie / m1;
-    // EoS and viscosity on the reference mesh
-    const double V = F.VE[c];
-    const double inv_v = F.iVE[c];
-    double dvdt = 0.0;
-#pragma unroll
-    for (int a = 0; a < 8; ++a) dvdt += dot(corner_g(F.G, F.nc, c, a), U[a]);
-    const double div = dvdt * inv_v;
-    const double L = F.LE[c];
-    const double rho = m1 * inv_v;
-    const double p = (F.gamma - 1.0) * rho * e;
-    const double cs2 = F.gamma * (F.gamma - 1.0) * fmax(e, 0.0);
-    const double cs = sqrt(cs2);
-    double q_rho = 0.0;  // q / rho
-    if (div < 0.0) {
-      const double ld = L * div;
-      q_rho = F.c_q * ld * ld + F.c_l * cs * L * fabs(div);
-    }
-    const double q = rho * q_rho;
     F.m[c] = m1;
     F.e[c] = e;
-    F.vol[c] = V;
-    F.rho[c] = rho;
-    F.p[c] = p;
-    F.q[c] = q;
-    F.cs[c] = cs;
-    F.sig[c] = p + q;
-    // dt_c = cfl L / sqrt(cs^2 + 2 q / rho), as the rate (cs^2 + 2 q / rho) / (cfl L)^2
-    rate = (cs2 + 2.0 * q_rho) * F.iL2[c];
+    rate = ale_eos_cell(F, c, U, m1, e);
     if (rate != rate) {
       set_status(S, SALE_ENAN);
       rate = 0.0;
     }
   }
   block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
+}
+
+// EoS, viscosity and a proposed dt on the reference mesh without a remap
+// (refresh after fields were set from the host).
+__global__ void __launch_bounds__(kBlock) k_ale_eos(Fields<double> F, DevScalars *S, int mode) {
+  if (S->status != 0) return;  // uniform over the grid
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  double rate = 0.0;
+  if (c < F.nc) {
+    int i, j, k;
+    cell_ijk(c, F.nx, F.ny, i, j, k);
+    P3 U[8];
+    ale_cell_velocities(F, i, j, k, U);
+    rate = ale_eos_cell(F, c, U, F.m[c], F.e[c]);
+    if (rate != rate) {
+      set_status(S, SALE_ENAN);
+      rate = 0.0;
+    }
+  }
+  block_min_dt_and_finalize<double, true>(F, S, rate, mode, 0.0);
 }
 
 static inline unsigned grid_ale(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
@@ -403,6 +438,7 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleFluxes: k_ale_fluxes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleRemapNodes: k_ale_remap_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S); break;
+    case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
     case kAleRemapEos: k_ale_remap_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     default: break;
   }

@@ -999,7 +999,8 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
 extern "C" int sale_refresh(sale_state *st) {
   int rc = ready(st, "sale_refresh");
   if (rc) return rc;
-  launch_k(st, st->precision == SALE_FP64 ? kEos : kMixEos, kDtPropose);
+  // on the reference mesh the FP64 refresh reads the cached geometry
+  launch_k(st, st->precision == SALE_FP64 ? (st->x_is_ref ? kAleEos : kEos) : kMixEos, kDtPropose);
   CUDA_TRY(cudaGetLastError());
   return SALE_OK;
 }
@@ -1316,7 +1317,7 @@ static const char *const kKernelNames[kNumKernels] = {
     "init_nodes",   "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",     "remap_nodes",
     "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
     "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
-    "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes"};
+    "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes", "ale_eos"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

@@ -67,6 +67,7 @@ enum KernelId : int {
   kMixEos,
   kAleEdges,     // ALE path: side-quad terms of the swept hexes, per mesh edge
   kAleRemapNodes,
+  kAleEos,       // ALE path: EoS + dt on the reference mesh (refresh)
   kNumKernels
 };
 

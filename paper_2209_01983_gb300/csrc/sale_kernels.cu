@@ -468,7 +468,7 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
 template <typename R>
 void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t st) {
-  if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes) {
+  if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes || kid == kAleEos) {
     if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
     return;
   }
