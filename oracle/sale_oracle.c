@@ -488,6 +488,56 @@ void oracle_swept_volumes(const oracle_state *s, double *dvx, double *dvy,
             (k == 0 || k == nz) ? 0.0 : swept_volume(s, 2, i, j, k);
 }
 
+/* Second-order cell remap (reading: van Leer 1977).  In every cell and along
+ * every logical axis the density and specific energy get the limited slope
+ * of van Leer: the harmonic mean of the two one-sided differences when they
+ * have the same sign, else zero (also zero next to a wall, where one
+ * difference is missing).  A face then carries the average of the donor's
+ * linear profile q(xi) = q_d + s_d xi, xi in [-1/2, 1/2] across the donor,
+ * over the slab of relative thickness nu = |dV| / V_d that the face sweeps
+ * out of the donor:  q_d + side * s_d (1 - nu) / 2,  side = +1 when the
+ * slab lies at the donor's high face, -1 at its low face (nu capped at 1). */
+static double vanleer_slope(double dm, double dp) {
+  return dm * dp > 0.0 ? 2.0 * dm * dp / (dm + dp) : 0.0;
+}
+
+static double slab_average(double q, double slope, double nu, double side) {
+  return q + side * 0.5 * slope * (1.0 - (nu < 1.0 ? nu : 1.0));
+}
+
+/* Slope of field q (cells) at cell (i,j,k) along axis ax. */
+static double cell_slope(const oracle_state *s, const double *q, int i, int j, int k, int ax) {
+  const int n_ax = ax == 0 ? s->nx : ax == 1 ? s->ny : s->nz;
+  const int idx = ax == 0 ? i : ax == 1 ? j : k;
+  if (idx == 0 || idx == n_ax - 1) return 0.0;
+  const int di = ax == 0, dj = ax == 1, dk = ax == 2;
+  const double qm = q[cell_id(s, i - di, j - dj, k - dk)];
+  const double q0 = q[cell_id(s, i, j, k)];
+  const double qp = q[cell_id(s, i + di, j + dj, k + dk)];
+  return vanleer_slope(q0 - qm, qp - q0);
+}
+
+/* Mass and energy flux of the face between cells lo and hi along ax with
+ * swept volume dv (> 0: hi donates). */
+static void face_fluxes(const oracle_state *s, const double *rho_l, const double *vol_l, int lo_i, int lo_j,
+                        int lo_k, int ax, double dv, double *mu, double *eflux) {
+  const int di = ax == 0, dj = ax == 1, dk = ax == 2;
+  const long long lo = cell_id(s, lo_i, lo_j, lo_k), hi = cell_id(s, lo_i + di, lo_j + dj, lo_k + dk);
+  const int hi_donates = dv > 0.0;
+  const long long dn = hi_donates ? hi : lo;
+  double rho_f = rho_l[dn], e_f = s->e[dn];
+  if (s->prm.remap_order == 2) {
+    const int di_ = hi_donates ? lo_i + di : lo_i, dj_ = hi_donates ? lo_j + dj : lo_j,
+              dk_ = hi_donates ? lo_k + dk : lo_k;
+    const double nu = fabs(dv) / vol_l[dn];
+    const double side = hi_donates ? -1.0 : 1.0;
+    rho_f = slab_average(rho_l[dn], cell_slope(s, rho_l, di_, dj_, dk_, ax), nu, side);
+    e_f = slab_average(s->e[dn], cell_slope(s, s->e, di_, dj_, dk_, ax), nu, side);
+  }
+  *mu = rho_f * dv;
+  *eflux = *mu * e_f;
+}
+
 int oracle_remap_step(oracle_state *s) {
   if (s->status) return s->status;
   const int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -497,11 +547,11 @@ int oracle_remap_step(oracle_state *s) {
   const long long nfz = (long long)nx * ny * (nz + 1);
   double *dvx = alloc_zero(nfx), *dvy = alloc_zero(nfy), *dvz = alloc_zero(nfz);
   double *mux = alloc_zero(nfx), *muy = alloc_zero(nfy), *muz = alloc_zero(nfz);
-  double *rho_l = alloc_zero(nc), *m_new = alloc_zero(nc), *ie_new = alloc_zero(nc);
+  double *rho_l = alloc_zero(nc), *m_new = alloc_zero(nc), *ie_new = alloc_zero(nc), *vol_l = alloc_zero(nc);
   double *mn_new = alloc_zero(nn), *px = alloc_zero(nn), *py = alloc_zero(nn);
   double *pz = alloc_zero(nn), *ke = alloc_zero(nn), *dke = alloc_zero(nn);
   double *all[] = {dvx, dvy, dvz, mux, muy, muz, rho_l, m_new, ie_new,
-                   mn_new, px, py, pz, ke, dke};
+                   mn_new, px, py, pz, ke, dke, vol_l};
   const size_t nall = sizeof(all) / sizeof(all[0]);
   for (size_t i = 0; i < nall; ++i)
     if (!all[i]) {
@@ -516,7 +566,8 @@ int oracle_remap_step(oracle_state *s) {
         long long c = cell_id(s, i, j, k);
         double X[24];
         gather_hex(s, i, j, k, s->x, s->y, s->z, X);
-        rho_l[c] = s->m[c] / oracle_hex_volume(X);
+        vol_l[c] = oracle_hex_volume(X);
+        rho_l[c] = s->m[c] / vol_l[c];
       }
 
   /* 1. Swept volumes of every face. */
@@ -533,39 +584,39 @@ int oracle_remap_step(oracle_state *s) {
       for (int i = 1; i < nx; ++i) {
         long long f = i + (long long)(nx + 1) * (j + (long long)ny * k);
         long long lo = cell_id(s, i - 1, j, k), hi = cell_id(s, i, j, k);
-        long long dn = dvx[f] > 0.0 ? hi : lo;
-        double mu = rho_l[dn] * dvx[f];
+        double mu, ef;
+        face_fluxes(s, rho_l, vol_l, i - 1, j, k, 0, dvx[f], &mu, &ef);
         mux[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
-        ie_new[lo] += mu * s->e[dn];
-        ie_new[hi] -= mu * s->e[dn];
+        ie_new[lo] += ef;
+        ie_new[hi] -= ef;
       }
   for (int k = 0; k < nz; ++k)
     for (int j = 1; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         long long f = i + (long long)nx * (j + (long long)(ny + 1) * k);
         long long lo = cell_id(s, i, j - 1, k), hi = cell_id(s, i, j, k);
-        long long dn = dvy[f] > 0.0 ? hi : lo;
-        double mu = rho_l[dn] * dvy[f];
+        double mu, ef;
+        face_fluxes(s, rho_l, vol_l, i, j - 1, k, 1, dvy[f], &mu, &ef);
         muy[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
-        ie_new[lo] += mu * s->e[dn];
-        ie_new[hi] -= mu * s->e[dn];
+        ie_new[lo] += ef;
+        ie_new[hi] -= ef;
       }
   for (int k = 1; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
       for (int i = 0; i < nx; ++i) {
         long long f = i + (long long)nx * (j + (long long)ny * k);
         long long lo = cell_id(s, i, j, k - 1), hi = cell_id(s, i, j, k);
-        long long dn = dvz[f] > 0.0 ? hi : lo;
-        double mu = rho_l[dn] * dvz[f];
+        double mu, ef;
+        face_fluxes(s, rho_l, vol_l, i, j, k - 1, 2, dvz[f], &mu, &ef);
         muz[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
-        ie_new[lo] += mu * s->e[dn];
-        ie_new[hi] -= mu * s->e[dn];
+        ie_new[lo] += ef;
+        ie_new[hi] -= ef;
       }
 
   /* 3. Node (dual-mesh) fluxes along every mesh edge (a -> b = a + e_ax).

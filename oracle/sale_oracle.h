@@ -15,7 +15,11 @@
  *     node mean;
  *   - compatible energy update (Caramana, Burton, Shashkov, Whalen 1998);
  *   - donor-cell (upwind) remap of mass, energy, momentum (Amsden et al.
- *     1980, "SALE"), with kinetic-energy fix-up.
+ *     1980, "SALE"), with kinetic-energy fix-up;
+ *   - optionally, second-order cell remap: van Leer's limited
+ *     piecewise-linear profile in the donor cell (van Leer 1977, "Towards
+ *     the ultimate conservative difference scheme IV"), averaged over the
+ *     slab the face sweeps.
  *
  * Layout: SoA, x index fastest.  Cell c = i + nx*(j + ny*k); node
  * n = i + (nx+1)*(j + (ny+1)*k).  Local node a = di + 2*dj + 4*dk of cell
@@ -46,6 +50,7 @@ typedef struct oracle_params {
   double dt_init;    /* cap on the first dt (<=0 or inf: none)            */
   int ke_fix;        /* 1: remap returns lost kinetic energy to cells     */
   int reflect[6];    /* x-lo,x-hi,y-lo,y-hi,z-lo,z-hi: 1 = reflecting wall */
+  int remap_order;   /* cell remap: 2 = van Leer piecewise linear, else first-order donor cell */
 } oracle_params;
 
 typedef struct oracle_state {

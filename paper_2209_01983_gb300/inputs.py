@@ -92,6 +92,7 @@ class ProblemDesc:
     dt_init: float = math.inf
     dt_growth: float = 1.1
     ke_fix: int = 1
+    remap_order: int = 1  # cell remap: 1 donor cell, 2 van Leer piecewise linear
 
 
 def mesh_nodes(md: MeshDesc):
