@@ -18,6 +18,7 @@ value = all ranks' cell-updates / the slowest rank's time.
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import json
 import math
 import os
@@ -48,6 +49,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="keep the default 32x8 tiles of the FP32-mixed kernels")
     ap.add_argument("--tile", type=int, default=None, help="FP32-mixed tile shape to use instead of tuning")
+    ap.add_argument("--remap-order", type=int, default=1, choices=(1, 2),
+                    help="cell remap: 1 donor cell, 2 van Leer piecewise linear")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
@@ -168,8 +171,10 @@ def reference_arm(args):
 
 
 def workload_config(args, precision):
-    return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-ale-every-cycle",
-            "cells": args.n ** 3, "gamma": 1.4, "remap_every": 1, "precision": precision,
+    order = "" if args.remap_order == 1 else "-remap2"
+    return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-ale-every-cycle{order}",
+            "cells": args.n ** 3, "gamma": 1.4, "remap_every": 1, "remap_order": args.remap_order,
+            "precision": precision,
             "l2": "state larger than the 129 MB L2 (no flush)", "parallelism": "replicas"}
 
 
@@ -243,6 +248,7 @@ def measure(args, precision, local, barrier):
     from paper_2209_01983_gb300 import costs, inputs, sale
 
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
+    pd = dataclasses.replace(pd, remap_order=args.remap_order)
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     tuning = None
@@ -278,7 +284,7 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    table = costs.table(precision, "ale", jitter=args.jitter > 0)
+    table = costs.table(precision, "ale", jitter=args.jitter > 0, order=args.remap_order)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
     if missing:

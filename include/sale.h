@@ -94,7 +94,11 @@ typedef struct {
  * Velocities start at zero.  cfl: Courant number; c_q, c_l: quadratic and
  * linear viscosity coefficients; dt_init: cap on the first step (<= 0 or
  * inf: none); dt_growth: max ratio of successive steps; ke_fix: return the
- * kinetic energy lost in the momentum remap to the cells (1) or not (0). */
+ * kinetic energy lost in the momentum remap to the cells (1) or not (0);
+ * remap_order: cell remap of density and specific energy, 1 (or 0) the
+ * first-order donor cell, 2 van Leer's limited piecewise-linear profile in
+ * the donor averaged over the swept slab (the node remap stays donor
+ * node). */
 typedef struct {
   int kind;
   double gamma;
@@ -102,6 +106,7 @@ typedef struct {
   double rho_bg, p_bg, rho_blast, p_blast, e_deposit;
   double cfl, c_q, c_l, dt_init, dt_growth;
   int ke_fix;
+  int remap_order;
 } sale_problem_desc;
 
 /* Diagnostics (FP64 sums in a fixed reduction order). */

@@ -93,15 +93,38 @@ MIXED_ALE_JIT["mix_cells"] = ("cell", 4 * (4 + 24 + 3 + 1 + 1 + 2 + 2 + 3), 48 +
 MIXED_ALE_JIT["mix_remap_eos"] = ("cell", 4 * (6 + 4 + 1 + 3 + 24 + 2 + 6), 40 + 48 + 40 + 30)
 
 
-def table(precision: str, path: str = "ale", jitter: bool = True):
+# Second-order cell remap (van Leer piecewise-linear donor cell).
+SLOPE = 7  # two one-sided differences, sign test, harmonic mean
+SLAB = 6   # 1 - min(nu, 1), scaled slope, add
+FP64_ALE_O2 = dict(FP64_ALE)
+# rho_L, e read (the neighbours' from cache); 6 slopes written
+FP64_ALE_O2["ale_slopes"] = ("cell", 8 * (2 + 6), 6 * SLOPE)
+# 3 swept volumes, rho_L, e, 1/V_L, 6 slopes read; 9 fluxes / dual-flux parts written
+FP64_ALE_O2["ale_fluxes"] = ("cell", 8 * (3 + 3 + 6 + 9), 15 + 6 * (2 * SLAB + 1))
+# 3 swept volumes, V_E, m read; V_L, rho_L, 1/V_L written
+FP64_ALE_O2["ale_density"] = ("cell", 8 * (3 + 2 + 3), 9)
+MIXED_O2 = {
+    # 3 swept volumes, V_E, m read; V_L, rho_L written
+    "mix_density": ("cell", 4 * (3 + 2 + 2), 8),
+    # 3 swept volumes, rho_L, e, V_L read; 6 fluxes written (slopes in registers)
+    "mix_fluxes": ("cell", 4 * (3 + 3 + 6), 3 * (2 * SLOPE + 2 * SLAB + 3)),
+}
+
+
+def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1):
     if precision == "fp64":
-        return FP64_ALE if path == "ale" else FP64
+        if path != "ale":
+            return FP64
+        return FP64_ALE_O2 if order == 2 else FP64_ALE
     if precision == "fp32_mixed":
-        return MIXED_ALE_JIT if jitter else MIXED_ALE
+        t = dict(MIXED_ALE_JIT if jitter else MIXED_ALE)
+        if order == 2:
+            t.update(MIXED_O2)
+        return t
     raise KeyError(precision)
 
 
-def cycle_cost(precision: str, path: str = "ale", jitter: bool = True):
+def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1):
     """(bytes, flops) of one full cycle per cell."""
-    t = table(precision, path, jitter)
+    t = table(precision, path, jitter, order)
     return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

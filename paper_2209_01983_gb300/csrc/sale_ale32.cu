@@ -402,11 +402,61 @@ __device__ __forceinline__ void m_face_flux(const Fields<float> &F, int c, int i
   ep[c] = f * e_d;
 }
 
+// Second-order remap: the low-face flux along AX from the donor's limited
+// linear profile of rho_L and e (F.vol, F.rho hold V_L and rho_L from the
+// density pass), averaged over the swept slab.
+template <int AX, bool IN>
+__device__ __forceinline__ void m_face_flux2(const Fields<float> &F, int c, int i, int j, int k, float *mu,
+                                             float *ep) {
+  const int idx = AX == 0 ? i : AX == 1 ? j : k;
+  const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
+  const float *dv = AX == 0 ? F.dvx : AX == 1 ? F.dvy : F.dvz;
+  if (!IN && idx == 0) {
+    mu[c] = 0.f;
+    ep[c] = 0.f;
+    return;
+  }
+  const int stride = AX == 0 ? 1 : AX == 1 ? F.nx : F.nx * F.ny;
+  const float v = dv[c];
+  const bool hd = v > 0.f;
+  const int d = hd ? c : c - stride;
+  const int di = hd ? idx : idx - 1;  // donor index along AX
+  const float rho_d = F.rho[d], e_d = F.e[d];
+  float sr = 0.f, se = 0.f;
+  if (di > 0 && di < n_ax - 1) {
+    sr = vanleer_slope_f(rho_d - F.rho[d - stride], F.rho[d + stride] - rho_d);
+    se = vanleer_slope_f(e_d - F.e[d - stride], F.e[d + stride] - e_d);
+  }
+  const float nu = fabsf(v) / F.vol[d];
+  const float side = hd ? -1.f : 1.f;
+  const float f = slab_average_f(rho_d, sr, nu, side) * v;
+  mu[c] = f;
+  ep[c] = f * slab_average_f(e_d, se, nu, side);
+}
+
+// Lagrangian volume and density of every cell (second-order remap only,
+// which needs them at the donor's neighbours too).
+template <bool IN>
+__device__ __forceinline__ void m_density_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active || F.remap_order != 2) return;
+  const int c = i + F.nx * (j + F.ny * k);
+  const float VL = lag_volume<IN>(F, c, i, j, k);
+  if (!(VL > 0.f)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
+  F.vol[c] = VL;
+  F.rho[c] = F.m[c] / VL;
+}
+
 // Lagrangian densities (closure) and donor-cell fluxes of the low faces.
 template <bool IN>
 __device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
   if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
   const int c = i + F.nx * (j + F.ny * k);
+  if (F.remap_order == 2) {
+    m_face_flux2<0, IN>(F, c, i, j, k, F.mux, F.epx);
+    m_face_flux2<1, IN>(F, c, i, j, k, F.muy, F.epy);
+    m_face_flux2<2, IN>(F, c, i, j, k, F.muz, F.epz);
+    return;
+  }
   const float VL = lag_volume<IN>(F, c, i, j, k);
   if (!(VL > 0.f)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
   const float rho_c = F.m[c] / VL;
@@ -623,6 +673,7 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
     case kMixRemapNodes: m_remap_nodes_body<IN>(F, S, i, j, k); break;
     case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
+    case kMixDensity: m_density_body<IN>(F, S, i, j, k); break;
     default: break;
   }
 }
@@ -730,6 +781,7 @@ void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, i
     case kMixRemapNodes: launch_one<kMixRemapNodes>(F, S, mode, shape, st); break;
     case kMixRemapEos: launch_one<kMixRemapEos>(F, S, mode, shape, st); break;
     case kMixEos: launch_one<kMixEos>(F, S, mode, shape, st); break;
+    case kMixDensity: launch_one<kMixDensity>(F, S, mode, shape, st); break;
     default: break;
   }
 }
@@ -743,6 +795,7 @@ static void launch_batch_shaped(int kid, const BatchItem *items, const int4 *tab
     case kMixFluxes: kb_m<kMixFluxes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixRemapNodes: kb_m<kMixRemapNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixRemapEos: kb_m<kMixRemapEos, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixDensity: kb_m<kMixDensity, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;
   }
 }

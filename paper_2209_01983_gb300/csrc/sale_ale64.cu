@@ -210,43 +210,92 @@ __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevSca
   if (!(VL > 0.0)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
   F.vol[c] = VL;
   F.rho[c] = F.m[c] / VL;
+  if (F.remap_order == 2) F.ivl[c] = 1.0 / VL;  // the six faces' swept fractions multiply by it
+}
+
+// Limited slopes of the Lagrangian density and the specific energy along
+// x, y, z of every cell (second-order remap; zero next to a wall).
+__global__ void __launch_bounds__(kBlock) k_ale_slopes(Fields<double> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  const int idx[3] = {i, j, k}, n_ax[3] = {F.nx, F.ny, F.nz};
+  const long long stride[3] = {1, F.nx, (long long)F.nx * F.ny};
+  double *sr[3] = {F.srx, F.sry, F.srz}, *se[3] = {F.sex, F.sey, F.sez};
+  const double r0 = F.rho[c], e0 = F.e[c];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    double s_r = 0.0, s_e = 0.0;
+    if (idx[a] > 0 && idx[a] < n_ax[a] - 1) {
+      s_r = vanleer_slope(r0 - F.rho[c - stride[a]], F.rho[c + stride[a]] - r0);
+      s_e = vanleer_slope(e0 - F.e[c - stride[a]], F.e[c + stride[a]] - e0);
+    }
+    sr[a][c] = s_r;
+    se[a][c] = s_e;
+  }
+}
+
+// Mass flux through a face with swept volume v whose donor is dn (the
+// face is the donor's low face when hi_donates); with O2 the donor density
+// and energy are the slab averages of its limited linear profile.  The
+// energy flux is returned in ef.
+template <bool O2>
+__device__ __forceinline__ double ale_donor_flux(const Fields<double> &F, const double *sr, const double *se,
+                                                 long long dn, bool hi_donates, double v, double &ef) {
+  double rho_f = F.rho[dn], e_f = F.e[dn];
+  if (O2) {
+    const double nu = fabs(v) * F.ivl[dn];
+    const double side = hi_donates ? -1.0 : 1.0;
+    rho_f = slab_average(rho_f, sr[dn], nu, side);
+    e_f = slab_average(e_f, se[dn], nu, side);
+  }
+  const double f = rho_f * v;
+  ef = f * e_f;
+  return f;
 }
 
 // Donor-cell fluxes of the low face normal to AX; also the cell's part of
 // the dual-mesh mass flux along AX, (mu_low + mu_high) / 8, mu_high being
 // the low-face flux of the +AX neighbour (0 on the high wall).  The node
 // remap sums four such parts per mesh edge instead of eight fluxes.
-template <int AX>
+template <int AX, bool O2>
 __device__ __forceinline__ void ale_face_flux(const Fields<double> &F, long long c, int idx, int n_ax,
                                               const double *dv, double *mu, double *ep, double *mq) {
   const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+  const double *sr = AX == 0 ? F.srx : AX == 1 ? F.sry : F.srz;
+  const double *se = AX == 0 ? F.sex : AX == 1 ? F.sey : F.sez;
   double lo = 0.0;
   if (idx == 0) {
     mu[c] = 0.0;
     ep[c] = 0.0;
   } else {
     const double v = dv[c];
-    const long long dn = v > 0.0 ? c : c - stride;
-    lo = F.rho[dn] * v;
+    const bool hd = v > 0.0;
+    double ef;
+    lo = ale_donor_flux<O2>(F, sr, se, hd ? c : c - stride, hd, v, ef);
     mu[c] = lo;
-    ep[c] = lo * F.e[dn];
+    ep[c] = ef;
   }
   double hi = 0.0;
   if (idx + 1 < n_ax) {
     const double v = dv[c + stride];
-    hi = F.rho[v > 0.0 ? c + stride : c] * v;
+    const bool hd = v > 0.0;
+    double ef;
+    hi = ale_donor_flux<O2>(F, sr, se, hd ? c + stride : c, hd, v, ef);
   }
   mq[c] = (lo + hi) * 0.125;
 }
 
+template <bool O2>
 __global__ void __launch_bounds__(kBlock) k_ale_fluxes(Fields<double> F, DevScalars *S) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
-  ale_face_flux<0>(F, c, i, F.nx, F.dvx, F.mux, F.epx, F.mqx);
-  ale_face_flux<1>(F, c, j, F.ny, F.dvy, F.muy, F.epy, F.mqy);
-  ale_face_flux<2>(F, c, k, F.nz, F.dvz, F.muz, F.epz, F.mqz);
+  ale_face_flux<0, O2>(F, c, i, F.nx, F.dvx, F.mux, F.epx, F.mqx);
+  ale_face_flux<1, O2>(F, c, j, F.ny, F.dvy, F.muy, F.epy, F.mqy);
+  ale_face_flux<2, O2>(F, c, k, F.nz, F.dvz, F.muz, F.epz, F.mqz);
 }
 
 // Dual mass flux of the mesh edge from node (i,j,k) to its +AX neighbour:
@@ -436,7 +485,11 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleCells: k_ale_cells<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kAleFluxes: k_ale_fluxes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kAleSlopes: k_ale_slopes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kAleFluxes:
+      if (F.remap_order == 2) k_ale_fluxes<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      else k_ale_fluxes<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      break;
     case kAleRemapNodes: k_ale_remap_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S); break;
     case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
     case kAleRemapEos: k_ale_remap_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;

@@ -219,6 +219,7 @@ struct sale_state {
   double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
   double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
+  double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
   float4 *off4;                          // FP32-mixed path: jitter offsets
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
@@ -273,6 +274,7 @@ static size_t carve(sale_state *st, char *base) {
   }
   st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
+  for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
   st->off4 = nullptr;
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
   st->G4 = nullptr;
@@ -289,6 +291,7 @@ static size_t carve(sale_state *st, char *base) {
     st->ste = (double *)cv.take(sizeof(double) * 9 * nn);
     for (int d = 0; d < 3; ++d) st->mq[d] = (double *)cv.take(sizeof(double) * nc);
     st->kd = (double *)cv.take(sizeof(double) * nn);
+    for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
@@ -377,6 +380,14 @@ static Fields<R> fields_t(const sale_state *st) {
   F.c_q32 = (float)F.c_q;
   F.c_l32 = (float)F.c_l;
   F.ke_fix = st->prob.ke_fix;
+  F.remap_order = st->prob.remap_order == 2 ? 2 : 1;
+  F.srx = (R *)st->slope[0];
+  F.sry = (R *)st->slope[1];
+  F.srz = (R *)st->slope[2];
+  F.sex = (R *)st->slope[3];
+  F.sey = (R *)st->slope[4];
+  F.sez = (R *)st->slope[5];
+  F.ivl = (R *)st->slope[6];
   for (int f = 0; f < 6; ++f) F.reflect[f] = st->reflect[f];
   return F;
 }
@@ -409,6 +420,7 @@ static int validate_problem(const sale_problem_desc &p) {
     if (!(pres[i] >= 0.0) || !std::isfinite(pres[i])) return fail(SALE_EINVAL, "problem: pressures must be finite and >= 0");
   }
   if (!std::isfinite(p.e_deposit) || p.e_deposit < 0.0) return fail(SALE_EINVAL, "problem: e_deposit must be finite and >= 0");
+  if (p.remap_order < 0 || p.remap_order > 2) return fail(SALE_EINVAL, "problem: remap_order must be 0, 1 or 2");
   return SALE_OK;
 }
 
@@ -485,7 +497,7 @@ static void record(sale_state *st, cudaEvent_t ev) {
 static void dispatch(sale_state *st, int kid, int mode, double dt_override) {
   if (st->precision == SALE_FP64) {
     launch_kernel(kid, fields_t<double>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
-  } else if (kid >= kMixNodes && kid <= kMixEos) {
+  } else if ((kid >= kMixNodes && kid <= kMixEos) || kid == kMixDensity) {
     launch_m_kernel(kid, fields_t<float>(st), st->S, mode, st->tile_shape, st->stream);
   } else {
     launch_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
@@ -727,6 +739,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
   if (st->precision == SALE_FP32_MIXED) {
     launch_k(st, kMixNodes, 0, dt_override);
     launch_k(st, kMixCells, 0, dt_override);
+    if (st->prob.remap_order == 2) launch_k(st, kMixDensity);
     launch_k(st, kMixFluxes);
     launch_k(st, kMixRemapNodes);
     st->upar ^= 1;
@@ -737,6 +750,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
   launch_k(st, kAleEdges, 0, dt_override);
   launch_k(st, kAleCells, 0, dt_override);
   launch_k(st, kAleDensity);
+  if (st->prob.remap_order == 2) launch_k(st, kAleSlopes);
   launch_k(st, kAleFluxes);
   launch_k(st, kAleRemapNodes);
   st->upar ^= 1;
@@ -1054,6 +1068,7 @@ struct sale_batch {
   std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
   std::vector<sale_mesh_desc> meshes;
   int shape = 0;                    // thread-tile shape
+  bool any_order2 = false;          // some mesh uses the second-order remap
   int order = 0;                    // 0: meshes in input order, 1: largest mesh first
   std::map<long long, cudaGraphExec_t> graphs;
 };
@@ -1209,6 +1224,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
     b->st.push_back(sti);
   }
   b->meshes.assign(meshes, meshes + n);
+  for (int i = 0; i < n; ++i) b->any_order2 = b->any_order2 || probs[i].remap_order == 2;
   rc = upload_batch_tables(b);
   if (rc == SALE_OK) rc = upload_batch_items(b);
   if (rc) {
@@ -1229,6 +1245,8 @@ extern "C" sale_state *sale_batch_state(sale_batch *b, int i) {
 static void launch_batch_cycle(sale_batch *b, int p) {
   launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
   launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
+  if (b->any_order2)  // first-order meshes leave this pass at once
+    launch_m_batch(kMixDensity, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
   launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
   launch_m_batch(kMixRemapNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
   launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->shape, b->stream);
@@ -1317,7 +1335,8 @@ static const char *const kKernelNames[kNumKernels] = {
     "init_nodes",   "eos_dt",    "lagrange_nodes", "lagrange_cells", "remap_faces",     "remap_nodes",
     "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
     "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
-    "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes", "ale_eos"};
+    "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes", "ale_eos",     "ale_slopes",
+    "mix_density"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

@@ -57,6 +57,24 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
+// Second-order cell remap (van Leer 1977): the limited slope of a cell
+// quantity along one axis is the harmonic mean of its two one-sided
+// differences when they agree in sign, else 0; a face carries the average
+// of the donor's linear profile over the slab of relative thickness nu it
+// sweeps, side = +1 at the donor's high face, -1 at its low face.
+__host__ __device__ __forceinline__ double vanleer_slope(double dm, double dp) {
+  return dm * dp > 0.0 ? 2.0 * dm * dp / (dm + dp) : 0.0;
+}
+__host__ __device__ __forceinline__ double slab_average(double q, double slope, double nu, double side) {
+  return q + side * 0.5 * slope * (1.0 - fmin(nu, 1.0));
+}
+__device__ __forceinline__ float vanleer_slope_f(float dm, float dp) {
+  return dm * dp > 0.f ? 2.f * dm * dp / (dm + dp) : 0.f;
+}
+__device__ __forceinline__ float slab_average_f(float q, float slope, float nu, float side) {
+  return q + side * 0.5f * slope * (1.f - fminf(nu, 1.f));
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

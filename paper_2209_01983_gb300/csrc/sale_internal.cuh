@@ -68,6 +68,8 @@ enum KernelId : int {
   kAleEdges,     // ALE path: side-quad terms of the swept hexes, per mesh edge
   kAleRemapNodes,
   kAleEos,       // ALE path: EoS + dt on the reference mesh (refresh)
+  kAleSlopes,    // ALE path, second-order remap: limited slopes of rho_L and e
+  kMixDensity,   // FP32-mixed path, second-order remap: V_L and rho_L
   kNumKernels
 };
 
@@ -122,6 +124,9 @@ struct Fields {
   double gamma, cfl, c_q, c_l, growth, dt_init;
   float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
   int ke_fix;
+  int remap_order;             // cell remap: 1 donor cell, 2 van Leer piecewise linear
+  R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
+  R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
   int remap_sets_x;            // node remap writes the reference positions to x
   int reflect[6];
 };

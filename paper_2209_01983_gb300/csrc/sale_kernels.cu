@@ -253,10 +253,25 @@ __device__ __forceinline__ void face_flux(const Fields<R> &F, long long c, int i
   }
   const double dv = swept_volume<AX>(F, i, j, k);
   const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
-  const long long dn = dv > 0.0 ? c : c - stride;
-  const double f = (double)F.rho[dn] * dv;
+  const bool hi_donates = dv > 0.0;
+  const long long dn = hi_donates ? c : c - stride;
+  double rho_f = (double)F.rho[dn], e_f = (double)F.e[dn];
+  if (F.remap_order == 2) {  // F.rho, F.vol hold the Lagrangian density and volume here
+    const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
+    const int di = hi_donates ? idx : idx - 1;  // donor index along AX
+    double sr = 0.0, se = 0.0;
+    if (di > 0 && di < n_ax - 1) {
+      sr = vanleer_slope(rho_f - (double)F.rho[dn - stride], (double)F.rho[dn + stride] - rho_f);
+      se = vanleer_slope(e_f - (double)F.e[dn - stride], (double)F.e[dn + stride] - e_f);
+    }
+    const double nu = fabs(dv) / (double)F.vol[dn];
+    const double side = hi_donates ? -1.0 : 1.0;
+    rho_f = slab_average(rho_f, sr, nu, side);
+    e_f = slab_average(e_f, se, nu, side);
+  }
+  const double f = rho_f * dv;
   mu[c] = (R)f;
-  ep[c] = (R)(f * (double)F.e[dn]);
+  ep[c] = (R)(f * e_f);
 }
 
 template <typename R>
@@ -468,7 +483,8 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
 template <typename R>
 void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t st) {
-  if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes || kid == kAleEos) {
+  if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes || kid == kAleEos ||
+      kid == kAleSlopes) {
     if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
     return;
   }

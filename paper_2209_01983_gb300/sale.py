@@ -40,7 +40,8 @@ class sale_problem_desc(C.Structure):
                 ("rho_bg", C.c_double), ("p_bg", C.c_double), ("rho_blast", C.c_double),
                 ("p_blast", C.c_double), ("e_deposit", C.c_double),
                 ("cfl", C.c_double), ("c_q", C.c_double), ("c_l", C.c_double),
-                ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int)]
+                ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int),
+                ("remap_order", C.c_int)]
 
 
 class sale_diag(C.Structure):
@@ -136,7 +137,7 @@ def problem_desc(pd: inputs.ProblemDesc) -> sale_problem_desc:
     p = sale_problem_desc()
     for name, _ in sale_problem_desc._fields_:
         v = getattr(pd, name)
-        setattr(p, name, int(v) if name in ("kind", "ke_fix") else float(v))
+        setattr(p, name, int(v) if name in ("kind", "ke_fix", "remap_order") else float(v))
     if not math.isfinite(p.dt_init):
         p.dt_init = 0.0
     return p
