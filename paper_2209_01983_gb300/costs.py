@@ -91,6 +91,9 @@ MIXED_ALE = {
 MIXED_ALE_JIT = dict(MIXED_ALE)
 MIXED_ALE_JIT["mix_cells"] = ("cell", 4 * (4 + 24 + 3 + 1 + 1 + 2 + 2 + 3), 48 + 40 + 6 + SWEPT32)
 MIXED_ALE_JIT["mix_remap_eos"] = ("cell", 4 * (6 + 4 + 1 + 3 + 24 + 2 + 6), 40 + 48 + 40 + 30)
+# the node force gathers sum_c (sigma_c - sigma_ref) G_c(a) from the cache:
+# sigma (per cell), the corner gradients (24 per cell), u, mn read; u, ubar written
+MIXED_ALE_JIT["mix_nodes"] = ("node", 4 * (1 + 24 + 3 + 1 + 3 + 3), 8 * 7 + 20)
 
 
 # Second-order cell remap (van Leer piecewise-linear donor cell).

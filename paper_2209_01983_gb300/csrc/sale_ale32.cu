@@ -145,22 +145,14 @@ __device__ __forceinline__ float grad_dot_f(const F3 (&X)[8], const F3 (&U)[8]) 
   return s * (1.f / 24.f);
 }
 
-// The same sum from the cached corner gradients of a jittered mesh: six
-// 16-byte loads instead of ~480 FP32 operations.
-__device__ __forceinline__ float grad_dot_cached(const float4 *G4, int c, const F3 (&U)[8]) {
-  const float4 *g = G4 + 6 * (size_t)c;
-  float v[24];
-#pragma unroll
-  for (int q = 0; q < 6; ++q) {
-    const float4 t = __ldg(g + q);
-    v[4 * q] = t.x;
-    v[4 * q + 1] = t.y;
-    v[4 * q + 2] = t.z;
-    v[4 * q + 3] = t.w;
-  }
+// The same sum from the cached corner gradients of a jittered mesh: 24
+// coalesced loads instead of ~480 FP32 operations.
+__device__ __forceinline__ float grad_dot_cached(const float *Gc, long long nc, int c, const F3 (&U)[8]) {
+  const float *g = Gc + c;
   float s = 0.f;
 #pragma unroll
-  for (int a = 0; a < 8; ++a) s += v[3 * a] * U[a].x + v[3 * a + 1] * U[a].y + v[3 * a + 2] * U[a].z;
+  for (int a = 0; a < 8; ++a)
+    s += __ldg(g + (3 * a) * nc) * U[a].x + __ldg(g + (3 * a + 1) * nc) * U[a].y + __ldg(g + (3 * a + 2) * nc) * U[a].z;
   return s;
 }
 
@@ -207,7 +199,7 @@ __device__ __forceinline__ void wall_bc_f(const Fields<float> &F, int i, int j, 
 
 __global__ void __launch_bounds__(kBlock) k_m_init_cells(Fields<float> F, DevScalars *S, const double *rho0,
                                                          const double *p0, long long dep_cell, double dep_e,
-                                                         float *VE, float *LE, float4 *G4) {
+                                                         float *VE, float *LE, float *Gc) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc) return;
   int i, j, k;
@@ -227,20 +219,14 @@ __global__ void __launch_bounds__(kBlock) k_m_init_cells(Fields<float> F, DevSca
   F.elo[c] = (float)(e - (double)(float)e);
   VE[c] = (float)V;
   LE[c] = (float)(V / sqrt(hex_max_face_area2(X)));
-  if (G4) {  // corner gradients of the reference cell, rounded once from FP64
+  if (Gc) {  // corner gradients of the reference cell, rounded once from FP64
     P3 g[8];
     hex_grad_shifted(X, g);
-    float4 *o = G4 + 6 * c;
 #pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      float v[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) {
-        const int w = 4 * q + r;
-        const P3 ga = g[w / 3];
-        v[r] = (float)(w % 3 == 0 ? ga.x : w % 3 == 1 ? ga.y : ga.z);
-      }
-      o[q] = make_float4(v[0], v[1], v[2], v[3]);
+    for (int a = 0; a < 8; ++a) {
+      Gc[(3 * a + 0) * F.nc + c] = (float)g[a].x;
+      Gc[(3 * a + 1) * F.nc + c] = (float)g[a].y;
+      Gc[(3 * a + 2) * F.nc + c] = (float)g[a].z;
     }
   }
 }
@@ -312,16 +298,49 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
                     ((s & 4) ? hi_ok[2] : lo_ok[2]);
     sig[s] = ok ? F.sig[c0 + (s & 1) + ((s >> 1) & 1) * csy + ((s >> 2) & 1) * csz] : 0.f;
   }
-  const float4 oa = off_at<JIT>(F, n);
   F3 f = {0.f, 0.f, 0.f};
-  node_faces2<JIT, 0>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 1>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 2>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 3>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 4>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 5>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  node_faces2<JIT, 6>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-  const float hm = h / (24.f * F.mn[n]);
+  float hm;
+  if constexpr (JIT) {
+    // Cached corner gradients: F_a = sum_c (sigma_c - sigma_ref) G_c(a).  The
+    // dropped sigma_ref sum_c G_c(a) is zero at interior nodes and normal to
+    // the (reflecting) walls at boundary nodes, where the wall condition
+    // removes it; the differences keep F exactly 0 where sigma is uniform.
+    float ref = 0.f;
+    bool have = false;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool ok = ((q & 1) ? hi_ok[0] : lo_ok[0]) && ((q & 2) ? hi_ok[1] : lo_ok[1]) &&
+                      ((q & 4) ? hi_ok[2] : lo_ok[2]);
+      if (ok && !have) {
+        ref = sig[q];
+        have = true;
+      }
+    }
+    const long long nc = F.nc;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const bool ok = ((q & 1) ? hi_ok[0] : lo_ok[0]) && ((q & 2) ? hi_ok[1] : lo_ok[1]) &&
+                      ((q & 4) ? hi_ok[2] : lo_ok[2]);
+      if (!ok) continue;
+      const int c = c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz;
+      const float *g = F.Gc + (3 * (7 - q)) * nc + c;  // this node is corner 7 - q of cell q
+      const float ds = sig[q] - ref;
+      f.x += ds * __ldg(g);
+      f.y += ds * __ldg(g + nc);
+      f.z += ds * __ldg(g + 2 * nc);
+    }
+    hm = h / F.mn[n];
+  } else {
+    const float4 oa = off_at<JIT>(F, n);
+    node_faces2<JIT, 0>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 1>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 2>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 3>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 4>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 5>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    node_faces2<JIT, 6>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    hm = h / (24.f * F.mn[n]);
+  }
   const float u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
   float u1 = u0 + hm * f.x, v1 = v0 + hm * f.y, w1 = w0 + hm * f.z;
   if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
@@ -347,7 +366,7 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
     const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
     ub[a] = {F.ub[na], F.vb[na], F.wb[na]};
   }
-  const float work = JIT ? grad_dot_cached(F.G4, c, ub) : grad_dot_f(E, ub);
+  const float work = JIT ? grad_dot_cached(F.Gc, F.nc, c, ub) : grad_dot_f(E, ub);
   // compatible energy update; the increment is FP32, the accumulation
   // float-float
   const float de = h * F.sig[c] * work / F.m[c];
@@ -562,7 +581,7 @@ __device__ __forceinline__ float m_eos_cell(const Fields<float> &F, int c, int i
   }
   float dvdt;
   if constexpr (JIT) {
-    dvdt = grad_dot_cached(F.G4, c, U);
+    dvdt = grad_dot_cached(F.Gc, F.nc, c, U);
   } else {
     F3 E[8];
     ref_hex2<JIT>(F, n0, sy, sz, E);
@@ -749,9 +768,9 @@ dim3 tile_grid(int ni, int nj, int nk, int shape) {
 }
 
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
-                         long long dep_cell, double dep_e, float *VE, float *LE, float4 *G4, cudaStream_t st) {
+                         long long dep_cell, double dep_e, float *VE, float *LE, float *Gc, cudaStream_t st) {
   k_m_init_cells<<<(unsigned)((F.nc + kBlock - 1) / kBlock), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e, VE,
-                                                                              LE, G4);
+                                                                              LE, Gc);
 }
 
 template <int KID, int SH>

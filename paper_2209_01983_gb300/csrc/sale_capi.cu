@@ -31,7 +31,7 @@ void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
-                         long long dep_cell, double dep_e, float *VE, float *LE, float4 *G4, cudaStream_t st);
+                         long long dep_cell, double dep_e, float *VE, float *LE, float *Gc, cudaStream_t st);
 void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st);
 }  // namespace sale
 
@@ -223,7 +223,7 @@ struct sale_state {
   float4 *off4;                          // FP32-mixed path: jitter offsets
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
-  float4 *G4;                            // FP32-mixed path, jittered mesh: corner gradients
+  float *Gc;                             // FP32-mixed path, jittered mesh: corner gradients
   bool jit = false;                      // the mesh is jittered
   float h32[3];
   int xpar, upar;
@@ -277,7 +277,7 @@ static size_t carve(sale_state *st, char *base) {
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
   st->off4 = nullptr;
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
-  st->G4 = nullptr;
+  st->Gc = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
     st->geoG = (double *)cv.take(sizeof(double) * 31 * nc);
@@ -298,7 +298,7 @@ static size_t carve(sale_state *st, char *base) {
     st->LE32 = (float *)cv.take(sizeof(float) * nc);
     st->mlo = (float *)cv.take(sizeof(float) * nc);
     st->elo = (float *)cv.take(sizeof(float) * nc);
-    if (st->jit) st->G4 = (float4 *)cv.take(sizeof(float4) * 6 * nc);
+    if (st->jit) st->Gc = (float *)cv.take(sizeof(float) * 24 * nc);
   }
   return align_up(cv.off);
 }
@@ -367,7 +367,7 @@ static Fields<R> fields_t(const sale_state *st) {
   F.hy = st->h32[1];
   F.hz = st->h32[2];
   F.off4 = st->off4;
-  F.G4 = st->G4;
+  F.Gc = st->Gc;
   F.remap_sets_x = st->remap_sets_x;
   F.gamma = st->prob.gamma;
   F.cfl = st->prob.cfl;
@@ -663,7 +663,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->geoIVE, st->geoIL2, st->stream);
   } else {
     const Fields<float> F = fields_t<float>(st);
-    launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->G4, st->stream);
+    launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->Gc, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_m_kernel(kMixEos, F, st->S, kDtInit, st->tile_shape, st->stream);
   }

@@ -118,9 +118,10 @@ struct Fields {
   float hx, hy, hz;
   const float4 *off4;          // per-node jitter offsets x, y, z (w unused); null: none
   // Jittered FP32-mixed meshes: dV/dx of the 8 corners of every reference
-  // cell, 24 floats per cell (corner-major, then axis) as 6 float4; null on
-  // unjittered meshes, where the gradient folds to constants.
-  const float4 *G4;
+  // cell, Gc[(3 * corner + axis) * nc + c] (coalesced across a row of cells
+  // and across a row of nodes); null on unjittered meshes, where the
+  // gradient folds to constants.
+  const float *Gc;
   double gamma, cfl, c_q, c_l, growth, dt_init;
   float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
   int ke_fix;
