@@ -31,7 +31,7 @@ class Params(C.Structure):
     _fields_ = [
         ("gamma", C.c_double), ("cfl", C.c_double), ("c_q", C.c_double),
         ("c_l", C.c_double), ("dt_growth", C.c_double), ("dt_init", C.c_double),
-        ("ke_fix", C.c_int), ("reflect", C.c_int * 6), ("remap_order", C.c_int),
+        ("ke_fix", C.c_int), ("reflect", C.c_int * 6), ("remap_order", C.c_int), ("time_order", C.c_int),
     ]
 
 
@@ -134,6 +134,7 @@ def params_from(pd, reflect=(1, 1, 1, 1, 1, 1)) -> Params:
     for i in range(6):
         p.reflect[i] = int(reflect[i])
     p.remap_order = int(getattr(pd, "remap_order", 1))
+    p.time_order = int(getattr(pd, "time_order", 1))
     return p
 
 

@@ -243,46 +243,51 @@ static void node_masses_from_cells(oracle_state *s) {
       }
 }
 
+/* EoS (R2), sound speed and artificial viscosity (R3) of one cell with
+ * node positions X and velocities U (24 values each), mass m and specific
+ * internal energy e.  Returns a status. */
+static int cell_state(const oracle_state *s, const double *X, const double *U, double m, double e, double *V_out,
+                      double *rho_out, double *p_out, double *q_out, double *cs_out, double *L_out) {
+  const double g = s->prm.gamma;
+  double G[24];
+  double V = oracle_hex_volume(X);
+  if (!(V > 0.0)) return isnan(V) ? ORACLE_ENAN : ORACLE_ENEGVOL;
+  double rho = m / V;
+  double p = (g - 1.0) * rho * e;
+  double cs = sqrt(g * (g - 1.0) * (e > 0.0 ? e : 0.0));
+  oracle_hex_volume_grad(X, G);
+  double dvdt = 0.0;
+  for (int a = 0; a < 8; ++a) dvdt += dot3(&G[a * 3], &U[a * 3]);
+  double div = dvdt / V;
+  double L = oracle_hex_char_length(X);
+  double q = 0.0;
+  if (div < 0.0) {
+    double ld = L * div;
+    q = rho * (s->prm.c_q * ld * ld + s->prm.c_l * cs * L * fabs(div));
+  }
+  if (isnan(p) || isnan(q) || isnan(cs)) return ORACLE_ENAN;
+  *V_out = V;
+  *rho_out = rho;
+  *p_out = p;
+  *q_out = q;
+  *cs_out = cs;
+  *L_out = L;
+  return ORACLE_OK;
+}
+
 /* EoS, sound speed, artificial viscosity and length scale at the current
  * positions and velocities. */
 int oracle_eos(oracle_state *s) {
-  const double g = s->prm.gamma;
   for (int k = 0; k < s->nz; ++k)
     for (int j = 0; j < s->ny; ++j)
       for (int i = 0; i < s->nx; ++i) {
         long long c = cell_id(s, i, j, k);
-        double X[24], G[24], U[24];
+        double X[24], U[24];
         gather_hex(s, i, j, k, s->x, s->y, s->z, X);
         gather_hex(s, i, j, k, s->u, s->v, s->w, U);
-        double V = oracle_hex_volume(X);
-        if (!(V > 0.0)) {
-          s->status = isnan(V) ? ORACLE_ENAN : ORACLE_ENEGVOL;
-          return s->status;
-        }
-        double rho = s->m[c] / V;
-        double e = s->e[c];
-        double p = (g - 1.0) * rho * e;
-        double cs = sqrt(g * (g - 1.0) * (e > 0.0 ? e : 0.0));
-        oracle_hex_volume_grad(X, G);
-        double dvdt = 0.0;
-        for (int a = 0; a < 8; ++a) dvdt += dot3(&G[a * 3], &U[a * 3]);
-        double div = dvdt / V;
-        double L = oracle_hex_char_length(X);
-        double q = 0.0;
-        if (div < 0.0) {
-          double ld = L * div;
-          q = rho * (s->prm.c_q * ld * ld + s->prm.c_l * cs * L * fabs(div));
-        }
-        if (isnan(p) || isnan(q) || isnan(cs)) {
-          s->status = ORACLE_ENAN;
-          return s->status;
-        }
-        s->vol[c] = V;
-        s->rho[c] = rho;
-        s->p[c] = p;
-        s->cs[c] = cs;
-        s->q[c] = q;
-        s->len[c] = L;
+        int rc = cell_state(s, X, U, s->m[c], s->e[c], &s->vol[c], &s->rho[c], &s->p[c], &s->q[c], &s->cs[c],
+                            &s->len[c]);
+        if (rc) return s->status = rc;
       }
   return ORACLE_OK;
 }
@@ -366,26 +371,72 @@ int oracle_set_state(oracle_state *s, const double *x, const double *y,
 /* Lagrangian step                                                     */
 /* ------------------------------------------------------------------ */
 
+/* Lagrangian step (R4).  Single stage: corner forces sigma^n dV/dx(x^n).
+ * Predictor-corrector (R15, time_order = 2): a half step of dt/2 first
+ * moves the nodes to x^{n+1/2} = x^n + dt/2 u^n and the cells to
+ * e^{n+1/2} = e^n - dt/(2m) sigma^n sum_a dV/dx_a(x^n).u^n_a, where the EoS
+ * and viscosity (with u^n) give sigma^{n+1/2}; the full step then uses the
+ * corner forces sigma^{n+1/2} dV/dx(x^{n+1/2}) for both the velocity and
+ * the compatible energy update, so total energy stays exact. */
 int oracle_lagrange_step(oracle_state *s, double dt) {
   if (s->status) return s->status;
   if (!(dt > 0.0)) return s->status = ORACLE_EDT;
   const long long nn = s->nn, nc = s->nc;
+  const int pc = s->prm.time_order == 2;
   double *fx = alloc_zero(nn), *fy = alloc_zero(nn), *fz = alloc_zero(nn);
   double *ubx = alloc_zero(nn), *uby = alloc_zero(nn), *ubz = alloc_zero(nn);
-  double *e_new = alloc_zero(nc);
-  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new) {
-    free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new);
+  double *e_new = alloc_zero(nc), *sig = alloc_zero(nc);
+  double *xh = alloc_zero(nn), *yh = alloc_zero(nn), *zh = alloc_zero(nn);
+  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh) {
+    free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
+    free(xh); free(yh); free(zh);
     return s->status = ORACLE_ENOMEM;
   }
 
-  /* Corner forces F_a += sigma_c dV_c/dx_a at x^n, gathered to nodes. */
+  /* Stress of every cell and the positions its corner forces are taken at. */
+  const double *gx = s->x, *gy = s->y, *gz = s->z;
+  for (long long c = 0; c < nc; ++c) sig[c] = s->p[c] + s->q[c];
+  if (pc) {
+    for (long long n = 0; n < nn; ++n) {
+      xh[n] = s->x[n] + 0.5 * dt * s->u[n];
+      yh[n] = s->y[n] + 0.5 * dt * s->v[n];
+      zh[n] = s->z[n] + 0.5 * dt * s->w[n];
+    }
+    for (int k = 0; k < s->nz; ++k)
+      for (int j = 0; j < s->ny; ++j)
+        for (int i = 0; i < s->nx; ++i) {
+          long long c = cell_id(s, i, j, k);
+          double X[24], G[24], U[24], XH[24];
+          gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+          gather_hex(s, i, j, k, s->u, s->v, s->w, U);
+          oracle_hex_volume_grad(X, G);
+          double work = 0.0;
+          for (int a = 0; a < 8; ++a) work += dot3(&G[a * 3], &U[a * 3]);
+          double e_half = s->e[c] - 0.5 * dt / s->m[c] * sig[c] * work;
+          gather_hex(s, i, j, k, xh, yh, zh, XH);
+          double V, rho, p, q, cs, L;
+          int rc = cell_state(s, XH, U, s->m[c], e_half, &V, &rho, &p, &q, &cs, &L);
+          if (rc) {
+            free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
+            free(xh); free(yh); free(zh);
+            return s->status = rc;
+          }
+          e_new[c] = p + q;  /* sigma^{n+1/2}, moved into sig below */
+        }
+    memcpy(sig, e_new, sizeof(double) * (size_t)nc);
+    gx = xh;
+    gy = yh;
+    gz = zh;
+  }
+
+  /* Corner forces F_a += sigma_c dV_c/dx_a, gathered to nodes. */
   for (int k = 0; k < s->nz; ++k)
     for (int j = 0; j < s->ny; ++j)
       for (int i = 0; i < s->nx; ++i) {
         long long c = cell_id(s, i, j, k);
-        double sigma = s->p[c] + s->q[c];
+        double sigma = sig[c];
         double X[24], G[24];
-        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        gather_hex(s, i, j, k, gx, gy, gz, X);
         oracle_hex_volume_grad(X, G);
         for (int a = 0; a < 8; ++a) {
           long long n = node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
@@ -412,14 +463,14 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
         s->w[n] = wn;
       }
 
-  /* Compatible internal-energy update, with gradients at x^n. */
+  /* Compatible internal-energy update with the same corner forces. */
   for (int k = 0; k < s->nz; ++k)
     for (int j = 0; j < s->ny; ++j)
       for (int i = 0; i < s->nx; ++i) {
         long long c = cell_id(s, i, j, k);
-        double sigma = s->p[c] + s->q[c];
+        double sigma = sig[c];
         double X[24], G[24], UB[24];
-        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        gather_hex(s, i, j, k, gx, gy, gz, X);
         gather_hex(s, i, j, k, ubx, uby, ubz, UB);
         oracle_hex_volume_grad(X, G);
         double work = 0.0;
@@ -434,7 +485,8 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
     s->z[n] += dt * ubz[n];
   }
   memcpy(s->e, e_new, sizeof(double) * (size_t)nc);
-  free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new);
+  free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
+  free(xh); free(yh); free(zh);
 
   s->t += dt;
   s->dt_last = dt;

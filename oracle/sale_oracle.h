@@ -13,7 +13,8 @@
  *   - hex volume: exact trilinear-hex volume, as the divergence-theorem sum
  *     over the six faces, each face fanned into four triangles from its
  *     node mean;
- *   - compatible energy update (Caramana, Burton, Shashkov, Whalen 1998);
+ *   - compatible energy update (Caramana, Burton, Shashkov, Whalen 1998),
+ *     single stage or with a midpoint predictor for second order in time;
  *   - donor-cell (upwind) remap of mass, energy, momentum (Amsden et al.
  *     1980, "SALE"), with kinetic-energy fix-up;
  *   - optionally, second-order cell remap: van Leer's limited
@@ -51,6 +52,7 @@ typedef struct oracle_params {
   int ke_fix;        /* 1: remap returns lost kinetic energy to cells     */
   int reflect[6];    /* x-lo,x-hi,y-lo,y-hi,z-lo,z-hi: 1 = reflecting wall */
   int remap_order;   /* cell remap: 2 = van Leer piecewise linear, else first-order donor cell */
+  int time_order;    /* Lagrange step: 2 = predictor-corrector, else single stage */
 } oracle_params;
 
 typedef struct oracle_state {

@@ -93,6 +93,7 @@ class ProblemDesc:
     dt_growth: float = 1.1
     ke_fix: int = 1
     remap_order: int = 1  # cell remap: 1 donor cell, 2 van Leer piecewise linear
+    time_order: int = 1   # Lagrange step: 1 single stage, 2 predictor-corrector
 
 
 def mesh_nodes(md: MeshDesc):
