@@ -98,7 +98,12 @@ typedef struct {
  * remap_order: cell remap of density and specific energy, 1 (or 0) the
  * first-order donor cell, 2 van Leer's limited piecewise-linear profile in
  * the donor averaged over the swept slab (the node remap stays donor
- * node). */
+ * node); time_order: Lagrangian step, 1 (or 0) single stage with the
+ * corner forces of x^n, 2 predictor-corrector: a half step to
+ * x^n + dt/2 u^n gives sigma^{n+1/2}, and the corner forces there move the
+ * nodes and update the energy (second order in time, energy exact).
+ * Options other than the defaults may need more device memory: size the
+ * buffer with sale_state_bytes_for(). */
 typedef struct {
   int kind;
   double gamma;
@@ -107,6 +112,7 @@ typedef struct {
   double cfl, c_q, c_l, dt_init, dt_growth;
   int ke_fix;
   int remap_order;
+  int time_order;
 } sale_problem_desc;
 
 /* Diagnostics (FP64 sums in a fixed reduction order). */
@@ -130,9 +136,14 @@ void sale_mesh_destroy(sale_mesh *mesh);
  * all x, then all y, then all z. */
 int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n);
 
-/* Device bytes a state of this mesh and precision needs (0 on bad args). */
+/* Device bytes a state of this mesh and precision needs with the default
+ * scheme options (0 on bad args). */
 size_t sale_state_bytes(const sale_mesh *mesh, int precision);
-/* Initialise a state in the caller's device buffer (>= sale_state_bytes,
+/* Device bytes for this mesh, problem and precision: includes the scratch
+ * of the second-order remap (FP64) and of the predictor-corrector step
+ * (half-step corner gradients) when the problem asks for them. */
+size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision);
+/* Initialise a state in the caller's device buffer (>= sale_state_bytes_for,
  * 256-byte aligned) on `cuda_stream` (a cudaStream_t; NULL = legacy
  * default stream).  Computes volumes, masses, energies, node masses, the
  * EoS/viscosity state and the first dt.  The mesh may be destroyed after. */

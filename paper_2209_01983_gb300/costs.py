@@ -114,20 +114,41 @@ MIXED_O2 = {
 }
 
 
-def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1):
+# Predictor-corrector half step (time_order 2): e^{n+1/2} from the cached
+# gradient, then volume, full gradient, face areas, EoS and viscosity at
+# x^{n+1/2}; the 24 corner gradients there are written for the corrector,
+# whose node and cell passes read them instead of the reference ones.
+FP64_PC = {
+    # G, u, m, e, sigma, x_ref read; sigma, 24 half-step gradients written
+    "ale_predict": ("cell", 8 * (24 + 3 + 3 + 3 + 3 + 24 + 1), 48 + 5 + 24 + VOL + GRAD + LEN + 40),
+}
+MIXED_PC = {
+    # offsets or cached gradient, u, m, e, sigma read; sigma, 24 gradients written
+    "mix_predict": ("cell", 4 * (24 + 4 + 3 + 3 + 24 + 1), 48 + 5 + 24 + VOL + GRAD + LEN + 40),
+    # the node force from the half-step gradients, as on jittered meshes
+    "mix_nodes": ("node", 4 * (1 + 24 + 3 + 1 + 3 + 3), 8 * 7 + 20),
+}
+
+
+def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1):
     if precision == "fp64":
         if path != "ale":
             return FP64
-        return FP64_ALE_O2 if order == 2 else FP64_ALE
+        t = dict(FP64_ALE_O2 if order == 2 else FP64_ALE)
+        if time_order == 2:
+            t.update(FP64_PC)
+        return t
     if precision == "fp32_mixed":
         t = dict(MIXED_ALE_JIT if jitter else MIXED_ALE)
         if order == 2:
             t.update(MIXED_O2)
+        if time_order == 2:
+            t.update(MIXED_PC)
         return t
     raise KeyError(precision)
 
 
-def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1):
+def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1):
     """(bytes, flops) of one full cycle per cell."""
-    t = table(precision, path, jitter, order)
+    t = table(precision, path, jitter, order, time_order)
     return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

@@ -156,6 +156,46 @@ __device__ __forceinline__ float grad_dot_cached(const float *Gc, long long nc, 
   return s;
 }
 
+// FP32 geometry of a hex given relative to its node 0 (predictor-corrector
+// half step, where the nodes are off the reference mesh): volume, full
+// corner gradient and the largest squared face area, by the same fan
+// formulas as the FP64 routines.
+__device__ __forceinline__ float hex_volume_f(const F3 (&X)[8]) {
+  float s = 0.f;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const F3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)], p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
+    s += dotf(p0 + p1 + p2 + p3, crossf(p2 - p0, p3 - p1));
+  }
+  return s * (1.f / 24.f);
+}
+
+__device__ __forceinline__ void hex_grad_f(const F3 (&X)[8], F3 (&G)[8]) {
+#pragma unroll
+  for (int a = 0; a < 8; ++a) G[a] = {0.f, 0.f, 0.f};
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const F3 pa = X[face_node(f, (k + 1) & 3)], pb = X[face_node(f, (k + 2) & 3)], pc = X[face_node(f, (k + 3) & 3)];
+      G[face_node(f, k)] = G[face_node(f, k)] + crossf(pa + 2.f * pb + pc, pc - pa);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < 8; ++a) G[a] = (1.f / 24.f) * G[a];
+}
+
+__device__ __forceinline__ float hex_max_face_area2_f(const F3 (&X)[8]) {
+  float amax = 0.f;
+#pragma unroll
+  for (int f = 0; f < 6; ++f) {
+    const F3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)], p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
+    const F3 D = crossf(p2 - p0, p3 - p1);
+    amax = fmaxf(amax, 0.25f * dotf(D, D));
+  }
+  return amax;
+}
+
 // Side quad (L_a, E_a, E_b, L_b) term, expanded in the displacements.
 __device__ __forceinline__ float side_term(const F3 (&E)[8], const F3 (&D)[8], int a, int b) {
   return 4.f * dotf(crossf(E[a], E[b]), D[a] + D[b]) - 2.f * dotf(E[a] + E[b], crossf(D[a], D[b]));
@@ -300,11 +340,13 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   }
   F3 f = {0.f, 0.f, 0.f};
   float hm;
-  if constexpr (JIT) {
-    // Cached corner gradients: F_a = sum_c (sigma_c - sigma_ref) G_c(a).  The
+  if (JIT || F.time_order == 2) {
+    // Cached corner gradients (of the reference mesh, or of x^{n+1/2} for
+    // the predictor-corrector): F_a = sum_c (sigma_c - sigma_ref) G_c(a).  The
     // dropped sigma_ref sum_c G_c(a) is zero at interior nodes and normal to
     // the (reflecting) walls at boundary nodes, where the wall condition
     // removes it; the differences keep F exactly 0 where sigma is uniform.
+    const float *Gsrc = F.time_order == 2 ? F.Gh : F.Gc;
     float ref = 0.f;
     bool have = false;
 #pragma unroll
@@ -323,7 +365,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
                       ((q & 4) ? hi_ok[2] : lo_ok[2]);
       if (!ok) continue;
       const int c = c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz;
-      const float *g = F.Gc + (3 * (7 - q)) * nc + c;  // this node is corner 7 - q of cell q
+      const float *g = Gsrc + (3 * (7 - q)) * nc + c;  // this node is corner 7 - q of cell q
       const float ds = sig[q] - ref;
       f.x += ds * __ldg(g);
       f.y += ds * __ldg(g + nc);
@@ -366,7 +408,9 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
     const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
     ub[a] = {F.ub[na], F.vb[na], F.wb[na]};
   }
-  const float work = JIT ? grad_dot_cached(F.Gc, F.nc, c, ub) : grad_dot_f(E, ub);
+  const float work = F.time_order == 2 ? grad_dot_cached(F.Gh, F.nc, c, ub)
+                     : JIT              ? grad_dot_cached(F.Gc, F.nc, c, ub)
+                                        : grad_dot_f(E, ub);
   // compatible energy update; the increment is FP32, the accumulation
   // float-float
   const float de = h * F.sig[c] * work / F.m[c];
@@ -381,6 +425,54 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
   F.dvx[c] = IN || i > 0 ? vx : 0.f;
   F.dvy[c] = IN || j > 0 ? vy : 0.f;
   F.dvz[c] = IN || k > 0 ? vz : 0.f;
+}
+
+// Predictor-corrector half step of cell (i,j,k): e^{n+1/2} from sigma^n and
+// u^n on the reference mesh, then EoS and viscosity on x_ref + dt/2 u^n;
+// sigma^{n+1/2} replaces sigma, the corner gradients there go to Gh.
+template <bool JIT, bool IN>
+__device__ __forceinline__ void m_predict_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
+  const float h = S->next_h32;
+  const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
+  const int n0 = i + sy * j + sz * k;
+  const int c = i + F.nx * (j + F.ny * k);
+  F3 E[8], U[8];
+  ref_hex2<JIT>(F, n0, sy, sz, E);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    U[a] = {F.u[na], F.v[na], F.w[na]};
+  }
+  const float work = JIT ? grad_dot_cached(F.Gc, F.nc, c, U) : grad_dot_f(E, U);
+  const float m = F.m[c];
+  const float e = F.e[c] - 0.5f * h * F.sig[c] * work / m;
+  F3 X[8], G[8];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) X[a] = E[a] + (0.5f * h) * (U[a] - U[0]);
+  const float V = hex_volume_f(X);
+  if (!(V > 0.f)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
+  hex_grad_f(X, G);
+  float dvdt = 0.f;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    dvdt += dotf(G[a], U[a]);
+    F.Gh[(3 * a + 0) * F.nc + c] = G[a].x;
+    F.Gh[(3 * a + 1) * F.nc + c] = G[a].y;
+    F.Gh[(3 * a + 2) * F.nc + c] = G[a].z;
+  }
+  const float rho = m / V;
+  const float g = F.gamma32;
+  const float p = (g - 1.f) * rho * e;
+  const float cs = sqrtf(g * (g - 1.f) * fmaxf(e, 0.f));
+  const float div = dvdt / V;
+  const float L = V * rsqrtf(hex_max_face_area2_f(X));
+  float q = 0.f;
+  if (div < 0.f) {
+    const float ld = L * div;
+    q = rho * (F.c_q32 * ld * ld + F.c_l32 * cs * L * fabsf(div));
+  }
+  F.sig[c] = p + q;
 }
 
 // Lagrangian volume of a cell by closure: V_E minus its net swept volume.
@@ -693,6 +785,7 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
     case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
     case kMixDensity: m_density_body<IN>(F, S, i, j, k); break;
+    case kMixPredict: m_predict_body<JIT, IN>(F, S, i, j, k); break;
     default: break;
   }
 }
@@ -717,7 +810,9 @@ __device__ __forceinline__ void run_tile(const Fields<float> &F, DevScalars *S, 
 // the others; the node gathers lose more to occupancy than they gain from
 // the extra loads in flight of an uncapped build.
 __host__ __device__ constexpr int min_blocks(int kid, int threads) {
-  return kid == kMixCells ? 768 / threads : (kid == kMixRemapEos || kid == kMixEos || kid == kMixNodes || kid == kMixRemapNodes) ? 1024 / threads : 1;
+  return (kid == kMixCells || kid == kMixPredict) ? 768 / threads
+         : (kid == kMixRemapEos || kid == kMixEos || kid == kMixNodes || kid == kMixRemapNodes) ? 1024 / threads
+                                                                                                 : 1;
 }
 
 template <int KID, bool JIT, int SH>
@@ -801,6 +896,7 @@ void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, i
     case kMixRemapEos: launch_one<kMixRemapEos>(F, S, mode, shape, st); break;
     case kMixEos: launch_one<kMixEos>(F, S, mode, shape, st); break;
     case kMixDensity: launch_one<kMixDensity>(F, S, mode, shape, st); break;
+    case kMixPredict: launch_one<kMixPredict>(F, S, mode, shape, st); break;
     default: break;
   }
 }

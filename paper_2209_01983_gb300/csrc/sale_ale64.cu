@@ -90,13 +90,14 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
   const double h = step_dt(S, dt_override);
   int i, j, k;
   node_ijk(n, F.nx, F.ny, i, j, k);
+  const double *Gs = F.time_order == 2 ? F.Gh : F.G;  // predictor-corrector: gradients at x^{n+1/2}
   P3 f = {0.0, 0.0, 0.0};
 #pragma unroll
   for (int s = 0; s < 8; ++s) {
     const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
     if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
     const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
-    f = f + F.sig[c] * corner_g(F.G, F.nc, c, 7 - s);
+    f = f + F.sig[c] * corner_g(Gs, F.nc, c, 7 - s);
   }
   const double hm = h / F.mn[n];
   const double u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
@@ -166,10 +167,11 @@ __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScala
   // compatible energy update with the cached reference gradient
   P3 ub[8];
   double work = 0.0;
+  const double *Gs = F.time_order == 2 ? F.Gh : F.G;  // predictor-corrector: gradients at x^{n+1/2}
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     ub[a] = {F.ub[nid[a]], F.vb[nid[a]], F.wb[nid[a]]};
-    work += dot(corner_g(F.G, F.nc, c, a), ub[a]);
+    work += dot(corner_g(Gs, F.nc, c, a), ub[a]);
   }
   const double m = F.m[c];
   F.e[c] = F.e[c] - h / m * F.sig[c] * work;
@@ -411,6 +413,44 @@ __device__ __forceinline__ void ale_cell_velocities(const Fields<double> &F, int
   }
 }
 
+// Predictor-corrector half step on the reference mesh: e^{n+1/2} with the
+// cached gradient and u^n, then the EoS and viscosity on x_ref + dt/2 u^n.
+// sigma^{n+1/2} replaces sigma; the corner gradients at x^{n+1/2} go to Gh
+// for the corrector's node and cell passes.
+__global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, DevScalars *S, double dt_override) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 U[8], X[8];
+  ale_cell_velocities(F, i, j, k, U);
+  double work = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    work += dot(corner_g(F.G, F.nc, c, a), U[a]);
+    const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a] = {F.xr[n] + 0.5 * h * U[a].x, F.yr[n] + 0.5 * h * U[a].y, F.zr[n] + 0.5 * h * U[a].z};
+  }
+  const double m = F.m[c];
+  const double e = F.e[c] - 0.5 * h / m * F.sig[c] * work;
+  shift0(X);
+  const double V = hex_volume_shifted(X);
+  if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
+  const double dvdt = grad_store_dot(X, U, F.Gh, F.nc, c);
+  const double rho = m / V;
+  const double p = (F.gamma - 1.0) * rho * e;
+  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  const double div = dvdt / V;
+  const double L = V / sqrt(hex_max_face_area2(X));
+  double q = 0.0;
+  if (div < 0.0) {
+    const double ld = L * div;
+    q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
+  }
+  F.sig[c] = p + q;
+}
+
 __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
   if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -483,6 +523,7 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
   switch (kid) {
     case kAleNodes: k_ale_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleCells: k_ale_cells<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleSlopes: k_ale_slopes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;

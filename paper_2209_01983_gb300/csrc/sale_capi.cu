@@ -224,7 +224,10 @@ struct sale_state {
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
   float *Gc;                             // FP32-mixed path, jittered mesh: corner gradients
+  void *Gh;                              // predictor-corrector: half-step corner gradients (24 per cell)
   bool jit = false;                      // the mesh is jittered
+  bool o2 = false;                       // second-order remap scratch carved (FP64)
+  bool pc = false;                       // predictor-corrector scratch carved
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
@@ -278,6 +281,7 @@ static size_t carve(sale_state *st, char *base) {
   st->off4 = nullptr;
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
   st->Gc = nullptr;
+  st->Gh = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
     st->geoG = (double *)cv.take(sizeof(double) * 31 * nc);
@@ -291,7 +295,8 @@ static size_t carve(sale_state *st, char *base) {
     st->ste = (double *)cv.take(sizeof(double) * 9 * nn);
     for (int d = 0; d < 3; ++d) st->mq[d] = (double *)cv.take(sizeof(double) * nc);
     st->kd = (double *)cv.take(sizeof(double) * nn);
-    for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
+    if (st->o2)
+      for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
@@ -300,6 +305,7 @@ static size_t carve(sale_state *st, char *base) {
     st->elo = (float *)cv.take(sizeof(float) * nc);
     if (st->jit) st->Gc = (float *)cv.take(sizeof(float) * 24 * nc);
   }
+  if (st->pc) st->Gh = cv.take(E * 24 * nc);
   return align_up(cv.off);
 }
 
@@ -381,6 +387,8 @@ static Fields<R> fields_t(const sale_state *st) {
   F.c_l32 = (float)F.c_l;
   F.ke_fix = st->prob.ke_fix;
   F.remap_order = st->prob.remap_order == 2 ? 2 : 1;
+  F.time_order = st->prob.time_order == 2 ? 2 : 1;
+  F.Gh = (R *)st->Gh;
   F.srx = (R *)st->slope[0];
   F.sry = (R *)st->slope[1];
   F.srz = (R *)st->slope[2];
@@ -392,12 +400,14 @@ static Fields<R> fields_t(const sale_state *st) {
   return F;
 }
 
-static size_t state_bytes(long long nc, long long nn, int precision, bool jit) {
+static size_t state_bytes(long long nc, long long nn, int precision, bool jit, bool o2 = false, bool pc = false) {
   sale_state tmp;
   tmp.nc = nc;
   tmp.nn = nn;
   tmp.precision = precision;
   tmp.jit = jit;
+  tmp.o2 = o2 && precision == SALE_FP64;
+  tmp.pc = pc;
   tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   return carve(&tmp, nullptr);
 }
@@ -405,6 +415,12 @@ static size_t state_bytes(long long nc, long long nn, int precision, bool jit) {
 extern "C" size_t sale_state_bytes(const sale_mesh *mesh, int precision) {
   if (!mesh || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0);
+}
+
+extern "C" size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision) {
+  if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
+  return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0, prob->remap_order == 2,
+                     prob->time_order == 2);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -421,6 +437,7 @@ static int validate_problem(const sale_problem_desc &p) {
   }
   if (!std::isfinite(p.e_deposit) || p.e_deposit < 0.0) return fail(SALE_EINVAL, "problem: e_deposit must be finite and >= 0");
   if (p.remap_order < 0 || p.remap_order > 2) return fail(SALE_EINVAL, "problem: remap_order must be 0, 1 or 2");
+  if (p.time_order < 0 || p.time_order > 2) return fail(SALE_EINVAL, "problem: time_order must be 0, 1 or 2");
   return SALE_OK;
 }
 
@@ -497,7 +514,7 @@ static void record(sale_state *st, cudaEvent_t ev) {
 static void dispatch(sale_state *st, int kid, int mode, double dt_override) {
   if (st->precision == SALE_FP64) {
     launch_kernel(kid, fields_t<double>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
-  } else if ((kid >= kMixNodes && kid <= kMixEos) || kid == kMixDensity) {
+  } else if ((kid >= kMixNodes && kid <= kMixEos) || kid == kMixDensity || kid == kMixPredict) {
     launch_m_kernel(kid, fields_t<float>(st), st->S, mode, st->tile_shape, st->stream);
   } else {
     launch_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
@@ -570,8 +587,7 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
-  rc = check_device_buffer("sale_state_init", device_buf, bytes,
-                           state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0));
+  rc = check_device_buffer("sale_state_init", device_buf, bytes, sale_state_bytes_for(mesh, prob, precision));
   if (rc) return rc;
   return state_init_at(mesh, prob, precision, device_buf, cuda_stream, out);
 }
@@ -589,6 +605,8 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   st->nn = mesh->nn;
   st->precision = precision;
   st->jit = mesh->d.jitter > 0.0;
+  st->o2 = precision == SALE_FP64 && prob->remap_order == 2;
+  st->pc = prob->time_order == 2;
   st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
@@ -737,6 +755,7 @@ static void launch_remap(sale_state *st) {
 // stay implicit (x_ref + dt ubar) and are never written.
 static void launch_ale_cycle(sale_state *st, double dt_override) {
   if (st->precision == SALE_FP32_MIXED) {
+    if (st->prob.time_order == 2) launch_k(st, kMixPredict, 0, dt_override);
     launch_k(st, kMixNodes, 0, dt_override);
     launch_k(st, kMixCells, 0, dt_override);
     if (st->prob.remap_order == 2) launch_k(st, kMixDensity);
@@ -746,6 +765,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
     launch_k(st, kMixRemapEos, kDtAdvance, dt_override);
     return;
   }
+  if (st->prob.time_order == 2) launch_k(st, kAlePredict, 0, dt_override);
   launch_k(st, kAleNodes, 0, dt_override);
   launch_k(st, kAleEdges, 0, dt_override);
   launch_k(st, kAleCells, 0, dt_override);
@@ -762,9 +782,14 @@ static void launch_cycle(sale_state *st, bool remap, double dt_override) {
     launch_ale_cycle(st, dt_override);
     return;
   }
+  const bool pc = st->prob.time_order == 2;
+  if (pc) {  // half step: positions x^{n+1/2} (next-position buffer), then sigma^{n+1/2}
+    launch_k(st, kPcPositions, 0, dt_override);
+    launch_k(st, kPcPredict, 0, dt_override);
+  }
   launch_k(st, kLagNodes, 0, dt_override);
   launch_k(st, kLagCells, 0, dt_override);
-  st->xpar ^= 1;
+  if (!pc) st->xpar ^= 1;  // the corrector moves the nodes in place
   if (remap) launch_remap(st);
   launch_k(st, kEos, kDtAdvance, dt_override);
   st->x_is_ref = remap;
@@ -805,7 +830,7 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
         st->upar ^= 1;
         continue;
       }
-      st->xpar ^= 1;
+      if (st->prob.time_order != 2) st->xpar ^= 1;
       if (remap) st->upar ^= 1;
       st->x_is_ref = remap;
     }
@@ -1194,6 +1219,8 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   for (int i = 0; i < n; ++i) {
     int rc = validate_problem(probs[i]);
     if (rc) return fail(rc, "sale_batch_create: mesh %d: %s", i, sale_last_error());
+    if (probs[i].time_order == 2)
+      return fail(SALE_EINVAL, "sale_batch_create: mesh %d: batches run the single-stage Lagrangian step", i);
   }
   std::vector<size_t> soff((size_t)n);
   size_t parts[4];
@@ -1336,7 +1363,7 @@ static const char *const kKernelNames[kNumKernels] = {
     "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
     "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
     "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes", "ale_eos",     "ale_slopes",
-    "mix_density"};
+    "mix_density",  "pc_positions", "pc_predict", "ale_predict", "mix_predict"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

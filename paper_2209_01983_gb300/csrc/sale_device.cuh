@@ -75,6 +75,33 @@ __device__ __forceinline__ float slab_average_f(float q, float slope, float nu, 
   return q + side * 0.5f * slope * (1.f - fminf(nu, 1.f));
 }
 
+// Corner A's gradient of a shifted hex, stored to G[(3A + axis) nc + c]
+// and dotted with U[A] into dvdt (one corner at a time keeps the full
+// 24-value gradient out of registers).
+template <int A, typename R>
+__device__ __forceinline__ void corner_grad_store(const P3 (&X)[8], const P3 (&U)[8], R *G, long long nc,
+                                                  long long c, double &dvdt) {
+  const P3 g = hex_corner_grad_shifted<A>(X);
+  dvdt += dot(g, U[A]);
+  G[(3ll * A + 0) * nc + c] = (R)g.x;
+  G[(3ll * A + 1) * nc + c] = (R)g.y;
+  G[(3ll * A + 2) * nc + c] = (R)g.z;
+}
+
+template <typename R>
+__device__ __forceinline__ double grad_store_dot(const P3 (&X)[8], const P3 (&U)[8], R *G, long long nc, long long c) {
+  double dvdt = 0.0;
+  corner_grad_store<0>(X, U, G, nc, c, dvdt);
+  corner_grad_store<1>(X, U, G, nc, c, dvdt);
+  corner_grad_store<2>(X, U, G, nc, c, dvdt);
+  corner_grad_store<3>(X, U, G, nc, c, dvdt);
+  corner_grad_store<4>(X, U, G, nc, c, dvdt);
+  corner_grad_store<5>(X, U, G, nc, c, dvdt);
+  corner_grad_store<6>(X, U, G, nc, c, dvdt);
+  corner_grad_store<7>(X, U, G, nc, c, dvdt);
+  return dvdt;
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

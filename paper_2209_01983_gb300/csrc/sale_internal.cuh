@@ -70,6 +70,10 @@ enum KernelId : int {
   kAleEos,       // ALE path: EoS + dt on the reference mesh (refresh)
   kAleSlopes,    // ALE path, second-order remap: limited slopes of rho_L and e
   kMixDensity,   // FP32-mixed path, second-order remap: V_L and rho_L
+  kPcPositions,  // predictor-corrector (general path): half-step positions
+  kPcPredict,    //   half-step energy, EoS, viscosity: sigma^{n+1/2}
+  kAlePredict,   // predictor-corrector, FP64 Eulerian path
+  kMixPredict,   // predictor-corrector, FP32-mixed path
   kNumKernels
 };
 
@@ -126,6 +130,8 @@ struct Fields {
   float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
   int ke_fix;
   int remap_order;             // cell remap: 1 donor cell, 2 van Leer piecewise linear
+  int time_order;              // Lagrangian step: 1 single stage, 2 predictor-corrector
+  R *Gh;                       // predictor-corrector: corner gradients at x^{n+1/2}, Gh[(3 a + axis) nc + c]
   R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
   R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
   int remap_sets_x;            // node remap writes the reference positions to x

@@ -141,41 +141,103 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
 // Lagrangian step
 // ---------------------------------------------------------------------------
 
-// One corner of the hex around a node: accumulate sigma_c dV_c/dx_node.
+// One corner of the hex around a node: accumulate sigma_c dV_c/dx_node,
+// the gradient taken at the positions (gx, gy, gz).
 template <int S8, typename R>
-__device__ __forceinline__ void add_corner_force(const Fields<R> &F, int i, int j, int k, P3 &f) {
+__device__ __forceinline__ void add_corner_force(const Fields<R> &F, const R *gx, const R *gy, const R *gz, int i,
+                                                 int j, int k, P3 &f) {
   const int ci = i - 1 + (S8 & 1), cj = j - 1 + ((S8 >> 1) & 1), ck = k - 1 + ((S8 >> 2) & 1);
   if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) return;
   P3 X[8];
-  load_hex(F.x, F.y, F.z, F.nx, F.ny, ci, cj, ck, X);
+  load_hex(gx, gy, gz, F.nx, F.ny, ci, cj, ck, X);
   shift0(X);
   const P3 g = hex_corner_grad_shifted<7 - S8>(X);
   const double sig = (double)F.sig[cell_index(F.nx, F.ny, ci, cj, ck)];
   f = f + sig * g;
 }
 
+// Predictor-corrector (time_order 2) half step: x^{n+1/2} = x^n + dt/2 u^n
+// of every node, into the next-position buffer.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_pc_positions(Fields<R> F, DevScalars *S, double dt_override) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  F.xn[n] = (R)((double)F.x[n] + 0.5 * h * (double)F.u[n]);
+  F.yn[n] = (R)((double)F.y[n] + 0.5 * h * (double)F.v[n]);
+  F.zn[n] = (R)((double)F.z[n] + 0.5 * h * (double)F.w[n]);
+}
+
+// Predictor of every cell: e^{n+1/2} = e^n - dt/(2m) sigma^n sum_a
+// dV/dx_a(x^n).u^n_a, then the EoS and viscosity on x^{n+1/2} with u^n;
+// sigma^{n+1/2} replaces sigma (read only by this cell's thread).
+template <typename R>
+__global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalars *S, double dt_override) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 X[8], U[8], G[8];
+  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
+  shift0(X);
+  hex_grad_shifted(X, G);
+  double work = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) work += dot(G[a], U[a]);
+  const double m = (double)F.m[c];
+  const double e = (double)F.e[c] - 0.5 * h / m * (double)F.sig[c] * work;
+  load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+  shift0(X);
+  const double V = hex_volume_shifted(X);
+  if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
+  hex_grad_shifted(X, G);
+  double dvdt = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) dvdt += dot(G[a], U[a]);
+  const double rho = m / V;
+  const double p = (F.gamma - 1.0) * rho * e;
+  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  const double div = dvdt / V;
+  const double L = V / sqrt(hex_max_face_area2(X));
+  double q = 0.0;
+  if (div < 0.0) {
+    const double ld = L * div;
+    q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
+  }
+  F.sig[c] = (R)(p + q);
+}
+
+// Lagrangian node pass.  Single stage: corner forces of x^n, new positions
+// into the next-position buffer.  Predictor-corrector: corner forces of
+// x^{n+1/2} (next-position buffer), new positions in place.
 template <typename R>
 __global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScalars *S, double dt_override) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= F.nn) return;
+  const bool pc = F.time_order == 2;
   if (!cycle_active(S)) {  // inactive cycle: positions carry over unchanged
-    F.xn[n] = F.x[n];
-    F.yn[n] = F.y[n];
-    F.zn[n] = F.z[n];
+    if (!pc) {
+      F.xn[n] = F.x[n];
+      F.yn[n] = F.y[n];
+      F.zn[n] = F.z[n];
+    }
     return;
   }
   const double h = step_dt(S, dt_override);
   int i, j, k;
   node_ijk(n, F.nx, F.ny, i, j, k);
+  const R *gx = pc ? F.xn : F.x, *gy = pc ? F.yn : F.y, *gz = pc ? F.zn : F.z;
   P3 f = {0.0, 0.0, 0.0};
-  add_corner_force<0>(F, i, j, k, f);
-  add_corner_force<1>(F, i, j, k, f);
-  add_corner_force<2>(F, i, j, k, f);
-  add_corner_force<3>(F, i, j, k, f);
-  add_corner_force<4>(F, i, j, k, f);
-  add_corner_force<5>(F, i, j, k, f);
-  add_corner_force<6>(F, i, j, k, f);
-  add_corner_force<7>(F, i, j, k, f);
+  add_corner_force<0>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<1>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<2>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<3>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<4>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<5>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<6>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<7>(F, gx, gy, gz, i, j, k, f);
   const double mn = (double)F.mn[n];
   const double u0 = (double)F.u[n], v0 = (double)F.v[n], w0 = (double)F.w[n];
   double u1 = u0 + h * f.x / mn, v1 = v0 + h * f.y / mn, w1 = w0 + h * f.z / mn;
@@ -187,9 +249,10 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScala
   F.ub[n] = (R)ub;
   F.vb[n] = (R)vb;
   F.wb[n] = (R)wb;
-  F.xn[n] = (R)((double)F.x[n] + h * ub);
-  F.yn[n] = (R)((double)F.y[n] + h * vb);
-  F.zn[n] = (R)((double)F.z[n] + h * wb);
+  R *ox = pc ? F.x : F.xn, *oy = pc ? F.y : F.yn, *oz = pc ? F.z : F.zn;
+  ox[n] = (R)((double)F.x[n] + h * ub);
+  oy[n] = (R)((double)F.y[n] + h * vb);
+  oz[n] = (R)((double)F.z[n] + h * wb);
 }
 
 template <typename R>
@@ -199,8 +262,10 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
   const double h = step_dt(S, dt_override);
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
+  const bool pc = F.time_order == 2;  // gradient at x^{n+1/2}, new positions in place
   P3 X[8], UB[8], G[8];
-  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  if (pc) load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+  else load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   load_hex(F.ub, F.vb, F.wb, F.nx, F.ny, i, j, k, UB);
   shift0(X);
   hex_grad_shifted(X, G);
@@ -209,7 +274,8 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
   for (int a = 0; a < 8; ++a) work += dot(G[a], UB[a]);
   const double m = (double)F.m[c];
   const double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
-  load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+  if (pc) load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  else load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
   const double V1 = hex_volume_shifted(X);
   if (!(V1 > 0.0)) set_status(S, V1 != V1 ? SALE_ENAN : SALE_ENEGVOL);
@@ -484,7 +550,7 @@ template <typename R>
 void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t st) {
   if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes || kid == kAleEos ||
-      kid == kAleSlopes) {
+      kid == kAleSlopes || kid == kAlePredict) {
     if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
     return;
   }
@@ -493,6 +559,8 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
     case kEos: k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override); break;
     case kLagNodes: k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kLagCells: k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kPcPositions: k_pc_positions<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kPcPredict: k_pc_predict<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kRemapFaces: k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
     case kRemapNodes: k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S); break;
     case kRemapCells: k_remap_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;

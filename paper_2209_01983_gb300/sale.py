@@ -41,7 +41,7 @@ class sale_problem_desc(C.Structure):
                 ("p_blast", C.c_double), ("e_deposit", C.c_double),
                 ("cfl", C.c_double), ("c_q", C.c_double), ("c_l", C.c_double),
                 ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int),
-                ("remap_order", C.c_int)]
+                ("remap_order", C.c_int), ("time_order", C.c_int)]
 
 
 class sale_diag(C.Structure):
@@ -65,6 +65,7 @@ sale_mesh_create = _sig("sale_mesh_create", C.c_int, [C.POINTER(sale_mesh_desc),
 sale_mesh_destroy = _sig("sale_mesh_destroy", None, [_vp])
 sale_mesh_nodes = _sig("sale_mesh_nodes", C.c_int, [_vp, _dp, C.c_size_t])
 sale_state_bytes = _sig("sale_state_bytes", C.c_size_t, [_vp, C.c_int])
+sale_state_bytes_for = _sig("sale_state_bytes_for", C.c_size_t, [_vp, _vp, C.c_int])
 sale_state_init = _sig("sale_state_init", C.c_int,
                        [_vp, C.POINTER(sale_problem_desc), C.c_int, _vp, C.c_size_t, _vp, C.POINTER(_vp)])
 sale_state_destroy = _sig("sale_state_destroy", None, [_vp])
@@ -100,7 +101,7 @@ SALE_STATIC_MAX_NODES = 131072
 sale_last_error = _sig("sale_last_error", C.c_char_p, [])
 
 #: every symbol declared in include/sale.h
-EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes",
+EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes", "sale_state_bytes_for",
            "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
            "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
            "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
@@ -137,7 +138,7 @@ def problem_desc(pd: inputs.ProblemDesc) -> sale_problem_desc:
     p = sale_problem_desc()
     for name, _ in sale_problem_desc._fields_:
         v = getattr(pd, name)
-        setattr(p, name, int(v) if name in ("kind", "ke_fix", "remap_order") else float(v))
+        setattr(p, name, int(v) if name in ("kind", "ke_fix", "remap_order", "time_order") else float(v))
     if not math.isfinite(p.dt_init):
         p.dt_init = 0.0
     return p
@@ -172,13 +173,14 @@ class State:
 
         self.md, self.pd = md, pd
         self.mesh = Mesh(md)
-        nbytes = sale_state_bytes(self.mesh._h, precision)
+        self._prob = problem_desc(pd)
+        nbytes = sale_state_bytes_for(self.mesh._h, C.byref(self._prob), precision)
         if nbytes == 0:
             raise SaleError(SALE_EINVAL, f"unsupported precision {precision}")
         self.buffer = torch.empty(nbytes, dtype=torch.uint8, device=device)
         self.stream = stream if stream is not None else torch.cuda.Stream(device=device)
         self._h = _vp()
-        check(sale_state_init(self.mesh._h, C.byref(problem_desc(pd)), precision,
+        check(sale_state_init(self.mesh._h, C.byref(self._prob), precision,
                               _vp(self.buffer.data_ptr()), nbytes, _vp(self.stream.cuda_stream),
                               C.byref(self._h)))
         self.ncell, self.nnode = md.ncell, md.nnode

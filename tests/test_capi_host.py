@@ -71,3 +71,22 @@ def test_null_arguments_rejected(sale):
     assert sale.sale_lagrange_step(None, 0.0) == sale.SALE_EINVAL
     assert sale.sale_run_to_time(None, 1.0, 1, 0, None) == sale.SALE_EINVAL
     assert b"null" in sale.sale_last_error()
+
+
+def test_state_bytes_for_scheme_options(sale):
+    import dataclasses
+    md, pd = inputs.sedov_octant(8, jitter=0.1)
+    m = sale.Mesh(md)
+    for prec in (sale.SALE_FP64, sale.SALE_FP32_MIXED):
+        base = sale.sale_state_bytes(m._h, prec)
+        assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(pd)), prec) == base
+        pc = dataclasses.replace(pd, time_order=2)
+        # half-step corner gradients: 24 values per cell
+        extra = sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(pc)), prec) - base
+        assert extra >= 24 * md.ncell * (8 if prec == sale.SALE_FP64 else 4)
+    o2 = dataclasses.replace(pd, remap_order=2)
+    assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(o2)), sale.SALE_FP64) >= \
+        sale.sale_state_bytes(m._h, sale.SALE_FP64) + 7 * 8 * md.ncell
+    assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(o2)), sale.SALE_FP32_MIXED) == \
+        sale.sale_state_bytes(m._h, sale.SALE_FP32_MIXED)
+    assert sale.sale_state_bytes_for(m._h, None, sale.SALE_FP64) == 0
