@@ -32,6 +32,7 @@ class Params(C.Structure):
         ("gamma", C.c_double), ("cfl", C.c_double), ("c_q", C.c_double),
         ("c_l", C.c_double), ("dt_growth", C.c_double), ("dt_init", C.c_double),
         ("ke_fix", C.c_int), ("reflect", C.c_int * 6), ("remap_order", C.c_int), ("time_order", C.c_int),
+        ("c_hg", C.c_double),
     ]
 
 
@@ -135,6 +136,7 @@ def params_from(pd, reflect=(1, 1, 1, 1, 1, 1)) -> Params:
         p.reflect[i] = int(reflect[i])
     p.remap_order = int(getattr(pd, "remap_order", 1))
     p.time_order = int(getattr(pd, "time_order", 1))
+    p.c_hg = float(getattr(pd, "c_hg", 0.0))
     return p
 
 

@@ -371,6 +371,46 @@ int oracle_set_state(oracle_state *s, const double *x, const double *y,
 /* Lagrangian step                                                     */
 /* ------------------------------------------------------------------ */
 
+/* Viscous hourglass corner forces of one cell (reading R16, Flanagan and
+ * Belytschko 1981).  With local node a = di + 2 dj + 4 dk and signs
+ * s = 2 d - 1, the four hourglass patterns are h_1 = s_x s_y, h_2 = s_y s_z,
+ * h_3 = s_z s_x, h_4 = s_x s_y s_z.  With b_a = dV/dx_a / V (the mean shape
+ * function gradients) the hourglass shape vectors are
+ *     gamma_alpha(a) = h_alpha(a) - sum_i (sum_b h_alpha(b) x_b,i) b_a,i,
+ * which vanish on every linear field; the hourglass rates are
+ * q_alpha = sum_a gamma_alpha(a) u_a and the corner forces
+ *     f_a = -kappa sum_alpha gamma_alpha(a) q_alpha,
+ * kappa = c_hg rho cs V^(2/3).  X, U: the cell's 8 nodes (24 values). */
+static void hourglass_forces(const double *X, const double *U, double V, double rho, double cs, double c_hg,
+                             double *fh) {
+  double G[24];
+  oracle_hex_volume_grad(X, G);
+  double h[4][8];
+  for (int a = 0; a < 8; ++a) {
+    const double sx = (a & 1) ? 1.0 : -1.0, sy = (a & 2) ? 1.0 : -1.0, sz = (a & 4) ? 1.0 : -1.0;
+    h[0][a] = sx * sy;
+    h[1][a] = sy * sz;
+    h[2][a] = sz * sx;
+    h[3][a] = sx * sy * sz;
+  }
+  double gam[4][8];
+  for (int al = 0; al < 4; ++al) {
+    double hx[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 8; ++b)
+      for (int i = 0; i < 3; ++i) hx[i] += h[al][b] * X[b * 3 + i];
+    for (int a = 0; a < 8; ++a) gam[al][a] = h[al][a] - dot3(hx, &G[a * 3]) / V;
+  }
+  const double kappa = c_hg * rho * cs * cbrt(V) * cbrt(V);
+  for (int a = 0; a < 24; ++a) fh[a] = 0.0;
+  for (int al = 0; al < 4; ++al) {
+    double q[3] = {0.0, 0.0, 0.0};
+    for (int b = 0; b < 8; ++b)
+      for (int i = 0; i < 3; ++i) q[i] += gam[al][b] * U[b * 3 + i];
+    for (int a = 0; a < 8; ++a)
+      for (int i = 0; i < 3; ++i) fh[a * 3 + i] -= kappa * gam[al][a] * q[i];
+  }
+}
+
 /* Lagrangian step (R4).  Single stage: corner forces sigma^n dV/dx(x^n).
  * Predictor-corrector (R15, time_order = 2): a half step of dt/2 first
  * moves the nodes to x^{n+1/2} = x^n + dt/2 u^n and the cells to
@@ -387,11 +427,25 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
   double *ubx = alloc_zero(nn), *uby = alloc_zero(nn), *ubz = alloc_zero(nn);
   double *e_new = alloc_zero(nc), *sig = alloc_zero(nc);
   double *xh = alloc_zero(nn), *yh = alloc_zero(nn), *zh = alloc_zero(nn);
-  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh) {
+  const int hg = s->prm.c_hg > 0.0;
+  double *fh = hg ? alloc_zero(24 * nc) : NULL;
+  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh || (hg && !fh)) {
     free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-    free(xh); free(yh); free(zh);
+    free(xh); free(yh); free(zh); free(fh);
     return s->status = ORACLE_ENOMEM;
   }
+
+  /* Hourglass corner forces of x^n, u^n (R16), held for the whole step. */
+  if (hg)
+    for (int k = 0; k < s->nz; ++k)
+      for (int j = 0; j < s->ny; ++j)
+        for (int i = 0; i < s->nx; ++i) {
+          long long c = cell_id(s, i, j, k);
+          double X[24], U[24];
+          gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+          gather_hex(s, i, j, k, s->u, s->v, s->w, U);
+          hourglass_forces(X, U, s->vol[c], s->rho[c], s->cs[c], s->prm.c_hg, &fh[24 * c]);
+        }
 
   /* Stress of every cell and the positions its corner forces are taken at. */
   const double *gx = s->x, *gy = s->y, *gz = s->z;
@@ -410,15 +464,18 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
           gather_hex(s, i, j, k, s->x, s->y, s->z, X);
           gather_hex(s, i, j, k, s->u, s->v, s->w, U);
           oracle_hex_volume_grad(X, G);
-          double work = 0.0;
+          double work = 0.0, work_hg = 0.0;
           for (int a = 0; a < 8; ++a) work += dot3(&G[a * 3], &U[a * 3]);
+          if (hg)
+            for (int a = 0; a < 8; ++a) work_hg += dot3(&fh[24 * c + a * 3], &U[a * 3]);
           double e_half = s->e[c] - 0.5 * dt / s->m[c] * sig[c] * work;
+          if (hg) e_half -= 0.5 * dt / s->m[c] * work_hg;
           gather_hex(s, i, j, k, xh, yh, zh, XH);
           double V, rho, p, q, cs, L;
           int rc = cell_state(s, XH, U, s->m[c], e_half, &V, &rho, &p, &q, &cs, &L);
           if (rc) {
             free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-            free(xh); free(yh); free(zh);
+            free(xh); free(yh); free(zh); free(fh);
             return s->status = rc;
           }
           e_new[c] = p + q;  /* sigma^{n+1/2}, moved into sig below */
@@ -440,9 +497,12 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
         oracle_hex_volume_grad(X, G);
         for (int a = 0; a < 8; ++a) {
           long long n = node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-          fx[n] += sigma * G[a * 3 + 0];
-          fy[n] += sigma * G[a * 3 + 1];
-          fz[n] += sigma * G[a * 3 + 2];
+          double cf[3] = {sigma * G[a * 3 + 0], sigma * G[a * 3 + 1], sigma * G[a * 3 + 2]};
+          if (hg)
+            for (int d = 0; d < 3; ++d) cf[d] += fh[24 * c + a * 3 + d];
+          fx[n] += cf[0];
+          fy[n] += cf[1];
+          fz[n] += cf[2];
         }
       }
 
@@ -473,9 +533,12 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
         gather_hex(s, i, j, k, gx, gy, gz, X);
         gather_hex(s, i, j, k, ubx, uby, ubz, UB);
         oracle_hex_volume_grad(X, G);
-        double work = 0.0;
+        double work = 0.0, work_hg = 0.0;
         for (int a = 0; a < 8; ++a) work += dot3(&G[a * 3], &UB[a * 3]);
+        if (hg)
+          for (int a = 0; a < 8; ++a) work_hg += dot3(&fh[24 * c + a * 3], &UB[a * 3]);
         e_new[c] = s->e[c] - dt / s->m[c] * sigma * work;
+        if (hg) e_new[c] -= dt / s->m[c] * work_hg;
       }
 
   /* Move the mesh with the time-centred velocity. */
@@ -486,7 +549,7 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
   }
   memcpy(s->e, e_new, sizeof(double) * (size_t)nc);
   free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-  free(xh); free(yh); free(zh);
+  free(xh); free(yh); free(zh); free(fh);
 
   s->t += dt;
   s->dt_last = dt;

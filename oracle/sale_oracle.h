@@ -15,6 +15,9 @@
  *     node mean;
  *   - compatible energy update (Caramana, Burton, Shashkov, Whalen 1998),
  *     single stage or with a midpoint predictor for second order in time;
+ *   - optional viscous hourglass control (Flanagan, Belytschko, "A uniform
+ *     strain hexahedron and quadrilateral with orthogonal hourglass
+ *     control", IJNME 17, 1981);
  *   - donor-cell (upwind) remap of mass, energy, momentum (Amsden et al.
  *     1980, "SALE"), with kinetic-energy fix-up;
  *   - optionally, second-order cell remap: van Leer's limited
@@ -53,6 +56,7 @@ typedef struct oracle_params {
   int reflect[6];    /* x-lo,x-hi,y-lo,y-hi,z-lo,z-hi: 1 = reflecting wall */
   int remap_order;   /* cell remap: 2 = van Leer piecewise linear, else first-order donor cell */
   int time_order;    /* Lagrange step: 2 = predictor-corrector, else single stage */
+  double c_hg;       /* Flanagan-Belytschko viscous hourglass coefficient (0: none) */
 } oracle_params;
 
 typedef struct oracle_state {

@@ -94,6 +94,7 @@ class ProblemDesc:
     ke_fix: int = 1
     remap_order: int = 1  # cell remap: 1 donor cell, 2 van Leer piecewise linear
     time_order: int = 1   # Lagrange step: 1 single stage, 2 predictor-corrector
+    c_hg: float = 0.0     # viscous hourglass coefficient (0: no hourglass control)
 
 
 def mesh_nodes(md: MeshDesc):
