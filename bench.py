@@ -53,6 +53,7 @@ def parse():
                     help="cell remap: 1 donor cell, 2 van Leer piecewise linear")
     ap.add_argument("--time-order", type=int, default=1, choices=(1, 2),
                     help="Lagrangian step: 1 single stage, 2 predictor-corrector")
+    ap.add_argument("--c-hg", type=float, default=0.0, help="viscous hourglass coefficient (0: none)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
@@ -173,10 +174,11 @@ def reference_arm(args):
 
 
 def workload_config(args, precision):
-    order = ("" if args.remap_order == 1 else "-remap2") + ("" if args.time_order == 1 else "-pc")
+    order = ("" if args.remap_order == 1 else "-remap2") + ("" if args.time_order == 1 else "-pc") + \
+        ("" if args.c_hg == 0 else f"-hg{args.c_hg}")
     return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-ale-every-cycle{order}",
             "cells": args.n ** 3, "gamma": 1.4, "remap_every": 1, "remap_order": args.remap_order,
-            "time_order": args.time_order,
+            "time_order": args.time_order, "c_hg": args.c_hg,
             "precision": precision,
             "l2": "state larger than the 129 MB L2 (no flush)", "parallelism": "replicas"}
 
@@ -251,7 +253,7 @@ def measure(args, precision, local, barrier):
     from paper_2209_01983_gb300 import costs, inputs, sale
 
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
-    pd = dataclasses.replace(pd, remap_order=args.remap_order, time_order=args.time_order)
+    pd = dataclasses.replace(pd, remap_order=args.remap_order, time_order=args.time_order, c_hg=args.c_hg)
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     tuning = None
@@ -287,7 +289,8 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    table = costs.table(precision, "ale", jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order)
+    table = costs.table(precision, "ale", jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
+                        hourglass=args.c_hg > 0)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
     if missing:

@@ -101,9 +101,13 @@ typedef struct {
  * node); time_order: Lagrangian step, 1 (or 0) single stage with the
  * corner forces of x^n, 2 predictor-corrector: a half step to
  * x^n + dt/2 u^n gives sigma^{n+1/2}, and the corner forces there move the
- * nodes and update the energy (second order in time, energy exact).
+ * nodes and update the energy (second order in time, energy exact);
+ * c_hg: viscous hourglass control (Flanagan-Belytschko) with corner forces
+ * -c_hg rho cs V^(2/3) sum_alpha gamma_alpha (gamma_alpha . u) from the
+ * start of the step, in both the velocity and the energy update (0: none).
  * Options other than the defaults may need more device memory: size the
- * buffer with sale_state_bytes_for(). */
+ * buffer with sale_state_bytes_for().  Batches take only the default
+ * time_order and c_hg. */
 typedef struct {
   int kind;
   double gamma;
@@ -113,6 +117,7 @@ typedef struct {
   int ke_fix;
   int remap_order;
   int time_order;
+  double c_hg;
 } sale_problem_desc;
 
 /* Diagnostics (FP64 sums in a fixed reduction order). */
@@ -140,8 +145,9 @@ int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n);
  * scheme options (0 on bad args). */
 size_t sale_state_bytes(const sale_mesh *mesh, int precision);
 /* Device bytes for this mesh, problem and precision: includes the scratch
- * of the second-order remap (FP64) and of the predictor-corrector step
- * (half-step corner gradients) when the problem asks for them. */
+ * of the second-order remap (FP64), of the predictor-corrector step
+ * (half-step corner gradients) and of the hourglass control (corner
+ * forces) when the problem asks for them. */
 size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision);
 /* Initialise a state in the caller's device buffer (>= sale_state_bytes_for,
  * 256-byte aligned) on `cuda_stream` (a cudaStream_t; NULL = legacy

@@ -130,13 +130,30 @@ MIXED_PC = {
 }
 
 
-def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1):
+# Viscous hourglass control: per cell the 4 patterns' sums over the 8
+# nodes (positions, velocities), the velocity-gradient sums M, the rates q,
+# W, and 24 corner forces written; the node and cell passes read them.
+HG = 2 * 4 * 8 * 3 + 8 * 9 * 2 + 4 * (9 * 2 + 9 * 2) + 8 * (12 + 18 + 3) + 12
+FP64_HG = {
+    # x_ref, u, G (cached), V_E, rho, cs read; 24 corner forces written
+    "ale_hourglass": ("cell", 8 * (3 + 3 + 24 + 3 + 24), HG),
+}
+MIXED_HG = {
+    # offsets or cached gradient, u, V_E, rho, e read; 24 corner forces written
+    "mix_hourglass": ("cell", 4 * (24 + 4 + 3 + 3 + 24), HG),
+}
+
+
+def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
+          hourglass: bool = False):
     if precision == "fp64":
         if path != "ale":
             return FP64
         t = dict(FP64_ALE_O2 if order == 2 else FP64_ALE)
         if time_order == 2:
             t.update(FP64_PC)
+        if hourglass:
+            t.update(FP64_HG)
         return t
     if precision == "fp32_mixed":
         t = dict(MIXED_ALE_JIT if jitter else MIXED_ALE)
@@ -144,11 +161,14 @@ def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1
             t.update(MIXED_O2)
         if time_order == 2:
             t.update(MIXED_PC)
+        if hourglass:
+            t.update(MIXED_HG)
         return t
     raise KeyError(precision)
 
 
-def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1):
+def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
+               hourglass: bool = False):
     """(bytes, flops) of one full cycle per cell."""
-    t = table(precision, path, jitter, order, time_order)
+    t = table(precision, path, jitter, order, time_order, hourglass)
     return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

@@ -196,6 +196,55 @@ __device__ __forceinline__ float hex_max_face_area2_f(const F3 (&X)[8]) {
   return amax;
 }
 
+// FP32 twin of hourglass_store (viscous Flanagan-Belytschko corner forces):
+// X relative to node 0, G the corner gradients, U the node velocities.
+__device__ __forceinline__ void hourglass_store_f(const F3 (&X)[8], const F3 (&G)[8], const F3 (&U)[8], float V,
+                                                  float rho, float cs, float c_hg, float *fh, long long nc, int c) {
+  const float iv = 1.f / V;
+  F3 hx[4], hu[4];
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    hx[al] = {0.f, 0.f, 0.f};
+    hu[al] = {0.f, 0.f, 0.f};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const float sg = hg_pattern(al, b);
+      hx[al] = hx[al] + sg * X[b];
+      hu[al] = hu[al] + sg * U[b];
+    }
+  }
+  F3 M[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    M[0] = M[0] + G[b].x * U[b];
+    M[1] = M[1] + G[b].y * U[b];
+    M[2] = M[2] + G[b].z * U[b];
+  }
+  F3 W[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+  F3 q[4];
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    q[al] = hu[al] - iv * (hx[al].x * M[0] + hx[al].y * M[1] + hx[al].z * M[2]);
+    W[0] = W[0] + hx[al].x * q[al];
+    W[1] = W[1] + hx[al].y * q[al];
+    W[2] = W[2] + hx[al].z * q[al];
+  }
+  const float cv = cbrtf(V);
+  const float kappa = c_hg * rho * cs * cv * cv;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    F3 f = hg_pattern(0, a) * q[0] + hg_pattern(1, a) * q[1] + hg_pattern(2, a) * q[2] + hg_pattern(3, a) * q[3];
+    f = f - iv * (G[a].x * W[0] + G[a].y * W[1] + G[a].z * W[2]);
+    fh[(3 * a + 0) * nc + c] = -kappa * f.x;
+    fh[(3 * a + 1) * nc + c] = -kappa * f.y;
+    fh[(3 * a + 2) * nc + c] = -kappa * f.z;
+  }
+}
+
+__device__ __forceinline__ F3 hg_corner_f(const float *fh, long long nc, int c, int a) {
+  return {__ldg(fh + (3 * a) * nc + c), __ldg(fh + (3 * a + 1) * nc + c), __ldg(fh + (3 * a + 2) * nc + c)};
+}
+
 // Side quad (L_a, E_a, E_b, L_b) term, expanded in the displacements.
 __device__ __forceinline__ float side_term(const F3 (&E)[8], const F3 (&D)[8], int a, int b) {
   return 4.f * dotf(crossf(E[a], E[b]), D[a] + D[b]) - 2.f * dotf(E[a] + E[b], crossf(D[a], D[b]));
@@ -370,6 +419,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
       f.x += ds * __ldg(g);
       f.y += ds * __ldg(g + nc);
       f.z += ds * __ldg(g + 2 * nc);
+      if (F.fh) f = f + hg_corner_f(F.fh, nc, c, 7 - q);
     }
     hm = h / F.mn[n];
   } else {
@@ -381,6 +431,14 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
     node_faces2<JIT, 4>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
     node_faces2<JIT, 5>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
     node_faces2<JIT, 6>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
+    if (F.fh) {  // hourglass corner forces, on the face terms' scale of 24
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        const bool ok = ((q & 1) ? hi_ok[0] : lo_ok[0]) && ((q & 2) ? hi_ok[1] : lo_ok[1]) &&
+                        ((q & 4) ? hi_ok[2] : lo_ok[2]);
+        if (ok) f = f + 24.f * hg_corner_f(F.fh, F.nc, c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz, 7 - q);
+      }
+    }
     hm = h / (24.f * F.mn[n]);
   }
   const float u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
@@ -413,7 +471,13 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
                                         : grad_dot_f(E, ub);
   // compatible energy update; the increment is FP32, the accumulation
   // float-float
-  const float de = h * F.sig[c] * work / F.m[c];
+  float de = h * F.sig[c] * work / F.m[c];
+  if (F.fh) {
+    float work_hg = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dotf(hg_corner_f(F.fh, F.nc, c, a), ub[a]);
+    de += h * work_hg / F.m[c];
+  }
   const DF e1 = df_add_f(load_df(F.e, F.elo, c), -de);
   F.e[c] = e1.hi;
   F.elo[c] = e1.lo;
@@ -425,6 +489,32 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
   F.dvx[c] = IN || i > 0 ? vx : 0.f;
   F.dvy[c] = IN || j > 0 ? vy : 0.f;
   F.dvz[c] = IN || k > 0 ? vz : 0.f;
+}
+
+// Hourglass corner forces of cell (i,j,k) on the reference mesh from u^n
+// and the state at n (rho = m / V_E; cs from e).
+template <bool JIT, bool IN>
+__device__ __forceinline__ void m_hourglass_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
+  if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
+  const int sy = F.nx + 1, sz = (F.nx + 1) * (F.ny + 1);
+  const int n0 = i + sy * j + sz * k;
+  const int c = i + F.nx * (j + F.ny * k);
+  F3 E[8], U[8], G[8];
+  ref_hex2<JIT>(F, n0, sy, sz, E);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    U[a] = {F.u[na], F.v[na], F.w[na]};
+  }
+  if constexpr (JIT) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) G[a] = hg_corner_f(F.Gc, F.nc, c, a);
+  } else {
+    hex_grad_f(E, G);
+  }
+  const float e = F.e[c];
+  const float g = F.gamma32;
+  hourglass_store_f(E, G, U, F.VE[c], F.rho[c], sqrtf(g * (g - 1.f) * fmaxf(e, 0.f)), F.c_hg32, F.fh, F.nc, c);
 }
 
 // Predictor-corrector half step of cell (i,j,k): e^{n+1/2} from sigma^n and
@@ -446,7 +536,13 @@ __device__ __forceinline__ void m_predict_body(const Fields<float> &F, DevScalar
   }
   const float work = JIT ? grad_dot_cached(F.Gc, F.nc, c, U) : grad_dot_f(E, U);
   const float m = F.m[c];
-  const float e = F.e[c] - 0.5f * h * F.sig[c] * work / m;
+  float e = F.e[c] - 0.5f * h * F.sig[c] * work / m;
+  if (F.fh) {
+    float work_hg = 0.f;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dotf(hg_corner_f(F.fh, F.nc, c, a), U[a]);
+    e -= 0.5f * h * work_hg / m;
+  }
   F3 X[8], G[8];
 #pragma unroll
   for (int a = 0; a < 8; ++a) X[a] = E[a] + (0.5f * h) * (U[a] - U[0]);
@@ -786,6 +882,7 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
     case kMixDensity: m_density_body<IN>(F, S, i, j, k); break;
     case kMixPredict: m_predict_body<JIT, IN>(F, S, i, j, k); break;
+    case kMixHourglass: m_hourglass_body<JIT, IN>(F, S, i, j, k); break;
     default: break;
   }
 }
@@ -897,6 +994,7 @@ void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, i
     case kMixEos: launch_one<kMixEos>(F, S, mode, shape, st); break;
     case kMixDensity: launch_one<kMixDensity>(F, S, mode, shape, st); break;
     case kMixPredict: launch_one<kMixPredict>(F, S, mode, shape, st); break;
+    case kMixHourglass: launch_one<kMixHourglass>(F, S, mode, shape, st); break;
     default: break;
   }
 }

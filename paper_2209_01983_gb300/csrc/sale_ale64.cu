@@ -97,7 +97,9 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
     const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
     if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
     const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
-    f = f + F.sig[c] * corner_g(Gs, F.nc, c, 7 - s);
+    P3 cf = F.sig[c] * corner_g(Gs, F.nc, c, 7 - s);
+    if (F.fh) cf = cf + hourglass_corner(F.fh, F.nc, c, 7 - s);
+    f = f + cf;
   }
   const double hm = h / F.mn[n];
   const double u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
@@ -174,7 +176,14 @@ __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScala
     work += dot(corner_g(Gs, F.nc, c, a), ub[a]);
   }
   const double m = F.m[c];
-  F.e[c] = F.e[c] - h / m * F.sig[c] * work;
+  double e1 = F.e[c] - h / m * F.sig[c] * work;
+  if (F.fh) {
+    double work_hg = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), ub[a]);
+    e1 -= h / m * work_hg;
+  }
+  F.e[c] = e1;
   // swept volumes of the three low faces: the Lagrangian face terms here
   // (nodes relative to reference node 0), the reference faces from the
   // cache, the side quads from k_ale_edges (a side quad traversed the other
@@ -413,6 +422,25 @@ __device__ __forceinline__ void ale_cell_velocities(const Fields<double> &F, int
   }
 }
 
+// Hourglass corner forces on the reference mesh (cached gradients) from
+// u^n and the state at n.
+__global__ void __launch_bounds__(kBlock) k_ale_hourglass(Fields<double> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 U[8], X[8], G[8];
+  ale_cell_velocities(F, i, j, k, U);
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    X[a] = {F.xr[n], F.yr[n], F.zr[n]};
+    G[a] = corner_g(F.G, F.nc, c, a);
+  }
+  shift0(X);
+  hourglass_store(X, G, U, F.VE[c], F.rho[c], F.cs[c], F.c_hg, F.fh, F.nc, c);
+}
+
 // Predictor-corrector half step on the reference mesh: e^{n+1/2} with the
 // cached gradient and u^n, then the EoS and viscosity on x_ref + dt/2 u^n.
 // sigma^{n+1/2} replaces sigma; the corner gradients at x^{n+1/2} go to Gh
@@ -433,7 +461,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
     X[a] = {F.xr[n] + 0.5 * h * U[a].x, F.yr[n] + 0.5 * h * U[a].y, F.zr[n] + 0.5 * h * U[a].z};
   }
   const double m = F.m[c];
-  const double e = F.e[c] - 0.5 * h / m * F.sig[c] * work;
+  double e = F.e[c] - 0.5 * h / m * F.sig[c] * work;
+  if (F.fh) {
+    double work_hg = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), U[a]);
+    e -= 0.5 * h / m * work_hg;
+  }
   shift0(X);
   const double V = hex_volume_shifted(X);
   if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
@@ -524,6 +558,7 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
     case kAleNodes: k_ale_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAleHourglass: k_ale_hourglass<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleCells: k_ale_cells<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleSlopes: k_ale_slopes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;

@@ -225,9 +225,11 @@ struct sale_state {
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
   float *Gc;                             // FP32-mixed path, jittered mesh: corner gradients
   void *Gh;                              // predictor-corrector: half-step corner gradients (24 per cell)
+  void *fh;                              // hourglass control: corner forces of the step (24 per cell)
   bool jit = false;                      // the mesh is jittered
   bool o2 = false;                       // second-order remap scratch carved (FP64)
   bool pc = false;                       // predictor-corrector scratch carved
+  bool hg = false;                       // hourglass scratch carved
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
@@ -282,6 +284,7 @@ static size_t carve(sale_state *st, char *base) {
   st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
   st->Gc = nullptr;
   st->Gh = nullptr;
+  st->fh = nullptr;
   if (fp64) {
     // one block, the corner gradients indexed with stride nc
     st->geoG = (double *)cv.take(sizeof(double) * 31 * nc);
@@ -306,6 +309,7 @@ static size_t carve(sale_state *st, char *base) {
     if (st->jit) st->Gc = (float *)cv.take(sizeof(float) * 24 * nc);
   }
   if (st->pc) st->Gh = cv.take(E * 24 * nc);
+  if (st->hg) st->fh = cv.take(E * 24 * nc);
   return align_up(cv.off);
 }
 
@@ -389,6 +393,9 @@ static Fields<R> fields_t(const sale_state *st) {
   F.remap_order = st->prob.remap_order == 2 ? 2 : 1;
   F.time_order = st->prob.time_order == 2 ? 2 : 1;
   F.Gh = (R *)st->Gh;
+  F.fh = (R *)st->fh;
+  F.c_hg = st->prob.c_hg;
+  F.c_hg32 = (float)st->prob.c_hg;
   F.srx = (R *)st->slope[0];
   F.sry = (R *)st->slope[1];
   F.srz = (R *)st->slope[2];
@@ -400,7 +407,8 @@ static Fields<R> fields_t(const sale_state *st) {
   return F;
 }
 
-static size_t state_bytes(long long nc, long long nn, int precision, bool jit, bool o2 = false, bool pc = false) {
+static size_t state_bytes(long long nc, long long nn, int precision, bool jit, bool o2 = false, bool pc = false,
+                          bool hg = false) {
   sale_state tmp;
   tmp.nc = nc;
   tmp.nn = nn;
@@ -408,6 +416,7 @@ static size_t state_bytes(long long nc, long long nn, int precision, bool jit, b
   tmp.jit = jit;
   tmp.o2 = o2 && precision == SALE_FP64;
   tmp.pc = pc;
+  tmp.hg = hg;
   tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   return carve(&tmp, nullptr);
 }
@@ -420,7 +429,7 @@ extern "C" size_t sale_state_bytes(const sale_mesh *mesh, int precision) {
 extern "C" size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision) {
   if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0, prob->remap_order == 2,
-                     prob->time_order == 2);
+                     prob->time_order == 2, prob->c_hg > 0.0);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -438,6 +447,7 @@ static int validate_problem(const sale_problem_desc &p) {
   if (!std::isfinite(p.e_deposit) || p.e_deposit < 0.0) return fail(SALE_EINVAL, "problem: e_deposit must be finite and >= 0");
   if (p.remap_order < 0 || p.remap_order > 2) return fail(SALE_EINVAL, "problem: remap_order must be 0, 1 or 2");
   if (p.time_order < 0 || p.time_order > 2) return fail(SALE_EINVAL, "problem: time_order must be 0, 1 or 2");
+  if (!(p.c_hg >= 0.0) || !std::isfinite(p.c_hg)) return fail(SALE_EINVAL, "problem: c_hg must be finite and >= 0");
   return SALE_OK;
 }
 
@@ -514,7 +524,8 @@ static void record(sale_state *st, cudaEvent_t ev) {
 static void dispatch(sale_state *st, int kid, int mode, double dt_override) {
   if (st->precision == SALE_FP64) {
     launch_kernel(kid, fields_t<double>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
-  } else if ((kid >= kMixNodes && kid <= kMixEos) || kid == kMixDensity || kid == kMixPredict) {
+  } else if ((kid >= kMixNodes && kid <= kMixEos) || kid == kMixDensity || kid == kMixPredict ||
+             kid == kMixHourglass) {
     launch_m_kernel(kid, fields_t<float>(st), st->S, mode, st->tile_shape, st->stream);
   } else {
     launch_kernel(kid, fields_t<float>(st), st->S, mode, dt_override, st->diag_partial, st->diag_out, st->stream);
@@ -607,6 +618,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   st->jit = mesh->d.jitter > 0.0;
   st->o2 = precision == SALE_FP64 && prob->remap_order == 2;
   st->pc = prob->time_order == 2;
+  st->hg = prob->c_hg > 0.0;
   st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
@@ -755,6 +767,7 @@ static void launch_remap(sale_state *st) {
 // stay implicit (x_ref + dt ubar) and are never written.
 static void launch_ale_cycle(sale_state *st, double dt_override) {
   if (st->precision == SALE_FP32_MIXED) {
+    if (st->hg) launch_k(st, kMixHourglass);
     if (st->prob.time_order == 2) launch_k(st, kMixPredict, 0, dt_override);
     launch_k(st, kMixNodes, 0, dt_override);
     launch_k(st, kMixCells, 0, dt_override);
@@ -765,6 +778,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
     launch_k(st, kMixRemapEos, kDtAdvance, dt_override);
     return;
   }
+  if (st->hg) launch_k(st, kAleHourglass);
   if (st->prob.time_order == 2) launch_k(st, kAlePredict, 0, dt_override);
   launch_k(st, kAleNodes, 0, dt_override);
   launch_k(st, kAleEdges, 0, dt_override);
@@ -783,6 +797,7 @@ static void launch_cycle(sale_state *st, bool remap, double dt_override) {
     return;
   }
   const bool pc = st->prob.time_order == 2;
+  if (st->hg) launch_k(st, kHourglass);  // hourglass corner forces of x^n, u^n
   if (pc) {  // half step: positions x^{n+1/2} (next-position buffer), then sigma^{n+1/2}
     launch_k(st, kPcPositions, 0, dt_override);
     launch_k(st, kPcPredict, 0, dt_override);
@@ -1219,8 +1234,9 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   for (int i = 0; i < n; ++i) {
     int rc = validate_problem(probs[i]);
     if (rc) return fail(rc, "sale_batch_create: mesh %d: %s", i, sale_last_error());
-    if (probs[i].time_order == 2)
-      return fail(SALE_EINVAL, "sale_batch_create: mesh %d: batches run the single-stage Lagrangian step", i);
+    if (probs[i].time_order == 2 || probs[i].c_hg > 0.0)
+      return fail(SALE_EINVAL, "sale_batch_create: mesh %d: batches run the single-stage step without hourglass control",
+                  i);
   }
   std::vector<size_t> soff((size_t)n);
   size_t parts[4];
@@ -1363,7 +1379,8 @@ static const char *const kKernelNames[kNumKernels] = {
     "remap_cells",  "diagnostics", "ale_nodes",    "ale_cells",      "ale_density",     "ale_fluxes",
     "ale_remap_eos", "geo_init",  "mix_nodes",     "mix_cells",      "mix_fluxes",      "mix_remap_nodes",
     "mix_remap_eos", "mix_eos",   "ale_edges",   "ale_remap_nodes", "ale_eos",     "ale_slopes",
-    "mix_density",  "pc_positions", "pc_predict", "ale_predict", "mix_predict"};
+    "mix_density",  "pc_positions", "pc_predict", "ale_predict", "mix_predict", "hourglass",
+    "ale_hourglass", "mix_hourglass"};
 
 extern "C" int sale_kernel_count(void) { return kNumKernels; }
 

@@ -102,6 +102,63 @@ __device__ __forceinline__ double grad_store_dot(const P3 (&X)[8], const P3 (&U)
   return dvdt;
 }
 
+// Viscous hourglass corner forces of a cell (Flanagan-Belytschko): X its
+// nodes relative to node 0, G = dV/dx of its corners, U its node
+// velocities; with b = G / V, gamma_alpha(a) = h_alpha(a) - hx_alpha . b_a
+// (hx_alpha = sum_b h_alpha(b) x_b), q_alpha = sum_a gamma_alpha(a) u_a,
+// f_a = -kappa sum_alpha gamma_alpha(a) q_alpha, kappa = c_hg rho cs V^(2/3).
+// Evaluated through M_i = sum_b b_b,i u_b and W_i = sum_alpha hx_alpha,i
+// q_alpha / V, so gamma is never formed; stored to fh[(3a + axis) nc + c].
+template <typename R>
+__device__ __forceinline__ void hourglass_store(const P3 (&X)[8], const P3 (&G)[8], const P3 (&U)[8], double V,
+                                                double rho, double cs, double c_hg, R *fh, long long nc,
+                                                long long c) {
+  const double iv = 1.0 / V;
+  P3 hx[4], hu[4];
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    hx[al] = {0.0, 0.0, 0.0};
+    hu[al] = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+      const double sg = hg_pattern(al, b);
+      hx[al] = hx[al] + sg * X[b];
+      hu[al] = hu[al] + sg * U[b];
+    }
+  }
+  P3 M[3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+#pragma unroll
+  for (int b = 0; b < 8; ++b) {
+    M[0] = M[0] + G[b].x * U[b];
+    M[1] = M[1] + G[b].y * U[b];
+    M[2] = M[2] + G[b].z * U[b];
+  }
+  P3 W[3] = {{0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}, {0.0, 0.0, 0.0}};
+  P3 q[4];
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    q[al] = hu[al] - iv * (hx[al].x * M[0] + hx[al].y * M[1] + hx[al].z * M[2]);
+    W[0] = W[0] + hx[al].x * q[al];
+    W[1] = W[1] + hx[al].y * q[al];
+    W[2] = W[2] + hx[al].z * q[al];
+  }
+  const double cv = cbrt(V);
+  const double kappa = c_hg * rho * cs * cv * cv;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    P3 f = hg_pattern(0, a) * q[0] + hg_pattern(1, a) * q[1] + hg_pattern(2, a) * q[2] + hg_pattern(3, a) * q[3];
+    f = f - iv * (G[a].x * W[0] + G[a].y * W[1] + G[a].z * W[2]);
+    fh[(3ll * a + 0) * nc + c] = (R)(-kappa * f.x);
+    fh[(3ll * a + 1) * nc + c] = (R)(-kappa * f.y);
+    fh[(3ll * a + 2) * nc + c] = (R)(-kappa * f.z);
+  }
+}
+
+template <typename R>
+__device__ __forceinline__ P3 hourglass_corner(const R *fh, long long nc, long long c, int a) {
+  return {(double)fh[(3ll * a + 0) * nc + c], (double)fh[(3ll * a + 1) * nc + c], (double)fh[(3ll * a + 2) * nc + c]};
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

@@ -74,6 +74,9 @@ enum KernelId : int {
   kPcPredict,    //   half-step energy, EoS, viscosity: sigma^{n+1/2}
   kAlePredict,   // predictor-corrector, FP64 Eulerian path
   kMixPredict,   // predictor-corrector, FP32-mixed path
+  kHourglass,    // hourglass corner forces: general path
+  kAleHourglass, //   FP64 Eulerian path
+  kMixHourglass, //   FP32-mixed path
   kNumKernels
 };
 
@@ -132,11 +135,25 @@ struct Fields {
   int remap_order;             // cell remap: 1 donor cell, 2 van Leer piecewise linear
   int time_order;              // Lagrangian step: 1 single stage, 2 predictor-corrector
   R *Gh;                       // predictor-corrector: corner gradients at x^{n+1/2}, Gh[(3 a + axis) nc + c]
+  R *fh;                       // hourglass corner forces of the step, fh[(3 a + axis) nc + c]; null: no control
+  double c_hg;                 // hourglass coefficient
+  float c_hg32;
   R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
   R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
   int remap_sets_x;            // node remap writes the reference positions to x
   int reflect[6];
 };
+
+// Hourglass patterns of the hex (local node a = di + 2 dj + 4 dk, signs
+// s = 2 d - 1): s_x s_y, s_y s_z, s_z s_x, s_x s_y s_z.
+__host__ __device__ constexpr float hg_pattern(int alpha, int a) {
+  return (alpha == 0   ? (((a & 1) != 0) == ((a & 2) != 0))
+          : alpha == 1 ? (((a & 2) != 0) == ((a & 4) != 0))
+          : alpha == 2 ? (((a & 4) != 0) == ((a & 1) != 0))
+                       : ((((a & 1) != 0) + ((a & 2) != 0) + ((a & 4) != 0)) % 2 == 1))
+             ? 1.f
+             : -1.f;
+}
 
 // Thread-tile shapes of the FP32-mixed kernels (x by y threads over one k
 // plane); the autotuner picks one per state or batch.

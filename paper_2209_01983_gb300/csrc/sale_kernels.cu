@@ -152,8 +152,27 @@ __device__ __forceinline__ void add_corner_force(const Fields<R> &F, const R *gx
   load_hex(gx, gy, gz, F.nx, F.ny, ci, cj, ck, X);
   shift0(X);
   const P3 g = hex_corner_grad_shifted<7 - S8>(X);
-  const double sig = (double)F.sig[cell_index(F.nx, F.ny, ci, cj, ck)];
-  f = f + sig * g;
+  const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
+  const double sig = (double)F.sig[c];
+  P3 cf = sig * g;
+  if (F.fh) cf = cf + hourglass_corner(F.fh, F.nc, c, 7 - S8);
+  f = f + cf;
+}
+
+// Hourglass corner forces of every cell from x^n, u^n and the state at n
+// (c_hg > 0), held for the node and cell passes of the step.
+template <typename R>
+__global__ void __launch_bounds__(kBlock) k_hourglass(Fields<R> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 X[8], U[8], G[8];
+  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
+  shift0(X);
+  hex_grad_shifted(X, G);
+  hourglass_store(X, G, U, (double)F.vol[c], (double)F.rho[c], (double)F.cs[c], F.c_hg, F.fh, F.nc, c);
 }
 
 // Predictor-corrector (time_order 2) half step: x^{n+1/2} = x^n + dt/2 u^n
@@ -187,7 +206,13 @@ __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalar
 #pragma unroll
   for (int a = 0; a < 8; ++a) work += dot(G[a], U[a]);
   const double m = (double)F.m[c];
-  const double e = (double)F.e[c] - 0.5 * h / m * (double)F.sig[c] * work;
+  double e = (double)F.e[c] - 0.5 * h / m * (double)F.sig[c] * work;
+  if (F.fh) {
+    double work_hg = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), U[a]);
+    e -= 0.5 * h / m * work_hg;
+  }
   load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
   const double V = hex_volume_shifted(X);
@@ -273,7 +298,13 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
 #pragma unroll
   for (int a = 0; a < 8; ++a) work += dot(G[a], UB[a]);
   const double m = (double)F.m[c];
-  const double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
+  double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
+  if (F.fh) {
+    double work_hg = 0.0;
+#pragma unroll
+    for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), UB[a]);
+    e1 -= h / m * work_hg;
+  }
   if (pc) load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   else load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
@@ -550,7 +581,7 @@ template <typename R>
 void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t st) {
   if ((kid >= kAleNodes && kid <= kAleRemapEos) || kid == kAleEdges || kid == kAleRemapNodes || kid == kAleEos ||
-      kid == kAleSlopes || kid == kAlePredict) {
+      kid == kAleSlopes || kid == kAlePredict || kid == kAleHourglass) {
     if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
     return;
   }
@@ -560,6 +591,7 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
     case kLagNodes: k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kLagCells: k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kPcPositions: k_pc_positions<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kHourglass: k_hourglass<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
     case kPcPredict: k_pc_predict<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kRemapFaces: k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
     case kRemapNodes: k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S); break;

@@ -41,7 +41,7 @@ class sale_problem_desc(C.Structure):
                 ("p_blast", C.c_double), ("e_deposit", C.c_double),
                 ("cfl", C.c_double), ("c_q", C.c_double), ("c_l", C.c_double),
                 ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int),
-                ("remap_order", C.c_int), ("time_order", C.c_int)]
+                ("remap_order", C.c_int), ("time_order", C.c_int), ("c_hg", C.c_double)]
 
 
 class sale_diag(C.Structure):
