@@ -142,7 +142,8 @@ void sale_mesh_destroy(sale_mesh *mesh);
 int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n);
 
 /* Device bytes a state of this mesh and precision needs with the default
- * scheme options (0 on bad args). */
+ * scheme options (0 on bad args, and for FP32-mixed meshes of more than
+ * 2^31 - 1 nodes, which its 32-bit indexing does not reach). */
 size_t sale_state_bytes(const sale_mesh *mesh, int precision);
 /* Device bytes for this mesh, problem and precision: includes the scratch
  * of the second-order remap (FP64), of the predictor-corrector step

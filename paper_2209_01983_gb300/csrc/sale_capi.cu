@@ -421,13 +421,19 @@ static size_t state_bytes(long long nc, long long nn, int precision, bool jit, b
   return carve(&tmp, nullptr);
 }
 
+// The FP32-mixed kernels index cells and nodes with 32-bit integers.
+static bool mixed_fits(const sale_mesh *mesh, int precision) {
+  return precision != SALE_FP32_MIXED || mesh->nn <= 0x7FFFFFFFll;
+}
+
 extern "C" size_t sale_state_bytes(const sale_mesh *mesh, int precision) {
-  if (!mesh || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
+  if (!mesh || (precision != SALE_FP64 && precision != SALE_FP32_MIXED) || !mixed_fits(mesh, precision)) return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0);
 }
 
 extern "C" size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision) {
-  if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED)) return 0;
+  if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED) || !mixed_fits(mesh, precision))
+    return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0, prob->remap_order == 2,
                      prob->time_order == 2, prob->c_hg > 0.0);
 }
@@ -598,6 +604,8 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
+  if (!mixed_fits(mesh, precision))
+    return fail(SALE_EINVAL, "sale_state_init: FP32-mixed states index nodes in 32 bits (at most 2^31 - 1 nodes)");
   rc = check_device_buffer("sale_state_init", device_buf, bytes, sale_state_bytes_for(mesh, prob, precision));
   if (rc) return rc;
   return state_init_at(mesh, prob, precision, device_buf, cuda_stream, out);
@@ -1160,8 +1168,10 @@ static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, s
 
 extern "C" size_t sale_batch_bytes(int n, const sale_mesh_desc *meshes, int precision) {
   if (n < 1 || !meshes || precision != SALE_FP32_MIXED) return 0;
-  for (int i = 0; i < n; ++i)
+  for (int i = 0; i < n; ++i) {
     if (meshes[i].nx < 1 || meshes[i].ny < 1 || meshes[i].nz < 1) return 0;
+    if ((long long)(meshes[i].nx + 1) * (meshes[i].ny + 1) * (meshes[i].nz + 1) > 0x7FFFFFFFll) return 0;
+  }
   size_t parts[4];
   return batch_layout(n, meshes, precision, nullptr, parts);
 }
