@@ -41,15 +41,15 @@ FP64 = {
 # per cell that uses them.
 QUAD = 29  # fan term of one quad: 4-point sum 9, diagonals 6, cross 9, dot 5
 EDGES = 3 * QUAD + 9 + 3 + 18 + 9 + 6 * 7  # 3 side quads, relative positions, L, shifts
-SWEPT3 = 3 * QUAD + 18 + 21 + 3 + 12 + 3  # Lagrangian faces + assembly of 9 side terms
+
 FP64_ALE = {
     # sigma, G (24/cell), u, mn read; u, ubar, 0.5|u|^2 written
     "ale_nodes": ("node", 8 * (1 + 24 + 3 + 1 + 3 + 3 + 1), 48 + 20 + 5),
-    # x_ref, ubar read; 9 side-quad terms written
-    "ale_edges": ("node", 8 * (3 + 3 + 9), EDGES),
-    # G, ubar, m, e, sigma, x_ref, 3 reference-face terms, 9 side terms read;
-    # e, 3 swept volumes written
-    "ale_cells": ("cell", 8 * (24 + 3 + 3 + 3 + 3 + 9 + 1 + 3), 48 + 5 + SWEPT3),
+    # x_ref, ubar, 3 reference-face terms read; 9 side-quad terms and 3
+    # Lagrangian + reference low-face terms written
+    "ale_edges": ("node", 8 * (3 + 3 + 3 + 12), EDGES + 3 * QUAD + 27 + 3),
+    # G, ubar, m, e, sigma, 12 swept-hex terms read; e, 3 swept volumes written
+    "ale_cells": ("cell", 8 * (24 + 3 + 3 + 12 + 1 + 3), 48 + 5 + 12 + 3),
     # 3 swept volumes, V_E, m read; V_L, rho_L written
     "ale_density": ("cell", 8 * (3 + 2 + 2), 8),
     # 3 swept volumes, rho_L, e read; 3 mass + 3 energy fluxes + 3 dual-flux parts written

@@ -15,7 +15,8 @@
 //                    0.5 |u|^2 for the node remap
 //   k_ale_edges      side quads of the swept hexes, one per mesh edge (each
 //                    is shared by three cells' swept hexes), with the origin
-//                    shifts those cells need
+//                    shifts those cells need, and each cell's Lagrangian
+//                    low-face terms
 //   k_ale_cells      compatible energy e_L = e - dt/m (p+q) sum_a G(a).ubar_a;
 //                    swept volumes of the three low faces between the
 //                    Lagrangian face (x_ref + dt ubar) and the reference face
@@ -119,15 +120,11 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
 // same term for origin n - e_Q of each other axis Q (the node 0 of the other
 // cells whose low faces hold the edge): T(o) = T(n) + 4 (x_n - x_o) . A, A
 // the quad's diagonal cross product.  ste[(3 AX + v) nn + n], v = 0 for
-// origin n, v = 1, 2 for the other two axes in increasing order.
+// origin n, v = 1, 2 for the other two axes in increasing order.  Eb, Lb:
+// reference and Lagrangian position of b relative to x_n.
 template <int AX>
 __device__ __forceinline__ void edge_side_terms(const Fields<double> &F, long long n, const int (&ijk)[3],
-                                                const int (&nmax)[3], const long long (&stride)[3], P3 xa, P3 La,
-                                                double h) {
-  if (ijk[AX] == nmax[AX]) return;  // no edge along AX from this node
-  const long long b = n + stride[AX];
-  const P3 Eb = P3{F.xr[b], F.yr[b], F.zr[b]} - xa;
-  const P3 Lb = Eb + h * P3{F.ub[b], F.vb[b], F.wb[b]};
+                                                const long long (&stride)[3], P3 xa, P3 La, P3 Eb, P3 Lb) {
   const P3 A = cross(Eb - La, Lb);  // diagonals (E_b - L_a) and (L_b - E_a), E_a = 0
   const double T = 2.0 * dot(La, A);  // 2 (L_a + E_a) . A
   F.ste[(3 * AX) * F.nn + n] = T;
@@ -142,6 +139,11 @@ __device__ __forceinline__ void edge_side_terms(const Fields<double> &F, long lo
   }
 }
 
+// Per node n: the side quads of the three mesh edges leaving it and, when n
+// is node 0 of a cell, that cell's three low Lagrangian face terms plus their
+// reference-face terms (ste[(9 + axis) nn + n]), all with n as origin.  The
+// faces use n's +x, +y, +z neighbours (shared with the edges) and three
+// diagonal neighbours.
 __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScalars *S, double dt_override) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= F.nn || !cycle_active(S)) return;
@@ -152,9 +154,24 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   const long long stride[3] = {1, F.nx + 1, (long long)(F.nx + 1) * (F.ny + 1)};
   const P3 xa = {F.xr[n], F.yr[n], F.zr[n]};
   const P3 La = h * P3{F.ub[n], F.vb[n], F.wb[n]};
-  edge_side_terms<0>(F, n, ijk, nmax, stride, xa, La, h);
-  edge_side_terms<1>(F, n, ijk, nmax, stride, xa, La, h);
-  edge_side_terms<2>(F, n, ijk, nmax, stride, xa, La, h);
+  auto rel = [&](long long b, P3 &E) {  // reference and Lagrangian position of node b relative to x_n
+    E = P3{F.xr[b], F.yr[b], F.zr[b]} - xa;
+    return E + h * P3{F.ub[b], F.vb[b], F.wb[b]};
+  };
+  P3 Lb[3], Eb;
+  if (i < F.nx) { Lb[0] = rel(n + stride[0], Eb); edge_side_terms<0>(F, n, ijk, stride, xa, La, Eb, Lb[0]); }
+  if (j < F.ny) { Lb[1] = rel(n + stride[1], Eb); edge_side_terms<1>(F, n, ijk, stride, xa, La, Eb, Lb[1]); }
+  if (k < F.nz) { Lb[2] = rel(n + stride[2], Eb); edge_side_terms<2>(F, n, ijk, stride, xa, La, Eb, Lb[2]); }
+  if (i < F.nx && j < F.ny && k < F.nz) {
+    const P3 Lyz = rel(n + stride[1] + stride[2], Eb), Lxz = rel(n + stride[0] + stride[2], Eb),
+             Lxy = rel(n + stride[0] + stride[1], Eb);
+    const long long c = cell_index(F.nx, F.ny, i, j, k);
+    const long long nn = F.nn;
+    (void)nmax;
+    F.ste[9 * nn + n] = quad_term(La, Lb[2], Lyz, Lb[1]) + F.TE[c];
+    F.ste[10 * nn + n] = quad_term(La, Lb[0], Lxz, Lb[2]) + F.TE[F.nc + c];
+    F.ste[11 * nn + n] = quad_term(La, Lb[1], Lxy, Lb[0]) + F.TE[2 * F.nc + c];
+  }
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
@@ -184,23 +201,18 @@ __global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScala
     e1 -= h / m * work_hg;
   }
   F.e[c] = e1;
-  // swept volumes of the three low faces: the Lagrangian face terms here
-  // (nodes relative to reference node 0), the reference faces from the
-  // cache, the side quads from k_ale_edges (a side quad traversed the other
-  // way round changes sign)
-  P3 Lr[7];
-  const P3 o = {F.xr[nid[0]], F.yr[nid[0]], F.zr[nid[0]]};
-  Lr[0] = h * ub[0];
-#pragma unroll
-  for (int a = 1; a < 7; ++a) Lr[a] = (P3{F.xr[nid[a]], F.yr[nid[a]], F.zr[nid[a]]} - o) + h * ub[a];
+  // swept volumes of the three low faces, assembled from k_ale_edges: the
+  // Lagrangian face plus reference face terms and the side quads (a side
+  // quad traversed the other way round changes sign), all with the cell's
+  // reference node 0 as origin
   const long long nn = F.nn, n0 = nid[0], n1 = nid[1], n2 = nid[2], n4 = nid[4];
   const double *ste = F.ste;
   const double cx0 = ste[n0], cxy = ste[nn + n2], cxz = ste[2 * nn + n4];
   const double cy0 = ste[3 * nn + n0], cyx = ste[4 * nn + n1], cyz = ste[5 * nn + n4];
   const double cz0 = ste[6 * nn + n0], czx = ste[7 * nn + n1], czy = ste[8 * nn + n2];
-  const double sx = quad_term(Lr[0], Lr[4], Lr[6], Lr[2]) + F.TE[c] + cz0 - czy - cy0 + cyz;
-  const double sy = quad_term(Lr[0], Lr[1], Lr[5], Lr[4]) + F.TE[F.nc + c] - cz0 + czx + cx0 - cxz;
-  const double sz = quad_term(Lr[0], Lr[2], Lr[3], Lr[1]) + F.TE[2 * F.nc + c] + cy0 - cyx - cx0 + cxy;
+  const double sx = ste[9 * nn + n0] + cz0 - czy - cy0 + cyz;
+  const double sy = ste[10 * nn + n0] - cz0 + czx + cx0 - cxz;
+  const double sz = ste[11 * nn + n0] + cy0 - cyx - cx0 + cxy;
   F.dvx[c] = i > 0 ? sx * kInvSixth24 : 0.0;
   F.dvy[c] = j > 0 ? sy * kInvSixth24 : 0.0;
   F.dvz[c] = k > 0 ? sz * kInvSixth24 : 0.0;

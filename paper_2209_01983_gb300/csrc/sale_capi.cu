@@ -295,7 +295,7 @@ static size_t carve(sale_state *st, char *base) {
       st->geoIVE = st->geoTE + 3 * nc;
       st->geoIL2 = st->geoIVE + nc;
     }
-    st->ste = (double *)cv.take(sizeof(double) * 9 * nn);
+    st->ste = (double *)cv.take(sizeof(double) * 12 * nn);
     for (int d = 0; d < 3; ++d) st->mq[d] = (double *)cv.take(sizeof(double) * nc);
     st->kd = (double *)cv.take(sizeof(double) * nn);
     if (st->o2)

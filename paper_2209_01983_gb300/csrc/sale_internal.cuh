@@ -112,7 +112,9 @@ struct Fields {
   R *dvx, *dvy, *dvz;          // swept volumes of the low x/y/z faces
   // FP64 Eulerian path: 1 / V_E and 1 / (cfl L_E)^2 of the reference mesh,
   // the side-quad terms of the swept hexes along every mesh edge (nine node
-  // arrays, ste[slot * nn + n], slot = 3 * axis + origin variant), each
+  // arrays, ste[slot * nn + n], slot = 3 * axis + origin variant) and the
+  // Lagrangian + reference low-face terms of the cell whose node 0 is n
+  // (slots 9, 10, 11 for x, y, z), each
   // cell's dual-mesh flux part (mu_low + mu_high) / 8 along x/y/z, and the
   // node kinetic energy per unit mass 0.5 |u|^2 after the Lagrangian step.
   const R *iVE, *iL2;
