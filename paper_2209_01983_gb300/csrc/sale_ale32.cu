@@ -370,7 +370,9 @@ __device__ __forceinline__ void node_faces2(const Fields<float> &F, int n, int s
 // The single-mesh kernels and the batched kernels wrap the same bodies, so
 // a mesh advanced inside a batch is bitwise equal to the mesh alone.
 
-template <bool JIT, bool IN>
+// OPT: the state may use the predictor-corrector step or hourglass control
+// (their branches are compiled out otherwise, as for every batch).
+template <bool JIT, bool IN, bool OPT>
 __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
   if ((!IN && (i > F.nx || j > F.ny || k > F.nz)) || !S->next_active) return;
   const float h = S->next_h32;
@@ -389,13 +391,15 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   }
   F3 f = {0.f, 0.f, 0.f};
   float hm;
-  if (JIT || F.time_order == 2) {
+  const bool pc = OPT && F.time_order == 2;
+  const float *fh = OPT ? F.fh : nullptr;
+  if (JIT || pc) {
     // Cached corner gradients (of the reference mesh, or of x^{n+1/2} for
     // the predictor-corrector): F_a = sum_c (sigma_c - sigma_ref) G_c(a).  The
     // dropped sigma_ref sum_c G_c(a) is zero at interior nodes and normal to
     // the (reflecting) walls at boundary nodes, where the wall condition
     // removes it; the differences keep F exactly 0 where sigma is uniform.
-    const float *Gsrc = F.time_order == 2 ? F.Gh : F.Gc;
+    const float *Gsrc = pc ? F.Gh : F.Gc;
     float ref = 0.f;
     bool have = false;
 #pragma unroll
@@ -419,7 +423,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
       f.x += ds * __ldg(g);
       f.y += ds * __ldg(g + nc);
       f.z += ds * __ldg(g + 2 * nc);
-      if (F.fh) f = f + hg_corner_f(F.fh, nc, c, 7 - q);
+      if (fh) f = f + hg_corner_f(fh, nc, c, 7 - q);
     }
     hm = h / F.mn[n];
   } else {
@@ -431,12 +435,12 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
     node_faces2<JIT, 4>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
     node_faces2<JIT, 5>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
     node_faces2<JIT, 6>(F, n, sy, sz, oa, lo_ok, hi_ok, sig, f);
-    if (F.fh) {  // hourglass corner forces, on the face terms' scale of 24
+    if (fh) {  // hourglass corner forces, on the face terms' scale of 24
 #pragma unroll
       for (int q = 0; q < 8; ++q) {
         const bool ok = ((q & 1) ? hi_ok[0] : lo_ok[0]) && ((q & 2) ? hi_ok[1] : lo_ok[1]) &&
                         ((q & 4) ? hi_ok[2] : lo_ok[2]);
-        if (ok) f = f + 24.f * hg_corner_f(F.fh, F.nc, c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz, 7 - q);
+        if (ok) f = f + 24.f * hg_corner_f(fh, F.nc, c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz, 7 - q);
       }
     }
     hm = h / (24.f * F.mn[n]);
@@ -452,7 +456,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
   F.wb[n] = 0.5f * (w0 + w1);
 }
 
-template <bool JIT, bool IN>
+template <bool JIT, bool IN, bool OPT>
 __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
   if ((!IN && (i >= F.nx || j >= F.ny || k >= F.nz)) || !S->next_active) return;
   const float h = S->next_h32;
@@ -466,13 +470,13 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
     const int na = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
     ub[a] = {F.ub[na], F.vb[na], F.wb[na]};
   }
-  const float work = F.time_order == 2 ? grad_dot_cached(F.Gh, F.nc, c, ub)
+  const float work = (OPT && F.time_order == 2) ? grad_dot_cached(F.Gh, F.nc, c, ub)
                      : JIT              ? grad_dot_cached(F.Gc, F.nc, c, ub)
                                         : grad_dot_f(E, ub);
   // compatible energy update; the increment is FP32, the accumulation
   // float-float
   float de = h * F.sig[c] * work / F.m[c];
-  if (F.fh) {
+  if (OPT && F.fh) {
     float work_hg = 0.f;
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dotf(hg_corner_f(F.fh, F.nc, c, a), ub[a]);
@@ -870,12 +874,12 @@ __device__ __forceinline__ void m_eos_body(const Fields<float> &F, DevScalars *S
 // (cells and nodes alike), so every neighbour a body reads exists, no node
 // is on a wall and every node is shared by eight cells: the bodies drop
 // those tests, with bitwise the same results.
-template <bool JIT, bool IN>
+template <bool JIT, bool IN, bool OPT>
 __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevScalars *S, int i, int j, int k,
                                          unsigned nblk, int mode) {
   switch (kid) {
-    case kMixNodes: m_nodes_body<JIT, IN>(F, S, i, j, k); break;
-    case kMixCells: m_cells_body<JIT, IN>(F, S, i, j, k); break;
+    case kMixNodes: m_nodes_body<JIT, IN, OPT>(F, S, i, j, k); break;
+    case kMixCells: m_cells_body<JIT, IN, OPT>(F, S, i, j, k); break;
     case kMixFluxes: m_fluxes_body<IN>(F, S, i, j, k); break;
     case kMixRemapNodes: m_remap_nodes_body<IN>(F, S, i, j, k); break;
     case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
@@ -894,12 +898,12 @@ __device__ __forceinline__ bool tile_interior(const Fields<float> &F, int bx, in
          k <= F.nz - 2;
 }
 
-template <int KID, bool JIT, int SH>
+template <int KID, bool JIT, int SH, bool OPT>
 __device__ __forceinline__ void run_tile(const Fields<float> &F, DevScalars *S, int bx, int by, int k, unsigned nblk,
                                          int mode) {
   const int i = bx * tile_x(SH) + threadIdx.x, j = by * tile_y(SH) + threadIdx.y;
-  if (KID != kMixEos && tile_interior<SH>(F, bx, by, k)) run_body<JIT, true>(KID, F, S, i, j, k, nblk, mode);
-  else run_body<JIT, false>(KID, F, S, i, j, k, nblk, mode);
+  if (KID != kMixEos && tile_interior<SH>(F, bx, by, k)) run_body<JIT, true, OPT>(KID, F, S, i, j, k, nblk, mode);
+  else run_body<JIT, false, OPT>(KID, F, S, i, j, k, nblk, mode);
 }
 
 // Blocks per SM the register budget is held to, per kernel and block size:
@@ -912,15 +916,16 @@ __host__ __device__ constexpr int min_blocks(int kid, int threads) {
                                                                                                  : 1;
 }
 
-template <int KID, bool JIT, int SH>
+template <int KID, bool JIT, int SH, bool OPT>
 __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
     k_m(Fields<float> F, DevScalars *S, int mode) {
   const unsigned nblk = gridDim.x * gridDim.y * gridDim.z;
-  run_tile<KID, JIT, SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z, nblk, mode);
+  run_tile<KID, JIT, SH, OPT>(F, S, blockIdx.x, blockIdx.y, blockIdx.z, nblk, mode);
 }
 
 // Batched: block b works on mesh tab[b].x, tile (tab[b].y, tab[b].z) of
-// plane tab[b].w; the mesh's descriptor is staged in shared memory.
+// plane tab[b].w; the part of the mesh's descriptor these kernels read is
+// staged in shared memory.
 template <int KID, int SH>
 __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
     kb_m(const BatchItem *items, const int4 *tab) {
@@ -929,10 +934,11 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   const int tid = threadIdx.x + tile_x(SH) * threadIdx.y;
   const int *src = reinterpret_cast<const int *>(items + t.x);
   int *dst = reinterpret_cast<int *>(&it);
-  for (int w = tid; w < (int)(sizeof(BatchItem) / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
+  for (int w = tid; w < (int)(kBatchItemStaged / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
   __syncthreads();
-  if (it.F.off4) run_tile<KID, true, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
-  else run_tile<KID, false, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
+  // batches take neither the predictor-corrector step nor hourglass control
+  if (it.F.off4) run_tile<KID, true, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
+  else run_tile<KID, false, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
 }
 
 // Per mesh of a batch: t_end = inf, cycle_limit = cycle + cycles, decide.
@@ -970,8 +976,15 @@ static void launch_shaped(const Fields<float> &F, DevScalars *S, int mode, cudaS
   const bool node = KID == kMixNodes || KID == kMixRemapNodes;
   const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1, SH) : tile_grid(F.nx, F.ny, F.nz, SH);
   const dim3 b(tile_x(SH), tile_y(SH));
-  if (F.off4) k_m<KID, true, SH><<<g, b, 0, st>>>(F, S, mode);
-  else k_m<KID, false, SH><<<g, b, 0, st>>>(F, S, mode);
+  if constexpr (KID == kMixNodes || KID == kMixCells) {
+    if (F.time_order == 2 || F.fh) {
+      if (F.off4) k_m<KID, true, SH, true><<<g, b, 0, st>>>(F, S, mode);
+      else k_m<KID, false, SH, true><<<g, b, 0, st>>>(F, S, mode);
+      return;
+    }
+  }
+  if (F.off4) k_m<KID, true, SH, false><<<g, b, 0, st>>>(F, S, mode);
+  else k_m<KID, false, SH, false><<<g, b, 0, st>>>(F, S, mode);
 }
 
 template <int KID>

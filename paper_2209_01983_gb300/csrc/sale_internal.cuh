@@ -14,6 +14,7 @@
 // to limit cancellation.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 
 #include "sale.h"
@@ -90,11 +91,10 @@ enum DtMode : int {
 // Device pointers and constants of one state (passed by value).
 template <typename R>
 struct Fields {
+  // --- read by the FP32-mixed kernels (a batch stages this prefix, up to
+  // xr, in shared memory) ---
   int nx, ny, nz;
   long long nc, nn;
-  const double *xr, *yr, *zr;  // reference mesh (Eulerian rezone target)
-  R *x, *y, *z;                // current node positions
-  R *xn, *yn, *zn;             // next node positions (written by the step)
   R *u, *v, *w;                // node velocity
   R *ub, *vb, *wb;             // time-centred / remapped node velocity
   R *mn;                       // node mass
@@ -105,22 +105,8 @@ struct Fields {
   R *rho, *p, *q, *cs, *vol;   // derived cell fields
   R *mux, *muy, *muz;          // mass flux through the low x/y/z face
   R *epx, *epy, *epz;          // internal-energy flux through those faces
-  // Cached reference-mesh geometry (ALE path): dV/dx of every cell corner,
-  // G[(corner*3 + axis) * nc + c], reference volume and length scale.
-  const R *G, *VE, *LE;
-  const R *TE;                 // reference-face terms of the low-face swept hexes (3 per cell)
+  const R *VE, *LE;            // reference volume and length scale
   R *dvx, *dvy, *dvz;          // swept volumes of the low x/y/z faces
-  // FP64 Eulerian path: 1 / V_E and 1 / (cfl L_E)^2 of the reference mesh,
-  // the side-quad terms of the swept hexes along every mesh edge (nine node
-  // arrays, ste[slot * nn + n], slot = 3 * axis + origin variant) and the
-  // Lagrangian + reference low-face terms of the cell whose node 0 is n
-  // (slots 9, 10, 11 for x, y, z), each
-  // cell's dual-mesh flux part (mu_low + mu_high) / 8 along x/y/z, and the
-  // node kinetic energy per unit mass 0.5 |u|^2 after the Lagrangian step.
-  const R *iVE, *iL2;
-  R *ste;
-  R *mqx, *mqy, *mqz;
-  R *kd;
   // Structured reference mesh of the FP32-mixed path: node (i,j,k) sits at
   // lo + (i,j,k) * h + off[node]; coordinate differences are formed as
   // index difference * h + offset difference (no absolute coordinates).
@@ -131,19 +117,37 @@ struct Fields {
   // and across a row of nodes); null on unjittered meshes, where the
   // gradient folds to constants.
   const float *Gc;
-  double gamma, cfl, c_q, c_l, growth, dt_init;
-  float gamma32, cfl32, c_q32, c_l32;  // the same constants as FP32
+  R *Gh;                       // predictor-corrector: corner gradients at x^{n+1/2}, Gh[(3 a + axis) nc + c]
+  R *fh;                       // hourglass corner forces of the step, fh[(3 a + axis) nc + c]; null: no control
+  double gamma, growth, dt_init;
+  float gamma32, cfl32, c_q32, c_l32, c_hg32;  // FP32 copies of the constants
   int ke_fix;
   int remap_order;             // cell remap: 1 donor cell, 2 van Leer piecewise linear
   int time_order;              // Lagrangian step: 1 single stage, 2 predictor-corrector
-  R *Gh;                       // predictor-corrector: corner gradients at x^{n+1/2}, Gh[(3 a + axis) nc + c]
-  R *fh;                       // hourglass corner forces of the step, fh[(3 a + axis) nc + c]; null: no control
-  double c_hg;                 // hourglass coefficient
-  float c_hg32;
+  int reflect[6];
+  // --- FP64 paths only ---
+  const double *xr, *yr, *zr;  // reference mesh (Eulerian rezone target)
+  R *x, *y, *z;                // current node positions
+  R *xn, *yn, *zn;             // next node positions (written by the step)
+  // Cached reference-mesh geometry (ALE path): dV/dx of every cell corner,
+  // G[(corner*3 + axis) * nc + c].
+  const R *G;
+  const R *TE;                 // reference-face terms of the low-face swept hexes (3 per cell)
+  // FP64 Eulerian path: 1 / V_E and 1 / (cfl L_E)^2 of the reference mesh,
+  // the side-quad terms of the swept hexes along every mesh edge (nine node
+  // arrays, ste[slot * nn + n], slot = 3 * axis + origin variant) and the
+  // Lagrangian + reference low-face terms of the cell whose node 0 is n
+  // (slots 9, 10, 11 for x, y, z), each cell's dual-mesh flux part
+  // (mu_low + mu_high) / 8 along x/y/z, and the node kinetic energy per
+  // unit mass 0.5 |u|^2 after the Lagrangian step.
+  const R *iVE, *iL2;
+  R *ste;
+  R *mqx, *mqy, *mqz;
+  R *kd;
+  double cfl, c_q, c_l, c_hg;
   R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
   R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
   int remap_sets_x;            // node remap writes the reference positions to x
-  int reflect[6];
 };
 
 // Hourglass patterns of the hex (local node a = di + 2 dj + 4 dk, signs
@@ -166,11 +170,15 @@ constexpr int kMaxWarpsPerBlock = 16;
 
 // One mesh of a batch, as seen by the batched kernels.
 struct BatchItem {
-  Fields<float> F;
   DevScalars *S;
   unsigned nblk_cell;  // blocks of this mesh in a cell kernel
   unsigned pad;
+  Fields<float> F;
 };
+
+// Bytes of a BatchItem the FP32-mixed kernels read: its header and the
+// mixed prefix of F (everything before the FP64-only xr).
+constexpr size_t kBatchItemStaged = offsetof(BatchItem, F) + offsetof(Fields<float>, xr);
 
 // Per-mesh summary the host reads after a batched run.
 struct BatchStatus {
