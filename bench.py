@@ -363,7 +363,8 @@ def e2e_rate(args, res, world):
         sale.check(sale.sale_run_to_time(st._h, math.inf, 1, 1, None))
         sale.check(sale.sale_diagnostics(st._h, sale.C.byref(dd)))
 
-    step()  # untimed: captures the one-cycle graph
+    step()  # untimed: capture the one-cycle graphs (one per velocity-buffer role)
+    step()
     torch.cuda.synchronize()
     times = []
     t0 = time.perf_counter()

@@ -124,19 +124,13 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
 // reference and Lagrangian position of b relative to x_n.
 template <int AX>
 __device__ __forceinline__ void edge_side_terms(const Fields<double> &F, long long n, const int (&ijk)[3],
-                                                const long long (&stride)[3], P3 xa, P3 La, P3 Eb, P3 Lb) {
+                                                const P3 (&back)[3], P3 La, P3 Eb, P3 Lb) {
   const P3 A = cross(Eb - La, Lb);  // diagonals (E_b - L_a) and (L_b - E_a), E_a = 0
   const double T = 2.0 * dot(La, A);  // 2 (L_a + E_a) . A
   F.ste[(3 * AX) * F.nn + n] = T;
   constexpr int Q1 = AX == 0 ? 1 : 0, Q2 = AX == 2 ? 1 : 2;
-  if (ijk[Q1] > 0) {
-    const long long o = n - stride[Q1];
-    F.ste[(3 * AX + 1) * F.nn + n] = T + 4.0 * dot(xa - P3{F.xr[o], F.yr[o], F.zr[o]}, A);
-  }
-  if (ijk[Q2] > 0) {
-    const long long o = n - stride[Q2];
-    F.ste[(3 * AX + 2) * F.nn + n] = T + 4.0 * dot(xa - P3{F.xr[o], F.yr[o], F.zr[o]}, A);
-  }
+  if (ijk[Q1] > 0) F.ste[(3 * AX + 1) * F.nn + n] = T + 4.0 * dot(back[Q1], A);
+  if (ijk[Q2] > 0) F.ste[(3 * AX + 2) * F.nn + n] = T + 4.0 * dot(back[Q2], A);
 }
 
 // Per node n: the side quads of the three mesh edges leaving it and, when n
@@ -150,7 +144,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   const double h = step_dt(S, dt_override);
   int i, j, k;
   node_ijk(n, F.nx, F.ny, i, j, k);
-  const int ijk[3] = {i, j, k}, nmax[3] = {F.nx, F.ny, F.nz};
+  const int ijk[3] = {i, j, k};
   const long long stride[3] = {1, F.nx + 1, (long long)(F.nx + 1) * (F.ny + 1)};
   const P3 xa = {F.xr[n], F.yr[n], F.zr[n]};
   const P3 La = h * P3{F.ub[n], F.vb[n], F.wb[n]};
@@ -158,16 +152,26 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
     E = P3{F.xr[b], F.yr[b], F.zr[b]} - xa;
     return E + h * P3{F.ub[b], F.vb[b], F.wb[b]};
   };
+  // x_n minus its -x, -y, -z neighbours: the origin shifts of the side quads
+  P3 back[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    if (ijk[a] > 0) {
+      const long long o = n - stride[a];
+      back[a] = xa - P3{F.xr[o], F.yr[o], F.zr[o]};
+    } else {
+      back[a] = {0.0, 0.0, 0.0};
+    }
+  }
   P3 Lb[3], Eb;
-  if (i < F.nx) { Lb[0] = rel(n + stride[0], Eb); edge_side_terms<0>(F, n, ijk, stride, xa, La, Eb, Lb[0]); }
-  if (j < F.ny) { Lb[1] = rel(n + stride[1], Eb); edge_side_terms<1>(F, n, ijk, stride, xa, La, Eb, Lb[1]); }
-  if (k < F.nz) { Lb[2] = rel(n + stride[2], Eb); edge_side_terms<2>(F, n, ijk, stride, xa, La, Eb, Lb[2]); }
+  if (i < F.nx) { Lb[0] = rel(n + stride[0], Eb); edge_side_terms<0>(F, n, ijk, back, La, Eb, Lb[0]); }
+  if (j < F.ny) { Lb[1] = rel(n + stride[1], Eb); edge_side_terms<1>(F, n, ijk, back, La, Eb, Lb[1]); }
+  if (k < F.nz) { Lb[2] = rel(n + stride[2], Eb); edge_side_terms<2>(F, n, ijk, back, La, Eb, Lb[2]); }
   if (i < F.nx && j < F.ny && k < F.nz) {
     const P3 Lyz = rel(n + stride[1] + stride[2], Eb), Lxz = rel(n + stride[0] + stride[2], Eb),
              Lxy = rel(n + stride[0] + stride[1], Eb);
     const long long c = cell_index(F.nx, F.ny, i, j, k);
     const long long nn = F.nn;
-    (void)nmax;
     F.ste[9 * nn + n] = quad_term(La, Lb[2], Lyz, Lb[1]) + F.TE[c];
     F.ste[10 * nn + n] = quad_term(La, Lb[0], Lxz, Lb[2]) + F.TE[F.nc + c];
     F.ste[11 * nn + n] = quad_term(La, Lb[1], Lxy, Lb[0]) + F.TE[2 * F.nc + c];
