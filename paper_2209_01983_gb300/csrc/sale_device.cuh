@@ -177,7 +177,7 @@ template <typename R, bool RATE = false>
 __device__ __forceinline__ void block_min_dt_and_finalize(const Fields<R> &F, DevScalars *S, double dtc,
                                                           int mode, double dt_override) {
   __shared__ double smin[kBlock / 32];
-  __shared__ bool last;
+  bool last = false;  // set in thread 0 only: no second barrier needed
   dtc = RATE ? warp_max(dtc) : warp_min(dtc);
   if ((threadIdx.x & 31) == 0) smin[threadIdx.x >> 5] = dtc;
   __syncthreads();
@@ -196,7 +196,6 @@ __device__ __forceinline__ void block_min_dt_and_finalize(const Fields<R> &F, De
       last = (done == gridDim.x - 1);
     }
   }
-  __syncthreads();
   if (!last || threadIdx.x != 0) return;
   // Last block: every other block has published its minimum.
   __threadfence();
@@ -237,7 +236,7 @@ template <typename R>
 __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, DevScalars *S, float dtc, int mode,
                                                             double dt_override, unsigned nblk) {
   __shared__ float smin32[kMaxWarpsPerBlock];
-  __shared__ bool last32;
+  bool last32 = false;  // set in thread 0 only: no second barrier needed
   const int tid = threadIdx.x + blockDim.x * (threadIdx.y + blockDim.y * threadIdx.z);
   const int nwarps = (int)((blockDim.x * blockDim.y * blockDim.z + 31) / 32);
   dtc = warp_min_f32(dtc);
@@ -253,7 +252,6 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
       last32 = (done == nblk - 1);
     }
   }
-  __syncthreads();
   if (!last32 || tid != 0) return;
   __threadfence();
   volatile DevScalars *VS = S;
