@@ -76,8 +76,8 @@ MIXED_ALE = {
     "mix_cells": ("cell", 4 * (4 + 3 + 1 + 1 + 2 + 2 + 3), GRAD32 + 40 + 6 + SWEPT32),
     # swept volumes, V_E, m, e read; 3 mass + 3 energy fluxes written
     "mix_fluxes": ("cell", 4 * (3 + 3 + 6), 30),
-    # 3 mass fluxes, u, mn read; u', mn', dKE written
-    "mix_remap_nodes": ("node", 4 * (3 + 3 + 1 + 3 + 1 + 1), 125),
+    # 3 mass fluxes, u, mn (hi, lo) read; u', mn' (hi, lo), dKE written
+    "mix_remap_nodes": ("node", 4 * (3 + 3 + 2 + 3 + 2 + 1), 125 + 6 * 9),
     # 6 fluxes, m, e (hi, lo), dKE, u', offsets (float4), V_E, L_E read;
     # m, e (hi, lo), rho, sigma written
     "mix_remap_eos": ("cell", 4 * (6 + 4 + 1 + 3 + 4 + 2 + 6), 40 + GRAD32 + 40 + 30),

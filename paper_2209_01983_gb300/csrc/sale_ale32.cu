@@ -704,7 +704,7 @@ __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j
 }
 
 template <int AX, int SIDE, bool IN>
-__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, float &m, F3 &p,
+__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, DF &m, F3 &p,
                                             float &ke) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
@@ -717,7 +717,7 @@ __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j
   const int dn = psi > 0.f ? lo + stride : lo;
   const F3 ud = {F.u[dn], F.v[dn], F.w[dn]};
   const float flux = SIDE == 0 ? psi : -psi;
-  m += flux;
+  m = df_add_f(m, flux);  // float-float: the node mass absorbs fluxes ~1% of it every cycle
   p = p + flux * ud;
   ke += flux * 0.5f * dotf(ud, ud);
 }
@@ -734,7 +734,7 @@ __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevSc
   }
   const float m0 = F.mn[n];
   const F3 u0 = {F.u[n], F.v[n], F.w[n]};
-  float m = m0;
+  DF m = {m0, F.mnlo[n]};
   F3 p = m0 * u0;
   float ke = 0.5f * m0 * dotf(u0, u0);
   m_node_edge<0, 0, IN>(F, i, j, k, n, m, p, ke);
@@ -743,15 +743,16 @@ __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevSc
   m_node_edge<1, 1, IN>(F, i, j, k, n, m, p, ke);
   m_node_edge<2, 0, IN>(F, i, j, k, n, m, p, ke);
   m_node_edge<2, 1, IN>(F, i, j, k, n, m, p, ke);
-  if (!(m > 0.f)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
-  const float inv_m = 1.f / m;
+  if (!(m.hi > 0.f)) set_status(S, m.hi != m.hi ? SALE_ENAN : SALE_ENEGVOL);
+  const float inv_m = 1.f / m.hi;
   float u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
   if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
   F.ub[n] = u1;
   F.vb[n] = v1;
   F.wb[n] = w1;
-  F.mn[n] = m;
-  F.dke[n] = ke - 0.5f * m * (u1 * u1 + v1 * v1 + w1 * w1);
+  F.mn[n] = m.hi;
+  F.mnlo[n] = m.lo;
+  F.dke[n] = ke - 0.5f * m.hi * (u1 * u1 + v1 * v1 + w1 * w1);
 }
 
 // ---------------------------------------------------------------------------

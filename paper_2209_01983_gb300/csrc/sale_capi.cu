@@ -222,6 +222,7 @@ struct sale_state {
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
   float4 *off4;                          // FP32-mixed path: jitter offsets
   float *mlo, *elo;                      // FP32-mixed path: low parts of m, e
+  float *mnlo;                           // FP32-mixed path: low part of the node mass
   float *VE32, *LE32;                    // FP32-mixed path: V_E, L_E
   float *Gc;                             // FP32-mixed path, jittered mesh: corner gradients
   void *Gh;                              // predictor-corrector: half-step corner gradients (24 per cell)
@@ -281,7 +282,7 @@ static size_t carve(sale_state *st, char *base) {
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
   st->off4 = nullptr;
-  st->VE32 = st->LE32 = st->mlo = st->elo = nullptr;
+  st->VE32 = st->LE32 = st->mlo = st->elo = st->mnlo = nullptr;
   st->Gc = nullptr;
   st->Gh = nullptr;
   st->fh = nullptr;
@@ -306,6 +307,7 @@ static size_t carve(sale_state *st, char *base) {
     st->LE32 = (float *)cv.take(sizeof(float) * nc);
     st->mlo = (float *)cv.take(sizeof(float) * nc);
     st->elo = (float *)cv.take(sizeof(float) * nc);
+    st->mnlo = (float *)cv.take(sizeof(float) * nn);
     if (st->jit) st->Gc = (float *)cv.take(sizeof(float) * 24 * nc);
   }
   if (st->pc) st->Gh = cv.take(E * 24 * nc);
@@ -373,6 +375,7 @@ static Fields<R> fields_t(const sale_state *st) {
   }
   F.mlo = (R *)st->mlo;
   F.elo = (R *)st->elo;
+  F.mnlo = (R *)st->mnlo;
   F.hx = st->h32[0];
   F.hy = st->h32[1];
   F.hz = st->h32[2];
@@ -1006,7 +1009,7 @@ extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *
     CUDA_TRY(cudaMemcpyAsync(tmp, p, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));
     for (size_t i = 0; i < n; ++i) host_out[i] = (double)tmp[i];  // ascending: never overwrites unread floats
-    const float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : nullptr;
+    const float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : !strcmp(name, "mn") ? st->mnlo : nullptr;
     if (lo) {  // float-float cell quantity: add the low part
       std::vector<float> low;
       try {
@@ -1047,7 +1050,7 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
     for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_in[i];
     CUDA_TRY(cudaMemcpyAsync(p, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
     CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp is rewritten next
-    float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : nullptr;
+    float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : !strcmp(name, "mn") ? st->mnlo : nullptr;
     if (lo) {  // float-float cell quantity: low part = rest after the FP32 high part
       for (size_t i = 0; i < n; ++i) tmp[i] = (float)(host_in[i] - (double)(float)host_in[i]);
       CUDA_TRY(cudaMemcpyAsync(lo, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));

@@ -101,6 +101,7 @@ struct Fields {
   R *dke;                      // kinetic energy lost by the node remap
   R *m, *e;                    // cell mass, specific internal energy
   R *mlo, *elo;                // FP32-mixed path: low parts of m and e (float-float); null otherwise
+  R *mnlo;                     // FP32-mixed path: low part of the node mass (float-float); null otherwise
   R *sig;                      // p + q
   R *rho, *p, *q, *cs, *vol;   // derived cell fields
   R *mux, *muy, *muz;          // mass flux through the low x/y/z face

@@ -63,9 +63,11 @@ __global__ void k_init_nodes(Fields<R> F) {
   for (int s = 0; s < 8; ++s) {
     const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
     if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
-    mn += (double)F.m[cell_index(F.nx, F.ny, ci, cj, ck)] / 8.0;
+    const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
+    mn += ((double)F.m[c] + (F.mlo ? (double)F.mlo[c] : 0.0)) / 8.0;
   }
   F.mn[n] = (R)mn;
+  if (F.mnlo) F.mnlo[n] = (R)(mn - (double)(R)mn);  // float-float node mass of the mixed path
   F.u[n] = F.v[n] = F.w[n] = (R)0;
 }
 
