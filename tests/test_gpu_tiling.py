@@ -31,9 +31,20 @@ def ragged_sedov():
     return md, pd
 
 
-def test_state_tile_shapes_bitwise(sale):
+def interior_sedov():
+    # large enough that each shape has tiles inside 1 <= index <= n - 2 (the
+    # interior bodies), and different ones per shape: equal results across
+    # shapes then also mean interior and general bodies agree bitwise
+    md, pd = inputs.sedov_octant(6, jitter=0.1)
+    md = inputs.MeshDesc(70, 20, 6, lo=md.lo, hi=(1.2 * 70 / 6, 1.2 * 20 / 6, 1.2), jitter=0.1,
+                         seed=md.seed, reflect=md.reflect)
+    return md, pd
+
+
+@pytest.mark.parametrize("mesh", [ragged_sedov, interior_sedov])
+def test_state_tile_shapes_bitwise(sale, mesh):
     from paper_2209_01983_gb300 import autotune
-    md, pd = ragged_sedov()
+    md, pd = mesh()
     ref = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
     assert ref.run_to_time(max_cycles=24, remap_every=1) == 24
     want = {f: ref.field(f) for f in FIELDS}
