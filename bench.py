@@ -399,7 +399,7 @@ def gpu_arm(args):
         res = measure(args, prec, local, barrier)
         res["value"], res["ms_max"] = replica_rate(res["ms"], res["md"].ncell, args.steps, world, dist,
                                                    f"cuda:{local}")
-        if not args.no_e2e and prec == precisions[0]:
+        if not args.no_e2e:
             res["e2e"] = e2e_rate(args, res, world)
         res["st"].close()
         del res["st"]
@@ -437,7 +437,8 @@ def gpu_arm(args):
         variants[prec] = {"value": x["value"], "ms_per_step": x["ms_max"] / args.steps, "dtype": dtypes[prec],
                           "speedup_vs_" + main_p: x["value"] / r["value"], "roofline": x["roofline"],
                           "full_cycle": x["full_cycle"], "kernels": x["kernels"], "clocks": x["clocks"],
-                          "gpu_launches": x["gpu_launches"], "check": x["check"], "tuning": x["tuning"]}
+                          "gpu_launches": x["gpu_launches"], "check": x["check"], "tuning": x["tuning"],
+                          "e2e": x.get("e2e")}
     if variants:
         line["variants"] = variants
     print(json.dumps(line), flush=True)

@@ -1036,6 +1036,38 @@ void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned n
   }
 }
 
+// Field transfers of FP32-mixed states: FP64 values to FP32 (hi, optional lo)
+// pairs and back, with the same roundings as the host would take: hi = x
+// rounded to FP32, lo = (x - hi) rounded to FP32; x = hi + lo in FP64.
+__global__ void k_split64(const double *__restrict__ in, float *__restrict__ hi, float *__restrict__ lo,
+                          long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const double x = in[i];
+    const float h = (float)x;
+    hi[i] = h;
+    if (lo) lo[i] = (float)(x - (double)h);
+  }
+}
+
+__global__ void k_join64(const float *__restrict__ hi, const float *__restrict__ lo, double *__restrict__ out,
+                         long long n) {
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = lo ? (double)hi[i] + (double)lo[i] : (double)hi[i];
+}
+
+static unsigned grid_stride_blocks(long long n) {
+  const long long b = (n + kBlock - 1) / kBlock;
+  return (unsigned)(b < 152 * 16 ? (b > 0 ? b : 1) : 152 * 16);
+}
+
+void launch_split64(const double *in, float *hi, float *lo, long long n, cudaStream_t st) {
+  k_split64<<<grid_stride_blocks(n), kBlock, 0, st>>>(in, hi, lo, n);
+}
+
+void launch_join64(const float *hi, const float *lo, double *out, long long n, cudaStream_t st) {
+  k_join64<<<grid_stride_blocks(n), kBlock, 0, st>>>(hi, lo, out, n);
+}
+
 void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st) {
   kb_set_limits<<<(n + 127) / 128, 128, 0, st>>>(items, n, cycles);
 }

@@ -33,6 +33,8 @@ void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
                          long long dep_cell, double dep_e, float *VE, float *LE, float *Gc, cudaStream_t st);
 void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, int shape, cudaStream_t st);
+void launch_split64(const double *in, float *hi, float *lo, long long n, cudaStream_t st);
+void launch_join64(const float *hi, const float *lo, double *out, long long n, cudaStream_t st);
 }  // namespace sale
 
 using namespace sale;
@@ -989,6 +991,20 @@ static void *field_ptr(const sale_state *st, const char *name, bool *node, bool 
   return nullptr;
 }
 
+// FP32-mixed states: the per-face flux and swept-volume arrays (mu, ep, dv;
+// carved back to back, >= 36 bytes per cell) hold nothing between cycles, so
+// field transfers stage FP64 values there and convert them on the device.
+static void mixed_stage(const sale_state *st, double **buf, size_t *cap) {
+  char *b = (char *)st->mu[0];
+  char *e = (char *)st->dv[2] + sizeof(float) * (size_t)st->nc;
+  *buf = (double *)b;
+  *cap = (size_t)(e - b) / sizeof(double);
+}
+
+static float *mixed_lo(const sale_state *st, const char *name) {
+  return !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : !strcmp(name, "mn") ? st->mnlo : nullptr;
+}
+
 extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *host_out, size_t n) {
   sale_state *st = const_cast<sale_state *>(cst);
   if (!st || !name || !host_out) return fail(SALE_EINVAL, "sale_copy_field: null argument");
@@ -1004,22 +1020,17 @@ extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *
   if (elem == sizeof(double)) {
     CUDA_TRY(cudaMemcpyAsync(host_out, p, sizeof(double) * n, cudaMemcpyDeviceToHost, st->stream));
   } else {
-    // FP32 field: copy into the tail half of the caller's buffer, widen in place
-    float *tmp = (float *)(host_out + n) - n;
-    CUDA_TRY(cudaMemcpyAsync(tmp, p, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
-    CUDA_TRY(cudaStreamSynchronize(st->stream));
-    for (size_t i = 0; i < n; ++i) host_out[i] = (double)tmp[i];  // ascending: never overwrites unread floats
-    const float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : !strcmp(name, "mn") ? st->mnlo : nullptr;
-    if (lo) {  // float-float cell quantity: add the low part
-      std::vector<float> low;
-      try {
-        low.resize(n);
-      } catch (...) {
-        return fail(SALE_ENOMEM, "sale_copy_field: out of host memory");
-      }
-      CUDA_TRY(cudaMemcpyAsync(low.data(), lo, sizeof(float) * n, cudaMemcpyDeviceToHost, st->stream));
-      CUDA_TRY(cudaStreamSynchronize(st->stream));
-      for (size_t i = 0; i < n; ++i) host_out[i] += (double)low[i];
+    // FP32 field (plus its low part for float-float quantities): widened to
+    // FP64 on the device in staging-sized chunks, then copied out
+    double *stage;
+    size_t cap;
+    mixed_stage(st, &stage, &cap);
+    const float *lo = mixed_lo(st, name);
+    for (size_t off = 0; off < n; off += cap) {
+      const size_t k = std::min(cap, n - off);
+      launch_join64((const float *)p + off, lo ? lo + off : nullptr, stage, (long long)k, st->stream);
+      CUDA_TRY(cudaGetLastError());
+      CUDA_TRY(cudaMemcpyAsync(host_out + off, stage, sizeof(double) * k, cudaMemcpyDeviceToHost, st->stream));
     }
   }
   DevScalars h;
@@ -1041,20 +1052,17 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
   if (elem == sizeof(double)) {
     CUDA_TRY(cudaMemcpyAsync(p, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, st->stream));
   } else {
-    std::vector<float> tmp;
-    try {
-      tmp.resize(n);
-    } catch (...) {
-      return fail(SALE_ENOMEM, "sale_set_field: out of host memory");
-    }
-    for (size_t i = 0; i < n; ++i) tmp[i] = (float)host_in[i];
-    CUDA_TRY(cudaMemcpyAsync(p, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
-    CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp is rewritten next
-    float *lo = !strcmp(name, "m") ? st->mlo : !strcmp(name, "e") ? st->elo : !strcmp(name, "mn") ? st->mnlo : nullptr;
-    if (lo) {  // float-float cell quantity: low part = rest after the FP32 high part
-      for (size_t i = 0; i < n; ++i) tmp[i] = (float)(host_in[i] - (double)(float)host_in[i]);
-      CUDA_TRY(cudaMemcpyAsync(lo, tmp.data(), sizeof(float) * n, cudaMemcpyHostToDevice, st->stream));
-      CUDA_TRY(cudaStreamSynchronize(st->stream));  // tmp dies here
+    // FP32 field: FP64 values staged on the device in chunks and split there
+    // into the FP32 value and, for float-float quantities, its low part
+    double *stage;
+    size_t cap;
+    mixed_stage(st, &stage, &cap);
+    float *lo = mixed_lo(st, name);
+    for (size_t off = 0; off < n; off += cap) {
+      const size_t k = std::min(cap, n - off);
+      CUDA_TRY(cudaMemcpyAsync(stage, host_in + off, sizeof(double) * k, cudaMemcpyHostToDevice, st->stream));
+      launch_split64(stage, (float *)p + off, lo ? lo + off : nullptr, (long long)k, st->stream);
+      CUDA_TRY(cudaGetLastError());
     }
   }
   if (!strcmp(name, "x") || !strcmp(name, "y") || !strcmp(name, "z")) st->x_is_ref = false;

@@ -104,3 +104,28 @@ def test_mixed_node_mass_stays_consistent(sale):
                for dk in (0, 1) for dj in (0, 1) for di in (0, 1)).ravel() / 8.0
     mn = st.field("mn")
     assert float(np.max(np.abs(mn - want) / want)) <= 5e-5
+
+
+def test_mixed_field_transfer_roundings(sale):
+    # FP32-mixed fields take FP64 input as hi = fl32(x) (plus lo = fl32(x - hi)
+    # for the float-float m, e and m_n) and read back as hi (+ lo) in FP64,
+    # converted on the device: exactly the host formulas, at any size
+    md, pd = inputs.sedov_octant(11, jitter=0.1)
+    st = sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
+    st.run_to_time(max_cycles=3, remap_every=1)
+    rng = np.random.default_rng(5)
+
+    def hi(x):
+        return x.astype(np.float32).astype(np.float64)
+
+    for name, ff in (("e", True), ("m", True), ("mn", True), ("u", False), ("w", False)):
+        x = st.field(name) * (1.0 + 1e-3 * rng.uniform(-1, 1, st.field(name).size)) + 1e-9
+        st.set_field(name, x)
+        want = hi(x) + hi(x - hi(x)) if ff else hi(x)
+        assert np.array_equal(st.field(name), want), name
+        if ff:
+            assert float(np.max(np.abs(st.field(name) - x) / np.abs(x))) <= 2.0 ** -45
+    st.refresh()
+    rho, p, e = st.field("rho"), st.field("p"), st.field("e")
+    assert np.allclose(p, 0.4 * rho * e, rtol=1e-6, atol=0)
+    assert st.run_to_time(max_cycles=3, remap_every=1) == 3
