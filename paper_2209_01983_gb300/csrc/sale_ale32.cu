@@ -703,15 +703,19 @@ __device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j
   return 0.125f * psi;
 }
 
-template <int AX, int SIDE, bool IN>
-__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, DF &m, F3 &p,
-                                            float &ke) {
+// Whether the edge of node (i,j,k) along AX on side SIDE (0: towards +AX)
+// lies in the mesh.
+template <int AX, int SIDE>
+__device__ __forceinline__ bool m_edge_exists(const Fields<float> &F, int i, int j, int k) {
   const int idx = AX == 0 ? i : AX == 1 ? j : k;
   const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
-  if (!IN && SIDE == 0 && idx == n_ax) return;
-  if (!IN && SIDE == 1 && idx == 0) return;
-  const float psi = m_edge_psi<AX, IN>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
-                                   (SIDE == 1 && AX == 2) ? k - 1 : k);
+  return SIDE == 0 ? idx != n_ax : idx != 0;
+}
+
+// Momentum, mass and kinetic energy carried into node n through one of its
+// edges by the dual flux psi of that edge (positive: towards +AX), upwinded.
+template <int AX, int SIDE>
+__device__ __forceinline__ void m_edge_apply(const Fields<float> &F, int n, float psi, DF &m, F3 &p, float &ke) {
   const int stride = AX == 0 ? 1 : AX == 1 ? (F.nx + 1) : (F.nx + 1) * (F.ny + 1);
   const int lo = SIDE == 0 ? n : n - stride;
   const int dn = psi > 0.f ? lo + stride : lo;
@@ -720,6 +724,31 @@ __device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j
   m = df_add_f(m, flux);  // float-float: the node mass absorbs fluxes ~1% of it every cycle
   p = p + flux * ud;
   ke += flux * 0.5f * dotf(ud, ud);
+}
+
+template <int AX, int SIDE, bool IN>
+__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, DF &m, F3 &p,
+                                            float &ke) {
+  if (!IN && !m_edge_exists<AX, SIDE>(F, i, j, k)) return;
+  const float psi = m_edge_psi<AX, IN>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
+                                   (SIDE == 1 && AX == 2) ? k - 1 : k);
+  m_edge_apply<AX, SIDE>(F, n, psi, m, p, ke);
+}
+
+// New node velocity, mass and kinetic-energy defect from the remapped sums.
+template <bool IN>
+__device__ __forceinline__ void m_remap_node_store(const Fields<float> &F, DevScalars *S, int i, int j, int k, int n,
+                                                   DF m, F3 p, float ke) {
+  if (!(m.hi > 0.f)) set_status(S, m.hi != m.hi ? SALE_ENAN : SALE_ENEGVOL);
+  const float inv_m = 1.f / m.hi;
+  float u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
+  if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
+  F.ub[n] = u1;
+  F.vb[n] = v1;
+  F.wb[n] = w1;
+  F.mn[n] = m.hi;
+  F.mnlo[n] = m.lo;
+  F.dke[n] = ke - 0.5f * m.hi * (u1 * u1 + v1 * v1 + w1 * w1);
 }
 
 template <bool IN>
@@ -743,16 +772,129 @@ __device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevSc
   m_node_edge<1, 1, IN>(F, i, j, k, n, m, p, ke);
   m_node_edge<2, 0, IN>(F, i, j, k, n, m, p, ke);
   m_node_edge<2, 1, IN>(F, i, j, k, n, m, p, ke);
-  if (!(m.hi > 0.f)) set_status(S, m.hi != m.hi ? SALE_ENAN : SALE_ENEGVOL);
-  const float inv_m = 1.f / m.hi;
-  float u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
-  if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
-  F.ub[n] = u1;
-  F.vb[n] = v1;
-  F.wb[n] = w1;
-  F.mn[n] = m.hi;
-  F.mnlo[n] = m.lo;
-  F.dke[n] = ke - 0.5f * m.hi * (u1 * u1 + v1 * v1 + w1 * w1);
+  m_remap_node_store<IN>(F, S, i, j, k, n, m, p, ke);
+}
+
+// The node remap of one mesh, marching in k: a block covers a tile of node
+// columns over kRemapChunk node planes.  An edge's dual flux sums, over the
+// (up to) four cells around it in order, the pair (low-face + high-face mass
+// flux along the edge) of each cell.  The pairs of the cell plane between
+// two node planes serve the edges of both, and the k-edge below a node is
+// the k-edge above the node beneath it, so a column forms each pair and each
+// k-edge flux once: the same additions in the same order as the per-node
+// evaluation, with cells outside the mesh read as zero.
+constexpr int kRemapChunk = 16;
+
+struct RemapCarry {
+  float x0[2], x1[2];  // x-edge pairs of the cell plane below: edges at ci = i, i - 1; cells cj = j - 1, j
+  float y0[2], y1[2];  // y-edge pairs: edges at cj = j, j - 1; cells ci = i - 1, i
+  float zc[4];         // mu_z of the cells (i - 1 + (s & 1), j - 1 + (s >> 1)) of this node's cell plane
+  float psi_below;     // dual flux of the k-edge ending at this node
+};
+
+template <bool IN>
+__device__ __forceinline__ float mu_at(const float *mu, const Fields<float> &F, int ci, int cj, int ck) {
+  if (!IN && (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz)) return 0.f;
+  return mu[ci + F.nx * (cj + F.ny * ck)];
+}
+
+// The x- and y-edge pairs of the cell plane ck around node column (i, j).
+template <bool IN>
+__device__ __forceinline__ void remap_plane_pairs(const Fields<float> &F, int i, int j, int ck, float (&x0)[2],
+                                                  float (&x1)[2], float (&y0)[2], float (&y1)[2]) {
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    const float a = mu_at<IN>(F.mux, F, i - 1, j - 1 + d, ck), b = mu_at<IN>(F.mux, F, i, j - 1 + d, ck),
+                c = mu_at<IN>(F.mux, F, i + 1, j - 1 + d, ck);
+    x1[d] = a + b;
+    x0[d] = b + c;
+    const float e = mu_at<IN>(F.muy, F, i - 1 + d, j - 1, ck), f = mu_at<IN>(F.muy, F, i - 1 + d, j, ck),
+                g = mu_at<IN>(F.muy, F, i - 1 + d, j + 1, ck);
+    y1[d] = e + f;
+    y0[d] = f + g;
+  }
+}
+
+__device__ __forceinline__ float edge_psi4(float a, float b, float c, float d) {
+  float psi = 0.f;
+  psi += a;
+  psi += b;
+  psi += c;
+  psi += d;
+  return 0.125f * psi;
+}
+
+template <bool IN>
+__device__ __forceinline__ void m_remap_node_step(const Fields<float> &F, DevScalars *S, int i, int j, int k,
+                                                  RemapCarry &cr) {
+  float x0[2], x1[2], y0[2], y1[2], zn[4];
+  remap_plane_pairs<IN>(F, i, j, k, x0, x1, y0, y1);
+#pragma unroll
+  for (int s = 0; s < 4; ++s) zn[s] = mu_at<IN>(F.muz, F, i - 1 + (s & 1), j - 1 + (s >> 1), k + 1);
+  const float px0 = edge_psi4(cr.x0[0], cr.x0[1], x0[0], x0[1]);
+  const float px1 = edge_psi4(cr.x1[0], cr.x1[1], x1[0], x1[1]);
+  const float py0 = edge_psi4(cr.y0[0], cr.y0[1], y0[0], y0[1]);
+  const float py1 = edge_psi4(cr.y1[0], cr.y1[1], y1[0], y1[1]);
+  const float pz0 = edge_psi4(cr.zc[0] + zn[0], cr.zc[1] + zn[1], cr.zc[2] + zn[2], cr.zc[3] + zn[3]);
+  const float pz1 = cr.psi_below;
+#pragma unroll
+  for (int d = 0; d < 2; ++d) {
+    cr.x0[d] = x0[d];
+    cr.x1[d] = x1[d];
+    cr.y0[d] = y0[d];
+    cr.y1[d] = y1[d];
+  }
+#pragma unroll
+  for (int s = 0; s < 4; ++s) cr.zc[s] = zn[s];
+  cr.psi_below = pz0;
+
+  const int n = i + (F.nx + 1) * (j + (F.ny + 1) * k);
+  const float m0 = F.mn[n];
+  const F3 u0 = {F.u[n], F.v[n], F.w[n]};
+  DF m = {m0, F.mnlo[n]};
+  F3 p = m0 * u0;
+  float ke = 0.5f * m0 * dotf(u0, u0);
+  if (IN || m_edge_exists<0, 0>(F, i, j, k)) m_edge_apply<0, 0>(F, n, px0, m, p, ke);
+  if (IN || m_edge_exists<0, 1>(F, i, j, k)) m_edge_apply<0, 1>(F, n, px1, m, p, ke);
+  if (IN || m_edge_exists<1, 0>(F, i, j, k)) m_edge_apply<1, 0>(F, n, py0, m, p, ke);
+  if (IN || m_edge_exists<1, 1>(F, i, j, k)) m_edge_apply<1, 1>(F, n, py1, m, p, ke);
+  if (IN || m_edge_exists<2, 0>(F, i, j, k)) m_edge_apply<2, 0>(F, n, pz0, m, p, ke);
+  if (IN || m_edge_exists<2, 1>(F, i, j, k)) m_edge_apply<2, 1>(F, n, pz1, m, p, ke);
+  m_remap_node_store<IN>(F, S, i, j, k, n, m, p, ke);
+}
+
+template <int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+    k_m_remap_nodes_march(Fields<float> F, DevScalars *S) {
+  const int i = blockIdx.x * tile_x(SH) + threadIdx.x, j = blockIdx.y * tile_y(SH) + threadIdx.y;
+  const int k0 = blockIdx.z * kRemapChunk;
+  const int k1 = min(k0 + kRemapChunk, F.nz + 1);
+  if (i > F.nx || j > F.ny) return;
+  if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
+    for (int k = k0; k < k1; ++k) {
+      const int n = i + (F.nx + 1) * (j + (F.ny + 1) * k);
+      F.ub[n] = F.u[n];
+      F.vb[n] = F.v[n];
+      F.wb[n] = F.w[n];
+    }
+    return;
+  }
+  // the x/y extent of the tile's cells and neighbours lies in the mesh
+  const int i0 = blockIdx.x * tile_x(SH), j0 = blockIdx.y * tile_y(SH);
+  const bool xy_in = i0 >= 1 && i0 + tile_x(SH) <= F.nx - 1 && j0 >= 1 && j0 + tile_y(SH) <= F.ny - 1;
+  RemapCarry cr;
+  remap_plane_pairs<false>(F, i, j, k0 - 1, cr.x0, cr.x1, cr.y0, cr.y1);
+  float zb[4];
+#pragma unroll
+  for (int s = 0; s < 4; ++s) {
+    zb[s] = mu_at<false>(F.muz, F, i - 1 + (s & 1), j - 1 + (s >> 1), k0 - 1);
+    cr.zc[s] = mu_at<false>(F.muz, F, i - 1 + (s & 1), j - 1 + (s >> 1), k0);
+  }
+  cr.psi_below = edge_psi4(zb[0] + cr.zc[0], zb[1] + cr.zc[1], zb[2] + cr.zc[2], zb[3] + cr.zc[3]);
+  for (int k = k0; k < k1; ++k) {
+    if (xy_in && k >= 1 && k <= F.nz - 2) m_remap_node_step<true>(F, S, i, j, k, cr);
+    else m_remap_node_step<false>(F, S, i, j, k, cr);
+  }
 }
 
 // ---------------------------------------------------------------------------
@@ -974,6 +1116,11 @@ void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rh
 
 template <int KID, int SH>
 static void launch_shaped(const Fields<float> &F, DevScalars *S, int mode, cudaStream_t st) {
+  if constexpr (KID == kMixRemapNodes) {
+    const dim3 g = tile_grid(F.nx + 1, F.ny + 1, (F.nz + 1 + kRemapChunk - 1) / kRemapChunk, SH);
+    k_m_remap_nodes_march<SH><<<g, dim3(tile_x(SH), tile_y(SH)), 0, st>>>(F, S);
+    return;
+  }
   const bool node = KID == kMixNodes || KID == kMixRemapNodes;
   const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1, SH) : tile_grid(F.nx, F.ny, F.nz, SH);
   const dim3 b(tile_x(SH), tile_y(SH));
