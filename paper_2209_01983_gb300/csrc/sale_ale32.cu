@@ -680,29 +680,6 @@ __device__ __forceinline__ void m_fluxes_body(const Fields<float> &F, DevScalars
 // Node remap (FP32)
 // ---------------------------------------------------------------------------
 
-// Dual mass flux along the mesh edge from node (i,j,k) to its +AX
-// neighbour: sum over the (up to four) cells around the edge of
-// (mu_low_face + mu_high_face) / 8.
-template <int AX, bool IN>
-__device__ __forceinline__ float m_edge_psi(const Fields<float> &F, int i, int j, int k) {
-  const float *mu = AX == 0 ? F.mux : AX == 1 ? F.muy : F.muz;
-  const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
-  const int stride = AX == 0 ? 1 : AX == 1 ? F.nx : F.nx * F.ny;
-  float psi = 0.f;
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    int ci = i, cj = j, ck = k;
-    if (AX == 0) { cj = j - 1 + (s & 1); ck = k - 1 + (s >> 1); }
-    if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
-    if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
-    if (!IN && (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz)) continue;
-    const int c = ci + F.nx * (cj + F.ny * ck);
-    const int hi_idx = (AX == 0 ? ci : AX == 1 ? cj : ck) + 1;
-    psi += mu[c] + (IN || hi_idx < n_ax ? mu[c + stride] : 0.f);
-  }
-  return 0.125f * psi;
-}
-
 // Whether the edge of node (i,j,k) along AX on side SIDE (0: towards +AX)
 // lies in the mesh.
 template <int AX, int SIDE>
@@ -726,15 +703,6 @@ __device__ __forceinline__ void m_edge_apply(const Fields<float> &F, int n, floa
   ke += flux * 0.5f * dotf(ud, ud);
 }
 
-template <int AX, int SIDE, bool IN>
-__device__ __forceinline__ void m_node_edge(const Fields<float> &F, int i, int j, int k, int n, DF &m, F3 &p,
-                                            float &ke) {
-  if (!IN && !m_edge_exists<AX, SIDE>(F, i, j, k)) return;
-  const float psi = m_edge_psi<AX, IN>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
-                                   (SIDE == 1 && AX == 2) ? k - 1 : k);
-  m_edge_apply<AX, SIDE>(F, n, psi, m, p, ke);
-}
-
 // New node velocity, mass and kinetic-energy defect from the remapped sums.
 template <bool IN>
 __device__ __forceinline__ void m_remap_node_store(const Fields<float> &F, DevScalars *S, int i, int j, int k, int n,
@@ -751,40 +719,15 @@ __device__ __forceinline__ void m_remap_node_store(const Fields<float> &F, DevSc
   F.dke[n] = ke - 0.5f * m.hi * (u1 * u1 + v1 * v1 + w1 * w1);
 }
 
-template <bool IN>
-__device__ __forceinline__ void m_remap_nodes_body(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
-  if (!IN && (i > F.nx || j > F.ny || k > F.nz)) return;
-  const int n = i + (F.nx + 1) * (j + (F.ny + 1) * k);
-  if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
-    F.ub[n] = F.u[n];
-    F.vb[n] = F.v[n];
-    F.wb[n] = F.w[n];
-    return;
-  }
-  const float m0 = F.mn[n];
-  const F3 u0 = {F.u[n], F.v[n], F.w[n]};
-  DF m = {m0, F.mnlo[n]};
-  F3 p = m0 * u0;
-  float ke = 0.5f * m0 * dotf(u0, u0);
-  m_node_edge<0, 0, IN>(F, i, j, k, n, m, p, ke);
-  m_node_edge<0, 1, IN>(F, i, j, k, n, m, p, ke);
-  m_node_edge<1, 0, IN>(F, i, j, k, n, m, p, ke);
-  m_node_edge<1, 1, IN>(F, i, j, k, n, m, p, ke);
-  m_node_edge<2, 0, IN>(F, i, j, k, n, m, p, ke);
-  m_node_edge<2, 1, IN>(F, i, j, k, n, m, p, ke);
-  m_remap_node_store<IN>(F, S, i, j, k, n, m, p, ke);
-}
-
-// The node remap of one mesh, marching in k: a block covers a tile of node
-// columns over kRemapChunk node planes.  An edge's dual flux sums, over the
-// (up to) four cells around it in order, the pair (low-face + high-face mass
-// flux along the edge) of each cell.  The pairs of the cell plane between
-// two node planes serve the edges of both, and the k-edge below a node is
-// the k-edge above the node beneath it, so a column forms each pair and each
-// k-edge flux once: the same additions in the same order as the per-node
-// evaluation, with cells outside the mesh read as zero.
-constexpr int kRemapChunk = 16;
-
+// The node remap marches in k: a block covers a tile of node columns over
+// kRemapChunk node planes.  The dual mass flux of a mesh edge is 1/8 of the
+// sum, over the (up to) four cells around the edge, of each cell's pair
+// (low-face + high-face mass flux along the edge), added in a fixed cell
+// order; cells outside the mesh read as zero.  The pairs of the cell plane
+// between two node planes serve the edges of both, and the k-edge below a
+// node is the k-edge above the node beneath it, so a column forms each pair
+// and each k-edge flux once, and every node sees bitwise the same fluxes as
+// its neighbours across the edge.
 struct RemapCarry {
   float x0[2], x1[2];  // x-edge pairs of the cell plane below: edges at ci = i, i - 1; cells cj = j - 1, j
   float y0[2], y1[2];  // y-edge pairs: edges at cj = j, j - 1; cells ci = i - 1, i
@@ -863,11 +806,11 @@ __device__ __forceinline__ void m_remap_node_step(const Fields<float> &F, DevSca
   m_remap_node_store<IN>(F, S, i, j, k, n, m, p, ke);
 }
 
+// Tile (bx, by) of node columns over the node planes of chunk kc.
 template <int SH>
-__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
-    k_m_remap_nodes_march(Fields<float> F, DevScalars *S) {
-  const int i = blockIdx.x * tile_x(SH) + threadIdx.x, j = blockIdx.y * tile_y(SH) + threadIdx.y;
-  const int k0 = blockIdx.z * kRemapChunk;
+__device__ __forceinline__ void m_remap_column(const Fields<float> &F, DevScalars *S, int bx, int by, int kc) {
+  const int i = bx * tile_x(SH) + threadIdx.x, j = by * tile_y(SH) + threadIdx.y;
+  const int k0 = kc * kRemapChunk;
   const int k1 = min(k0 + kRemapChunk, F.nz + 1);
   if (i > F.nx || j > F.ny) return;
   if (!S->next_active) {  // inactive cycle: velocity carries over unchanged
@@ -880,7 +823,7 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * 
     return;
   }
   // the x/y extent of the tile's cells and neighbours lies in the mesh
-  const int i0 = blockIdx.x * tile_x(SH), j0 = blockIdx.y * tile_y(SH);
+  const int i0 = bx * tile_x(SH), j0 = by * tile_y(SH);
   const bool xy_in = i0 >= 1 && i0 + tile_x(SH) <= F.nx - 1 && j0 >= 1 && j0 + tile_y(SH) <= F.ny - 1;
   RemapCarry cr;
   remap_plane_pairs<false>(F, i, j, k0 - 1, cr.x0, cr.x1, cr.y0, cr.y1);
@@ -895,6 +838,12 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * 
     if (xy_in && k >= 1 && k <= F.nz - 2) m_remap_node_step<true>(F, S, i, j, k, cr);
     else m_remap_node_step<false>(F, S, i, j, k, cr);
   }
+}
+
+template <int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+    k_m_remap_nodes_march(Fields<float> F, DevScalars *S) {
+  m_remap_column<SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z);
 }
 
 // ---------------------------------------------------------------------------
@@ -1024,7 +973,6 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
     case kMixNodes: m_nodes_body<JIT, IN, OPT>(F, S, i, j, k); break;
     case kMixCells: m_cells_body<JIT, IN, OPT>(F, S, i, j, k); break;
     case kMixFluxes: m_fluxes_body<IN>(F, S, i, j, k); break;
-    case kMixRemapNodes: m_remap_nodes_body<IN>(F, S, i, j, k); break;
     case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
     case kMixDensity: m_density_body<IN>(F, S, i, j, k); break;
@@ -1082,6 +1030,21 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   // batches take neither the predictor-corrector step nor hourglass control
   if (it.F.off4) run_tile<KID, true, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
   else run_tile<KID, false, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
+}
+
+// Batched node remap: block b marches over chunk tab[b].w of the node
+// columns of tile (tab[b].y, tab[b].z) of mesh tab[b].x.
+template <int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+    kb_m_remap_nodes_march(const BatchItem *items, const int4 *tab) {
+  __shared__ BatchItem it;
+  const int4 t = tab[blockIdx.x];
+  const int tid = threadIdx.x + tile_x(SH) * threadIdx.y;
+  const int *src = reinterpret_cast<const int *>(items + t.x);
+  int *dst = reinterpret_cast<int *>(&it);
+  for (int w = tid; w < (int)(kBatchItemStaged / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
+  __syncthreads();
+  m_remap_column<SH>(it.F, it.S, t.y, t.z, t.w);
 }
 
 // Per mesh of a batch: t_end = inf, cycle_limit = cycle + cycles, decide.
@@ -1167,7 +1130,7 @@ static void launch_batch_shaped(int kid, const BatchItem *items, const int4 *tab
     case kMixNodes: kb_m<kMixNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixCells: kb_m<kMixCells, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixFluxes: kb_m<kMixFluxes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixRemapNodes: kb_m<kMixRemapNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapNodes: kb_m_remap_nodes_march<SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixRemapEos: kb_m<kMixRemapEos, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixDensity: kb_m<kMixDensity, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;

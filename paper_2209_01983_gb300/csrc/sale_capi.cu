@@ -1122,7 +1122,8 @@ struct sale_batch {
   std::vector<sale_state *> st;     // one state per mesh, carved from the batch buffer
   BatchItem *items[2];              // per velocity-buffer parity
   int4 *tab_cell, *tab_node;        // block -> (mesh, tile x, tile y, plane)
-  unsigned nb_cell, nb_node;
+  int4 *tab_chunk;                  // node remap: block -> (mesh, tile x, tile y, chunk of kRemapChunk planes)
+  unsigned nb_cell, nb_node, nb_chunk;
   BatchStatus *status;              // device gather area
   std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
   std::vector<sale_mesh_desc> meshes;
@@ -1141,7 +1142,7 @@ static unsigned cell_tiles(const sale_mesh_desc &d, int shape) { return tiles_of
 static unsigned node_tiles(const sale_mesh_desc &d, int shape) { return tiles_of(d.nx + 1, d.ny + 1, d.nz + 1, shape); }
 static void append_tiles(std::vector<int4> &tab, int mesh, int ni, int nj, int nk, int shape) {
   const int tx = tile_x(shape), ty = tile_y(shape);
-  for (int k = 0; k < nk; ++k)
+  for (int k = 0; k < nk; ++k)  // k: plane, or chunk of planes
     for (int by = 0; by < (nj + ty - 1) / ty; ++by)
       for (int bx = 0; bx < (ni + tx - 1) / tx; ++bx) tab.push_back(make_int4(mesh, bx, by, k));
 }
@@ -1166,6 +1167,8 @@ static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, s
   off = align_up(off + sizeof(int4) * nbc);
   hdr_parts[2] = off;  // node block table
   off = align_up(off + sizeof(int4) * nbn);
+  hdr_parts[4] = off;  // node-remap chunk table (no larger than the node table)
+  off = align_up(off + sizeof(int4) * nbn);
   hdr_parts[3] = off;  // status gather
   off = align_up(off + sizeof(BatchStatus) * n);
   for (int i = 0; i < n; ++i) {
@@ -1183,7 +1186,7 @@ extern "C" size_t sale_batch_bytes(int n, const sale_mesh_desc *meshes, int prec
     if (meshes[i].nx < 1 || meshes[i].ny < 1 || meshes[i].nz < 1) return 0;
     if ((long long)(meshes[i].nx + 1) * (meshes[i].ny + 1) * (meshes[i].nz + 1) > 0x7FFFFFFFll) return 0;
   }
-  size_t parts[4];
+  size_t parts[5];
   return batch_layout(n, meshes, precision, nullptr, parts);
 }
 
@@ -1224,21 +1227,24 @@ static int upload_batch_tables(sale_batch *b) {
   for (int i = 0; i < b->n; ++i) ord[i] = i;
   if (b->order == 1)  // largest meshes first: their blocks start early, the short tail is small meshes
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return b->st[a]->nc > b->st[c]->nc; });
-  std::vector<int4> tc, tn;
+  std::vector<int4> tc, tn, tk;
   try {
     for (int i : ord) {
       const sale_mesh_desc &d = b->meshes[i];
       append_tiles(tc, i, d.nx, d.ny, d.nz, b->shape);
       append_tiles(tn, i, d.nx + 1, d.ny + 1, d.nz + 1, b->shape);
+      append_tiles(tk, i, d.nx + 1, d.ny + 1, (d.nz + 1 + kRemapChunk - 1) / kRemapChunk, b->shape);
     }
   } catch (...) {
     return fail(SALE_ENOMEM, "batch: out of host memory");
   }
   b->nb_cell = (unsigned)tc.size();
   b->nb_node = (unsigned)tn.size();
+  b->nb_chunk = (unsigned)tk.size();
   CUDA_TRY(cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, b->stream));
   CUDA_TRY(cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, b->stream));
-  CUDA_TRY(cudaStreamSynchronize(b->stream));  // tc, tn die here
+  CUDA_TRY(cudaMemcpyAsync(b->tab_chunk, tk.data(), sizeof(int4) * tk.size(), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));  // tc, tn, tk die here
   return SALE_OK;
 }
 
@@ -1260,7 +1266,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
                   i);
   }
   std::vector<size_t> soff((size_t)n);
-  size_t parts[4];
+  size_t parts[5];
   const size_t need = batch_layout(n, meshes, precision, soff.data(), parts);
   int rc = check_device_buffer("sale_batch_create", device_buf, bytes, need);
   if (rc) return rc;
@@ -1273,6 +1279,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   b->items[1] = b->items[0] + n;
   b->tab_cell = (int4 *)(base + parts[1]);
   b->tab_node = (int4 *)(base + parts[2]);
+  b->tab_chunk = (int4 *)(base + parts[4]);
   b->status = (BatchStatus *)(base + parts[3]);
   for (int i = 0; i < n; ++i) {
     sale_mesh *m = nullptr;
@@ -1312,7 +1319,7 @@ static void launch_batch_cycle(sale_batch *b, int p) {
   if (b->any_order2)  // first-order meshes leave this pass at once
     launch_m_batch(kMixDensity, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
   launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
-  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
+  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_chunk, b->nb_chunk, b->shape, b->stream);
   launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->shape, b->stream);
 }
 
