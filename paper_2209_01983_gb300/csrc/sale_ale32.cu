@@ -43,6 +43,19 @@ __device__ __forceinline__ F3 crossf(F3 a, F3 b) {
 }
 __device__ __forceinline__ float dotf(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
+// The same products with every rounding fixed by intrinsics: the compiler
+// may contract a * b + c * d either way, and may choose differently in two
+// kernels that inline the same function (a batch block and a single-mesh
+// block of the remap + EoS pass); the quantities a batch must reproduce
+// bitwise go through these.
+__device__ __forceinline__ float dot_rn(F3 a, F3 b) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmul_rn(a.x, b.x)));
+}
+__device__ __forceinline__ F3 cross_rn(F3 a, F3 b) {
+  return {__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
+          __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x))};
+}
+
 // ---------------------------------------------------------------------------
 // Float-float arithmetic for the conserved cell quantities
 // ---------------------------------------------------------------------------
@@ -139,7 +152,7 @@ __device__ __forceinline__ float grad_dot_f(const F3 (&X)[8], const F3 (&U)[8]) 
       const F3 pa = X[face_node(f, (k + 1) & 3)];
       const F3 pb = X[face_node(f, (k + 2) & 3)];
       const F3 pc = X[face_node(f, (k + 3) & 3)];
-      s += dotf(crossf(pa + 2.f * pb + pc, pc - pa), U[face_node(f, k)]);
+      s = __fadd_rn(s, dot_rn(cross_rn(pa + 2.f * pb + pc, pc - pa), U[face_node(f, k)]));
     }
   }
   return s * (1.f / 24.f);
@@ -151,8 +164,11 @@ __device__ __forceinline__ float grad_dot_cached(const float *Gc, long long nc, 
   const float *g = Gc + c;
   float s = 0.f;
 #pragma unroll
-  for (int a = 0; a < 8; ++a)
-    s += __ldg(g + (3 * a) * nc) * U[a].x + __ldg(g + (3 * a + 1) * nc) * U[a].y + __ldg(g + (3 * a + 2) * nc) * U[a].z;
+  for (int a = 0; a < 8; ++a) {
+    s = __fmaf_rn(__ldg(g + (3 * a) * nc), U[a].x, s);
+    s = __fmaf_rn(__ldg(g + (3 * a + 1) * nc), U[a].y, s);
+    s = __fmaf_rn(__ldg(g + (3 * a + 2) * nc), U[a].z, s);
+  }
   return s;
 }
 
@@ -871,36 +887,37 @@ __device__ __forceinline__ float m_eos_cell(const Fields<float> &F, int c, int i
     ref_hex2<JIT>(F, n0, sy, sz, E);
     dvdt = grad_dot_f(E, U);
   }
+  // every rounding fixed (see dot_rn): sigma and the CFL step feed the
+  // next cycle of every kernel that calls this
   const float V = F.VE[c];
   const float inv_v = 1.f / V;
-  const float div = dvdt * inv_v;
+  const float div = __fmul_rn(dvdt, inv_v);
   const float L = F.LE[c];
-  const float rho = m * inv_v;
+  const float rho = __fmul_rn(m, inv_v);
   const float g = F.gamma32;
-  const float p = (g - 1.f) * rho * e;
-  const float cs = sqrtf(g * (g - 1.f) * fmaxf(e, 0.f));
+  const float p = __fmul_rn(__fmul_rn(g - 1.f, rho), e);
+  const float cs = sqrtf(__fmul_rn(__fmul_rn(g, g - 1.f), fmaxf(e, 0.f)));
   float q_rho = 0.f;
   if (div < 0.f) {
-    const float ld = L * div;
-    q_rho = F.c_q32 * ld * ld + F.c_l32 * cs * L * fabsf(div);
+    const float ld = __fmul_rn(L, div);
+    q_rho = __fmaf_rn(__fmul_rn(F.c_q32, ld), ld, __fmul_rn(__fmul_rn(__fmul_rn(F.c_l32, cs), L), fabsf(div)));
   }
-  const float q = rho * q_rho;
+  const float q = __fmul_rn(rho, q_rho);
   F.rho[c] = rho;
-  F.sig[c] = p + q;
+  F.sig[c] = __fadd_rn(p, q);
   if (store_all) {
     F.p[c] = p;
     F.q[c] = q;
     F.cs[c] = cs;
     F.vol[c] = V;
   }
-  return F.cfl32 * L / sqrtf(cs * cs + 2.f * q_rho);
+  return __fdiv_rn(__fmul_rn(F.cfl32, L), sqrtf(__fmaf_rn(cs, cs, 2.f * q_rho)));
 }
 
-// Cell remap + EoS + dt; nblk = blocks of this mesh (last-block detection).
+// Cell remap + EoS of cell (i,j,k) in an active cycle; returns its CFL
+// step (infinite outside the mesh).
 template <bool JIT, bool IN>
-__device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScalars *S, int i, int j, int k,
-                                                 unsigned nblk) {
-  if (!S->next_active) return;  // uniform over the mesh's blocks: S changes only in its last block
+__device__ __forceinline__ float m_remap_eos_cell(const Fields<float> &F, DevScalars *S, int i, int j, int k) {
   float dtc = INFINITY;
   if (IN || (i < F.nx && j < F.ny && k < F.nz)) {
     const int sy = F.nx, sz = F.nx * F.ny;
@@ -939,7 +956,7 @@ __device__ __forceinline__ void m_remap_eos_body(const Fields<float> &F, DevScal
     const float d = m_eos_cell<JIT>(F, c, i, j, k, m1.hi, e1.hi, false);
     dtc = d == d ? d : (set_status(S, SALE_ENAN), INFINITY);
   }
-  block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, 0.0, nblk);
+  return dtc;
 }
 
 // EoS/viscosity/dt without a remap: kDtInit / kDtPropose, or no dt at all
@@ -973,7 +990,6 @@ __device__ __forceinline__ void run_body(int kid, const Fields<float> &F, DevSca
     case kMixNodes: m_nodes_body<JIT, IN, OPT>(F, S, i, j, k); break;
     case kMixCells: m_cells_body<JIT, IN, OPT>(F, S, i, j, k); break;
     case kMixFluxes: m_fluxes_body<IN>(F, S, i, j, k); break;
-    case kMixRemapEos: m_remap_eos_body<JIT, IN>(F, S, i, j, k, nblk); break;
     case kMixEos: m_eos_body<JIT>(F, S, i, j, k, mode, nblk); break;
     case kMixDensity: m_density_body<IN>(F, S, i, j, k); break;
     case kMixPredict: m_predict_body<JIT, IN>(F, S, i, j, k); break;
@@ -1032,6 +1048,47 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   else run_tile<KID, false, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
 }
 
+// Remap + EoS + dt of tile (bx, by) over the cell planes of chunk kc (of
+// kEosPlanes): the blocks' dt minima, two same-address atomics each, are
+// kEosPlanes times fewer than with one plane per block, and the minimum is
+// exact.  nblk = blocks of this mesh (last-block detection).
+template <bool JIT, int SH>
+__device__ __forceinline__ void m_remap_eos_column(const Fields<float> &F, DevScalars *S, int bx, int by, int kc,
+                                                   unsigned nblk) {
+  if (!S->next_active) return;  // uniform over the mesh's blocks: S changes only in its last block
+  const int i = bx * tile_x(SH) + threadIdx.x, j = by * tile_y(SH) + threadIdx.y;
+  const int k0 = kc * kEosPlanes, k1 = min(k0 + kEosPlanes, F.nz);
+  float dtc = INFINITY;
+  for (int k = k0; k < k1; ++k) {
+    const float d = tile_interior<SH>(F, bx, by, k) ? m_remap_eos_cell<JIT, true>(F, S, i, j, k)
+                                                    : m_remap_eos_cell<JIT, false>(F, S, i, j, k);
+    dtc = fminf(dtc, d);
+  }
+  block_min_dt32_and_finalize(F, S, dtc, kDtAdvance, 0.0, nblk);
+}
+
+template <bool JIT, int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+    k_m_remap_eos_planes(Fields<float> F, DevScalars *S) {
+  m_remap_eos_column<JIT, SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y * gridDim.z);
+}
+
+// Batched remap + EoS + dt: block b covers chunk tab[b].w of tile
+// (tab[b].y, tab[b].z) of mesh tab[b].x.
+template <int SH>
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+    kb_m_remap_eos_planes(const BatchItem *items, const int4 *tab) {
+  __shared__ BatchItem it;
+  const int4 t = tab[blockIdx.x];
+  const int tid = threadIdx.x + tile_x(SH) * threadIdx.y;
+  const int *src = reinterpret_cast<const int *>(items + t.x);
+  int *dst = reinterpret_cast<int *>(&it);
+  for (int w = tid; w < (int)(kBatchItemStaged / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
+  __syncthreads();
+  if (it.F.off4) m_remap_eos_column<true, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell);
+  else m_remap_eos_column<false, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell);
+}
+
 // Batched node remap: block b marches over chunk tab[b].w of the node
 // columns of tile (tab[b].y, tab[b].z) of mesh tab[b].x.
 template <int SH>
@@ -1084,6 +1141,12 @@ static void launch_shaped(const Fields<float> &F, DevScalars *S, int mode, cudaS
     k_m_remap_nodes_march<SH><<<g, dim3(tile_x(SH), tile_y(SH)), 0, st>>>(F, S);
     return;
   }
+  if constexpr (KID == kMixRemapEos) {
+    const dim3 g = tile_grid(F.nx, F.ny, (F.nz + kEosPlanes - 1) / kEosPlanes, SH);
+    if (F.off4) k_m_remap_eos_planes<true, SH><<<g, dim3(tile_x(SH), tile_y(SH)), 0, st>>>(F, S);
+    else k_m_remap_eos_planes<false, SH><<<g, dim3(tile_x(SH), tile_y(SH)), 0, st>>>(F, S);
+    return;
+  }
   const bool node = KID == kMixNodes || KID == kMixRemapNodes;
   const dim3 g = node ? tile_grid(F.nx + 1, F.ny + 1, F.nz + 1, SH) : tile_grid(F.nx, F.ny, F.nz, SH);
   const dim3 b(tile_x(SH), tile_y(SH));
@@ -1131,7 +1194,7 @@ static void launch_batch_shaped(int kid, const BatchItem *items, const int4 *tab
     case kMixCells: kb_m<kMixCells, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixFluxes: kb_m<kMixFluxes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixRemapNodes: kb_m_remap_nodes_march<SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixRemapEos: kb_m<kMixRemapEos, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapEos: kb_m_remap_eos_planes<SH><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixDensity: kb_m<kMixDensity, SH><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;
   }

@@ -1123,7 +1123,8 @@ struct sale_batch {
   BatchItem *items[2];              // per velocity-buffer parity
   int4 *tab_cell, *tab_node;        // block -> (mesh, tile x, tile y, plane)
   int4 *tab_chunk;                  // node remap: block -> (mesh, tile x, tile y, chunk of kRemapChunk planes)
-  unsigned nb_cell, nb_node, nb_chunk;
+  int4 *tab_eos;                    // remap + EoS: block -> (mesh, tile x, tile y, chunk of kEosPlanes planes)
+  unsigned nb_cell, nb_node, nb_chunk, nb_eos;
   BatchStatus *status;              // device gather area
   std::vector<int> item_upar;       // each mesh's velocity parity when the descriptors were built
   std::vector<sale_mesh_desc> meshes;
@@ -1169,6 +1170,8 @@ static size_t batch_layout(int n, const sale_mesh_desc *meshes, int precision, s
   off = align_up(off + sizeof(int4) * nbn);
   hdr_parts[4] = off;  // node-remap chunk table (no larger than the node table)
   off = align_up(off + sizeof(int4) * nbn);
+  hdr_parts[5] = off;  // remap + EoS chunk table (no larger than the cell table)
+  off = align_up(off + sizeof(int4) * nbc);
   hdr_parts[3] = off;  // status gather
   off = align_up(off + sizeof(BatchStatus) * n);
   for (int i = 0; i < n; ++i) {
@@ -1186,7 +1189,7 @@ extern "C" size_t sale_batch_bytes(int n, const sale_mesh_desc *meshes, int prec
     if (meshes[i].nx < 1 || meshes[i].ny < 1 || meshes[i].nz < 1) return 0;
     if ((long long)(meshes[i].nx + 1) * (meshes[i].ny + 1) * (meshes[i].nz + 1) > 0x7FFFFFFFll) return 0;
   }
-  size_t parts[5];
+  size_t parts[6];
   return batch_layout(n, meshes, precision, nullptr, parts);
 }
 
@@ -1210,7 +1213,7 @@ static int upload_batch_items(sale_batch *b) {
       h[i].F = fields_t<float>(st);
       st->upar = keep;
       h[i].S = st->S;
-      h[i].nblk_cell = tiles_of(st->nx, st->ny, st->nz, b->shape);
+      h[i].nblk_cell = tiles_of(st->nx, st->ny, (st->nz + kEosPlanes - 1) / kEosPlanes, b->shape);
       h[i].pad = 0;
     }
     CUDA_TRY(cudaMemcpyAsync(b->items[rel], h.data(), sizeof(BatchItem) * b->n, cudaMemcpyHostToDevice, b->stream));
@@ -1227,13 +1230,14 @@ static int upload_batch_tables(sale_batch *b) {
   for (int i = 0; i < b->n; ++i) ord[i] = i;
   if (b->order == 1)  // largest meshes first: their blocks start early, the short tail is small meshes
     std::stable_sort(ord.begin(), ord.end(), [&](int a, int c) { return b->st[a]->nc > b->st[c]->nc; });
-  std::vector<int4> tc, tn, tk;
+  std::vector<int4> tc, tn, tk, te;
   try {
     for (int i : ord) {
       const sale_mesh_desc &d = b->meshes[i];
       append_tiles(tc, i, d.nx, d.ny, d.nz, b->shape);
       append_tiles(tn, i, d.nx + 1, d.ny + 1, d.nz + 1, b->shape);
       append_tiles(tk, i, d.nx + 1, d.ny + 1, (d.nz + 1 + kRemapChunk - 1) / kRemapChunk, b->shape);
+      append_tiles(te, i, d.nx, d.ny, (d.nz + kEosPlanes - 1) / kEosPlanes, b->shape);
     }
   } catch (...) {
     return fail(SALE_ENOMEM, "batch: out of host memory");
@@ -1241,10 +1245,12 @@ static int upload_batch_tables(sale_batch *b) {
   b->nb_cell = (unsigned)tc.size();
   b->nb_node = (unsigned)tn.size();
   b->nb_chunk = (unsigned)tk.size();
+  b->nb_eos = (unsigned)te.size();
   CUDA_TRY(cudaMemcpyAsync(b->tab_cell, tc.data(), sizeof(int4) * tc.size(), cudaMemcpyHostToDevice, b->stream));
   CUDA_TRY(cudaMemcpyAsync(b->tab_node, tn.data(), sizeof(int4) * tn.size(), cudaMemcpyHostToDevice, b->stream));
   CUDA_TRY(cudaMemcpyAsync(b->tab_chunk, tk.data(), sizeof(int4) * tk.size(), cudaMemcpyHostToDevice, b->stream));
-  CUDA_TRY(cudaStreamSynchronize(b->stream));  // tc, tn, tk die here
+  CUDA_TRY(cudaMemcpyAsync(b->tab_eos, te.data(), sizeof(int4) * te.size(), cudaMemcpyHostToDevice, b->stream));
+  CUDA_TRY(cudaStreamSynchronize(b->stream));  // tc, tn, tk, te die here
   return SALE_OK;
 }
 
@@ -1266,7 +1272,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
                   i);
   }
   std::vector<size_t> soff((size_t)n);
-  size_t parts[5];
+  size_t parts[6];
   const size_t need = batch_layout(n, meshes, precision, soff.data(), parts);
   int rc = check_device_buffer("sale_batch_create", device_buf, bytes, need);
   if (rc) return rc;
@@ -1280,6 +1286,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   b->tab_cell = (int4 *)(base + parts[1]);
   b->tab_node = (int4 *)(base + parts[2]);
   b->tab_chunk = (int4 *)(base + parts[4]);
+  b->tab_eos = (int4 *)(base + parts[5]);
   b->status = (BatchStatus *)(base + parts[3]);
   for (int i = 0; i < n; ++i) {
     sale_mesh *m = nullptr;
@@ -1320,7 +1327,7 @@ static void launch_batch_cycle(sale_batch *b, int p) {
     launch_m_batch(kMixDensity, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
   launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
   launch_m_batch(kMixRemapNodes, b->items[p], b->tab_chunk, b->nb_chunk, b->shape, b->stream);
-  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_cell, b->nb_cell, b->shape, b->stream);
+  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_eos, b->nb_eos, b->shape, b->stream);
 }
 
 extern "C" int sale_batch_set_schedule(sale_batch *b, int shape, int order) {
