@@ -501,10 +501,10 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
   F.sig[c] = p + q;
 }
 
-__global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
-  if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
-  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double rate = 0.0;  // CFL rate 1 / dt_c^2
+// Cell remap + EoS of cell c; returns its CFL rate 1 / dt_c^2 (0 outside
+// the mesh).
+__device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, DevScalars *S, long long c) {
+  double rate = 0.0;
   if (c < F.nc) {
     int i, j, k;
     cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -539,6 +539,20 @@ __global__ void __launch_bounds__(kBlock) k_ale_remap_eos(Fields<double> F, DevS
       rate = 0.0;
     }
   }
+  return rate;
+}
+
+// A thread takes kEosCellsPerThread cells, kBlock apart, so the blocks' dt
+// minima (two same-address atomics each) are that many times fewer; the
+// largest rate is exact, and dt with it.
+constexpr int kEosCellsPerThread = 4;
+
+__global__ void __launch_bounds__(kBlock, 3) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
+  if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
+  const long long c0 = blockIdx.x * (long long)(kBlock * kEosCellsPerThread) + threadIdx.x;
+  double rate = 0.0;  // CFL rate 1 / dt_c^2
+#pragma unroll 1
+  for (int r = 0; r < kEosCellsPerThread; ++r) rate = fmax(rate, ale_remap_eos_cell(F, S, c0 + (long long)r * kBlock));
   block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
 }
 
@@ -584,7 +598,10 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
       break;
     case kAleRemapNodes: k_ale_remap_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S); break;
     case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
-    case kAleRemapEos: k_ale_remap_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAleRemapEos:
+      k_ale_remap_eos<<<grid_ale((F.nc + kEosCellsPerThread - 1) / kEosCellsPerThread), kBlock, 0, st>>>(F, S,
+                                                                                                      dt_override);
+      break;
     default: break;
   }
 }
