@@ -333,6 +333,12 @@ def measure(args, precision, local, barrier):
             "cycle_tflops": cycle_flops * args.steps / secs / 1e12,
             "cycle_hbm_gbs": cycle_bytes * args.steps / secs / 1e9,
             "cycle_hbm_frac_of_measured": cycle_bytes * args.steps / secs / 1e9 / peaks["hbm_gbs"]}
+    # the unique-state minimum (every persistent field read and written once
+    # per cycle): 320 B per cell in FP64, 160 B in FP32
+    min_b = 320 if precision == "fp64" else 160
+    full["min_bytes_per_cell"] = min_b
+    full["min_bytes_gbs"] = min_b * md.ncell * args.steps / secs / 1e9
+    full["min_bytes_frac_of_measured"] = full["min_bytes_gbs"] / peaks["hbm_gbs"]
     launches = sum(v[1] for v in kern.values())
     d = st.diagnostics()
     return {"st": st, "md": md, "ms": ms, "roofline": roof, "kernels": kernels, "full_cycle": full,
