@@ -85,6 +85,27 @@ __global__ void __launch_bounds__(kBlock) k_geo_init(Fields<double> F, DevScalar
   TE[2 * F.nc + c] = quad_term(X[0], X[1], X[3], X[2]);
 }
 
+// Reference offsets from every node to the six neighbours the edge pass
+// reads (+x, +y, +z, yz, xz, xy): the same subtractions it would otherwise
+// repeat every cycle.
+__global__ void __launch_bounds__(kBlock) k_geo_init_nodes(Fields<double> F, double *rE) {
+  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (n >= F.nn) return;
+  int i, j, k;
+  node_ijk(n, F.nx, F.ny, i, j, k);
+  const long long sx = 1, sy = F.nx + 1, sz = (long long)(F.nx + 1) * (F.ny + 1);
+  const bool in[6] = {i < F.nx, j < F.ny, k < F.nz, j < F.ny && k < F.nz, i < F.nx && k < F.nz,
+                      i < F.nx && j < F.ny};
+  const long long b[6] = {n + sx, n + sy, n + sz, n + sy + sz, n + sx + sz, n + sx + sy};
+#pragma unroll
+  for (int s = 0; s < 6; ++s) {
+    const bool ok = in[s];
+    rE[(3ll * s + 0) * F.nn + n] = ok ? F.xr[b[s]] - F.xr[n] : 0.0;
+    rE[(3ll * s + 1) * F.nn + n] = ok ? F.yr[b[s]] - F.yr[n] : 0.0;
+    rE[(3ll * s + 2) * F.nn + n] = ok ? F.zr[b[s]] - F.zr[n] : 0.0;
+  }
+}
+
 __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScalars *S, double dt_override) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= F.nn || !cycle_active(S)) return;
@@ -146,32 +167,27 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   node_ijk(n, F.nx, F.ny, i, j, k);
   const int ijk[3] = {i, j, k};
   const long long stride[3] = {1, F.nx + 1, (long long)(F.nx + 1) * (F.ny + 1)};
-  const P3 xa = {F.xr[n], F.yr[n], F.zr[n]};
   const P3 La = h * P3{F.ub[n], F.vb[n], F.wb[n]};
-  auto rel = [&](long long b, P3 &E) {  // reference and Lagrangian position of node b relative to x_n
-    E = P3{F.xr[b], F.yr[b], F.zr[b]} - xa;
+  const long long nn = F.nn;
+  auto off = [&](int slot, long long m) {  // cached reference offset of node m to its neighbour in slot
+    return P3{F.rE[(3ll * slot) * nn + m], F.rE[(3ll * slot + 1) * nn + m], F.rE[(3ll * slot + 2) * nn + m]};
+  };
+  auto rel = [&](int slot, long long b, P3 &E) {  // reference and Lagrangian position of node b relative to x_n
+    E = off(slot, n);
     return E + h * P3{F.ub[b], F.vb[b], F.wb[b]};
   };
   // x_n minus its -x, -y, -z neighbours: the origin shifts of the side quads
   P3 back[3];
 #pragma unroll
-  for (int a = 0; a < 3; ++a) {
-    if (ijk[a] > 0) {
-      const long long o = n - stride[a];
-      back[a] = xa - P3{F.xr[o], F.yr[o], F.zr[o]};
-    } else {
-      back[a] = {0.0, 0.0, 0.0};
-    }
-  }
+  for (int a = 0; a < 3; ++a) back[a] = ijk[a] > 0 ? off(a, n - stride[a]) : P3{0.0, 0.0, 0.0};
   P3 Lb[3], Eb;
-  if (i < F.nx) { Lb[0] = rel(n + stride[0], Eb); edge_side_terms<0>(F, n, ijk, back, La, Eb, Lb[0]); }
-  if (j < F.ny) { Lb[1] = rel(n + stride[1], Eb); edge_side_terms<1>(F, n, ijk, back, La, Eb, Lb[1]); }
-  if (k < F.nz) { Lb[2] = rel(n + stride[2], Eb); edge_side_terms<2>(F, n, ijk, back, La, Eb, Lb[2]); }
+  if (i < F.nx) { Lb[0] = rel(0, n + stride[0], Eb); edge_side_terms<0>(F, n, ijk, back, La, Eb, Lb[0]); }
+  if (j < F.ny) { Lb[1] = rel(1, n + stride[1], Eb); edge_side_terms<1>(F, n, ijk, back, La, Eb, Lb[1]); }
+  if (k < F.nz) { Lb[2] = rel(2, n + stride[2], Eb); edge_side_terms<2>(F, n, ijk, back, La, Eb, Lb[2]); }
   if (i < F.nx && j < F.ny && k < F.nz) {
-    const P3 Lyz = rel(n + stride[1] + stride[2], Eb), Lxz = rel(n + stride[0] + stride[2], Eb),
-             Lxy = rel(n + stride[0] + stride[1], Eb);
+    const P3 Lyz = rel(3, n + stride[1] + stride[2], Eb), Lxz = rel(4, n + stride[0] + stride[2], Eb),
+             Lxy = rel(5, n + stride[0] + stride[1], Eb);
     const long long c = cell_index(F.nx, F.ny, i, j, k);
-    const long long nn = F.nn;
     F.ste[9 * nn + n] = quad_term(La, Lb[2], Lyz, Lb[1]) + F.TE[c];
     F.ste[10 * nn + n] = quad_term(La, Lb[0], Lxz, Lb[2]) + F.TE[F.nc + c];
     F.ste[11 * nn + n] = quad_term(La, Lb[1], Lxy, Lb[0]) + F.TE[2 * F.nc + c];
@@ -577,6 +593,10 @@ __global__ void __launch_bounds__(kBlock) k_ale_eos(Fields<double> F, DevScalars
 }
 
 static inline unsigned grid_ale(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+void launch_geo_init_nodes(const Fields<double> &F, double *rE, cudaStream_t st) {
+  k_geo_init_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, rE);
+}
 
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st) {
