@@ -40,14 +40,17 @@ FP64 = {
 # the swept hexes computed once per mesh edge (k_ale_edges) instead of once
 # per cell that uses them.
 QUAD = 29  # fan term of one quad: 4-point sum 9, diagonals 6, cross 9, dot 5
-EDGES = 3 * QUAD + 9 + 3 + 18 + 9 + 6 * 7  # 3 side quads, relative positions, L, shifts
+# 3 side quads, Lagrangian offsets, L, origin shifts; the reference offsets
+# to the neighbours are cached (read, not subtracted)
+EDGES = 3 * QUAD + 9 + 3 + 6 * 7
 
 FP64_ALE = {
     # sigma, G (24/cell), u, mn read; u, ubar, 0.5|u|^2 written
     "ale_nodes": ("node", 8 * (1 + 24 + 3 + 1 + 3 + 3 + 1), 48 + 20 + 5),
-    # x_ref, ubar, 3 reference-face terms read; 9 side-quad terms and 3
-    # Lagrangian + reference low-face terms written
-    "ale_edges": ("node", 8 * (3 + 3 + 3 + 12), EDGES + 3 * QUAD + 27 + 3),
+    # reference offsets to 6 neighbours (18), ubar, 3 reference-face terms
+    # read; 9 side-quad terms and 3 Lagrangian + reference low-face terms
+    # written
+    "ale_edges": ("node", 8 * (18 + 3 + 3 + 12), EDGES + 3 * QUAD + 27 + 3),
     # G, ubar, m, e, sigma, 12 swept-hex terms read; e, 3 swept volumes written
     "ale_cells": ("cell", 8 * (24 + 3 + 3 + 12 + 1 + 3), 48 + 5 + 12 + 3),
     # 3 swept volumes, V_E, m read; V_L, rho_L written
