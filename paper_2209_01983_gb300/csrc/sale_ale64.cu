@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   }
 }
 
-__global__ void __launch_bounds__(kBlock) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
+__global__ void __launch_bounds__(kBlock, 4) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   const double h = step_dt(S, dt_override);
