@@ -341,77 +341,99 @@ __global__ void __launch_bounds__(kBlock) k_ale_fluxes(Fields<double> F, DevScal
   ale_face_flux<2, O2>(F, c, k, F.nz, F.dvz, F.muz, F.epz, F.mqz);
 }
 
-// Dual mass flux of the mesh edge from node (i,j,k) to its +AX neighbour:
-// the sum of the dual-flux parts of the (up to four) cells around the edge.
-template <int AX>
-__device__ __forceinline__ double ale_edge_psi(const Fields<double> &F, int i, int j, int k) {
-  const double *mq = AX == 0 ? F.mqx : AX == 1 ? F.mqy : F.mqz;
-  double psi = -0.0;  // -0 + x = x for every x: the first addition folds away
-#pragma unroll
-  for (int s = 0; s < 4; ++s) {
-    int ci = i, cj = j, ck = k;
-    if (AX == 0) { cj = j - 1 + (s & 1); ck = k - 1 + (s >> 1); }
-    if (AX == 1) { ci = i - 1 + (s & 1); ck = k - 1 + (s >> 1); }
-    if (AX == 2) { ci = i - 1 + (s & 1); cj = j - 1 + (s >> 1); }
-    if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
-    psi += mq[cell_index(F.nx, F.ny, ci, cj, ck)];
-  }
-  return psi;
-}
-
-// Upwind transport of mass, momentum and kinetic energy across one edge on
-// the low (SIDE = 0: edge from this node to +AX) or high (SIDE = 1: from
-// the -AX neighbour) side of the node.
+// Upwind transport of mass, momentum and kinetic energy into node n across
+// one of its edges, whose dual flux is psi (positive: towards +AX), on the
+// low (SIDE = 0: edge from this node to +AX) or high (SIDE = 1: from the
+// -AX neighbour) side of the node.
 template <int AX, int SIDE>
-__device__ __forceinline__ void ale_node_edge(const Fields<double> &F, int i, int j, int k, long long n, double &m,
-                                              P3 &p, double &ke) {
-  const int idx = AX == 0 ? i : AX == 1 ? j : k;
-  const int n_ax = AX == 0 ? F.nx : AX == 1 ? F.ny : F.nz;
-  if (SIDE == 0 && idx == n_ax) return;
-  if (SIDE == 1 && idx == 0) return;
-  const double psi = ale_edge_psi<AX>(F, (SIDE == 1 && AX == 0) ? i - 1 : i, (SIDE == 1 && AX == 1) ? j - 1 : j,
-                                      (SIDE == 1 && AX == 2) ? k - 1 : k);
+__device__ __forceinline__ void ale_edge_apply(const Fields<double> &F, long long n, double psi, double &m, P3 &p,
+                                               double &ke) {
   const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)(F.nx + 1) : (long long)(F.nx + 1) * (F.ny + 1);
   const long long lo = SIDE == 0 ? n : n - stride;
   const long long dn = psi > 0.0 ? lo + stride : lo;
-  const double sgn = SIDE == 0 ? 1.0 : -1.0;
-  m += sgn * psi;
-  p.x += sgn * psi * F.u[dn];
-  p.y += sgn * psi * F.v[dn];
-  p.z += sgn * psi * F.w[dn];
-  ke += sgn * psi * F.kd[dn];
+  const double flux = SIDE == 0 ? psi : -psi;
+  m += flux;
+  p.x += flux * F.u[dn];
+  p.y += flux * F.v[dn];
+  p.z += flux * F.w[dn];
+  ke += flux * F.kd[dn];
 }
 
-__global__ void __launch_bounds__(kBlock) k_ale_remap_nodes(Fields<double> F, DevScalars *S) {
-  const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  if (n >= F.nn) return;
+// Dual-flux part (mu_low + mu_high) / 8 of cell (ci, cj, ck) along one
+// axis; zero outside the mesh.
+__device__ __forceinline__ double mq_at(const double *mq, const Fields<double> &F, int ci, int cj, int ck) {
+  if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) return 0.0;
+  return mq[cell_index(F.nx, F.ny, ci, cj, ck)];
+}
+
+// Node remap marching in k: a block covers a tile of node columns over
+// kAleRemapChunk node planes.  The dual flux of a mesh edge is the sum of
+// the dual-flux parts of the (up to) four cells around it; for an x- or
+// y-edge two of them lie in the cell plane below the node and two above, and
+// the pair above one node is the pair below the next, and the k-edge below a
+// node is the k-edge above the node beneath it: a column adds each pair and
+// each k-edge flux once.
+constexpr int kAleRemapChunk = 16;
+constexpr int kAleTx = 32, kAleTy = 8;
+
+__global__ void __launch_bounds__(kAleTx * kAleTy) k_ale_remap_nodes(Fields<double> F, DevScalars *S) {
+  const int i = blockIdx.x * kAleTx + threadIdx.x, j = blockIdx.y * kAleTy + threadIdx.y;
+  const int k0 = blockIdx.z * kAleRemapChunk, k1 = min(k0 + kAleRemapChunk, F.nz + 1);
+  if (i > F.nx || j > F.ny) return;
+  const long long sz = (long long)(F.nx + 1) * (F.ny + 1);
+  const long long n0 = i + (long long)(F.nx + 1) * j;
   if (!cycle_active(S)) {  // inactive cycle: velocity carries over unchanged
-    F.ub[n] = F.u[n];
-    F.vb[n] = F.v[n];
-    F.wb[n] = F.w[n];
+    for (int k = k0; k < k1; ++k) {
+      const long long n = n0 + sz * k;
+      F.ub[n] = F.u[n];
+      F.vb[n] = F.v[n];
+      F.wb[n] = F.w[n];
+    }
     return;
   }
-  int i, j, k;
-  node_ijk(n, F.nx, F.ny, i, j, k);
-  const double m0 = F.mn[n];
-  double m = m0;
-  P3 p = {m0 * F.u[n], m0 * F.v[n], m0 * F.w[n]};
-  double ke = m0 * F.kd[n];
-  ale_node_edge<0, 0>(F, i, j, k, n, m, p, ke);
-  ale_node_edge<0, 1>(F, i, j, k, n, m, p, ke);
-  ale_node_edge<1, 0>(F, i, j, k, n, m, p, ke);
-  ale_node_edge<1, 1>(F, i, j, k, n, m, p, ke);
-  ale_node_edge<2, 0>(F, i, j, k, n, m, p, ke);
-  ale_node_edge<2, 1>(F, i, j, k, n, m, p, ke);
-  if (!(m > 0.0)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
-  const double inv_m = 1.0 / m;
-  double u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
-  wall_bc(F, i, j, k, u1, v1, w1);
-  F.ub[n] = u1;
-  F.vb[n] = v1;
-  F.wb[n] = w1;
-  F.mn[n] = m;
-  F.dke[n] = ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1);
+  // pairs of the x-edges (at ci = i, i - 1) and y-edges (at cj = j, j - 1)
+  // in cell plane ck, and the k-edge flux through cell plane ck
+  auto pairs = [&](int ck, double (&pr)[4]) {
+    pr[0] = mq_at(F.mqx, F, i, j - 1, ck) + mq_at(F.mqx, F, i, j, ck);
+    pr[1] = mq_at(F.mqx, F, i - 1, j - 1, ck) + mq_at(F.mqx, F, i - 1, j, ck);
+    pr[2] = mq_at(F.mqy, F, i - 1, j, ck) + mq_at(F.mqy, F, i, j, ck);
+    pr[3] = mq_at(F.mqy, F, i - 1, j - 1, ck) + mq_at(F.mqy, F, i, j - 1, ck);
+  };
+  auto kflux = [&](int ck) {
+    return mq_at(F.mqz, F, i - 1, j - 1, ck) + mq_at(F.mqz, F, i, j - 1, ck) + mq_at(F.mqz, F, i - 1, j, ck) +
+           mq_at(F.mqz, F, i, j, ck);
+  };
+  double below[4];
+  pairs(k0 - 1, below);
+  double psi_below = kflux(k0 - 1);
+  for (int k = k0; k < k1; ++k) {
+    double above[4];
+    pairs(k, above);
+    const double psi_above = kflux(k);
+    const long long n = n0 + sz * k;
+    const double m0 = F.mn[n];
+    double m = m0;
+    P3 p = {m0 * F.u[n], m0 * F.v[n], m0 * F.w[n]};
+    double ke = m0 * F.kd[n];
+    if (i != F.nx) ale_edge_apply<0, 0>(F, n, below[0] + above[0], m, p, ke);
+    if (i != 0) ale_edge_apply<0, 1>(F, n, below[1] + above[1], m, p, ke);
+    if (j != F.ny) ale_edge_apply<1, 0>(F, n, below[2] + above[2], m, p, ke);
+    if (j != 0) ale_edge_apply<1, 1>(F, n, below[3] + above[3], m, p, ke);
+    if (k != F.nz) ale_edge_apply<2, 0>(F, n, psi_above, m, p, ke);
+    if (k != 0) ale_edge_apply<2, 1>(F, n, psi_below, m, p, ke);
+    if (!(m > 0.0)) set_status(S, m != m ? SALE_ENAN : SALE_ENEGVOL);
+    const double inv_m = 1.0 / m;
+    double u1 = p.x * inv_m, v1 = p.y * inv_m, w1 = p.z * inv_m;
+    wall_bc(F, i, j, k, u1, v1, w1);
+    F.ub[n] = u1;
+    F.vb[n] = v1;
+    F.wb[n] = w1;
+    F.mn[n] = m;
+    F.dke[n] = ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) below[q] = above[q];
+    psi_below = psi_above;
+  }
 }
 
 // EoS and viscosity of cell c on the reference mesh (cached gradient,
@@ -616,7 +638,12 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
       if (F.remap_order == 2) k_ale_fluxes<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
       else k_ale_fluxes<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
       break;
-    case kAleRemapNodes: k_ale_remap_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S); break;
+    case kAleRemapNodes: {
+      const dim3 g((unsigned)((F.nx + kAleTx) / kAleTx), (unsigned)((F.ny + kAleTy) / kAleTy),
+                   (unsigned)((F.nz + kAleRemapChunk) / kAleRemapChunk));
+      k_ale_remap_nodes<<<g, dim3(kAleTx, kAleTy), 0, st>>>(F, S);
+      break;
+    }
     case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
     case kAleRemapEos:
       k_ale_remap_eos<<<grid_ale((F.nc + kEosCellsPerThread - 1) / kEosCellsPerThread), kBlock, 0, st>>>(F, S,
