@@ -41,7 +41,16 @@ def interior_sedov():
     return md, pd
 
 
-@pytest.mark.parametrize("mesh", [ragged_sedov, interior_sedov])
+def interior_plain():
+    # the same on an unjittered mesh (geometry from the spacing, no gradient
+    # cache)
+    md, pd = inputs.sedov_octant(6)
+    md = inputs.MeshDesc(70, 20, 6, lo=md.lo, hi=(1.2 * 70 / 6, 1.2 * 20 / 6, 1.2), seed=md.seed,
+                         reflect=md.reflect)
+    return md, pd
+
+
+@pytest.mark.parametrize("mesh", [ragged_sedov, interior_sedov, interior_plain])
 def test_state_tile_shapes_bitwise(sale, mesh):
     from paper_2209_01983_gb300 import autotune
     md, pd = mesh()
