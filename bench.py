@@ -39,7 +39,8 @@ UNIT = "cell-updates/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed cycles (default 20; 200 for --config batch, the batch workload's cycles per mesh)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=("ours", "reference"))
     ap.add_argument("--precision", default="both", choices=("fp64", "fp32_mixed", "both"))
@@ -65,6 +66,8 @@ def parse():
     args = ap.parse_args()
     if args.n is None:
         args.n = 256 if args.config == "precision" else 384
+    if args.steps is None:
+        args.steps = 200 if args.config == "batch" else 20
     return args
 
 
