@@ -856,8 +856,11 @@ __device__ __forceinline__ void m_remap_column(const Fields<float> &F, DevScalar
   }
 }
 
+// Threads per SM the single-mesh node remap is compiled to keep resident.
+constexpr int kRemapResident = 1024;
+
 template <int SH>
-__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kRemapResident / (tile_x(SH) * tile_y(SH)))
     k_m_remap_nodes_march(Fields<float> F, DevScalars *S) {
   m_remap_column<SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z);
 }
@@ -1048,6 +1051,11 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   else run_tile<KID, false, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
 }
 
+// Threads per SM the remap + EoS pass is compiled to keep resident (its
+// register budget), single mesh and batch.
+constexpr int kEosResident = 1280;
+constexpr int kEosResidentBatch = 1024;  // batch blocks read the descriptor from shared memory: more registers live
+
 // Remap + EoS + dt of tile (bx, by) over the cell planes of chunk kc (of
 // kEosPlanes): the blocks' dt minima, two same-address atomics each, are
 // kEosPlanes times fewer than with one plane per block, and the minimum is
@@ -1068,7 +1076,7 @@ __device__ __forceinline__ void m_remap_eos_column(const Fields<float> &F, DevSc
 }
 
 template <bool JIT, int SH>
-__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kEosResident / (tile_x(SH) * tile_y(SH)))
     k_m_remap_eos_planes(Fields<float> F, DevScalars *S) {
   m_remap_eos_column<JIT, SH>(F, S, blockIdx.x, blockIdx.y, blockIdx.z, gridDim.x * gridDim.y * gridDim.z);
 }
@@ -1076,7 +1084,7 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * 
 // Batched remap + EoS + dt: block b covers chunk tab[b].w of tile
 // (tab[b].y, tab[b].z) of mesh tab[b].x.
 template <int SH>
-__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), 1024 / (tile_x(SH) * tile_y(SH)))
+__global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kEosResidentBatch / (tile_x(SH) * tile_y(SH)))
     kb_m_remap_eos_planes(const BatchItem *items, const int4 *tab) {
   __shared__ BatchItem it;
   const int4 t = tab[blockIdx.x];
