@@ -210,9 +210,19 @@ def replica_rate(ms_local, cells_per_rank, steps, world, dist=None, device="cpu"
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "dram_traffic_per_unit_sedov160.txt")
 
 
+def source_code(text):
+    """C/C++/CUDA source without its comments and blank lines (the sources
+    hold no comment markers inside string literals)."""
+    import re
+
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", "", text)
+    return "\n".join(ln.rstrip() for ln in text.splitlines() if ln.strip())
+
+
 def source_digest():
-    """Digest of the kernel sources: the ncu traffic figures hold only for
-    the kernels they were taken on."""
+    """Digest of the kernel sources' code: the ncu traffic figures hold only
+    for the kernels they were taken on (comments do not change a kernel)."""
     import glob
     import hashlib
 
@@ -220,8 +230,8 @@ def source_digest():
     csrc = os.path.join(ROOT, "paper_2209_01983_gb300", "csrc")
     for f in sorted(glob.glob(os.path.join(csrc, "*.cu")) + glob.glob(os.path.join(csrc, "*.cuh"))):
         h.update(os.path.basename(f).encode())
-        with open(f, "rb") as fh:
-            h.update(fh.read())
+        with open(f, encoding="utf-8") as fh:
+            h.update(source_code(fh.read()).encode())
     return h.hexdigest()[:16]
 
 

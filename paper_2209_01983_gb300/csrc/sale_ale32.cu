@@ -2,10 +2,10 @@
 // cycle) cycle.
 //
 // Field storage and the bulk of the arithmetic are FP32; FP64 is kept for
-// the reference hex volumes (computed once in FP64 and stored), the
-// Lagrangian internal-energy update (accumulated in FP64) and the
-// conservation sums (diagnostics).  FP64 runs at 1/64 of the FP32 rate on
-// GB300, so the FP64 islands are kept to a few operations per cell.
+// the reference hex volumes and corner gradients (computed once in FP64 and
+// stored) and the conservation sums (diagnostics).  The conserved cell mass
+// and energy and the node mass accumulate in float-float (FP32 hi + lo, about
+// 48 bits) instead of FP64, which runs at 1/64 of the FP32 rate on GB300.
 //
 // Two reformulations keep FP32 accurate where a plain FP32 evaluation
 // would cancel:
@@ -22,10 +22,12 @@
 //        T = S_E . (e1 x d2 + d1 x e2 + d1 x d2) + S_D . ((e1+d1) x (e2+d2))
 //    (e = reference diagonals, d = their displacement, S = node sums), so
 //    every term is O(h^2 |D|) like the swept volume itself.
-//  * The node force gathers face terms: F_a = (1/24) sum over the 12 mesh
+//  * The node force vanishes exactly where sigma is uniform: on a jittered
+//    mesh it is F_a = sum_c (sigma_c - sigma_ref) G_c(a) over the cached
+//    corner gradients (sum_c G_c(a) = 0 in exact arithmetic); on an
+//    unjittered one it gathers face terms, F_a = (1/24) sum over the 12 mesh
 //    faces at node a of (sigma_low - sigma_high) t_f, t_f = (p1 + 2 p2 + p3)
-//    x (p3 - p1) over the face's other nodes relative to a; it vanishes
-//    exactly where sigma is uniform.
+//    x (p3 - p1) over the face's other nodes relative to a.
 #include "sale_device.cuh"
 
 namespace sale {

@@ -16,7 +16,8 @@
 //   k_ale_edges      side quads of the swept hexes, one per mesh edge (each
 //                    is shared by three cells' swept hexes), with the origin
 //                    shifts those cells need, and each cell's Lagrangian
-//                    low-face terms
+//                    low-face terms, from the cached reference offsets of
+//                    every node to its neighbours (k_geo_init_nodes)
 //   k_ale_cells      compatible energy e_L = e - dt/m (p+q) sum_a G(a).ubar_a;
 //                    swept volumes of the three low faces between the
 //                    Lagrangian face (x_ref + dt ubar) and the reference face
@@ -24,7 +25,7 @@
 //                    closure; rho_L = m / V_L
 //   k_ale_fluxes     donor-cell mass and energy fluxes of the low faces, and
 //                    each cell's dual-mesh flux parts (mu_low + mu_high) / 8
-//   k_ale_remap_nodes  dual-mesh node remap from those parts
+//   k_ale_remap_nodes  dual-mesh node remap from those parts, marching in k
 //   k_ale_remap_eos  new cell mass/energy + kinetic-energy fix, then EoS,
 //                    viscosity, p+q and the CFL dt on the reference mesh
 //
