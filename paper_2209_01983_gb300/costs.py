@@ -60,8 +60,8 @@ FP64_ALE = {
     # 3 dual-flux parts (per cell), u, mn, 0.5|u|^2 read; u', mn', dKE written
     "ale_remap_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 1 + 1), 6 * 12 + 20),
     # 6 fluxes, m, e, dKE, u', G, V_E, L_E, 1/V_E, 1/(cfl L_E)^2 read;
-    # m, e, vol, rho, p, q, cs, sigma written
-    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 4 + 8), 35 + 48 + 30),
+    # m, e, vol, rho, p, q, sigma written (cs is a function of e, not stored)
+    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 4 + 7), 35 + 48 + 30),
 }
 
 

@@ -453,19 +453,17 @@ __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long lon
   const double rho = m * inv_v;
   const double p = (F.gamma - 1.0) * rho * e;
   const double cs2 = F.gamma * (F.gamma - 1.0) * fmax(e, 0.0);
-  const double cs = sqrt(cs2);
   double q_rho = 0.0;  // q / rho
-  if (div < 0.0) {
+  if (div < 0.0) {     // the sound speed itself only where the cell compresses
     const double ld = L * div;
-    q_rho = F.c_q * ld * ld + F.c_l * cs * L * fabs(div);
+    q_rho = F.c_q * ld * ld + F.c_l * sqrt(cs2) * L * fabs(div);
   }
   const double q = rho * q_rho;
   F.vol[c] = V;
   F.rho[c] = rho;
   F.p[c] = p;
   F.q[c] = q;
-  F.cs[c] = cs;
-  F.sig[c] = p + q;
+  F.sig[c] = p + q;  // cs is not stored: it is a function of e (sale_copy_field derives it)
   return (cs2 + 2.0 * q_rho) * F.iL2[c];
 }
 
@@ -493,7 +491,8 @@ __global__ void __launch_bounds__(kBlock) k_ale_hourglass(Fields<double> F, DevS
     G[a] = corner_g(F.G, F.nc, c, a);
   }
   shift0(X);
-  hourglass_store(X, G, U, F.VE[c], F.rho[c], F.cs[c], F.c_hg, F.fh, F.nc, c);
+  hourglass_store(X, G, U, F.VE[c], F.rho[c], sqrt(F.gamma * (F.gamma - 1.0) * fmax(F.e[c], 0.0)), F.c_hg, F.fh,
+                  F.nc, c);
 }
 
 // Predictor-corrector half step on the reference mesh: e^{n+1/2} with the

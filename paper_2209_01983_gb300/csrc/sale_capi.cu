@@ -1023,7 +1023,16 @@ extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *
   if (st->precision == SALE_FP32_MIXED && !node && !st->failed &&
       (!strcmp(name, "p") || !strcmp(name, "q") || !strcmp(name, "cs") || !strcmp(name, "vol")))
     dispatch(st, kMixEos, -1, 0.0);  // the mixed cycle stores only rho and p+q
-  if (elem == sizeof(double)) {
+  const bool cs_from_e = st->precision == SALE_FP64 && !strcmp(name, "cs");
+  if (cs_from_e) {
+    // FP64: the sound speed is a function of e, sqrt(gamma (gamma - 1)
+    // max(e, 0)), which the Eulerian kernels do not store; the same IEEE
+    // operations on the host give the device's value bit for bit
+    CUDA_TRY(cudaMemcpyAsync(host_out, st->e, sizeof(double) * n, cudaMemcpyDeviceToHost, st->stream));
+    CUDA_TRY(cudaStreamSynchronize(st->stream));
+    const double g = st->prob.gamma;
+    for (size_t i = 0; i < n; ++i) host_out[i] = std::sqrt(g * (g - 1.0) * std::fmax(host_out[i], 0.0));
+  } else if (elem == sizeof(double)) {
     CUDA_TRY(cudaMemcpyAsync(host_out, p, sizeof(double) * n, cudaMemcpyDeviceToHost, st->stream));
   } else {
     // FP32 field (plus its low part for float-float quantities): widened to

@@ -174,7 +174,9 @@ __global__ void __launch_bounds__(kBlock) k_hourglass(Fields<R> F, DevScalars *S
   load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
   shift0(X);
   hex_grad_shifted(X, G);
-  hourglass_store(X, G, U, (double)F.vol[c], (double)F.rho[c], (double)F.cs[c], F.c_hg, F.fh, F.nc, c);
+  // cs from e: the Eulerian kernels do not store it
+  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax((double)F.e[c], 0.0));
+  hourglass_store(X, G, U, (double)F.vol[c], (double)F.rho[c], cs, F.c_hg, F.fh, F.nc, c);
 }
 
 // Predictor-corrector (time_order 2) half step: x^{n+1/2} = x^n + dt/2 u^n
