@@ -179,13 +179,19 @@ int sale_diagnostics(const sale_state *st, sale_diag *out);
 
 /* Synchronising copy of a field to host FP64.  Names: node fields "x",
  * "y", "z", "u", "v", "w", "mn", "xref", "yref", "zref" (n = nnodes); cell
- * fields "m", "e", "rho", "p", "q", "cs", "vol" (n = ncells). */
+ * fields "m", "e", "rho", "p", "q", "cs", "vol" (n = ncells).  FP32-mixed
+ * fields are widened on the device (hi + lo for the float-float m, e, mn);
+ * FP64 "cs" is formed from e as sqrt(gamma (gamma - 1) max(e, 0)), the
+ * formula the kernels use. */
 int sale_copy_field(const sale_state *st, const char *name, double *host_out,
                     size_t n);
 /* Overwrite an evolving field from host FP64 (same names as copy_field for
  * "x","y","z","u","v","w","mn","m","e"); call sale_refresh() after the last
- * one to recompute derived fields and dt.  Asynchronous with respect to
- * the host only when host_in is pinned memory. */
+ * one to recompute derived fields and dt.  FP32-mixed states split each
+ * value on the device into hi = fl32(x) and, for m, e and mn, lo =
+ * fl32(x - hi).  Asynchronous with respect to the host only when host_in is
+ * pinned memory (which must then stay unchanged until the state's stream
+ * has passed the copy). */
 int sale_set_field(sale_state *st, const char *name, const double *host_in,
                    size_t n);
 int sale_refresh(sale_state *st);
