@@ -239,3 +239,33 @@ def test_momentum_conserved_without_walls():
     d = o.diagnostics()
     for comp in ("mom_x", "mom_y", "mom_z"):
         assert abs(d[comp]) <= 1e-13 * scale, comp
+
+
+def test_similarity_solution_gives_the_golden_alpha():
+    # the energy constant integrated from the self-similar profile (an
+    # independent construction) against the literature value in the golden
+    import sedov_similarity as ss
+    assert abs(ss.alpha(1.4) - read_golden("sedov_alpha.txt")["alpha"]) <= 5e-4
+
+
+def test_sedov_pressure_converges_to_similarity_solution():
+    # volume-weighted relative L1 of p against the similarity solution inside
+    # r <= 1.1 (the shock is at 0.76, the walls at 1.2) falls with every
+    # refinement; the energy sits in one cell at each resolution, so the
+    # approach is slow (first order at best)
+    import sedov_similarity as ss
+    t_end, errs = 0.5, []
+    for n in (12, 16, 20, 24):
+        md, pd = inputs.sedov_octant(n)
+        o = oracle.Oracle.from_problem(md, pd)
+        rc, _ = o.run(t_end=t_end, remap_every=1)
+        assert rc == 0
+        p, vol = o.field("p"), o.field("vol")
+        h = 1.2 / n
+        c = (np.arange(n) + 0.5) * h
+        r = np.sqrt(c[None, None, :] ** 2 + c[None, :, None] ** 2 + c[:, None, None] ** 2).ravel()
+        keep = r <= 1.1
+        pex = ss.pressure(r[keep], t_end, 8.0 * pd.e_deposit)
+        errs.append(float(np.sum(np.abs(p[keep] - pex) * vol[keep]) / np.sum(pex * vol[keep])))
+    assert all(a > b for a, b in zip(errs, errs[1:])), errs
+    assert errs[-1] <= 0.35, errs
