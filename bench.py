@@ -155,6 +155,61 @@ def oracle_rate(n, jitter, steps, warmup):
     return md.ncell * steps / dt, dt, md.ncell
 
 
+def _oracle_replica(n, jitter, steps, warmup, barrier, results):
+    """One oracle replica of oracle_rate_all_cores (a spawned process)."""
+    try:
+        import oracle
+        from paper_2209_01983_gb300 import inputs
+        md, pd = inputs.sedov_octant(n, jitter=jitter)
+        o = oracle.Oracle.from_problem(md, pd)
+        o.run(max_cycles=warmup, remap_every=1)
+        barrier.wait(timeout=300)
+        t0 = time.perf_counter()
+        rc, done = o.run(max_cycles=steps, remap_every=1)
+        results.put((rc, done, md.ncell, time.perf_counter() - t0))
+    except Exception as exc:  # reported by the parent
+        results.put(("error", repr(exc)))
+
+
+def oracle_rate_all_cores(n, jitter, steps, warmup, timeout_s=300.0):
+    """Whole-host rate of the oracle as it stands: one replica of the same
+    sample per host core, in spawned processes that start their timed cycles
+    together (a barrier); cell-updates of all over the slowest replica's
+    time.  Returns (rate, cores, seconds)."""
+    import multiprocessing as mp
+    import queue
+
+    oracle_build_once()
+    cores = len(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else (os.cpu_count() or 1)
+    ctx = mp.get_context("spawn")  # the parent holds a CUDA context
+    barrier, results = ctx.Barrier(cores), ctx.Queue()
+    procs = [ctx.Process(target=_oracle_replica, args=(n, jitter, steps, warmup, barrier, results))
+             for _ in range(cores)]
+    for pr in procs:
+        pr.start()
+    out, deadline = [], time.monotonic() + timeout_s
+    try:
+        while len(out) < cores:
+            out.append(results.get(timeout=max(1.0, deadline - time.monotonic())))
+    except queue.Empty:
+        raise RuntimeError(f"{cores - len(out)} of {cores} oracle replicas did not finish in {timeout_s:.0f} s")
+    finally:
+        for pr in procs:
+            pr.join(timeout=10)
+            if pr.is_alive():
+                pr.kill()  # only the replicas started here
+    bad = [r for r in out if r[0] != 0 or r[1] != steps]
+    if bad:
+        raise RuntimeError(f"oracle replica failed: {bad[0]}")
+    slowest = max(r[3] for r in out)
+    return sum(r[2] * steps for r in out) / slowest, cores, slowest
+
+
+def oracle_build_once():
+    import oracle
+    oracle.build()
+
+
 def reference_arm(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -436,6 +491,13 @@ def gpu_arm(args):
         cpu = {"value": rate, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"same workload at {n}^3 ({ncell} cells), 40 cycles after 5, "
                          f"serial FP64 C oracle, {secs:.1f} s"}
+        try:
+            arate, acores, asecs = oracle_rate_all_cores(n, args.jitter, 40, 5)
+            cpu["all_cores"] = {"value": arate, "unit": UNIT, "cores": acores, "kind": "oracle replicas",
+                                "sample": f"one replica of the same sample per host core, timed together, "
+                                          f"{asecs:.1f} s"}
+        except Exception as exc:  # the single-core figure stands on its own
+            cpu["all_cores"] = {"value": None, "error": repr(exc)[:200]}
     main_p = precisions[0]
     r = results[main_p]
     dtypes = {"fp64": "f64", "fp32_mixed": "f32 (f64 islands)"}

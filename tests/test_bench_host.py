@@ -35,3 +35,12 @@ def test_traffic_table_only_for_matching_digest(tmp_path, monkeypatch):
     f.write_text("# source-digest: 0000000000000000\n" + rows)
     table, note = bench.load_traffic()
     assert table == {} and "changed" in note
+
+
+def test_oracle_all_cores_replicas():
+    # one spawned replica per host core, timed together: at least one core's
+    # worth of throughput and no more than cores times the best single rate
+    rate, cores, secs = bench.oracle_rate_all_cores(8, 0.1, 3, 1, timeout_s=120)
+    single, _, _ = bench.oracle_rate(8, 0.1, 3, 1)
+    assert cores >= 1 and secs > 0
+    assert 0.2 * single < rate < 4.0 * cores * single
