@@ -8,6 +8,13 @@ full cycle (Lagrangian step + rezone/advection + EoS + CFL dt) of the whole
 mesh.  The state (>= 8 GB) is far larger than the 129 MB L2, so no flush is
 needed between steps.
 
+The default line also carries, under "variants": the FP32-mixed run of the
+same mesh; "batch512", the batch workload (512 independent meshes of 16..96
+cells per axis, FP32-mixed, every cycle of every mesh in the same five
+launches) with its speed-up over the same meshes advanced one by one in
+FP32-mixed and in FP64; and "precision", the precision workload (Sedov
+octant to t = 0.5) at 128^3, FP32-mixed against FP64.
+
     python bench.py [--gpus N] [--steps K] [--warmup W] [--precision fp64]
     python bench.py --impl reference     # the CPU oracle on a bounded sample
 
@@ -63,6 +70,12 @@ def parse():
     ap.add_argument("--t-end", type=float, default=0.5)
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--unbatched-steps", type=int, default=16)
+    ap.add_argument("--batch-steps", type=int, default=20,
+                    help="default run: timed cycles of the batch variant")
+    ap.add_argument("--no-batch", action="store_true", help="default run: skip the batch variant")
+    ap.add_argument("--no-precision", action="store_true", help="default run: skip the precision variant")
+    ap.add_argument("--precision-n", type=int, default=128,
+                    help="default run: cells per axis of the precision variant (to --t-end)")
     args = ap.parse_args()
     if args.n is None:
         args.n = 256 if args.config == "precision" else 384
@@ -342,7 +355,7 @@ def measure(args, precision, local, barrier):
     elif precision == "fp32_mixed" and not args.no_tune:
         # warm-up part 1: pick the tile shape (ordinary cycles, results unchanged)
         from paper_2209_01983_gb300 import autotune
-        tuning = autotune.tune_state(st, cycles=16, repeats=2)
+        tuning = autotune.tune_state(st, cycles=16, repeats=3)
     st.run_to_time(max_cycles=args.warmup, remap_every=1)
 
     # ---- timed region: K full cycles, graph replays on the state's stream
@@ -531,6 +544,12 @@ def gpu_arm(args):
                           "full_cycle": x["full_cycle"], "kernels": x["kernels"], "clocks": x["clocks"],
                           "gpu_launches": x["gpu_launches"], "check": x["check"], "tuning": x["tuning"],
                           "e2e": x.get("e2e")}
+    if not args.no_batch:
+        bt = measure_batch(args, local, args.batch_steps, args.unbatched_steps, args.batch_count)
+        bt["speedup_vs_" + main_p + "_single_mesh"] = bt["value"] / r["value"]
+        variants[f"batch{args.batch_count}"] = bt
+    if not args.no_precision:
+        variants["precision"] = measure_precision(args.precision_n, args.t_end, local)
     if variants:
         line["variants"] = variants
     print(json.dumps(line), flush=True)
@@ -539,36 +558,35 @@ def gpu_arm(args):
     return 0
 
 
-def batch_arm(args):
-    """512 independent shock-tube / Sedov-like meshes (16..96 cells per axis),
-    FP32-mixed, every cycle of every mesh in one graph launch; compared with
-    the same meshes advanced one at a time."""
+def measure_batch(args, local, steps, unbatched_steps, count):
+    """`count` independent shock-tube / Sedov-like meshes (16..96 cells per
+    axis), FP32-mixed, every cycle of every mesh in the same five launches
+    (replays of captured graphs); compared with the same meshes advanced one
+    at a time in FP32-mixed and in FP64."""
     import torch
 
     from paper_2209_01983_gb300 import inputs, sale
 
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    torch.cuda.set_device(local)
-    inst = inputs.batch_instances(args.batch_count, seed=2209)
+    inst = inputs.batch_instances(count, seed=2209)
     cells = sum(md.ncell for md, _ in inst)
     b = sale.Batch(inst, device=f"cuda:{local}")
     tuning = None
     if not args.no_tune:
         from paper_2209_01983_gb300 import autotune
-        tuning = autotune.tune_batch(b, cycles=4, repeats=2)
-    b.run(args.steps)  # untimed: captures and instantiates the graph of K cycles
+        tuning = autotune.tune_batch(b, cycles=4, repeats=3)
+    b.run(steps)  # untimed: captures and instantiates the graphs of these cycles
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     clocks = ClockSampler(local)
     torch.cuda.synchronize()
     clocks.start()
     time.sleep(0.3)
     ev0.record(b.stream)
-    b.run(args.steps)
+    b.run(steps)
     ev1.record(b.stream)
     ev1.synchronize()
     clk = clocks.stop()
     ms = ev0.elapsed_time(ev1)
-    value = cells * args.steps / (ms * 1e-3)
+    value = cells * steps / (ms * 1e-3)
     ts = [b.state(i).diagnostics()["t"] for i in (0, 1, len(inst) - 1)]
     b.close()
     del b
@@ -589,42 +607,53 @@ def batch_arm(args):
             st.close()
         return cells * cycles / (total * 1e-3)
 
-    k1 = args.unbatched_steps
-    rate_single_mixed = one_by_one("fp32_mixed", k1)
-    rate_single_fp64 = one_by_one("fp64", k1)
+    rate_single_mixed = one_by_one("fp32_mixed", unbatched_steps)
+    rate_single_fp64 = one_by_one("fp64", unbatched_steps)
+    return {"value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
+            "dtype": "f32 (f64 islands)", "cells": cells, "instances": len(inst),
+            "workload": f"batch of {len(inst)} shock-tube/Sedov meshes, 16..96 cells per axis, seed 2209, "
+                        f"FP32-mixed, Eulerian every cycle, {steps} cycles of every mesh per timed run",
+            "compare": {"one_by_one_fp32_mixed": rate_single_mixed, "one_by_one_fp64": rate_single_fp64,
+                        "speedup_vs_one_by_one_fp32_mixed": value / rate_single_mixed,
+                        "speedup_vs_one_by_one_fp64": value / rate_single_fp64,
+                        "one_by_one_cycles": unbatched_steps},
+            "gpu_launches": 5 * steps + 2, "clocks": clk, "check": {"t_samples": ts}, "tuning": tuning}
+
+
+def batch_arm(args):
+    """The batch workload alone: 200 cycles of each of 512 meshes."""
+    import torch
+
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    r = measure_batch(args, local, args.steps, args.unbatched_steps, args.batch_count)
     line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.steps,
-        "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-        "dtype": "f32 (f64 islands)", "data": "synthetic",
-        "config": {"workload": f"batch of {len(inst)} shock-tube/Sedov meshes, 16..96 cells per axis, "
-                               f"FP32-mixed, Eulerian every cycle, one graph launch of {args.steps} cycles",
-                   "cells": cells, "instances": len(inst), "seed": 2209,
+        "metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.steps,
+        "ms_per_step": r["ms_per_step"], "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": r["dtype"], "data": "synthetic",
+        "config": {"workload": r["workload"], "cells": r["cells"], "instances": r["instances"], "seed": 2209,
                    "l2": "state larger than the 129 MB L2 (no flush)"},
-        "compare": {"one_by_one_fp32_mixed": rate_single_mixed, "one_by_one_fp64": rate_single_fp64,
-                    "speedup_vs_one_by_one_fp32_mixed": value / rate_single_mixed,
-                    "speedup_vs_one_by_one_fp64": value / rate_single_fp64,
-                    "one_by_one_cycles": k1},
-        "gpu_launches": 5 * args.steps + 2, "clocks": clk, "check": {"t_samples": ts}, "tuning": tuning,
+        "compare": r["compare"], "gpu_launches": r["gpu_launches"], "clocks": r["clocks"], "check": r["check"],
+        "tuning": r["tuning"],
     }
     print(json.dumps(line), flush=True)
     return 0
 
 
-def precision_arm(args):
-    """Sedov octant at 256^3 to t = 0.5 in FP32-mixed and FP64: throughput of
-    both, the mixed run's relative L1 error in density and energy against
-    FP64, conservation drift, and both downsampled (conservative 4^3 block
-    averages) against the CPU oracle at 64^3."""
+def measure_precision(n, t_end, local=0, keep_fields=False):
+    """Sedov octant at n^3 to t_end in FP32-mixed and FP64, Eulerian every
+    cycle: throughput of both, the mixed run's relative L1 error in density
+    and energy against FP64 (volume-weighted, mass-weighted, and outside the
+    near-vacuum core), and conservation drift."""
     import numpy as np
     import torch
 
     from paper_2209_01983_gb300 import inputs, sale
 
-    n, t_end = args.n, args.t_end
     md, pd = inputs.sedov_octant(n)
     out = {}
     for prec, code in (("fp32_mixed", sale.SALE_FP32_MIXED), ("fp64", sale.SALE_FP64)):
-        st = sale.State(md, pd, precision=code)
+        st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
         d0 = st.diagnostics()
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ev0.record(st.stream)
@@ -651,6 +680,27 @@ def precision_arm(args):
     keep = b["rho"] >= 1e-3 * b["rho"].max()
     l1_core_out = {f: float(np.sum(np.abs(a[f] - b[f]) * w * keep) / np.sum(np.abs(b[f]) * w * keep))
                    for f in ("rho", "e")}
+    res = {"workload": f"sedov-octant-{n}^3-to-t{t_end}-ale-every-cycle", "cells": md.ncell,
+           "fp32_mixed": {k: v for k, v in out["fp32_mixed"].items() if k != "fields"},
+           "fp64": {k: v for k, v in out["fp64"].items() if k != "fields"},
+           "mixed_vs_fp64_l1_rel": l1, "mixed_vs_fp64_l1_rel_mass_weighted": l1_mass,
+           "mixed_vs_fp64_l1_rel_outside_core": l1_core_out,
+           "core_volume_fraction": float(np.sum(w * ~keep) / np.sum(w)),
+           "speedup_mixed_vs_fp64": out["fp32_mixed"]["value"] / out["fp64"]["value"]}
+    if keep_fields:
+        res["fields"] = {prec: out[prec]["fields"] for prec in out}
+    return res
+
+
+def precision_arm(args):
+    """Sedov octant at 256^3 to t = 0.5 in FP32-mixed and FP64 (see
+    measure_precision), and both downsampled (conservative 4^3 block
+    averages) for the comparison against the CPU oracle at 64^3."""
+    import numpy as np
+
+    n, t_end = args.n, args.t_end
+    r = measure_precision(n, t_end, keep_fields=bool(args.save_fields))
+    fields = r.pop("fields", None)
 
     def down(fl, k=4):  # conservative block averages: rho = sum m / sum V, e = sum m e / sum m
         nn = n // k
@@ -660,20 +710,14 @@ def precision_arm(args):
         v = fl["vol"].reshape(n, n, n).reshape(sh).sum(axis=(1, 3, 5))
         return {"rho": (m / v).ravel(), "e": (me / m).ravel()}
 
-    line = {"metric": METRIC, "config": {"workload": f"sedov-octant-{n}^3-to-t{t_end}-ale-every-cycle",
-                                         "cells": md.ncell},
-            "fp32_mixed": {k: v for k, v in out["fp32_mixed"].items() if k != "fields"},
-            "fp64": {k: v for k, v in out["fp64"].items() if k != "fields"},
-            "mixed_vs_fp64_l1_rel": l1, "mixed_vs_fp64_l1_rel_mass_weighted": l1_mass,
-            "mixed_vs_fp64_l1_rel_outside_core": l1_core_out,
-            "core_volume_fraction": float(np.sum(w * ~keep) / np.sum(w)),
-            "speedup_mixed_vs_fp64": out["fp32_mixed"]["value"] / out["fp64"]["value"]}
+    line = {"metric": METRIC, "config": {"workload": r.pop("workload"), "cells": r.pop("cells")}}
+    line.update(r)
     if args.save_fields and n % 4 == 0:
         # 4^3 block averages of both runs, for the oracle comparison that
         # runs on the host afterwards (--config precision-oracle)
         np.savez_compressed(args.save_fields, n=n, t_end=t_end,
                             **{f"{prec}_{f}": v for prec in ("fp32_mixed", "fp64")
-                               for f, v in down(out[prec]["fields"]).items()})
+                               for f, v in down(fields[prec]).items()})
         line["saved_fields"] = args.save_fields
     print(json.dumps(line), flush=True)
     return 0

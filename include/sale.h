@@ -200,14 +200,15 @@ int sale_refresh(sale_state *st);
 int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes);
 
 /* Remap step without any device allocation.  The paper has no counterpart
- * of this call; it serves callers that cannot allocate device memory
- * (code running during CUDA stream capture, plug-ins whose host program
- * owns every device allocation, loops that forbid allocator calls).  It
- * does what sale_remap_step does -- face swept volumes, donor-cell mass and
- * energy fluxes, dual-mesh node momentum and kinetic-energy fluxes, new
- * node velocity and mass, cell mass and energy with the kinetic-energy
- * fix -- on a mesh held entirely in the caller's device arrays (FP64, SoA,
- * layout as above), without EoS or dt.  Arguments:
+ * of this call; it serves callers that cannot allocate device memory:
+ * plug-ins whose host program owns every device allocation and hands them
+ * only their field arrays, and loops that must not call an allocator
+ * (cudaMalloc and cudaFree can synchronise the device).  It does what
+ * sale_remap_step does -- face swept volumes, donor-cell mass and energy
+ * fluxes, dual-mesh node momentum and kinetic-energy fluxes, new node
+ * velocity and mass, cell mass and energy with the kinetic-energy fix --
+ * on a mesh held entirely in the caller's device arrays (FP64, SoA, layout
+ * as above), without EoS or dt.  Arguments:
  *   nx, ny, nz   cells per axis; at most SALE_STATIC_MAX_CELLS cells and
  *                SALE_STATIC_MAX_NODES nodes, else SALE_EINVAL
  *   reflect[6]   host array, 1 = reflecting wall (x-lo,x-hi,..,z-hi), 0 = none
@@ -223,13 +224,16 @@ int sale_state_dims(const sale_state *st, long long *ncells, long long *nnodes);
  * Scratch (status word, face fluxes, node energy losses) lives in one fixed
  * static device array of the library (about 4 MB at the limits below),
  * present on every GPU that loads the library until the process exits.
- * Every call shares it and it keeps the last call's contents, so calls that
- * overlap on the GPU (other streams, other host threads) race: serialise
- * them.  The first call on a device looks up the array's device address
- * (and may load the library's GPU code); make that first call before any
- * stream capture.  Calls no device or host allocator.  Synchronises the
- * stream and returns the device status (SALE_ENEGVOL when a node or cell
- * mass is not positive). */
+ * Every call shares it and it keeps the last call's contents (the status
+ * word is cleared at the start of each call; the flux arrays are written in
+ * full before they are read), so calls that overlap on the GPU (other
+ * streams, other host threads) race: serialise them.  The first call on a
+ * device looks up the array's device address (and may load the library's
+ * GPU code); make that first call before any stream capture.  After a
+ * device reset (cudaDeviceReset) that address is stale: do not call this
+ * entry point again in a process that has reset the device.  Calls no
+ * device or host allocator.  Synchronises the stream and returns the
+ * device status (SALE_ENEGVOL when a node or cell mass is not positive). */
 #define SALE_STATIC_MAX_CELLS 65536
 #define SALE_STATIC_MAX_NODES 131072
 int sale_remap_static(int nx, int ny, int nz, const int *reflect, int ke_fix,
@@ -240,7 +244,8 @@ int sale_remap_static(int nx, int ny, int nz, const int *reflect, int ke_fix,
 /* Batches: n independent meshes (each its own problem, size and dt)
  * advanced together.  Every cycle of every mesh runs in the same five
  * kernel launches (a block-to-mesh table maps each block to its mesh), and
- * a whole sale_batch_run is one CUDA-graph launch.  Batches run the
+ * a sale_batch_run replays captured CUDA graphs of up to 64 cycles of
+ * every mesh (at most 64 graphs are kept per batch).  Batches run the
  * FP32-mixed Eulerian cycle (precision SALE_FP32_MIXED, remap every
  * cycle).  Memory: sale_batch_bytes() bytes of caller device memory
  * (256-byte aligned), alive until sale_batch_destroy(); meshes[i] follow

@@ -20,6 +20,7 @@ from __future__ import annotations
 
 import ctypes as C
 import json
+import statistics
 import os
 
 DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "sale_gb300", "tune.json")
@@ -49,13 +50,14 @@ def store_cache(path, key, value):
     os.replace(tmp, path)
 
 
-def choose(candidates, time_fn, repeats=2):
-    """The candidate with the smallest median time over `repeats` timings,
-    with every candidate's times.  time_fn(candidate) returns milliseconds."""
+def choose(candidates, time_fn, repeats=3):
+    """The candidate with the smallest median time over `repeats` timings
+    (statistics.median: the middle one for an odd count, the mean of the
+    two middle ones for an even count), with every candidate's median.
+    time_fn(candidate) returns milliseconds."""
     times = {}
     for c in candidates:
-        ts = sorted(float(time_fn(c)) for _ in range(repeats))
-        times[c] = ts[len(ts) // 2]
+        times[c] = statistics.median(float(time_fn(c)) for _ in range(repeats))
     best = min(candidates, key=lambda c: (times[c], candidates.index(c)))
     return best, times
 
@@ -92,7 +94,7 @@ def _timer(stream, run):
     return e0.elapsed_time(e1)
 
 
-def tune_state(st, cycles=16, repeats=2, cache="default", remap_every=1):
+def tune_state(st, cycles=16, repeats=3, cache="default", remap_every=1):
     """Pick and set the fastest tile shape of an FP32-mixed State.  Advances
     the state by about (1 + repeats) * cycles cycles per shape.  Returns
     {"shape", "tile", "ms_per_cycle": {shape: ms}, "cached"}."""
@@ -129,7 +131,7 @@ def tune_state(st, cycles=16, repeats=2, cache="default", remap_every=1):
     return res
 
 
-def tune_batch(b, cycles=4, repeats=2, cache="default"):
+def tune_batch(b, cycles=4, repeats=3, cache="default"):
     """Pick and set the fastest (tile shape, mesh order) of a Batch.  Advances
     every mesh by about (1 + repeats) * cycles cycles per candidate."""
     import hashlib

@@ -1361,6 +1361,32 @@ extern "C" int sale_batch_set_schedule(sale_batch *b, int shape, int order) {
   return rc;
 }
 
+// Cycles per replayed batch graph (even; see sale_batch_run).
+constexpr long long kBatchChunk = 64;
+static_assert(kBatchChunk % 2 == 0, "a batch chunk must keep the velocity roles");
+
+// The instantiated graph of n cycles of every mesh (captured on first use).
+static int batch_graph(sale_batch *b, long long n, cudaGraphExec_t *out) {
+  auto it = b->graphs.find(n);
+  if (it != b->graphs.end()) {
+    *out = it->second;
+    return SALE_OK;
+  }
+  cudaGraph_t g;
+  CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
+  int p = 0;
+  for (long long j = 0; j < n; ++j, p ^= 1) launch_batch_cycle(b, p);
+  cudaError_t e = cudaStreamEndCapture(b->stream, &g);
+  if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph capture");
+  cudaGraphExec_t ge;
+  e = cudaGraphInstantiate(&ge, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph instantiate");
+  b->graphs[n] = ge;
+  *out = ge;
+  return SALE_OK;
+}
+
 extern "C" int sale_batch_run(sale_batch *b, long long cycles, int remap_every, long long *cycles_done) {
   if (!b) return fail(SALE_EINVAL, "sale_batch_run: null batch");
   if (cycles_done) *cycles_done = 0;
@@ -1380,24 +1406,22 @@ extern "C" int sale_batch_run(sale_batch *b, long long cycles, int remap_every, 
       break;
     }
   launch_batch_limits(b->items[0], b->n, cycles, b->stream);
-  // the whole run is one graph: `cycles` cycles of every mesh
-  auto it = b->graphs.find(cycles);
+  // Replays of a graph of kBatchChunk cycles of every mesh, then one graph
+  // of the remaining cycles: at most kBatchChunk graphs are ever kept, and
+  // an even chunk leaves every mesh's velocity roles as they were, so each
+  // graph starts from the same descriptors.
+  const long long full = cycles / kBatchChunk, rest = cycles % kBatchChunk;
   cudaGraphExec_t ge;
-  if (it == b->graphs.end()) {
-    cudaGraph_t g;
-    CUDA_TRY(cudaStreamBeginCapture(b->stream, cudaStreamCaptureModeThreadLocal));
-    int p = 0;
-    for (long long j = 0; j < cycles; ++j, p ^= 1) launch_batch_cycle(b, p);
-    cudaError_t e = cudaStreamEndCapture(b->stream, &g);
-    if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph capture");
-    e = cudaGraphInstantiate(&ge, g, 0);
-    cudaGraphDestroy(g);
-    if (e != cudaSuccess) return cuda_fail(e, "sale_batch_run: graph instantiate");
-    b->graphs[cycles] = ge;
-  } else {
-    ge = it->second;
+  if (full > 0) {
+    int rc = batch_graph(b, kBatchChunk, &ge);
+    if (rc) return rc;
+    for (long long r = 0; r < full; ++r) CUDA_TRY(cudaGraphLaunch(ge, b->stream));
   }
-  CUDA_TRY(cudaGraphLaunch(ge, b->stream));
+  if (rest > 0) {
+    int rc = batch_graph(b, rest, &ge);
+    if (rc) return rc;
+    CUDA_TRY(cudaGraphLaunch(ge, b->stream));
+  }
   if (cycles & 1)  // odd run: every mesh's velocity roles swapped
     for (auto *st : b->st) st->upar ^= 1;
   launch_batch_gather(b->items[0], b->n, b->status, b->stream);

@@ -1,19 +1,23 @@
 // sale_static.cu -- remap step for callers that cannot allocate device
 // memory (see sale_remap_static in include/sale.h).
 //
-// Some callers have no way to call cudaMalloc: code running while a CUDA
-// stream is being captured into a graph (allocation is not allowed there),
-// plug-ins whose host application owns every device allocation, and
-// latency-critical loops that forbid allocator calls.  They already hold
-// their field arrays; what the remap additionally needs is scratch for the
-// face fluxes, the node kinetic-energy losses and a device status word.
-// Here that scratch is one fixed file-scope device array, sized for at most
-// SALE_STATIC_MAX_CELLS cells and SALE_STATIC_MAX_NODES nodes; it exists on
-// every GPU that loads the library, from module load until process exit.
+// Some callers have no way to call cudaMalloc: plug-ins whose host
+// application owns every device allocation and hands them only the arrays
+// they work on, and loops that must not call an allocator (cudaMalloc and
+// cudaFree can synchronise the device and stall every other stream).  They
+// already hold their field arrays; what the remap additionally needs is
+// scratch for the face fluxes, the node kinetic-energy losses and a device
+// status word.  Here that scratch is one fixed file-scope device array,
+// sized for at most SALE_STATIC_MAX_CELLS cells and SALE_STATIC_MAX_NODES
+// nodes; it exists on every GPU that loads the library, from module load
+// until process exit.
 //
 // Host code cannot use the array's name as a device address (it denotes a
 // host-side shadow), so the device address is looked up once per device
-// with cudaGetSymbolAddress and passed to the kernels.
+// with cudaGetSymbolAddress, on the first call on that device, and passed
+// to the kernels.  A device reset (cudaDeviceReset) unloads the module and
+// leaves that address stale: the entry point is not for processes that
+// reset a device they have called it on.
 #include <cmath>
 #include <mutex>
 

@@ -1,4 +1,4 @@
-"""Batched runs: many independent meshes advanced by one graph launch.
+"""Batched runs: many independent meshes advanced by replays of captured graphs.
 
 Each mesh of a batch must come out bitwise equal to the same mesh advanced
 on its own (same precision, same kernels), whatever its size, problem and
@@ -31,7 +31,9 @@ def small_instances(count=7):
 FIELDS = ("m", "e", "rho", "u", "v", "w", "mn")
 
 
-@pytest.mark.parametrize("runs", [(30,), (7, 8)])
+# (64 + 9): a replayed 64-cycle graph then a 9-cycle one; (131, 3): two
+# replays, an odd tail, then a run that starts from swapped velocity roles
+@pytest.mark.parametrize("runs", [(30,), (7, 8), (73,), (131, 3)])
 def test_batch_matches_single_meshes_bitwise(sale, runs):
     inst = small_instances()
     b = sale.Batch(inst)

@@ -1,11 +1,14 @@
 """The allocation-free remap entry point against the state-based remap.
 
-sale_remap_static serves callers that cannot allocate device memory (code
-under CUDA stream capture, plug-ins whose host owns all device memory,
-allocator-free loops): its scratch is a fixed static device array of the
-library.  This file checks, through the C ABI, that it reproduces
-sale_remap_step on the same Lagrangian state, on two calls in a row (the
-second call starts from scratch the first one left behind), and that it
+sale_remap_static serves callers that cannot allocate device memory:
+plug-ins whose host program owns every device allocation and passes them
+only their field arrays, and loops that must not call an allocator
+(cudaMalloc and cudaFree can synchronise the device).  Its scratch is a
+fixed static device array of the library.  This file checks, through the C
+ABI, that it reproduces sale_remap_step on the same Lagrangian state, on
+two calls in a row (the second call starts from the scratch the first one
+left behind); that the second call, once the library's GPU code is loaded,
+changes neither the device's free memory nor torch's allocator; and that it
 rejects meshes larger than its fixed scratch.  It sits last in collection
 order so a failure here comes after every other test has run.
 """
@@ -62,9 +65,15 @@ def test_static_remap_matches_state_remap(env):
         mn, m, e, rho = upload("mn"), upload("m"), upload("e"), upload("rho")
         torch.cuda.synchronize()
         p = lambda t: C.c_void_p(t.data_ptr())
+        free0 = torch.cuda.mem_get_info()[0]
+        torch0 = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
         rc = sale.sale_remap_static(md.nx, md.ny, md.nz, reflect, pd.ke_fix, p(xref), p(x), p(u_in),
                                     p(u_out), p(mn), p(m), p(e), p(rho), C.c_void_p(stream.cuda_stream))
         assert rc == sale.SALE_OK, sale.sale_last_error()
+        free1 = torch.cuda.mem_get_info()[0]
+        assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == torch0, call
+        if call == 1:  # the first call may load the library's GPU code (and its static array)
+            assert free1 == free0, (free0, free1)
         nn = md.nnode
         got_u = u_out.cpu().numpy()
         got_x = x.cpu().numpy()
