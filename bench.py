@@ -96,6 +96,27 @@ def load_peaks():
 # FP64 vector peak: 2 DFMA per clock per SM x 152 SMs x 2.07 GHz x 2 flop.
 FP64_PEAK_TFLOPS = 2 * 152 * 2.07e9 * 2 / 1e12
 
+_PROBES = {}
+
+
+def fma_probe_tflops(precision, local=0):
+    """FMA throughput of this GPU measured by the library's probe
+    (sale_fma_probe), TFLOP/s; None when it cannot run."""
+    if precision in _PROBES:
+        return _PROBES[precision]
+    import torch
+
+    from paper_2209_01983_gb300 import sale
+    code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
+    props = torch.cuda.get_device_properties(local)
+    buf = torch.empty(8 * 256 * props.multi_processor_count * 8, dtype=torch.uint8, device=f"cuda:{local}")
+    st = torch.cuda.Stream(device=f"cuda:{local}")
+    out = sale.C.c_double(0.0)
+    rc = sale.sale_fma_probe(code, sale._vp(buf.data_ptr()), buf.numel(), sale._vp(st.cuda_stream),
+                             sale.C.byref(out))
+    _PROBES[precision] = out.value / 1e12 if rc == sale.SALE_OK else None
+    return _PROBES[precision]
+
 
 # ---------------------------------------------------------------------------
 # clocks during the timed region
@@ -403,15 +424,22 @@ def measure(args, precision, local, barrier):
     top = next(iter(kernels))
     kt = kernels[top]
     if precision == "fp64":
+        probe = fma_probe_tflops("fp64", local)
         roof = {"bound": "alu", "achieved": kt["alg_tflops"], "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
                 "frac": kt["alg_tflops"] / FP64_PEAK_TFLOPS, "traffic": None, "kernel": top,
                 "peak_source": "derived: 2 DFMA/clk/SM x 152 SMs x 2.07 GHz (FP64 vector pipe)",
+                "peak_measured_probe": probe,
+                "frac_of_measured_probe": kt["alg_tflops"] / probe if probe else None,
+                "probe": "sale_fma_probe: 8 independent FP64 FMA chains per thread, 8 x 256 threads per SM",
                 "hbm_achieved_gbs": kt["alg_gbs"], "hbm_frac_of_measured": kt["alg_gbs"] / peaks["hbm_gbs"]}
     else:
+        probe = fma_probe_tflops("fp32", local)
         roof = {"bound": "hbm", "achieved": kt["alg_gbs"], "peak": peaks["hbm_gbs"], "unit": "GB/s",
                 "frac": kt["alg_gbs"] / peaks["hbm_gbs"], "traffic": None, "kernel": top,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)",
-                "fp32_tflops": kt["alg_tflops"], "fp32_frac_of_derived": kt["alg_tflops"] / FP32_PEAK_TFLOPS}
+                "fp32_tflops": kt["alg_tflops"], "fp32_frac_of_derived": kt["alg_tflops"] / FP32_PEAK_TFLOPS,
+                "fp32_peak_measured_probe": probe,
+                "fp32_frac_of_measured_probe": kt["alg_tflops"] / probe if probe else None}
     traffic, note = load_traffic()
     per_unit = traffic.get((precision, top))
     roof["traffic"] = per_unit * units(top) if per_unit is not None else None

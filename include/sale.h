@@ -292,6 +292,17 @@ int sale_profile_read(sale_state *st, double *ms, long long *launches, int n,
 int sale_kernel_count(void);
 const char *sale_kernel_name(int id);
 
+/* Measured fused multiply-add rate of the current GPU, for the roofline of
+ * the FP64 cycle (which is bound by the FP64 vector pipe rather than by
+ * HBM).  The paper has no counterpart of this call.  precision SALE_FP64
+ * times FP64 FMAs, SALE_FP32_MIXED FP32 ones: eight independent FMA chains
+ * per thread, 8 blocks of 256 threads per SM, best of three timed launches
+ * (CUDA events on cuda_stream, after one untimed launch).  device_buf
+ * (caller-owned device memory, at least 8 * 256 * SMs * sizeof(value)
+ * bytes) receives the chains' sums.  *flop_per_s = 2 x FMAs / second.
+ * Synchronises the stream.  SALE_ENOMEM when the buffer is too small. */
+int sale_fma_probe(int precision, void *device_buf, size_t bytes, void *cuda_stream, double *flop_per_s);
+
 const char *sale_last_error(void);
 
 #ifdef __cplusplus

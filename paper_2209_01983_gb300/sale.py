@@ -98,10 +98,11 @@ sale_remap_static = _sig("sale_remap_static", C.c_int,
                           _vp, _vp, _vp, _vp, _vp])
 SALE_STATIC_MAX_CELLS = 65536
 SALE_STATIC_MAX_NODES = 131072
+sale_fma_probe = _sig("sale_fma_probe", C.c_int, [C.c_int, _vp, C.c_size_t, _vp, C.POINTER(C.c_double)])
 sale_last_error = _sig("sale_last_error", C.c_char_p, [])
 
 #: every symbol declared in include/sale.h
-EXPORTS = ("sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes", "sale_state_bytes_for",
+EXPORTS = ("sale_fma_probe", "sale_mesh_create", "sale_mesh_destroy", "sale_mesh_nodes", "sale_state_bytes", "sale_state_bytes_for",
            "sale_state_init", "sale_state_destroy", "sale_lagrange_step", "sale_remap_step",
            "sale_run_to_time", "sale_diagnostics", "sale_copy_field", "sale_set_field",
            "sale_refresh", "sale_state_dims", "sale_profile", "sale_profile_read",
