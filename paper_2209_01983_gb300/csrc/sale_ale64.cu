@@ -351,7 +351,9 @@ __device__ __forceinline__ void ale_edge_apply(const Fields<double> &F, long lon
                                                double &ke) {
   const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)(F.nx + 1) : (long long)(F.nx + 1) * (F.ny + 1);
   const long long lo = SIDE == 0 ? n : n - stride;
-  const long long dn = psi > 0.0 ? lo + stride : lo;
+  // psi > 0 as an integer test of its bits (positive, not zero): the
+  // comparison stays off the FP64 pipe, which this kernel keeps ~90% busy
+  const long long dn = __double_as_longlong(psi) > 0ll ? lo + stride : lo;
   const double flux = SIDE == 0 ? psi : -psi;
   m += flux;
   p.x += flux * F.u[dn];
