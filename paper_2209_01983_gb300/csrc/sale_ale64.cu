@@ -251,7 +251,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevSca
   if (j + 1 < F.ny) net += F.dvy[c + sy];
   if (k + 1 < F.nz) net += F.dvz[c + sz];
   const double VL = F.VE[c] - net;
-  if (!(VL > 0.0)) set_status(S, VL != VL ? SALE_ENAN : SALE_ENEGVOL);
+  if (!pos_d(VL)) set_status(S, nan_d(VL) ? SALE_ENAN : SALE_ENEGVOL);  // a NaN with the sign clear: caught by the EoS
   F.vol[c] = VL;
   F.rho[c] = F.m[c] / VL;
   if (F.remap_order == 2) F.ivl[c] = 1.0 / VL;  // the six faces' swept fractions multiply by it
@@ -315,7 +315,7 @@ __device__ __forceinline__ void ale_face_flux(const Fields<double> &F, long long
     ep[c] = 0.0;
   } else {
     const double v = dv[c];
-    const bool hd = v > 0.0;
+    const bool hd = pos_d(v);
     double ef;
     lo = ale_donor_flux<O2>(F, sr, se, hd ? c : c - stride, hd, v, ef);
     mu[c] = lo;
@@ -324,7 +324,7 @@ __device__ __forceinline__ void ale_face_flux(const Fields<double> &F, long long
   double hi = 0.0;
   if (idx + 1 < n_ax) {
     const double v = dv[c + stride];
-    const bool hd = v > 0.0;
+    const bool hd = pos_d(v);
     double ef;
     hi = ale_donor_flux<O2>(F, sr, se, hd ? c + stride : c, hd, v, ef);
   }
@@ -454,9 +454,9 @@ __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long lon
   const double L = F.LE[c];
   const double rho = m * inv_v;
   const double p = (F.gamma - 1.0) * rho * e;
-  const double cs2 = F.gamma * (F.gamma - 1.0) * fmax(e, 0.0);
+  const double cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
   double q_rho = 0.0;  // q / rho
-  if (div < 0.0) {     // the sound speed itself only where the cell compresses
+  if (sign_d(div)) {   // div < 0 (-0 gives q = 0 either way); the sound speed itself only where the cell compresses
     const double ld = L * div;
     q_rho = F.c_q * ld * ld + F.c_l * sqrt(cs2) * L * fabs(div);
   }
@@ -569,12 +569,13 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
         ie += F.dke[node_index(F.nx, F.ny, ni, nj, nk)] * share;
       }
     }
-    if (!(m1 > 0.0)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
+    // (a NaN mass with the sign bit clear passes here and makes the rate NaN)
+    if (!pos_d(m1)) set_status(S, nan_d(m1) ? SALE_ENAN : SALE_ENEGVOL);
     const double e = ie / m1;
     F.m[c] = m1;
     F.e[c] = e;
     rate = ale_eos_cell(F, c, U, m1, e);
-    if (rate != rate) {
+    if (nan_d(rate)) {
       set_status(S, SALE_ENAN);
       rate = 0.0;
     }
@@ -592,7 +593,8 @@ __global__ void __launch_bounds__(kBlock, 3) k_ale_remap_eos(Fields<double> F, D
   const long long c0 = blockIdx.x * (long long)(kBlock * kEosCellsPerThread) + threadIdx.x;
   double rate = 0.0;  // CFL rate 1 / dt_c^2
 #pragma unroll 1
-  for (int r = 0; r < kEosCellsPerThread; ++r) rate = fmax(rate, ale_remap_eos_cell(F, S, c0 + (long long)r * kBlock));
+  for (int r = 0; r < kEosCellsPerThread; ++r)
+    rate = max_nonneg_d(rate, ale_remap_eos_cell(F, S, c0 + (long long)r * kBlock));  // rates are >= 0, not NaN
   block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
 }
 

@@ -11,6 +11,22 @@ namespace sale {
 
 constexpr unsigned long long kInfBits = 0x7FF0000000000000ull;
 
+// Sign, clamp, maximum and NaN tests of doubles as integer operations on
+// their bits.  The FP64 kernels keep GB300's FP64 pipe about 90% busy, and
+// each comparison, min/max or NaN test there takes a slot of that pipe;
+// these take integer slots instead and give the same result for every
+// non-NaN value (NaNs are still caught: see each use).
+__device__ __forceinline__ bool pos_d(double x) { return __double_as_longlong(x) > 0ll; }     // x > 0
+__device__ __forceinline__ bool sign_d(double x) { return __double_as_longlong(x) < 0ll; }    // sign bit set
+__device__ __forceinline__ double max0_d(double x) { return sign_d(x) ? 0.0 : x; }           // max(x, 0)
+__device__ __forceinline__ bool nan_d(double x) {
+  return (unsigned long long)(__double_as_longlong(x) & 0x7FFFFFFFFFFFFFFFll) > kInfBits;
+}
+// max(a, b) of two non-negative doubles: their bits order like the values.
+__device__ __forceinline__ double max_nonneg_d(double a, double b) {
+  return __double_as_longlong(a) >= __double_as_longlong(b) ? a : b;
+}
+
 template <typename R>
 __device__ __forceinline__ void load_hex(const R *px, const R *py, const R *pz, int nx, int ny, int i,
                                          int j, int k, P3 (&X)[8]) {
