@@ -26,6 +26,14 @@ NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr
                      "-I", INCLUDE, "-I", CSRC]
 
 
+# Per-file flags.  The FP32-mixed kernels are compiled without FMA
+# contraction: every tile shape is its own template instantiation, and a
+# compiler free to fuse a * b + c differently in each would make the result
+# depend on the launch shape; the kernels write the FMAs they want as
+# intrinsics (__fmaf_rn), which stay fused.
+FILE_FLAGS = {"sale_ale32.cu": ["-fmad=false"]}
+
+
 def _nvcc():
     for cand in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
         if cand and (os.path.isabs(cand) and os.path.exists(cand) or not os.path.isabs(cand)):
@@ -53,8 +61,9 @@ def build(force: bool = False, verbose: bool = False, ptxas_info: bool = False) 
     for src in sources():
         obj = os.path.join(BUILD, os.path.basename(src)[:-3] + ".o")
         objs.append(obj)
-        if force or _stale(obj, [src] + headers):
-            cmd = [nvcc] + NVCC_FLAGS + (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
+        if force or _stale(obj, [src, os.path.abspath(__file__)] + headers):
+            cmd = [nvcc] + NVCC_FLAGS + FILE_FLAGS.get(os.path.basename(src), []) + \
+                (["-Xptxas", "-v"] if ptxas_info else []) + ["-c", src, "-o", obj]
             jobs.append(cmd)
     if jobs:
         with cf.ThreadPoolExecutor(max_workers=min(len(jobs), os.cpu_count() or 4)) as ex:

@@ -57,6 +57,13 @@ __device__ __forceinline__ F3 cross_rn(F3 a, F3 b) {
   return {__fmaf_rn(a.y, b.z, -__fmul_rn(a.z, b.y)), __fmaf_rn(a.z, b.x, -__fmul_rn(a.x, b.z)),
           __fmaf_rn(a.x, b.y, -__fmul_rn(a.y, b.x))};
 }
+// s a + b, fused.  This file is compiled without automatic FMA contraction
+// (every tile shape is a separate instantiation of the kernels, and a
+// compiler free to fuse differently in each would make results depend on
+// the launch shape), so the multiply-adds it wants fused are written so.
+__device__ __forceinline__ F3 fma3(float s, F3 a, F3 b) {
+  return {__fmaf_rn(s, a.x, b.x), __fmaf_rn(s, a.y, b.y), __fmaf_rn(s, a.z, b.z)};
+}
 
 // ---------------------------------------------------------------------------
 // Float-float arithmetic for the conserved cell quantities
@@ -129,7 +136,8 @@ __device__ __forceinline__ float4 off_at(const Fields<float> &F, int n) {
 template <bool JIT>
 __device__ __forceinline__ F3 relp(const Fields<float> &F, float4 oa, int nb, int ox, int oy, int oz) {
   const float4 ob = off_at<JIT>(F, nb);
-  return {(float)ox * F.hx + (ob.x - oa.x), (float)oy * F.hy + (ob.y - oa.y), (float)oz * F.hz + (ob.z - oa.z)};
+  return {__fmaf_rn((float)ox, F.hx, ob.x - oa.x), __fmaf_rn((float)oy, F.hy, ob.y - oa.y),
+          __fmaf_rn((float)oz, F.hz, ob.z - oa.z)};
 }
 
 // Reference nodes of the cell whose node 0 is n0 (node strides sy, sz),
@@ -154,7 +162,7 @@ __device__ __forceinline__ float grad_dot_f(const F3 (&X)[8], const F3 (&U)[8]) 
       const F3 pa = X[face_node(f, (k + 1) & 3)];
       const F3 pb = X[face_node(f, (k + 2) & 3)];
       const F3 pc = X[face_node(f, (k + 3) & 3)];
-      s = __fadd_rn(s, dot_rn(cross_rn(pa + 2.f * pb + pc, pc - pa), U[face_node(f, k)]));
+      s = __fadd_rn(s, dot_rn(cross_rn(fma3(2.f, pb, pa) + pc, pc - pa), U[face_node(f, k)]));
     }
   }
   return s * (1.f / 24.f);
@@ -265,7 +273,8 @@ __device__ __forceinline__ F3 hg_corner_f(const float *fh, long long nc, int c, 
 
 // Side quad (L_a, E_a, E_b, L_b) term, expanded in the displacements.
 __device__ __forceinline__ float side_term(const F3 (&E)[8], const F3 (&D)[8], int a, int b) {
-  return 4.f * dotf(crossf(E[a], E[b]), D[a] + D[b]) - 2.f * dotf(E[a] + E[b], crossf(D[a], D[b]));
+  return __fmaf_rn(4.f, dot_rn(cross_rn(E[a], E[b]), D[a] + D[b]),
+                   -2.f * dot_rn(E[a] + E[b], cross_rn(D[a], D[b])));
 }
 
 // Lagrangian face (p0,p1,p2,p3) plus the reversed reference face, expanded.
@@ -274,7 +283,7 @@ __device__ __forceinline__ float pair_term(const F3 (&E)[8], const F3 (&D)[8], i
   const F3 d1 = D[p2] - D[p0], d2 = D[p3] - D[p1];
   const F3 se = E[p0] + E[p1] + E[p2] + E[p3];
   const F3 sd = D[p0] + D[p1] + D[p2] + D[p3];
-  return dotf(se, crossf(e1, d2) + crossf(d1, e2) + crossf(d1, d2)) + dotf(sd, crossf(e1 + d1, e2 + d2));
+  return dot_rn(se, cross_rn(e1, d2) + cross_rn(d1, e2) + cross_rn(d1, d2)) + dot_rn(sd, cross_rn(e1 + d1, e2 + d2));
 }
 
 // Swept volumes of the three low faces (see the file comment); E relative
@@ -372,7 +381,7 @@ __device__ __forceinline__ void node_face2(const Fields<float> &F, int n, int sy
   const F3 p1 = relp<JIT>(F, oa, n + X1 + Y1 * sy + Z1 * sz, X1, Y1, Z1);
   const F3 p2 = relp<JIT>(F, oa, n + X2 + Y2 * sy + Z2 * sz, X2, Y2, Z2);
   const F3 p3 = relp<JIT>(F, oa, n + X3 + Y3 * sy + Z3 * sz, X3, Y3, Z3);
-  f = f + ds * crossf(p1 + 2.f * p2 + p3, p3 - p1);
+  f = fma3(ds, cross_rn(fma3(2.f, p2, p1) + p3, p3 - p1), f);
 }
 
 template <bool JIT, int SB>
@@ -438,9 +447,9 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
       const int c = c0 + (q & 1) + ((q >> 1) & 1) * csy + ((q >> 2) & 1) * csz;
       const float *g = Gsrc + (3 * (7 - q)) * nc + c;  // this node is corner 7 - q of cell q
       const float ds = sig[q] - ref;
-      f.x += ds * __ldg(g);
-      f.y += ds * __ldg(g + nc);
-      f.z += ds * __ldg(g + 2 * nc);
+      f.x = __fmaf_rn(ds, __ldg(g), f.x);
+      f.y = __fmaf_rn(ds, __ldg(g + nc), f.y);
+      f.z = __fmaf_rn(ds, __ldg(g + 2 * nc), f.z);
       if (fh) f = f + hg_corner_f(fh, nc, c, 7 - q);
     }
     hm = h / F.mn[n];
@@ -464,7 +473,7 @@ __device__ __forceinline__ void m_nodes_body(const Fields<float> &F, DevScalars 
     hm = h / (24.f * F.mn[n]);
   }
   const float u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
-  float u1 = u0 + hm * f.x, v1 = v0 + hm * f.y, w1 = w0 + hm * f.z;
+  float u1 = __fmaf_rn(hm, f.x, u0), v1 = __fmaf_rn(hm, f.y, v0), w1 = __fmaf_rn(hm, f.z, w0);
   if (!IN) wall_bc_f(F, i, j, k, u1, v1, w1);
   F.u[n] = u1;
   F.v[n] = v1;
@@ -717,8 +726,8 @@ __device__ __forceinline__ void m_edge_apply(const Fields<float> &F, int n, floa
   const F3 ud = {F.u[dn], F.v[dn], F.w[dn]};
   const float flux = SIDE == 0 ? psi : -psi;
   m = df_add_f(m, flux);  // float-float: the node mass absorbs fluxes ~1% of it every cycle
-  p = p + flux * ud;
-  ke += flux * 0.5f * dotf(ud, ud);
+  p = fma3(flux, ud, p);
+  ke = __fmaf_rn(flux * 0.5f, dot_rn(ud, ud), ke);
 }
 
 // New node velocity, mass and kinetic-energy defect from the remapped sums.
@@ -734,7 +743,7 @@ __device__ __forceinline__ void m_remap_node_store(const Fields<float> &F, DevSc
   F.wb[n] = w1;
   F.mn[n] = m.hi;
   F.mnlo[n] = m.lo;
-  F.dke[n] = ke - 0.5f * m.hi * (u1 * u1 + v1 * v1 + w1 * w1);
+  F.dke[n] = __fmaf_rn(-0.5f * m.hi, dot_rn(F3{u1, v1, w1}, F3{u1, v1, w1}), ke);
 }
 
 // The node remap marches in k: a block covers a tile of node columns over
@@ -814,7 +823,7 @@ __device__ __forceinline__ void m_remap_node_step(const Fields<float> &F, DevSca
   const F3 u0 = {F.u[n], F.v[n], F.w[n]};
   DF m = {m0, F.mnlo[n]};
   F3 p = m0 * u0;
-  float ke = 0.5f * m0 * dotf(u0, u0);
+  float ke = 0.5f * m0 * dot_rn(u0, u0);
   if (IN || m_edge_exists<0, 0>(F, i, j, k)) m_edge_apply<0, 0>(F, n, px0, m, p, ke);
   if (IN || m_edge_exists<0, 1>(F, i, j, k)) m_edge_apply<0, 1>(F, n, px1, m, p, ke);
   if (IN || m_edge_exists<1, 0>(F, i, j, k)) m_edge_apply<1, 0>(F, n, py0, m, p, ke);

@@ -50,7 +50,22 @@ def interior_plain():
     return md, pd
 
 
-@pytest.mark.parametrize("mesh", [ragged_sedov, interior_sedov, interior_plain])
+def interior_sod(jitter=0.0):
+    # a shock tube whose diaphragm (x = 0.5, cells 38 and 39) lies in tiles
+    # that are interior for some shapes and not for others, with the
+    # velocity nonzero there from the first cycle on
+    md, pd = inputs.sod_x(78, 13, 10)
+    md.hi = (1.0, 13 / 78, 10 / 78)
+    md.jitter = jitter
+    return md, pd
+
+
+def interior_sod_jittered():
+    return interior_sod(0.1)
+
+
+@pytest.mark.parametrize("mesh", [ragged_sedov, interior_sedov, interior_plain, interior_sod,
+                                  interior_sod_jittered])
 def test_state_tile_shapes_bitwise(sale, mesh):
     from paper_2209_01983_gb300 import autotune
     md, pd = mesh()

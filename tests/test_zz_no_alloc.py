@@ -13,6 +13,7 @@ rejects meshes larger than its fixed scratch.  It sits last in collection
 order so a failure here comes after every other test has run.
 """
 import ctypes as C
+import gc
 
 import numpy as np
 import pytest
@@ -65,13 +66,19 @@ def test_static_remap_matches_state_remap(env):
         mn, m, e, rho = upload("mn"), upload("m"), upload("e"), upload("rho")
         torch.cuda.synchronize()
         p = lambda t: C.c_void_p(t.data_ptr())
-        free0 = torch.cuda.mem_get_info()[0]
-        torch0 = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
-        rc = sale.sale_remap_static(md.nx, md.ny, md.nz, reflect, pd.ke_fix, p(xref), p(x), p(u_in),
-                                    p(u_out), p(mn), p(m), p(e), p(rho), C.c_void_p(stream.cuda_stream))
+        gc.collect()
+        gc.disable()  # no tensor of this process is freed while the call is measured
+        try:
+            free0 = torch.cuda.mem_get_info()[0]
+            torch0 = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+            rc = sale.sale_remap_static(md.nx, md.ny, md.nz, reflect, pd.ke_fix, p(xref), p(x), p(u_in),
+                                        p(u_out), p(mn), p(m), p(e), p(rho), C.c_void_p(stream.cuda_stream))
+            torch1 = (torch.cuda.memory_allocated(), torch.cuda.memory_reserved())
+            free1 = torch.cuda.mem_get_info()[0]
+        finally:
+            gc.enable()
         assert rc == sale.SALE_OK, sale.sale_last_error()
-        free1 = torch.cuda.mem_get_info()[0]
-        assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == torch0, call
+        assert torch1 == torch0, call
         if call == 1:  # the first call may load the library's GPU code (and its static array)
             assert free1 == free0, (free0, free1)
         nn = md.nnode
