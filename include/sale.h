@@ -269,8 +269,8 @@ void sale_batch_destroy(sale_batch *b);
 
 /* Tuning knobs of the FP32-mixed kernels (no effect on results: every
  * thread's work is independent of the tiling and the dt minimum is exact).
- * Shapes 0..3 are thread tiles of tx x ty threads over one k plane:
- * (32,8), (32,4), (64,4), (128,2).  sale_set_tiling applies to an
+ * Shapes 0..4 are thread tiles of tx x ty threads over one k plane:
+ * (32,8), (32,4), (64,4), (128,2), (16,8).  sale_set_tiling applies to an
  * FP32-mixed state (EINVAL otherwise); sale_batch_set_schedule sets the
  * shape of a batch and the order of its meshes' tiles in a launch
  * (0: input order, 1: largest mesh first).  Both synchronise and drop

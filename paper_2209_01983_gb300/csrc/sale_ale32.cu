@@ -1186,6 +1186,7 @@ static void launch_one(const Fields<float> &F, DevScalars *S, int mode, int shap
     case 1: launch_shaped<KID, 1>(F, S, mode, st); break;
     case 2: launch_shaped<KID, 2>(F, S, mode, st); break;
     case 3: launch_shaped<KID, 3>(F, S, mode, st); break;
+    case 4: launch_shaped<KID, 4>(F, S, mode, st); break;
     default: launch_shaped<KID, 0>(F, S, mode, st); break;
   }
 }
@@ -1224,6 +1225,7 @@ void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned n
     case 1: launch_batch_shaped<1>(kid, items, tab, nblocks, st); break;
     case 2: launch_batch_shaped<2>(kid, items, tab, nblocks, st); break;
     case 3: launch_batch_shaped<3>(kid, items, tab, nblocks, st); break;
+    case 4: launch_batch_shaped<4>(kid, items, tab, nblocks, st); break;
     default: launch_batch_shaped<0>(kid, items, tab, nblocks, st); break;
   }
 }

@@ -168,14 +168,18 @@ __host__ __device__ constexpr float hg_pattern(int alpha, int a) {
 
 // Thread-tile shapes of the FP32-mixed kernels (x by y threads over one k
 // plane); the autotuner picks one per state or batch.
-constexpr int kNumTileShapes = 4;
+constexpr int kNumTileShapes = 5;
 // Node planes one block of the FP32-mixed node remap marches over, and cell
 // planes one block of its remap + EoS + dt pass covers.
 constexpr int kRemapChunk = 16;
 constexpr int kEosPlanes = 8;
 
-__host__ __device__ constexpr int tile_x(int shape) { return shape == 0 ? 32 : shape == 1 ? 32 : shape == 2 ? 64 : 128; }
-__host__ __device__ constexpr int tile_y(int shape) { return shape == 0 ? 8 : shape == 1 ? 4 : shape == 2 ? 4 : 2; }
+__host__ __device__ constexpr int tile_x(int shape) {
+  return shape == 0 ? 32 : shape == 1 ? 32 : shape == 2 ? 64 : shape == 3 ? 128 : 16;
+}
+__host__ __device__ constexpr int tile_y(int shape) {
+  return shape == 0 ? 8 : shape == 1 ? 4 : shape == 2 ? 4 : shape == 3 ? 2 : 8;
+}
 constexpr int kMaxWarpsPerBlock = 16;
 
 // One mesh of a batch, as seen by the batched kernels.

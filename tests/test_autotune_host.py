@@ -53,7 +53,7 @@ def test_tile_shapes_from_library(sale):
     assert shapes[0][1:] == (32, 8)
     assert len(shapes) >= 2
     for _, tx, ty in shapes:
-        assert tx % 32 == 0 and tx * ty <= 1024  # whole warps along x, a legal block
+        assert tx % 16 == 0 and (tx * ty) % 32 == 0 and tx * ty <= 1024  # whole warps, a legal block
     assert sale.sale_tile_shape(len(shapes), None, None) == sale.SALE_EINVAL
     assert sale.sale_tile_shape(-1, None, None) == sale.SALE_EINVAL
 
