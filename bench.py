@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--batch-steps", type=int, default=20,
                     help="default run: timed cycles of the batch variant")
     ap.add_argument("--no-batch", action="store_true", help="default run: skip the batch variant")
+    ap.add_argument("--no-one-by-one", action="store_true",
+                    help="batch: skip the comparison with the meshes advanced one by one")
     ap.add_argument("--no-precision", action="store_true", help="default run: skip the precision variant")
     ap.add_argument("--precision-n", type=int, default=128,
                     help="default run: cells per axis of the precision variant (to --t-end)")
@@ -635,16 +637,19 @@ def measure_batch(args, local, steps, unbatched_steps, count):
             st.close()
         return cells * cycles / (total * 1e-3)
 
-    rate_single_mixed = one_by_one("fp32_mixed", unbatched_steps)
-    rate_single_fp64 = one_by_one("fp64", unbatched_steps)
+    compare = None
+    if not args.no_one_by_one:
+        rate_single_mixed = one_by_one("fp32_mixed", unbatched_steps)
+        rate_single_fp64 = one_by_one("fp64", unbatched_steps)
+        compare = {"one_by_one_fp32_mixed": rate_single_mixed, "one_by_one_fp64": rate_single_fp64,
+                   "speedup_vs_one_by_one_fp32_mixed": value / rate_single_mixed,
+                   "speedup_vs_one_by_one_fp64": value / rate_single_fp64,
+                   "one_by_one_cycles": unbatched_steps}
     return {"value": value, "unit": UNIT, "steps": steps, "ms_per_step": ms / steps,
             "dtype": "f32 (f64 islands)", "cells": cells, "instances": len(inst),
             "workload": f"batch of {len(inst)} shock-tube/Sedov meshes, 16..96 cells per axis, seed 2209, "
                         f"FP32-mixed, Eulerian every cycle, {steps} cycles of every mesh per timed run",
-            "compare": {"one_by_one_fp32_mixed": rate_single_mixed, "one_by_one_fp64": rate_single_fp64,
-                        "speedup_vs_one_by_one_fp32_mixed": value / rate_single_mixed,
-                        "speedup_vs_one_by_one_fp64": value / rate_single_fp64,
-                        "one_by_one_cycles": unbatched_steps},
+            "compare": compare,
             "gpu_launches": 5 * steps + 2, "clocks": clk, "check": {"t_samples": ts}, "tuning": tuning}
 
 
