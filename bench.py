@@ -502,7 +502,10 @@ def e2e_rate(args, res, world):
         times.append(1e3 * (time.perf_counter() - ts))
     secs = time.perf_counter() - t0
     return {"value": world * md.ncell * steps / secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
-            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": [round(t, 2) for t in times]}
+            "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": [round(t, 2) for t in times],
+            "h2d": "u, v, w, node mass, cell mass, specific energy (FP64, pinned host memory) through sale_set_field",
+            "d2h": "the step's result as sale_diagnostics: mass, momentum, internal, kinetic and total energy, "
+                   "t, dt, cycle and status (the fields stay on the device)"}
 
 
 def gpu_arm(args):

@@ -44,14 +44,19 @@ __device__ __forceinline__ P3 corner_g(const double *G, long long nc, long long 
   return {g[0], g[nc], g[2 * nc]};
 }
 
-// Face term of the fan volume formula for the quad (p0,p1,p2,p3):
+// Half the face term of the fan volume formula for the quad (p0,p1,p2,p3):
 // T = (p0+p1+p2+p3) . (d1 x d2), d1 = p2 - p0, d2 = p3 - p1; a hex volume is
 // (1/24) times the sum of the terms of its six outward faces (same origin
 // for all six).  With p2 + p3 = p0 + p1 + d1 + d2 and (d1 + d2) . (d1 x d2)
-// = 0 this is T = 2 (p0 + p1) . (d1 x d2), five FP64 operations fewer.
+// = 0 this is T = 2 (p0 + p1) . (d1 x d2), five FP64 operations fewer.  The
+// edge pass stores T / 2 (one FP64 multiply fewer per term) and the cell
+// pass scales the sums by 1/12: halving is exact in binary floating point
+// and commutes with every rounding, and 1/12 = 2 (1/24) exactly, so the
+// swept volumes are bitwise those of the full terms scaled by 1/24.
 __device__ __forceinline__ double quad_term(P3 p0, P3 p1, P3 p2, P3 p3) {
-  return 2.0 * dot(p0 + p1, cross(p2 - p0, p3 - p1));
+  return dot(p0 + p1, cross(p2 - p0, p3 - p1));
 }
+constexpr double kInvTwelfth = 1.0 / 12.0;
 
 }  // namespace
 
@@ -138,21 +143,21 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
 }
 
 // Side quad (L_a, E_a, E_b, L_b) of the swept hexes along the mesh edge from
-// node a = n to b = n + e_AX: its fan term with node n as origin, and the
-// same term for origin n - e_Q of each other axis Q (the node 0 of the other
-// cells whose low faces hold the edge): T(o) = T(n) + 4 (x_n - x_o) . A, A
-// the quad's diagonal cross product.  ste[(3 AX + v) nn + n], v = 0 for
+// node a = n to b = n + e_AX: half its fan term with node n as origin, and
+// the same for origin n - e_Q of each other axis Q (the node 0 of the other
+// cells whose low faces hold the edge): T(o) / 2 = T(n) / 2 + 2 (x_n - x_o)
+// . A, A the quad's diagonal cross product.  ste[(3 AX + v) nn + n], v = 0 for
 // origin n, v = 1, 2 for the other two axes in increasing order.  Eb, Lb:
 // reference and Lagrangian position of b relative to x_n.
 template <int AX>
 __device__ __forceinline__ void edge_side_terms(const Fields<double> &F, long long n, const int (&ijk)[3],
                                                 const P3 (&back)[3], P3 La, P3 Eb, P3 Lb) {
   const P3 A = cross(Eb - La, Lb);  // diagonals (E_b - L_a) and (L_b - E_a), E_a = 0
-  const double T = 2.0 * dot(La, A);  // 2 (L_a + E_a) . A
+  const double T = dot(La, A);  // (L_a + E_a) . A, half the fan term
   F.ste[(3 * AX) * F.nn + n] = T;
   constexpr int Q1 = AX == 0 ? 1 : 0, Q2 = AX == 2 ? 1 : 2;
-  if (ijk[Q1] > 0) F.ste[(3 * AX + 1) * F.nn + n] = T + 4.0 * dot(back[Q1], A);
-  if (ijk[Q2] > 0) F.ste[(3 * AX + 2) * F.nn + n] = T + 4.0 * dot(back[Q2], A);
+  if (ijk[Q1] > 0) F.ste[(3 * AX + 1) * F.nn + n] = T + 2.0 * dot(back[Q1], A);
+  if (ijk[Q2] > 0) F.ste[(3 * AX + 2) * F.nn + n] = T + 2.0 * dot(back[Q2], A);
 }
 
 // Per node n: the side quads of the three mesh edges leaving it and, when n
@@ -234,9 +239,9 @@ __global__ void __launch_bounds__(kBlock, 4) k_ale_cells(Fields<double> F, DevSc
   const double sx = ste[9 * nn + n0] + cz0 - czy - cy0 + cyz;
   const double sy = ste[10 * nn + n0] - cz0 + czx + cx0 - cxz;
   const double sz = ste[11 * nn + n0] + cy0 - cyx - cx0 + cxy;
-  F.dvx[c] = i > 0 ? sx * kInvSixth24 : 0.0;
-  F.dvy[c] = j > 0 ? sy * kInvSixth24 : 0.0;
-  F.dvz[c] = k > 0 ? sz * kInvSixth24 : 0.0;
+  F.dvx[c] = i > 0 ? sx * kInvTwelfth : 0.0;  // the terms are halves (see quad_term)
+  F.dvy[c] = j > 0 ? sy * kInvTwelfth : 0.0;
+  F.dvz[c] = k > 0 ? sz * kInvTwelfth : 0.0;
 }
 
 __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevScalars *S) {
