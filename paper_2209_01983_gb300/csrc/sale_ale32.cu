@@ -1046,8 +1046,10 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
 
 // Batched: block b works on mesh tab[b].x, tile (tab[b].y, tab[b].z) of
 // plane tab[b].w; the part of the mesh's descriptor these kernels read is
-// staged in shared memory.
-template <int KID, int SH>
+// staged in shared memory.  AJ: some mesh of the batch is jittered (each
+// block then picks its mesh's body at run time); a batch of unjittered
+// meshes runs kernels compiled with that body alone, fewer registers live.
+template <int KID, int SH, bool AJ>
 __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_x(SH) * tile_y(SH)))
     kb_m(const BatchItem *items, const int4 *tab) {
   __shared__ BatchItem it;
@@ -1058,7 +1060,7 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), min_blocks(KID, tile_
   for (int w = tid; w < (int)(kBatchItemStaged / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
   __syncthreads();
   // batches take neither the predictor-corrector step nor hourglass control
-  if (it.F.off4) run_tile<KID, true, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
+  if (AJ && it.F.off4) run_tile<KID, true, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
   else run_tile<KID, false, SH, false>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell, 0);
 }
 
@@ -1094,7 +1096,7 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kEosResident / (tile_
 
 // Batched remap + EoS + dt: block b covers chunk tab[b].w of tile
 // (tab[b].y, tab[b].z) of mesh tab[b].x.
-template <int SH>
+template <int SH, bool AJ>
 __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kEosResidentBatch / (tile_x(SH) * tile_y(SH)))
     kb_m_remap_eos_planes(const BatchItem *items, const int4 *tab) {
   __shared__ BatchItem it;
@@ -1104,7 +1106,7 @@ __global__ void __launch_bounds__(tile_x(SH) * tile_y(SH), kEosResidentBatch / (
   int *dst = reinterpret_cast<int *>(&it);
   for (int w = tid; w < (int)(kBatchItemStaged / sizeof(int)); w += tile_x(SH) * tile_y(SH)) dst[w] = src[w];
   __syncthreads();
-  if (it.F.off4) m_remap_eos_column<true, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell);
+  if (AJ && it.F.off4) m_remap_eos_column<true, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell);
   else m_remap_eos_column<false, SH>(it.F, it.S, t.y, t.z, t.w, it.nblk_cell);
 }
 
@@ -1206,28 +1208,36 @@ void launch_m_kernel(int kid, const Fields<float> &F, DevScalars *S, int mode, i
   }
 }
 
-template <int SH>
+template <int SH, bool AJ>
 static void launch_batch_shaped(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, cudaStream_t st) {
   const dim3 b(tile_x(SH), tile_y(SH));
   switch (kid) {
-    case kMixNodes: kb_m<kMixNodes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixCells: kb_m<kMixCells, SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixFluxes: kb_m<kMixFluxes, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixNodes: kb_m<kMixNodes, SH, AJ><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixCells: kb_m<kMixCells, SH, AJ><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixFluxes: kb_m<kMixFluxes, SH, AJ><<<nblocks, b, 0, st>>>(items, tab); break;
     case kMixRemapNodes: kb_m_remap_nodes_march<SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixRemapEos: kb_m_remap_eos_planes<SH><<<nblocks, b, 0, st>>>(items, tab); break;
-    case kMixDensity: kb_m<kMixDensity, SH><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixRemapEos: kb_m_remap_eos_planes<SH, AJ><<<nblocks, b, 0, st>>>(items, tab); break;
+    case kMixDensity: kb_m<kMixDensity, SH, AJ><<<nblocks, b, 0, st>>>(items, tab); break;
     default: break;
   }
 }
 
-void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, cudaStream_t st) {
+template <bool AJ>
+static void launch_batch_any(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape,
+                             cudaStream_t st) {
   switch (shape) {
-    case 1: launch_batch_shaped<1>(kid, items, tab, nblocks, st); break;
-    case 2: launch_batch_shaped<2>(kid, items, tab, nblocks, st); break;
-    case 3: launch_batch_shaped<3>(kid, items, tab, nblocks, st); break;
-    case 4: launch_batch_shaped<4>(kid, items, tab, nblocks, st); break;
-    default: launch_batch_shaped<0>(kid, items, tab, nblocks, st); break;
+    case 1: launch_batch_shaped<1, AJ>(kid, items, tab, nblocks, st); break;
+    case 2: launch_batch_shaped<2, AJ>(kid, items, tab, nblocks, st); break;
+    case 3: launch_batch_shaped<3, AJ>(kid, items, tab, nblocks, st); break;
+    case 4: launch_batch_shaped<4, AJ>(kid, items, tab, nblocks, st); break;
+    default: launch_batch_shaped<0, AJ>(kid, items, tab, nblocks, st); break;
   }
+}
+
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, bool any_jit,
+                    cudaStream_t st) {
+  if (any_jit) launch_batch_any<true>(kid, items, tab, nblocks, shape, st);
+  else launch_batch_any<false>(kid, items, tab, nblocks, shape, st);
 }
 
 // Field transfers of FP32-mixed states: FP64 values to FP32 (hi, optional lo)

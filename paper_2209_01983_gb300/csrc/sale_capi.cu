@@ -1126,7 +1126,8 @@ extern "C" int sale_state_dims(const sale_state *st, long long *ncells, long lon
 // ---------------------------------------------------------------------------
 
 namespace sale {
-void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, cudaStream_t st);
+void launch_m_batch(int kid, const BatchItem *items, const int4 *tab, unsigned nblocks, int shape, bool any_jit,
+                    cudaStream_t st);
 void launch_batch_limits(const BatchItem *items, int n, long long cycles, cudaStream_t st);
 void launch_batch_gather(const BatchItem *items, int n, BatchStatus *out, cudaStream_t st);
 }  // namespace sale
@@ -1145,6 +1146,7 @@ struct sale_batch {
   std::vector<sale_mesh_desc> meshes;
   int shape = 0;                    // thread-tile shape
   bool any_order2 = false;          // some mesh uses the second-order remap
+  bool any_jit = false;             // some mesh is jittered (its kernels carry both bodies)
   int order = 0;                    // 0: meshes in input order, 1: largest mesh first
   std::map<long long, cudaGraphExec_t> graphs;
 };
@@ -1318,6 +1320,7 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   }
   b->meshes.assign(meshes, meshes + n);
   for (int i = 0; i < n; ++i) b->any_order2 = b->any_order2 || probs[i].remap_order == 2;
+  for (int i = 0; i < n; ++i) b->any_jit = b->any_jit || meshes[i].jitter > 0.0;
   rc = upload_batch_tables(b);
   if (rc == SALE_OK) rc = upload_batch_items(b);
   if (rc) {
@@ -1336,13 +1339,13 @@ extern "C" sale_state *sale_batch_state(sale_batch *b, int i) {
 // One cycle of every mesh: the four kernels before the velocity-buffer
 // toggle read descriptors of parity p, the fused remap/EoS/dt one p ^ 1.
 static void launch_batch_cycle(sale_batch *b, int p) {
-  launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->stream);
-  launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
+  launch_m_batch(kMixNodes, b->items[p], b->tab_node, b->nb_node, b->shape, b->any_jit, b->stream);
+  launch_m_batch(kMixCells, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->any_jit, b->stream);
   if (b->any_order2)  // first-order meshes leave this pass at once
-    launch_m_batch(kMixDensity, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
-  launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->stream);
-  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_chunk, b->nb_chunk, b->shape, b->stream);
-  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_eos, b->nb_eos, b->shape, b->stream);
+    launch_m_batch(kMixDensity, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->any_jit, b->stream);
+  launch_m_batch(kMixFluxes, b->items[p], b->tab_cell, b->nb_cell, b->shape, b->any_jit, b->stream);
+  launch_m_batch(kMixRemapNodes, b->items[p], b->tab_chunk, b->nb_chunk, b->shape, b->any_jit, b->stream);
+  launch_m_batch(kMixRemapEos, b->items[p ^ 1], b->tab_eos, b->nb_eos, b->shape, b->any_jit, b->stream);
 }
 
 extern "C" int sale_batch_set_schedule(sale_batch *b, int shape, int order) {
