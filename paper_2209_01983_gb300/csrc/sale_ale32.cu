@@ -40,10 +40,6 @@ struct F3 {
 __device__ __forceinline__ F3 operator+(F3 a, F3 b) { return {a.x + b.x, a.y + b.y, a.z + b.z}; }
 __device__ __forceinline__ F3 operator-(F3 a, F3 b) { return {a.x - b.x, a.y - b.y, a.z - b.z}; }
 __device__ __forceinline__ F3 operator*(float s, F3 a) { return {s * a.x, s * a.y, s * a.z}; }
-__device__ __forceinline__ F3 crossf(F3 a, F3 b) {
-  return {a.y * b.z - a.z * b.y, a.z * b.x - a.x * b.z, a.x * b.y - a.y * b.x};
-}
-__device__ __forceinline__ float dotf(F3 a, F3 b) { return a.x * b.x + a.y * b.y + a.z * b.z; }
 
 // The same products with every rounding fixed by intrinsics: the compiler
 // may contract a * b + c * d either way, and may choose differently in two
@@ -183,32 +179,42 @@ __device__ __forceinline__ float grad_dot_cached(const float *Gc, long long nc, 
 }
 
 // FP32 geometry of a hex given relative to its node 0 (predictor-corrector
-// half step, where the nodes are off the reference mesh): volume, full
-// corner gradient and the largest squared face area, by the same fan
-// formulas as the FP64 routines.
+// half step, where the nodes are off the reference mesh): volume, corner
+// gradients and the largest squared face area, by the same fan formulas as
+// the FP64 routines, every multiply-add fused explicitly.
+__device__ __forceinline__ float dot_acc(F3 a, F3 b, float s) {
+  return __fmaf_rn(a.z, b.z, __fmaf_rn(a.y, b.y, __fmaf_rn(a.x, b.x, s)));
+}
+
 __device__ __forceinline__ float hex_volume_f(const F3 (&X)[8]) {
   float s = 0.f;
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const F3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)], p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
-    s += dotf(p0 + p1 + p2 + p3, crossf(p2 - p0, p3 - p1));
+    s = dot_acc(p0 + p1 + p2 + p3, cross_rn(p2 - p0, p3 - p1), s);
   }
   return s * (1.f / 24.f);
 }
 
-__device__ __forceinline__ void hex_grad_f(const F3 (&X)[8], F3 (&G)[8]) {
+// dV/dx_A for one compile-time corner A: the three faces holding A, in
+// ascending face order.
+template <int A>
+__device__ __forceinline__ F3 hex_corner_grad_f(const F3 (&X)[8]) {
+  F3 g = {0.f, 0.f, 0.f};
 #pragma unroll
-  for (int a = 0; a < 8; ++a) G[a] = {0.f, 0.f, 0.f};
-#pragma unroll
-  for (int f = 0; f < 6; ++f) {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const F3 pa = X[face_node(f, (k + 1) & 3)], pb = X[face_node(f, (k + 2) & 3)], pc = X[face_node(f, (k + 3) & 3)];
-      G[face_node(f, k)] = G[face_node(f, k)] + crossf(pa + 2.f * pb + pc, pc - pa);
-    }
+  for (int t = 0; t < 3; ++t) {
+    const int f = 2 * t + ((A >> t) & 1);
+    const int k = face_slot(f, A);
+    const F3 pa = X[face_node(f, (k + 1) & 3)], pb = X[face_node(f, (k + 2) & 3)], pc = X[face_node(f, (k + 3) & 3)];
+    g = g + cross_rn(fma3(2.f, pb, pa) + pc, pc - pa);
   }
-#pragma unroll
-  for (int a = 0; a < 8; ++a) G[a] = (1.f / 24.f) * G[a];
+  return (1.f / 24.f) * g;
+}
+
+template <int A = 0>
+__device__ __forceinline__ void hex_grad_f(const F3 (&X)[8], F3 (&G)[8]) {
+  G[A] = hex_corner_grad_f<A>(X);
+  if constexpr (A < 7) hex_grad_f<A + 1>(X, G);
 }
 
 __device__ __forceinline__ float hex_max_face_area2_f(const F3 (&X)[8]) {
@@ -216,8 +222,8 @@ __device__ __forceinline__ float hex_max_face_area2_f(const F3 (&X)[8]) {
 #pragma unroll
   for (int f = 0; f < 6; ++f) {
     const F3 p0 = X[face_node(f, 0)], p1 = X[face_node(f, 1)], p2 = X[face_node(f, 2)], p3 = X[face_node(f, 3)];
-    const F3 D = crossf(p2 - p0, p3 - p1);
-    amax = fmaxf(amax, 0.25f * dotf(D, D));
+    const F3 D = cross_rn(p2 - p0, p3 - p1);
+    amax = fmaxf(amax, 0.25f * dot_rn(D, D));
   }
   return amax;
 }
@@ -235,32 +241,32 @@ __device__ __forceinline__ void hourglass_store_f(const F3 (&X)[8], const F3 (&G
 #pragma unroll
     for (int b = 0; b < 8; ++b) {
       const float sg = hg_pattern(al, b);
-      hx[al] = hx[al] + sg * X[b];
-      hu[al] = hu[al] + sg * U[b];
+      hx[al] = fma3(sg, X[b], hx[al]);
+      hu[al] = fma3(sg, U[b], hu[al]);
     }
   }
   F3 M[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
 #pragma unroll
   for (int b = 0; b < 8; ++b) {
-    M[0] = M[0] + G[b].x * U[b];
-    M[1] = M[1] + G[b].y * U[b];
-    M[2] = M[2] + G[b].z * U[b];
+    M[0] = fma3(G[b].x, U[b], M[0]);
+    M[1] = fma3(G[b].y, U[b], M[1]);
+    M[2] = fma3(G[b].z, U[b], M[2]);
   }
   F3 W[3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
   F3 q[4];
 #pragma unroll
   for (int al = 0; al < 4; ++al) {
-    q[al] = hu[al] - iv * (hx[al].x * M[0] + hx[al].y * M[1] + hx[al].z * M[2]);
-    W[0] = W[0] + hx[al].x * q[al];
-    W[1] = W[1] + hx[al].y * q[al];
-    W[2] = W[2] + hx[al].z * q[al];
+    q[al] = fma3(-iv, fma3(hx[al].z, M[2], fma3(hx[al].y, M[1], hx[al].x * M[0])), hu[al]);
+    W[0] = fma3(hx[al].x, q[al], W[0]);
+    W[1] = fma3(hx[al].y, q[al], W[1]);
+    W[2] = fma3(hx[al].z, q[al], W[2]);
   }
   const float cv = cbrtf(V);
   const float kappa = c_hg * rho * cs * cv * cv;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     F3 f = hg_pattern(0, a) * q[0] + hg_pattern(1, a) * q[1] + hg_pattern(2, a) * q[2] + hg_pattern(3, a) * q[3];
-    f = f - iv * (G[a].x * W[0] + G[a].y * W[1] + G[a].z * W[2]);
+    f = fma3(-iv, fma3(G[a].z, W[2], fma3(G[a].y, W[1], G[a].x * W[0])), f);
     fh[(3 * a + 0) * nc + c] = -kappa * f.x;
     fh[(3 * a + 1) * nc + c] = -kappa * f.y;
     fh[(3 * a + 2) * nc + c] = -kappa * f.z;
@@ -506,7 +512,7 @@ __device__ __forceinline__ void m_cells_body(const Fields<float> &F, DevScalars 
   if (OPT && F.fh) {
     float work_hg = 0.f;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) work_hg += dotf(hg_corner_f(F.fh, F.nc, c, a), ub[a]);
+    for (int a = 0; a < 8; ++a) work_hg = dot_acc(hg_corner_f(F.fh, F.nc, c, a), ub[a], work_hg);
     de += h * work_hg / F.m[c];
   }
   const DF e1 = df_add_f(load_df(F.e, F.elo, c), -de);
@@ -548,6 +554,22 @@ __device__ __forceinline__ void m_hourglass_body(const Fields<float> &F, DevScal
   hourglass_store_f(E, G, U, F.VE[c], F.rho[c], sqrtf(g * (g - 1.f) * fmaxf(e, 0.f)), F.c_hg32, F.fh, F.nc, c);
 }
 
+// Corner gradients of the half-step hex, written to Gh, and
+// dV/dt = sum_a G_a . u_a accumulated in corner order.  The corner's
+// velocity is read again here (a cache hit) rather than held in registers
+// through the volume and gradient sums.
+template <int A = 0>
+__device__ __forceinline__ void predict_corners(const Fields<float> &F, const F3 (&X)[8], int n0, int sy, int sz,
+                                                int c, float &dvdt) {
+  const F3 g = hex_corner_grad_f<A>(X);
+  const int na = n0 + (A & 1) + ((A >> 1) & 1) * sy + ((A >> 2) & 1) * sz;
+  dvdt = dot_acc(g, F3{F.u[na], F.v[na], F.w[na]}, dvdt);
+  F.Gh[(3 * A + 0) * F.nc + c] = g.x;
+  F.Gh[(3 * A + 1) * F.nc + c] = g.y;
+  F.Gh[(3 * A + 2) * F.nc + c] = g.z;
+  if constexpr (A < 7) predict_corners<A + 1>(F, X, n0, sy, sz, c, dvdt);
+}
+
 // Predictor-corrector half step of cell (i,j,k): e^{n+1/2} from sigma^n and
 // u^n on the reference mesh, then EoS and viscosity on x_ref + dt/2 u^n;
 // sigma^{n+1/2} replaces sigma, the corner gradients there go to Gh.
@@ -571,23 +593,17 @@ __device__ __forceinline__ void m_predict_body(const Fields<float> &F, DevScalar
   if (F.fh) {
     float work_hg = 0.f;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) work_hg += dotf(hg_corner_f(F.fh, F.nc, c, a), U[a]);
+    for (int a = 0; a < 8; ++a) work_hg = dot_acc(hg_corner_f(F.fh, F.nc, c, a), U[a], work_hg);
     e -= 0.5f * h * work_hg / m;
   }
-  F3 X[8], G[8];
+  F3 X[8];
 #pragma unroll
-  for (int a = 0; a < 8; ++a) X[a] = E[a] + (0.5f * h) * (U[a] - U[0]);
+  for (int a = 0; a < 8; ++a) X[a] = fma3(0.5f * h, U[a] - U[0], E[a]);
   const float V = hex_volume_f(X);
   if (!(V > 0.f)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
-  hex_grad_f(X, G);
+  // one corner gradient live at a time: stored, and its work taken, as made
   float dvdt = 0.f;
-#pragma unroll
-  for (int a = 0; a < 8; ++a) {
-    dvdt += dotf(G[a], U[a]);
-    F.Gh[(3 * a + 0) * F.nc + c] = G[a].x;
-    F.Gh[(3 * a + 1) * F.nc + c] = G[a].y;
-    F.Gh[(3 * a + 2) * F.nc + c] = G[a].z;
-  }
+  predict_corners(F, X, n0, sy, sz, c, dvdt);
   const float rho = m / V;
   const float g = F.gamma32;
   const float p = (g - 1.f) * rho * e;
