@@ -121,9 +121,19 @@ MIXED_O2 = {
 # gradient, then volume, full gradient, face areas, EoS and viscosity at
 # x^{n+1/2}; the 24 corner gradients there are written for the corrector,
 # whose node and cell passes read them instead of the reference ones.
+# The FP64 kernel evaluates the half-step geometry face by face: per face
+# the diagonals and their partner sums (12, 6 fewer on the three faces
+# through node 0), the face vector and |A|^2 (14), two corner terms
+# (2 x 15) and the other two from 2A (6 + 3); the corner sums accumulate
+# over the last four faces (4 x 12); the volume is sum_a x_a . R_a / 72
+# (Euler's relation for the cubic V: 7 dots, 6 adds, 1 scale), the 24
+# gradients are scaled by 1/24.
+HALF_GEOM64 = 6 * (12 + 14 + 30 + 9) - 3 * 6 + 4 * 12 + 7 * 5 + 6 + 1 + 24
 FP64_PC = {
-    # G, u, m, e, sigma, x_ref read; sigma, 24 half-step gradients written
-    "ale_predict": ("cell", 8 * (24 + 3 + 3 + 3 + 3 + 24 + 1), 48 + 5 + 24 + VOL + GRAD + LEN + 40),
+    # G, u, m, e, sigma, x_ref read; sigma, 24 half-step gradients written;
+    # work 48, e 5, positions 24 + 21 (relative to node 0), geometry,
+    # dV/dt 48, EoS and viscosity 40
+    "ale_predict": ("cell", 8 * (24 + 3 + 3 + 3 + 3 + 24 + 1), 48 + 5 + 24 + 21 + HALF_GEOM64 + 48 + 40),
 }
 MIXED_PC = {
     # offsets or cached gradient, u, m, e, sigma read; sigma, 24 gradients written
@@ -137,9 +147,15 @@ MIXED_PC = {
 # nodes (positions, velocities), the velocity-gradient sums M, the rates q,
 # W, and 24 corner forces written; the node and cell passes read them.
 HG = 2 * 4 * 8 * 3 + 8 * 9 * 2 + 4 * (9 * 2 + 9 * 2) + 8 * (12 + 18 + 3) + 12
+# FP64 Eulerian path: the projected shape vectors gamma_alpha(a) V^(1/3) of
+# the reference mesh are cached (32 per cell), so per cycle the rates
+# q_alpha = sum_a gamma_alpha(a) u_a (4 x 8 x 3 multiply-adds), their
+# scaling by -kappa (12 + 7 for kappa and cs) and the corner forces
+# f_a = sum_alpha gamma_alpha(a) q_alpha (8 x 4 x 3 multiply-adds)
+HG64 = 4 * 8 * 3 * 2 + 12 + 7 + 8 * 4 * 3 * 2
 FP64_HG = {
-    # x_ref, u, G (cached), V_E, rho, cs read; 24 corner forces written
-    "ale_hourglass": ("cell", 8 * (3 + 3 + 24 + 3 + 24), HG),
+    # u, 32 cached shape vectors, rho, e read; 24 corner forces written
+    "ale_hourglass": ("cell", 8 * (3 + 32 + 2 + 24), HG64),
 }
 MIXED_HG = {
     # offsets or cached gradient, u, V_E, rho, e read; 24 corner forces written

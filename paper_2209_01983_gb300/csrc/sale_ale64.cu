@@ -58,6 +58,42 @@ __device__ __forceinline__ double quad_term(P3 p0, P3 p1, P3 p2, P3 p3) {
 }
 constexpr double kInvTwelfth = 1.0 / 12.0;
 
+// Face F's contributions to the corner sums R_a = 24 dV/dx_a of a hex given
+// relative to its node 0 (X[0] = 0), and to max_f |A_f|^2 with the face
+// vector A_f = d02 x d13 (twice the face's vector area).  A corner's fan
+// term, (p_next + 2 p_opposite + p_prev) x (p_prev - p_next) over the
+// face's cycle q0..q3, shares the face's diagonals d02 = q2 - q0 and
+// d13 = q3 - q1 with its neighbours, and opposite corners' terms add up to
+// 2 A_f: t0 = (q1 + q3 + 2 q2) x d13, t1 = d02 x (q0 + q2 + 2 q3),
+// t2 = 2 A_f - t0, t3 = 2 A_f - t1.  The faces through node 0 start at it
+// (q0 = 0).  Every corner's x face (F = 0 or 1) comes first and sets its sum.
+template <int F>
+__device__ __forceinline__ void face_fan(const P3 (&X)[8], P3 (&R)[8], double &a2max) {
+  constexpr int n0 = face_node(F, 0), n1 = face_node(F, 1), n2 = face_node(F, 2), n3 = face_node(F, 3);
+  const P3 q1 = X[n1], q2 = X[n2], q3 = X[n3];
+  const P3 d02 = n0 == 0 ? q2 : q2 - X[n0];
+  const P3 s02 = n0 == 0 ? q2 : X[n0] + q2;
+  const P3 d13 = q3 - q1;
+  const P3 A = cross(d02, d13);
+  const double aa = dot(A, A);
+  a2max = F == 0 ? aa : max_nonneg_d(a2max, aa);
+  const P3 t0 = cross((q1 + q3) + 2.0 * q2, d13);
+  const P3 t1 = cross(d02, s02 + 2.0 * q3);
+  const P3 A2 = 2.0 * A;
+  const P3 t2 = A2 - t0, t3 = A2 - t1;
+  if constexpr (F < 2) {
+    R[n0] = t0;
+    R[n1] = t1;
+    R[n2] = t2;
+    R[n3] = t3;
+  } else {
+    R[n0] = R[n0] + t0;
+    R[n1] = R[n1] + t1;
+    R[n2] = R[n2] + t2;
+    R[n3] = R[n3] + t3;
+  }
+}
+
 }  // namespace
 
 // Reference geometry of every cell: corner gradients, volume, length scale.
@@ -482,24 +518,65 @@ __device__ __forceinline__ void ale_cell_velocities(const Fields<double> &F, int
   }
 }
 
-// Hourglass corner forces on the reference mesh (cached gradients) from
-// u^n and the state at n.
-__global__ void __launch_bounds__(kBlock) k_ale_hourglass(Fields<double> F, DevScalars *S) {
+// Projected hourglass shape vectors of every reference cell (Flanagan &
+// Belytschko 1981): gamma_alpha(a) = h_alpha(a) - hx_alpha . b_a with
+// b_a = G_a / V_E and hx_alpha = sum_b h_alpha(b) x_b.  They depend on the
+// reference mesh alone, so the Eulerian cycle reads them instead of
+// rebuilding them (about 350 FP64 operations per cell every cycle).  Stored
+// scaled by V_E^(1/3): the forces carry V^(2/3) = (V^(1/3))^2 through the
+// two products with gamma.
+__global__ void __launch_bounds__(kBlock) k_geo_init_hg(Fields<double> F, double *HG) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  P3 X[8];
+  load_hex(F.xr, F.yr, F.zr, F.nx, F.ny, i, j, k, X);
+  shift0(X);
+  const double V = F.VE[c];
+  const double iv = 1.0 / V, s = cbrt(V);
+#pragma unroll
+  for (int al = 0; al < 4; ++al) {
+    P3 hx = {0.0, 0.0, 0.0};
+#pragma unroll
+    for (int b = 0; b < 8; ++b) hx = hx + (double)hg_pattern(al, b) * X[b];
+#pragma unroll
+    for (int a = 0; a < 8; ++a)
+      HG[(8ll * al + a) * F.nc + c] = ((double)hg_pattern(al, a) - iv * dot(hx, corner_g(F.G, F.nc, c, a))) * s;
+  }
+}
+
+// Hourglass corner forces on the reference mesh from u^n and the state at
+// n: q_alpha = sum_a gamma_alpha(a) u_a, f_a = -kappa sum_alpha
+// gamma_alpha(a) q_alpha, kappa = c_hg rho cs V^(2/3), with the cached
+// scaled shape vectors (k_geo_init_hg).
+__global__ void __launch_bounds__(kBlock, 2) k_ale_hourglass(Fields<double> F, DevScalars *S) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
-  P3 U[8], X[8], G[8];
-  ale_cell_velocities(F, i, j, k, U);
+  const double *hg = F.HG + c;
+  const long long nc = F.nc;
+  P3 q[4];
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
     const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-    X[a] = {F.xr[n], F.yr[n], F.zr[n]};
-    G[a] = corner_g(F.G, F.nc, c, a);
+    const P3 u = {F.u[n], F.v[n], F.w[n]};
+#pragma unroll
+    for (int al = 0; al < 4; ++al) q[al] = a == 0 ? hg[(8ll * al) * nc] * u : q[al] + hg[(8ll * al + a) * nc] * u;
   }
-  shift0(X);
-  hourglass_store(X, G, U, F.VE[c], F.rho[c], sqrt(F.gamma * (F.gamma - 1.0) * fmax(F.e[c], 0.0)), F.c_hg, F.fh,
-                  F.nc, c);
+  const double kappa = F.c_hg * F.rho[c] * sqrt(F.gamma * (F.gamma - 1.0) * fmax(F.e[c], 0.0));
+#pragma unroll
+  for (int al = 0; al < 4; ++al) q[al] = -kappa * q[al];
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    P3 f = hg[a * nc] * q[0];
+#pragma unroll
+    for (int al = 1; al < 4; ++al) f = f + hg[(8ll * al + a) * nc] * q[al];
+    F.fh[(3ll * a + 0) * nc + c] = f.x;
+    F.fh[(3ll * a + 1) * nc + c] = f.y;
+    F.fh[(3ll * a + 2) * nc + c] = f.z;
+  }
 }
 
 // Predictor-corrector half step on the reference mesh: e^{n+1/2} with the
@@ -512,36 +589,58 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
   const double h = step_dt(S, dt_override);
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
-  P3 U[8], X[8];
-  ale_cell_velocities(F, i, j, k, U);
-  double work = 0.0;
+  const long long n0 = node_index(F.nx, F.ny, i, j, k);
+  const long long sy = F.nx + 1, sz = sy * (F.ny + 1);
+  P3 X[8];
+  double work = 0.0, work_hg = 0.0;
 #pragma unroll
   for (int a = 0; a < 8; ++a) {
-    work += dot(corner_g(F.G, F.nc, c, a), U[a]);
-    const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
-    X[a] = {F.xr[n] + 0.5 * h * U[a].x, F.yr[n] + 0.5 * h * U[a].y, F.zr[n] + 0.5 * h * U[a].z};
+    const long long n = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    const P3 u = {F.u[n], F.v[n], F.w[n]};
+    work += dot(corner_g(F.G, F.nc, c, a), u);
+    if (F.fh) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), u);
+    X[a] = {F.xr[n] + 0.5 * h * u.x, F.yr[n] + 0.5 * h * u.y, F.zr[n] + 0.5 * h * u.z};
   }
   const double m = F.m[c];
   double e = F.e[c] - 0.5 * h / m * F.sig[c] * work;
-  if (F.fh) {
-    double work_hg = 0.0;
+  if (F.fh) e -= 0.5 * h / m * work_hg;
+  // x^{n+1/2} relative to node 0
 #pragma unroll
-    for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), U[a]);
-    e -= 0.5 * h / m * work_hg;
-  }
-  shift0(X);
-  const double V = hex_volume_shifted(X);
+  for (int a = 1; a < 8; ++a) X[a] = X[a] - X[0];
+  X[0] = {0.0, 0.0, 0.0};
+  P3 R[8];
+  double a2max;
+  face_fan<0>(X, R, a2max);
+  face_fan<1>(X, R, a2max);
+  face_fan<2>(X, R, a2max);
+  face_fan<3>(X, R, a2max);
+  face_fan<4>(X, R, a2max);
+  face_fan<5>(X, R, a2max);
+  // V is homogeneous of degree 3 in the node positions, so (Euler)
+  // 3 V = sum_a x_a . dV/dx_a = sum_a x_a . R_a / 24, and x_0 = 0
+  double v72 = dot(X[1], R[1]);
+#pragma unroll
+  for (int a = 2; a < 8; ++a) v72 += dot(X[a], R[a]);
+  const double V = v72 * (1.0 / 72.0);
   if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
-  const double dvdt = grad_store_dot(X, U, F.Gh, F.nc, c);
+  double dvdt = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const P3 g = kInvSixth24 * R[a];
+    F.Gh[(3ll * a + 0) * F.nc + c] = g.x;
+    F.Gh[(3ll * a + 1) * F.nc + c] = g.y;
+    F.Gh[(3ll * a + 2) * F.nc + c] = g.z;
+    const long long n = n0 + (a & 1) + ((a >> 1) & 1) * sy + ((a >> 2) & 1) * sz;
+    dvdt += dot(g, P3{F.u[n], F.v[n], F.w[n]});
+  }
   const double rho = m / V;
   const double p = (F.gamma - 1.0) * rho * e;
   const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
-  const double div = dvdt / V;
-  const double L = V / sqrt(hex_max_face_area2(X));
+  // L div = (V / max_f |A_f / 2|) (dvdt / V) = 2 dvdt / sqrt(max_f |A_f|^2)
   double q = 0.0;
-  if (div < 0.0) {
-    const double ld = L * div;
-    q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
+  if (dvdt < 0.0) {
+    const double ld = 2.0 * dvdt * rsqrt(a2max);
+    q = rho * (F.c_q * ld * ld + F.c_l * cs * fabs(ld));
   }
   F.sig[c] = p + q;
 }
@@ -624,6 +723,10 @@ __global__ void __launch_bounds__(kBlock) k_ale_eos(Fields<double> F, DevScalars
 }
 
 static inline unsigned grid_ale(long long n) { return (unsigned)((n + kBlock - 1) / kBlock); }
+
+void launch_geo_init_hg(const Fields<double> &F, double *HG, cudaStream_t st) {
+  k_geo_init_hg<<<grid_ale(F.nc), kBlock, 0, st>>>(F, HG);
+}
 
 void launch_geo_init_nodes(const Fields<double> &F, double *rE, cudaStream_t st) {
   k_geo_init_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, rE);

@@ -29,6 +29,7 @@ template <typename R>
 void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt_override, double *partial,
                    double *out, cudaStream_t);
 void launch_geo_init_nodes(const Fields<double> &F, double *rE, cudaStream_t st);
+void launch_geo_init_hg(const Fields<double> &F, double *HG, cudaStream_t st);
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
@@ -221,6 +222,7 @@ struct sale_state {
   void *m, *e, *sig, *rho, *p, *q, *cs, *vol, *mu[3], *ep[3], *dv[3];
   double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
   double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
+  double *geoHG;                         //   hourglass shape vectors (32 per cell; control on)
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -282,7 +284,7 @@ static size_t carve(sale_state *st, char *base) {
     st->ep[d] = cv.take(E * nc);
     st->dv[d] = cv.take(E * nc);
   }
-  st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = nullptr;
+  st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = st->geoHG = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -307,6 +309,7 @@ static size_t carve(sale_state *st, char *base) {
     st->kd = (double *)cv.take(sizeof(double) * nn);
     if (st->o2)
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
+    if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
@@ -370,6 +373,7 @@ static Fields<R> fields_t(const sale_state *st) {
     F.TE = (const R *)st->geoTE;
     F.iVE = (const R *)st->geoIVE;
     F.iL2 = (const R *)st->geoIL2;
+    F.HG = (const R *)st->geoHG;
     F.ste = (R *)st->ste;
     F.rE = (const R *)st->relE;
     F.mqx = (R *)st->mq[0];
@@ -710,6 +714,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
     launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->geoIVE, st->geoIL2, st->stream);
     launch_geo_init_nodes(F, st->relE, st->stream);
+    if (st->geoHG) launch_geo_init_hg(F, st->geoHG, st->stream);
   } else {
     const Fields<float> F = fields_t<float>(st);
     launch_m_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->VE32, st->LE32, st->Gc, st->stream);

@@ -142,6 +142,11 @@ struct Fields {
   // (mu_low + mu_high) / 8 along x/y/z, and the node kinetic energy per
   // unit mass 0.5 |u|^2 after the Lagrangian step.
   const R *iVE, *iL2;
+  // FP64 Eulerian path with hourglass control: the four projected hourglass
+  // shape vectors of every reference cell, scaled by V_E^(1/3),
+  // HG[(8 alpha + a) nc + c] = (h_alpha(a) - hx_alpha . G_a / V_E) V_E^(1/3);
+  // null without control
+  const R *HG;
   // FP64 Eulerian path: reference offsets x_ref[b] - x_ref[n] from every
   // node n to its +x, +y, +z neighbours and its yz, xz, xy face-diagonal
   // neighbours, rE[(3 * slot + axis) * nn + n] (zero where b is off the mesh)

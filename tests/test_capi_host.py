@@ -90,7 +90,9 @@ def test_state_bytes_for_scheme_options(sale):
     assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(o2)), sale.SALE_FP32_MIXED) == \
         sale.sale_state_bytes(m._h, sale.SALE_FP32_MIXED)
     assert sale.sale_state_bytes_for(m._h, None, sale.SALE_FP64) == 0
-    hg = dataclasses.replace(pd, c_hg=0.1)  # hourglass corner forces: 24 values per cell
-    for prec, elem in ((sale.SALE_FP64, 8), (sale.SALE_FP32_MIXED, 4)):
+    # hourglass corner forces: 24 values per cell; FP64 also caches the 32
+    # projected shape vectors of every reference cell
+    hg = dataclasses.replace(pd, c_hg=0.1)
+    for prec, per_cell in ((sale.SALE_FP64, (24 + 32) * 8), (sale.SALE_FP32_MIXED, 24 * 4)):
         assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(hg)), prec) >= \
-            sale.sale_state_bytes(m._h, prec) + 24 * elem * md.ncell
+            sale.sale_state_bytes(m._h, prec) + per_cell * md.ncell
