@@ -165,7 +165,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
     if (F.fh) cf = cf + hourglass_corner(F.fh, F.nc, c, 7 - s);
     f = f + cf;
   }
-  const double hm = h / F.mn[n];
+  const double hm = h * F.imn[n];
   const double u0 = F.u[n], v0 = F.v[n], w0 = F.w[n];
   double u1 = u0 + hm * f.x, v1 = v0 + hm * f.y, w1 = w0 + hm * f.z;
   wall_bc(F, i, j, k, u1, v1, w1);
@@ -254,13 +254,13 @@ __global__ void __launch_bounds__(kBlock, 4) k_ale_cells(Fields<double> F, DevSc
     ub[a] = {F.ub[nid[a]], F.vb[nid[a]], F.wb[nid[a]]};
     work += dot(corner_g(Gs, F.nc, c, a), ub[a]);
   }
-  const double m = F.m[c];
-  double e1 = F.e[c] - h / m * F.sig[c] * work;
+  const double im = F.im[c];
+  double e1 = F.e[c] - h * im * F.sig[c] * work;
   if (F.fh) {
     double work_hg = 0.0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), ub[a]);
-    e1 -= h / m * work_hg;
+    e1 -= h * im * work_hg;
   }
   F.e[c] = e1;
   // swept volumes of the three low faces, assembled from k_ale_edges: the
@@ -473,6 +473,7 @@ __global__ void __launch_bounds__(kAleTx * kAleTy) k_ale_remap_nodes(Fields<doub
     F.vb[n] = v1;
     F.wb[n] = w1;
     F.mn[n] = m;
+    F.imn[n] = inv_m;
     F.dke[n] = ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1);
 #pragma unroll
     for (int q = 0; q < 4; ++q) below[q] = above[q];
@@ -602,8 +603,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
     X[a] = {F.xr[n] + 0.5 * h * u.x, F.yr[n] + 0.5 * h * u.y, F.zr[n] + 0.5 * h * u.z};
   }
   const double m = F.m[c];
-  double e = F.e[c] - 0.5 * h / m * F.sig[c] * work;
-  if (F.fh) e -= 0.5 * h / m * work_hg;
+  const double hm = 0.5 * h * F.im[c];
+  double e = F.e[c] - hm * F.sig[c] * work;
+  if (F.fh) e -= hm * work_hg;
   // x^{n+1/2} relative to node 0
 #pragma unroll
   for (int a = 1; a < 8; ++a) X[a] = X[a] - X[0];
@@ -675,8 +677,10 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
     }
     // (a NaN mass with the sign bit clear passes here and makes the rate NaN)
     if (!pos_d(m1)) set_status(S, nan_d(m1) ? SALE_ENAN : SALE_ENEGVOL);
-    const double e = ie / m1;
+    const double r = 1.0 / m1;
+    const double e = ie * r;
     F.m[c] = m1;
+    F.im[c] = r;
     F.e[c] = e;
     rate = ale_eos_cell(F, c, U, m1, e);
     if (nan_d(rate)) {

@@ -30,6 +30,7 @@ void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt
                    double *out, cudaStream_t);
 void launch_geo_init_nodes(const Fields<double> &F, double *rE, cudaStream_t st);
 void launch_geo_init_hg(const Fields<double> &F, double *HG, cudaStream_t st);
+void launch_recip(const double *a, double *r, long long n, cudaStream_t st);
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
@@ -223,6 +224,7 @@ struct sale_state {
   double *geoG, *geoVE, *geoLE, *geoTE;  // FP64 path: cached reference geometry
   double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
   double *geoHG;                         //   hourglass shape vectors (32 per cell; control on)
+  double *im, *imn;                      //   1 / m per cell, 1 / mn per node
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -285,6 +287,7 @@ static size_t carve(sale_state *st, char *base) {
     st->dv[d] = cv.take(E * nc);
   }
   st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = st->geoHG = nullptr;
+  st->im = st->imn = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -307,6 +310,8 @@ static size_t carve(sale_state *st, char *base) {
     st->relE = (double *)cv.take(sizeof(double) * 18 * nn);
     for (int d = 0; d < 3; ++d) st->mq[d] = (double *)cv.take(sizeof(double) * nc);
     st->kd = (double *)cv.take(sizeof(double) * nn);
+    st->im = (double *)cv.take(sizeof(double) * nc);
+    st->imn = (double *)cv.take(sizeof(double) * nn);
     if (st->o2)
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
     if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
@@ -380,6 +385,8 @@ static Fields<R> fields_t(const sale_state *st) {
     F.mqy = (R *)st->mq[1];
     F.mqz = (R *)st->mq[2];
     F.kd = (R *)st->kd;
+    F.im = (R *)st->im;
+    F.imn = (R *)st->imn;
   } else {
     F.VE = (const R *)st->VE32;
     F.LE = (const R *)st->LE32;
@@ -1071,6 +1078,11 @@ extern "C" int sale_set_field(sale_state *st, const char *name, const double *ho
   if (n != want) return fail(SALE_EINVAL, "sale_set_field: '%s' has %zu values, got n = %zu", name, want, n);
   if (elem == sizeof(double)) {
     CUDA_TRY(cudaMemcpyAsync(p, host_in, sizeof(double) * n, cudaMemcpyHostToDevice, st->stream));
+    double *inv = !strcmp(name, "m") ? st->im : !strcmp(name, "mn") ? st->imn : nullptr;
+    if (inv) {
+      launch_recip((const double *)p, inv, (long long)n, st->stream);
+      CUDA_TRY(cudaGetLastError());
+    }
   } else {
     // FP32 field: FP64 values staged on the device in chunks and split there
     // into the FP32 value and, for float-float quantities, its low part

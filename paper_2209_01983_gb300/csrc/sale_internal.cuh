@@ -100,6 +100,10 @@ struct Fields {
   R *mn;                       // node mass
   R *dke;                      // kinetic energy lost by the node remap
   R *m, *e;                    // cell mass, specific internal energy
+  // FP64 states: 1 / m and 1 / mn, written by every pass that writes m or mn
+  // (and after a host upload of either), so the force and energy updates
+  // multiply instead of dividing; null elsewhere
+  R *im, *imn;
   R *mlo, *elo;                // FP32-mixed path: low parts of m and e (float-float); null otherwise
   R *mnlo;                     // FP32-mixed path: low part of the node mass (float-float); null otherwise
   R *sig;                      // p + q

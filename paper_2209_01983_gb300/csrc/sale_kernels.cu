@@ -49,6 +49,7 @@ __global__ void k_init_cells(Fields<R> F, DevScalars *S, const double *rho0, con
   if (c == dep_cell) e = dep_e / m;
   F.m[c] = (R)m;
   F.e[c] = (R)e;
+  if (F.im) F.im[c] = (R)(1.0 / m);
 }
 
 // Node mass = sum of m_c / 8 over the cells holding the node; u = 0.
@@ -67,6 +68,7 @@ __global__ void k_init_nodes(Fields<R> F) {
     mn += ((double)F.m[c] + (F.mlo ? (double)F.mlo[c] : 0.0)) / 8.0;
   }
   F.mn[n] = (R)mn;
+  if (F.imn) F.imn[n] = (R)(1.0 / mn);
   if (F.mnlo) F.mnlo[n] = (R)(mn - (double)(R)mn);  // float-float node mass of the mixed path
   F.u[n] = F.v[n] = F.w[n] = (R)0;
 }
@@ -468,6 +470,7 @@ __global__ void __launch_bounds__(kBlock) k_remap_nodes(Fields<R> F, DevScalars 
   F.vb[n] = (R)v1;
   F.wb[n] = (R)w1;
   F.mn[n] = (R)m;
+  if (F.imn) F.imn[n] = (R)inv_m;
   F.dke[n] = (R)(ke - 0.5 * m * (u1 * u1 + v1 * v1 + w1 * w1));
   if (F.remap_sets_x) {
     F.x[n] = (R)F.xr[n];
@@ -503,6 +506,7 @@ __global__ void __launch_bounds__(kBlock) k_remap_cells(Fields<R> F, DevScalars 
   if (!(m1 > 0.0)) set_status(S, m1 != m1 ? SALE_ENAN : SALE_ENEGVOL);
   F.m[c] = (R)m1;
   F.e[c] = (R)(ie / m1);
+  if (F.im) F.im[c] = (R)(1.0 / m1);
 }
 
 // ---------------------------------------------------------------------------
@@ -571,6 +575,16 @@ void launch_reset(DevScalars *S, cudaStream_t st) { k_reset_scalars<<<1, 1, 0, s
 
 void launch_set_limits(DevScalars *S, double t_end, long long cycle_limit, cudaStream_t st) {
   k_set_limits<<<1, 1, 0, st>>>(S, t_end, cycle_limit);
+}
+
+// r = 1 / a elementwise (the reciprocal masses after a host upload).
+__global__ void k_recip(const double *__restrict__ a, double *__restrict__ r, long long n) {
+  const long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (i < n) r[i] = 1.0 / a[i];
+}
+
+void launch_recip(const double *a, double *r, long long n, cudaStream_t st) {
+  if (n > 0) k_recip<<<grid_for(n), kBlock, 0, st>>>(a, r, n);
 }
 
 template <typename R>
