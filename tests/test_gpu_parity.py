@@ -165,6 +165,48 @@ def test_tangled_mesh_reports_negvol(sale):
     assert ei.value.code == sale.SALE_ESTATE
 
 
+def test_uploaded_masses_drive_the_next_cycles(sale):
+    """Cell and node masses, velocities and energies uploaded through
+    sale_set_field (perturbed away from anything the cycle produced) drive
+    the following Eulerian cycles exactly as the oracle's set_state does:
+    the force and energy updates use the uploaded masses (and the
+    reciprocals the upload derives from them), not values cached from the
+    cycles before."""
+    md, pd = inputs.sedov_octant(12, jitter=0.1)
+    st = sale.State(md, pd)
+    o = oracle.Oracle.from_problem(md, pd)
+    assert st.run_to_time(max_cycles=10, remap_every=1) == 10
+    rc, n = o.run(max_cycles=10, remap_every=1)
+    assert rc == 0 and n == 10
+    rng = np.random.default_rng(2209)
+    f = {nm: o.field(nm) for nm in ("x", "y", "z", "u", "v", "w", "mn", "m", "e")}
+    # new cell masses, and node masses consistent with them (an eighth of
+    # each cell's mass to each of its nodes), new energies, a small velocity
+    # perturbation off the x walls
+    nx, ny, nz = md.nx, md.ny, md.nz
+    f["m"] = f["m"] * (1.0 + 0.1 * rng.random(f["m"].shape))
+    mc = f["m"].reshape(nz, ny, nx) / 8.0
+    mn = np.zeros((nz + 1, ny + 1, nx + 1))
+    for dk in (0, 1):
+        for dj in (0, 1):
+            for di in (0, 1):
+                mn[dk:dk + nz, dj:dj + ny, di:di + nx] += mc
+    f["mn"] = mn.reshape(-1)
+    f["e"] = f["e"] * (1.0 + 0.2 * rng.random(f["e"].shape))
+    inner = (f["x"] > 0.0) & (f["x"] < f["x"].max())
+    f["u"] = f["u"] + 1e-3 * rng.standard_normal(f["u"].shape) * inner
+    for nm in ("u", "v", "w", "mn", "m", "e"):
+        st.set_field(nm, f[nm])
+    st.refresh()
+    rc = o.set_state(*(f[k] for k in ("x", "y", "z", "u", "v", "w", "mn", "m", "e")), t=o.s.t, dt_last=o.s.dt_last)
+    assert rc == 0
+    assert st.diagnostics()["dt"] == pytest.approx(o.s.dt, rel=1e-12)
+    assert st.run_to_time(max_cycles=20, remap_every=1) == 20
+    rc, n = o.run(max_cycles=20, remap_every=1)
+    assert rc == 0 and n == 20
+    compare(st, o)
+
+
 def test_set_field_and_refresh(sale):
     md, pd = inputs.sedov_octant(8, jitter=0.1)
     st = sale.State(md, pd)
