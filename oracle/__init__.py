@@ -33,7 +33,13 @@ class Params(C.Structure):
         ("c_l", C.c_double), ("dt_growth", C.c_double), ("dt_init", C.c_double),
         ("ke_fix", C.c_int), ("reflect", C.c_int * 6), ("remap_order", C.c_int), ("time_order", C.c_int),
         ("c_hg", C.c_double),
+        ("shear0", C.c_double), ("shear_dp", C.c_double), ("shear_dt", C.c_double), ("cv", C.c_double),
+        ("e_ref", C.c_double), ("rho_ref", C.c_double), ("yield0", C.c_double), ("yield_max", C.c_double),
+        ("hard_beta", C.c_double), ("hard_n", C.c_double),
     ]
+
+STRENGTH_FIELDS = ("shear0", "shear_dp", "shear_dt", "cv", "e_ref", "rho_ref", "yield0", "yield_max",
+                   "hard_beta", "hard_n")
 
 
 class _State(C.Structure):
@@ -44,6 +50,7 @@ class _State(C.Structure):
         ("u", _dp), ("v", _dp), ("w", _dp), ("mn", _dp),
         ("m", _dp), ("e", _dp), ("vol", _dp), ("rho", _dp), ("p", _dp),
         ("q", _dp), ("cs", _dp), ("len", _dp),
+        ("sxx", _dp), ("syy", _dp), ("szz", _dp), ("sxy", _dp), ("syz", _dp), ("szx", _dp), ("eps_p", _dp),
         ("t", C.c_double), ("dt", C.c_double), ("dt_last", C.c_double),
         ("cycle", C.c_longlong), ("status", C.c_int),
     ]
@@ -91,6 +98,8 @@ def lib():
         L.oracle_run.argtypes = [C.POINTER(_State), C.c_double, C.c_longlong, C.c_int,
                                  C.POINTER(C.c_longlong)]
         L.oracle_diagnostics.argtypes = [C.POINTER(_State), _dp]
+        L.oracle_steinberg.argtypes = [C.POINTER(Params), C.c_double, C.c_double, C.c_double, C.c_double, _dp, _dp]
+        L.oracle_stress_update.argtypes = [_dp, _dp, C.c_double, C.c_double, C.c_double, _dp, _dp]
         _lib = L
     return _lib
 
@@ -126,6 +135,23 @@ def hex_char_length(X) -> float:
     return lib().oracle_hex_char_length(_ptr(_hexarr(X)))
 
 
+def steinberg(params: Params, p, rho, e, eps_p):
+    """(G, Y) of the Steinberg-Guinan model for one cell state."""
+    G, Y = C.c_double(0.0), C.c_double(0.0)
+    lib().oracle_steinberg(C.byref(params), p, rho, e, eps_p, C.byref(G), C.byref(Y))
+    return G.value, Y.value
+
+
+def stress_update(S6, L, dt, G, Y):
+    """One Wilkins stress update: (S_new[6], plastic strain added)."""
+    S6 = np.ascontiguousarray(S6, dtype=np.float64).reshape(6)
+    L = np.ascontiguousarray(L, dtype=np.float64).reshape(9)
+    out = np.zeros(6)
+    deps = C.c_double(0.0)
+    lib().oracle_stress_update(_ptr(S6), _ptr(L), dt, G, Y, _ptr(out), C.byref(deps))
+    return out, deps.value
+
+
 def params_from(pd, reflect=(1, 1, 1, 1, 1, 1)) -> Params:
     p = Params()
     p.gamma, p.cfl, p.c_q, p.c_l = pd.gamma, pd.cfl, pd.c_q, pd.c_l
@@ -137,6 +163,8 @@ def params_from(pd, reflect=(1, 1, 1, 1, 1, 1)) -> Params:
     p.remap_order = int(getattr(pd, "remap_order", 1))
     p.time_order = int(getattr(pd, "time_order", 1))
     p.c_hg = float(getattr(pd, "c_hg", 0.0))
+    for name in STRENGTH_FIELDS:
+        setattr(p, name, float(getattr(pd, name, 0.0)))
     return p
 
 
@@ -144,7 +172,7 @@ class Oracle:
     """One oracle state (owns C memory)."""
 
     NODE_FIELDS = ("x", "y", "z", "xr", "yr", "zr", "u", "v", "w", "mn")
-    CELL_FIELDS = ("m", "e", "vol", "rho", "p", "q", "cs", "len")
+    CELL_FIELDS = ("m", "e", "vol", "rho", "p", "q", "cs", "len", "sxx", "syy", "szz", "sxy", "syz", "szx", "eps_p")
 
     def __init__(self, nx, ny, nz, nodes, params: Params):
         x, y, z = (np.ascontiguousarray(a, dtype=np.float64) for a in nodes)

@@ -30,6 +30,16 @@
  *              mu e_donor; node mass/momentum/KE fluxes on the dual mesh
  *              psi = sum_{cells at edge} (mu_lo + mu_hi)/8, upwind by node;
  *              KE lost by the momentum remap returned to the cells.
+ *  Strength:   (optional, shear0 > 0) deviatoric stress S per cell after
+ *              Wilkins (1963): L = (1/V) sum_a ubar_a (x) dV/dx_a,
+ *              D' = sym(L) - tr(L)/3 I, W = skew(L),
+ *              S* = S + dt (2 G D' + W S - S W), radial return to the von
+ *              Mises surface sqrt(3/2 S:S) <= Y; G and Y from the
+ *              Steinberg-Guinan model (Steinberg, Cochran, Guinan 1980);
+ *              corner forces (p + q) dV/dx_a - S dV/dx_a, used in both the
+ *              velocity and the compatible energy update; the CFL speed
+ *              includes 4 G / (3 rho); S and the plastic strain are
+ *              remapped like e (donor cell, per unit mass).
  */
 #include "sale_oracle.h"
 
@@ -208,8 +218,8 @@ oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,
     *node_arrays[i] = alloc_zero(s->nn);
     if (!*node_arrays[i]) { oracle_destroy(s); return NULL; }
   }
-  double **cell_arrays[] = {&s->m, &s->e, &s->vol, &s->rho,
-                            &s->p, &s->q, &s->cs, &s->len};
+  double **cell_arrays[] = {&s->m, &s->e, &s->vol, &s->rho, &s->p, &s->q, &s->cs, &s->len,
+                            &s->sxx, &s->syy, &s->szz, &s->sxy, &s->syz, &s->szx, &s->eps_p};
   for (size_t i = 0; i < sizeof(cell_arrays) / sizeof(cell_arrays[0]); ++i) {
     *cell_arrays[i] = alloc_zero(s->nc);
     if (!*cell_arrays[i]) { oracle_destroy(s); return NULL; }
@@ -226,7 +236,8 @@ oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,
 void oracle_destroy(oracle_state *s) {
   if (!s) return;
   double *arrays[] = {s->x, s->y, s->z, s->xr, s->yr, s->zr, s->u, s->v, s->w,
-                      s->mn, s->m, s->e, s->vol, s->rho, s->p, s->q, s->cs, s->len};
+                      s->mn, s->m, s->e, s->vol, s->rho, s->p, s->q, s->cs, s->len,
+                      s->sxx, s->syy, s->szz, s->sxy, s->syz, s->szx, s->eps_p};
   for (size_t i = 0; i < sizeof(arrays) / sizeof(arrays[0]); ++i) free(arrays[i]);
   free(s);
 }
@@ -241,6 +252,81 @@ static void node_masses_from_cells(oracle_state *s) {
         for (int a = 0; a < 8; ++a)
           s->mn[node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1))] += share;
       }
+}
+
+/* ------------------------------------------------------------------ */
+/* Material strength (R17)                                             */
+/* ------------------------------------------------------------------ */
+
+/* Steinberg-Guinan (J. Appl. Phys. 51, 1498, 1980): the shear modulus
+ * grows with pressure, scaled by the cube root of the volume ratio
+ * eta = rho_ref / rho, and falls with temperature, T - T_ref =
+ * (e - e_ref) / cv:  G = G0 + G_p p eta^(1/3) + G_T (T - T_ref),  clamped
+ * at 0 (melt).  The yield stress work-hardens up to a cap and follows G:
+ * Y = min(Y0 (1 + beta eps_p)^n, Ymax) G / G0. */
+void oracle_steinberg(const oracle_params *prm, double p, double rho, double e, double eps_p, double *G,
+                      double *Y) {
+  const double eta = prm->rho_ref / rho;
+  double g = prm->shear0 + prm->shear_dp * p * cbrt(eta) + prm->shear_dt * (e - prm->e_ref) / prm->cv;
+  if (!(g > 0.0)) g = 0.0;
+  double y = prm->yield0 * pow(1.0 + prm->hard_beta * eps_p, prm->hard_n);
+  if (y > prm->yield_max) y = prm->yield_max;
+  *G = g;
+  *Y = y * g / prm->shear0;
+}
+
+/* One Wilkins (1963) update of the deviatoric stress.  With the strain
+ * rate D = (L + L^T)/2, its deviator D' = D - tr(D)/3 I and the spin
+ * W = (L - L^T)/2, the trial stress is S* = S + dt (2 G D' + W S - S W)
+ * (the Jaumann rate, which rotates S with the material).  Von Mises:
+ * J = sqrt(3/2 S*:S*); above the yield stress the trial stress is scaled
+ * back onto the surface J = Y (radial return) and the equivalent plastic
+ * strain grows by (J - Y) / (3 G). */
+void oracle_stress_update(const double *S6, const double *L, double dt, double G, double Y, double *S_out,
+                          double *deps) {
+  double S[3][3] = {{S6[0], S6[3], S6[5]}, {S6[3], S6[1], S6[4]}, {S6[5], S6[4], S6[2]}};
+  double D[3][3], W[3][3], T[3][3];
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      D[i][j] = 0.5 * (L[3 * i + j] + L[3 * j + i]);
+      W[i][j] = 0.5 * (L[3 * i + j] - L[3 * j + i]);
+    }
+  const double tr = (D[0][0] + D[1][1] + D[2][2]) / 3.0;
+  for (int i = 0; i < 3; ++i) D[i][i] -= tr;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) {
+      double ws = 0.0, sw = 0.0;
+      for (int k = 0; k < 3; ++k) {
+        ws += W[i][k] * S[k][j];
+        sw += S[i][k] * W[k][j];
+      }
+      T[i][j] = S[i][j] + dt * (2.0 * G * D[i][j] + ws - sw);
+    }
+  double ss = 0.0;
+  for (int i = 0; i < 3; ++i)
+    for (int j = 0; j < 3; ++j) ss += T[i][j] * T[i][j];
+  const double J = sqrt(1.5 * ss);
+  double scale = 1.0;
+  *deps = 0.0;
+  if (J > Y) {
+    scale = Y / J;
+    if (G > 0.0) *deps = (J - Y) / (3.0 * G);
+  }
+  S_out[0] = scale * T[0][0];
+  S_out[1] = scale * T[1][1];
+  S_out[2] = scale * T[2][2];
+  S_out[3] = scale * 0.5 * (T[0][1] + T[1][0]);
+  S_out[4] = scale * 0.5 * (T[1][2] + T[2][1]);
+  S_out[5] = scale * 0.5 * (T[2][0] + T[0][2]);
+}
+
+static int strength_on(const oracle_state *s) { return s->prm.shear0 > 0.0; }
+
+/* out = S_c g: the deviatoric stress of cell c applied to a 3-vector. */
+static void stress_apply(const oracle_state *s, long long c, const double *g, double *out) {
+  out[0] = s->sxx[c] * g[0] + s->sxy[c] * g[1] + s->szx[c] * g[2];
+  out[1] = s->sxy[c] * g[0] + s->syy[c] * g[1] + s->syz[c] * g[2];
+  out[2] = s->szx[c] * g[0] + s->syz[c] * g[1] + s->szz[c] * g[2];
 }
 
 /* EoS (R2), sound speed and artificial viscosity (R3) of one cell with
@@ -295,7 +381,13 @@ int oracle_eos(oracle_state *s) {
 double oracle_cfl_dt(const oracle_state *s) {
   double dt = INFINITY;
   for (long long c = 0; c < s->nc; ++c) {
-    double ceff = sqrt(s->cs[c] * s->cs[c] + 2.0 * s->q[c] / s->rho[c]);
+    double c2 = s->cs[c] * s->cs[c] + 2.0 * s->q[c] / s->rho[c];
+    if (strength_on(s)) {  /* longitudinal elastic wave: K/rho + 4 G / (3 rho) */
+      double G, Y;
+      oracle_steinberg(&s->prm, s->p[c], s->rho[c], s->e[c], s->eps_p[c], &G, &Y);
+      c2 += 4.0 * G / (3.0 * s->rho[c]);
+    }
+    double ceff = sqrt(c2);
     double dtc = s->prm.cfl * s->len[c] / ceff;
     if (dtc < dt) dt = dtc;
   }
@@ -423,15 +515,19 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
   if (!(dt > 0.0)) return s->status = ORACLE_EDT;
   const long long nn = s->nn, nc = s->nc;
   const int pc = s->prm.time_order == 2;
+  const int str = strength_on(s);
+  if (str && pc) return s->status = ORACLE_EINVAL;  /* strength takes the single-stage step */
   double *fx = alloc_zero(nn), *fy = alloc_zero(nn), *fz = alloc_zero(nn);
   double *ubx = alloc_zero(nn), *uby = alloc_zero(nn), *ubz = alloc_zero(nn);
   double *e_new = alloc_zero(nc), *sig = alloc_zero(nc);
   double *xh = alloc_zero(nn), *yh = alloc_zero(nn), *zh = alloc_zero(nn);
   const int hg = s->prm.c_hg > 0.0;
   double *fh = hg ? alloc_zero(24 * nc) : NULL;
-  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh || (hg && !fh)) {
+  double *s_new = str ? alloc_zero(7 * nc) : NULL;  /* S (6) and eps_p at n+1 */
+  if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh || (hg && !fh) ||
+      (str && !s_new)) {
     free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-    free(xh); free(yh); free(zh); free(fh);
+    free(xh); free(yh); free(zh); free(fh); free(s_new);
     return s->status = ORACLE_ENOMEM;
   }
 
@@ -498,6 +594,11 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
         for (int a = 0; a < 8; ++a) {
           long long n = node_id(s, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
           double cf[3] = {sigma * G[a * 3 + 0], sigma * G[a * 3 + 1], sigma * G[a * 3 + 2]};
+          if (str) {  /* the deviatoric part of the cell stress, -S dV/dx_a */
+            double sg[3];
+            stress_apply(s, c, &G[a * 3], sg);
+            for (int d = 0; d < 3; ++d) cf[d] -= sg[d];
+          }
           if (hg)
             for (int d = 0; d < 3; ++d) cf[d] += fh[24 * c + a * 3 + d];
           fx[n] += cf[0];
@@ -539,6 +640,25 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
           for (int a = 0; a < 8; ++a) work_hg += dot3(&fh[24 * c + a * 3], &UB[a * 3]);
         e_new[c] = s->e[c] - dt / s->m[c] * sigma * work;
         if (hg) e_new[c] -= dt / s->m[c] * work_hg;
+        if (str) {
+          /* the deviatoric forces' work, then the stress at n+1 from the
+           * time-centred velocity gradient and G, Y of the state at n */
+          double work_s = 0.0, Lg[9] = {0.0};
+          for (int a = 0; a < 8; ++a) {
+            double sg[3];
+            stress_apply(s, c, &G[a * 3], sg);
+            work_s += dot3(sg, &UB[a * 3]);
+            for (int i2 = 0; i2 < 3; ++i2)
+              for (int j2 = 0; j2 < 3; ++j2) Lg[3 * i2 + j2] += UB[a * 3 + i2] * G[a * 3 + j2];
+          }
+          e_new[c] += dt / s->m[c] * work_s;
+          for (int q9 = 0; q9 < 9; ++q9) Lg[q9] /= s->vol[c];
+          double Gm, Ym, deps;
+          oracle_steinberg(&s->prm, s->p[c], s->rho[c], s->e[c], s->eps_p[c], &Gm, &Ym);
+          const double S6[6] = {s->sxx[c], s->syy[c], s->szz[c], s->sxy[c], s->syz[c], s->szx[c]};
+          oracle_stress_update(S6, Lg, dt, Gm, Ym, &s_new[7 * c], &deps);
+          s_new[7 * c + 6] = s->eps_p[c] + deps;
+        }
       }
 
   /* Move the mesh with the time-centred velocity. */
@@ -548,8 +668,18 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
     s->z[n] += dt * ubz[n];
   }
   memcpy(s->e, e_new, sizeof(double) * (size_t)nc);
+  if (str)
+    for (long long c = 0; c < nc; ++c) {
+      s->sxx[c] = s_new[7 * c + 0];
+      s->syy[c] = s_new[7 * c + 1];
+      s->szz[c] = s_new[7 * c + 2];
+      s->sxy[c] = s_new[7 * c + 3];
+      s->syz[c] = s_new[7 * c + 4];
+      s->szx[c] = s_new[7 * c + 5];
+      s->eps_p[c] = s_new[7 * c + 6];
+    }
   free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-  free(xh); free(yh); free(zh); free(fh);
+  free(xh); free(yh); free(zh); free(fh); free(s_new);
 
   s->t += dt;
   s->dt_last = dt;
@@ -653,6 +783,18 @@ static void face_fluxes(const oracle_state *s, const double *rho_l, const double
   *eflux = *mu * e_f;
 }
 
+/* Strength (R17): the deviatoric stress and plastic strain are carried per
+ * unit mass with the face's mass flux mu from the same donor cell as e
+ * (first-order donor cell): ms[7 c + q] holds m S_q (q < 6) and m eps_p. */
+static void advect_strength(const oracle_state *s, double *ms, long long lo, long long hi, double mu, double dv) {
+  const long long dn = dv > 0.0 ? hi : lo;
+  const double q[7] = {s->sxx[dn], s->syy[dn], s->szz[dn], s->sxy[dn], s->syz[dn], s->szx[dn], s->eps_p[dn]};
+  for (int k = 0; k < 7; ++k) {
+    ms[7 * lo + k] += mu * q[k];
+    ms[7 * hi + k] -= mu * q[k];
+  }
+}
+
 int oracle_remap_step(oracle_state *s) {
   if (s->status) return s->status;
   const int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -665,8 +807,10 @@ int oracle_remap_step(oracle_state *s) {
   double *rho_l = alloc_zero(nc), *m_new = alloc_zero(nc), *ie_new = alloc_zero(nc), *vol_l = alloc_zero(nc);
   double *mn_new = alloc_zero(nn), *px = alloc_zero(nn), *py = alloc_zero(nn);
   double *pz = alloc_zero(nn), *ke = alloc_zero(nn), *dke = alloc_zero(nn);
+  const int str = strength_on(s);
+  double *ms_new = alloc_zero(str ? 7 * nc : 1);
   double *all[] = {dvx, dvy, dvz, mux, muy, muz, rho_l, m_new, ie_new,
-                   mn_new, px, py, pz, ke, dke, vol_l};
+                   mn_new, px, py, pz, ke, dke, vol_l, ms_new};
   const size_t nall = sizeof(all) / sizeof(all[0]);
   for (size_t i = 0; i < nall; ++i)
     if (!all[i]) {
@@ -693,6 +837,10 @@ int oracle_remap_step(oracle_state *s) {
   for (long long c = 0; c < nc; ++c) {
     m_new[c] = s->m[c];
     ie_new[c] = s->m[c] * s->e[c];
+    if (str) {
+      const double q[7] = {s->sxx[c], s->syy[c], s->szz[c], s->sxy[c], s->syz[c], s->szx[c], s->eps_p[c]};
+      for (int k = 0; k < 7; ++k) ms_new[7 * c + k] = s->m[c] * q[k];
+    }
   }
   for (int k = 0; k < nz; ++k)
     for (int j = 0; j < ny; ++j)
@@ -701,6 +849,7 @@ int oracle_remap_step(oracle_state *s) {
         long long lo = cell_id(s, i - 1, j, k), hi = cell_id(s, i, j, k);
         double mu, ef;
         face_fluxes(s, rho_l, vol_l, i - 1, j, k, 0, dvx[f], &mu, &ef);
+        if (str) advect_strength(s, ms_new, lo, hi, mu, dvx[f]);
         mux[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
@@ -714,6 +863,7 @@ int oracle_remap_step(oracle_state *s) {
         long long lo = cell_id(s, i, j - 1, k), hi = cell_id(s, i, j, k);
         double mu, ef;
         face_fluxes(s, rho_l, vol_l, i, j - 1, k, 1, dvy[f], &mu, &ef);
+        if (str) advect_strength(s, ms_new, lo, hi, mu, dvy[f]);
         muy[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
@@ -727,6 +877,7 @@ int oracle_remap_step(oracle_state *s) {
         long long lo = cell_id(s, i, j, k - 1), hi = cell_id(s, i, j, k);
         double mu, ef;
         face_fluxes(s, rho_l, vol_l, i, j, k - 1, 2, dvz[f], &mu, &ef);
+        if (str) advect_strength(s, ms_new, lo, hi, mu, dvz[f]);
         muz[f] = mu;
         m_new[lo] += mu;
         m_new[hi] -= mu;
@@ -825,6 +976,10 @@ int oracle_remap_step(oracle_state *s) {
   for (long long c = 0; c < nc; ++c) {
     s->m[c] = m_new[c];
     s->e[c] = ie_new[c] / m_new[c];
+    if (str) {
+      double *q[7] = {s->sxx, s->syy, s->szz, s->sxy, s->syz, s->szx, s->eps_p};
+      for (int k = 0; k < 7; ++k) q[k][c] = ms_new[7 * c + k] / m_new[c];
+    }
   }
   memcpy(s->x, s->xr, sizeof(double) * (size_t)nn);
   memcpy(s->y, s->yr, sizeof(double) * (size_t)nn);

@@ -23,7 +23,12 @@
  *   - optionally, second-order cell remap: van Leer's limited
  *     piecewise-linear profile in the donor cell (van Leer 1977, "Towards
  *     the ultimate conservative difference scheme IV"), averaged over the
- *     slab the face sweeps.
+ *     slab the face sweeps;
+ *   - optionally, material strength, the stress module of the paper's
+ *     case study (Sec. III-D): deviatoric stress with the Jaumann rate and
+ *     von Mises radial return (Wilkins 1963, "Calculation of elastic-plastic
+ *     flow"), shear modulus and yield from the Steinberg-Guinan model
+ *     (Steinberg, Cochran, Guinan, J. Appl. Phys. 51, 1980).
  *
  * Layout: SoA, x index fastest.  Cell c = i + nx*(j + ny*k); node
  * n = i + (nx+1)*(j + (ny+1)*k).  Local node a = di + 2*dj + 4*dk of cell
@@ -57,6 +62,18 @@ typedef struct oracle_params {
   int remap_order;   /* cell remap: 2 = van Leer piecewise linear, else first-order donor cell */
   int time_order;    /* Lagrange step: 2 = predictor-corrector, else single stage */
   double c_hg;       /* Flanagan-Belytschko viscous hourglass coefficient (0: none) */
+  /* Material strength (Steinberg-Guinan shear modulus and yield, Wilkins
+   * deviatoric stress); shear0 = 0: none, the pure hydro scheme.          */
+  double shear0;     /* G0, shear modulus at the reference state          */
+  double shear_dp;   /* dG/dp                                             */
+  double shear_dt;   /* dG/dT                                             */
+  double cv;         /* specific heat: T - T_ref = (e - e_ref) / cv       */
+  double e_ref;      /* specific internal energy at the reference T       */
+  double rho_ref;    /* reference density                                 */
+  double yield0;     /* Y0                                                */
+  double yield_max;  /* Ymax                                              */
+  double hard_beta;  /* work-hardening coefficient beta                   */
+  double hard_n;     /* work-hardening exponent n                         */
 } oracle_params;
 
 typedef struct oracle_state {
@@ -69,6 +86,8 @@ typedef struct oracle_state {
   double *mn;              /* node mass                                    */
   double *m, *e;           /* cell mass, specific internal energy          */
   double *vol, *rho, *p, *q, *cs, *len; /* derived cell quantities         */
+  double *sxx, *syy, *szz, *sxy, *syz, *szx; /* deviatoric stress (strength) */
+  double *eps_p;           /* equivalent plastic strain (strength)         */
   double t, dt, dt_last;   /* time, proposed next dt, last dt used         */
   long long cycle;
   int status;
@@ -80,6 +99,17 @@ void oracle_hex_volume_grad(const double *X, double *G); /* G[a*3+d] = dV/dX */
 /* face vector areas A[f*3+d], faces ordered x-lo,x-hi,y-lo,y-hi,z-lo,z-hi */
 void oracle_hex_face_areas(const double *X, double *A);
 double oracle_hex_char_length(const double *X);
+
+/* ---- material strength (single cell) ----
+ * Steinberg-Guinan shear modulus G and yield stress Y of a cell with EoS
+ * pressure p, density rho, specific energy e, plastic strain eps_p. */
+void oracle_steinberg(const oracle_params *prm, double p, double rho, double e, double eps_p, double *G,
+                      double *Y);
+/* Wilkins deviatoric stress update with von Mises radial return.  S[6] =
+ * (xx, yy, zz, xy, yz, zx), L[9] the velocity gradient L[3*i + j] =
+ * du_i/dx_j; S_out gets the new stress, *deps the plastic strain added. */
+void oracle_stress_update(const double *S, const double *L, double dt, double G, double Y, double *S_out,
+                          double *deps);
 
 /* ---- state ---- */
 oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,

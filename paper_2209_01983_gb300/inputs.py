@@ -95,6 +95,17 @@ class ProblemDesc:
     remap_order: int = 1  # cell remap: 1 donor cell, 2 van Leer piecewise linear
     time_order: int = 1   # Lagrange step: 1 single stage, 2 predictor-corrector
     c_hg: float = 0.0     # viscous hourglass coefficient (0: no hourglass control)
+    # material strength, Steinberg-Guinan model (shear0 = 0: none)
+    shear0: float = 0.0     # shear modulus G0 at the reference state
+    shear_dp: float = 0.0   # dG/dp
+    shear_dt: float = 0.0   # dG/dT
+    cv: float = 1.0         # specific heat: T - T_ref = (e - e_ref) / cv
+    e_ref: float = 0.0      # specific internal energy at the reference temperature
+    rho_ref: float = 1.0    # reference density
+    yield0: float = 0.0     # Y0
+    yield_max: float = 0.0  # Ymax
+    hard_beta: float = 0.0  # work-hardening coefficient
+    hard_n: float = 0.0     # work-hardening exponent
 
 
 def mesh_nodes(md: MeshDesc):
