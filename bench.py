@@ -41,6 +41,10 @@ if ROOT not in sys.path:
 
 METRIC = "cell-updates/sec per full Lagrange+remap cycle, FP64 vs FP32-mixed; % HBM roofline"
 UNIT = "cell-updates/s"
+# --strength: an elastic-plastic material for the Sedov blast (background
+# p = 1e-6); the blast region yields and work-hardens, the rest stays elastic
+STRENGTH = dict(shear0=0.05, shear_dp=0.3, shear_dt=-0.01, cv=1.0, e_ref=0.0, rho_ref=1.0, yield0=2e-3,
+                yield_max=1e-2, hard_beta=20.0, hard_n=0.3)
 
 
 def parse():
@@ -62,6 +66,8 @@ def parse():
     ap.add_argument("--time-order", type=int, default=1, choices=(1, 2),
                     help="Lagrangian step: 1 single stage, 2 predictor-corrector")
     ap.add_argument("--c-hg", type=float, default=0.0, help="viscous hourglass coefficient (0: none)")
+    ap.add_argument("--strength", action="store_true",
+                    help="material strength (Steinberg-Guinan elastic-plastic material, FP64 general kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
@@ -280,10 +286,11 @@ def reference_arm(args):
 
 def workload_config(args, precision):
     order = ("" if args.remap_order == 1 else "-remap2") + ("" if args.time_order == 1 else "-pc") + \
-        ("" if args.c_hg == 0 else f"-hg{args.c_hg}")
+        ("" if args.c_hg == 0 else f"-hg{args.c_hg}") + ("-strength" if args.strength else "")
     return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-ale-every-cycle{order}",
             "cells": args.n ** 3, "gamma": 1.4, "remap_every": 1, "remap_order": args.remap_order,
             "time_order": args.time_order, "c_hg": args.c_hg,
+            **({"strength": STRENGTH} if args.strength else {}),
             "precision": precision,
             "l2": "state larger than the 129 MB L2 (no flush)", "parallelism": "replicas"}
 
@@ -368,7 +375,8 @@ def measure(args, precision, local, barrier):
     from paper_2209_01983_gb300 import costs, inputs, sale
 
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
-    pd = dataclasses.replace(pd, remap_order=args.remap_order, time_order=args.time_order, c_hg=args.c_hg)
+    pd = dataclasses.replace(pd, remap_order=args.remap_order, time_order=args.time_order, c_hg=args.c_hg,
+                             **(STRENGTH if args.strength else {}))
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     tuning = None
@@ -405,7 +413,7 @@ def measure(args, precision, local, barrier):
     ms = ev0.elapsed_time(ev1)
 
     table = costs.table(precision, "ale", jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
-                        hourglass=args.c_hg > 0)
+                        hourglass=args.c_hg > 0, strength=args.strength)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
     if missing:
@@ -525,6 +533,8 @@ def gpu_arm(args):
             dist.barrier()
 
     precisions = ["fp64", "fp32_mixed"] if args.precision == "both" else [args.precision]
+    if args.strength:  # the stress module runs on FP64 states
+        precisions = ["fp64"]
     results = {}
     for prec in precisions:
         res = measure(args, prec, local, barrier)

@@ -105,9 +105,21 @@ typedef struct {
  * c_hg: viscous hourglass control (Flanagan-Belytschko) with corner forces
  * -c_hg rho cs V^(2/3) sum_alpha gamma_alpha (gamma_alpha . u) from the
  * start of the step, in both the velocity and the energy update (0: none).
+ * Material strength, the stress module of ScalSALE's case study (Sec.
+ * III-D; shear0 = 0: none, the pure hydro scheme; FP64 states, single-stage
+ * step): a deviatoric stress S per cell, advanced by the Jaumann rate with
+ * von Mises radial return (Wilkins 1963) from the time-centred velocity
+ * gradient; shear modulus and yield from the Steinberg-Guinan model,
+ * G = shear0 + shear_dp p (rho_ref / rho)^(1/3) + shear_dt (e - e_ref) / cv
+ * (clamped at 0) and Y = min(yield0 (1 + hard_beta eps_p)^hard_n,
+ * yield_max) G / shear0; the corner forces gain -S dV/dx_a (velocity and
+ * energy update alike, so total energy stays exact), the CFL speed
+ * 4 G / (3 rho), and the remap carries S and the plastic strain eps_p per
+ * unit mass with the donor cell's mass flux.  The fields "sxx", "syy",
+ * "szz", "sxy", "syz", "szx" and "eps_p" then exist.
  * Options other than the defaults may need more device memory: size the
  * buffer with sale_state_bytes_for().  Batches take only the default
- * time_order and c_hg. */
+ * time_order, c_hg and shear0. */
 typedef struct {
   int kind;
   double gamma;
@@ -118,6 +130,8 @@ typedef struct {
   int remap_order;
   int time_order;
   double c_hg;
+  double shear0, shear_dp, shear_dt, cv, e_ref, rho_ref;
+  double yield0, yield_max, hard_beta, hard_n;
 } sale_problem_desc;
 
 /* Diagnostics (FP64 sums in a fixed reduction order). */

@@ -225,6 +225,7 @@ struct sale_state {
   double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
   double *geoHG;                         //   hourglass shape vectors (32 per cell; control on)
   double *im, *imn;                      //   1 / m per cell, 1 / mn per node
+  double *sdev, *sold;                   //   strength: stress + plastic strain (7 per cell), remap copy
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -239,6 +240,7 @@ struct sale_state {
   bool o2 = false;                       // second-order remap scratch carved (FP64)
   bool pc = false;                       // predictor-corrector scratch carved
   bool hg = false;                       // hourglass scratch carved
+  bool str = false;                      // material strength (FP64): deviatoric stress carved
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
@@ -288,6 +290,7 @@ static size_t carve(sale_state *st, char *base) {
   }
   st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = st->geoHG = nullptr;
   st->im = st->imn = nullptr;
+  st->sdev = st->sold = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -315,6 +318,10 @@ static size_t carve(sale_state *st, char *base) {
     if (st->o2)
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
     if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
+    if (st->str) {
+      st->sdev = (double *)cv.take(sizeof(double) * 7 * nc);
+      st->sold = (double *)cv.take(sizeof(double) * 7 * nc);
+    }
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
     st->VE32 = (float *)cv.take(sizeof(float) * nc);
@@ -379,6 +386,8 @@ static Fields<R> fields_t(const sale_state *st) {
     F.iVE = (const R *)st->geoIVE;
     F.iL2 = (const R *)st->geoIL2;
     F.HG = (const R *)st->geoHG;
+    F.sdev = (R *)st->sdev;
+    F.sold = (R *)st->sold;
     F.ste = (R *)st->ste;
     F.rE = (const R *)st->relE;
     F.mqx = (R *)st->mq[0];
@@ -417,6 +426,8 @@ static Fields<R> fields_t(const sale_state *st) {
   F.fh = (R *)st->fh;
   F.c_hg = st->prob.c_hg;
   F.c_hg32 = (float)st->prob.c_hg;
+  F.str = {st->prob.shear0,  st->prob.shear_dp,  st->prob.shear_dt,  st->prob.cv,        st->prob.e_ref,
+           st->prob.rho_ref, st->prob.yield0,    st->prob.yield_max, st->prob.hard_beta, st->prob.hard_n};
   F.srx = (R *)st->slope[0];
   F.sry = (R *)st->slope[1];
   F.srz = (R *)st->slope[2];
@@ -429,7 +440,7 @@ static Fields<R> fields_t(const sale_state *st) {
 }
 
 static size_t state_bytes(long long nc, long long nn, int precision, bool jit, bool o2 = false, bool pc = false,
-                          bool hg = false) {
+                          bool hg = false, bool str = false) {
   sale_state tmp;
   tmp.nc = nc;
   tmp.nn = nn;
@@ -438,6 +449,7 @@ static size_t state_bytes(long long nc, long long nn, int precision, bool jit, b
   tmp.o2 = o2 && precision == SALE_FP64;
   tmp.pc = pc;
   tmp.hg = hg;
+  tmp.str = str && precision == SALE_FP64;
   tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   return carve(&tmp, nullptr);
 }
@@ -456,7 +468,7 @@ extern "C" size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem
   if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED) || !mixed_fits(mesh, precision))
     return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0, prob->remap_order == 2,
-                     prob->time_order == 2, prob->c_hg > 0.0);
+                     prob->time_order == 2, prob->c_hg > 0.0, prob->shear0 > 0.0);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -475,6 +487,18 @@ static int validate_problem(const sale_problem_desc &p) {
   if (p.remap_order < 0 || p.remap_order > 2) return fail(SALE_EINVAL, "problem: remap_order must be 0, 1 or 2");
   if (p.time_order < 0 || p.time_order > 2) return fail(SALE_EINVAL, "problem: time_order must be 0, 1 or 2");
   if (!(p.c_hg >= 0.0) || !std::isfinite(p.c_hg)) return fail(SALE_EINVAL, "problem: c_hg must be finite and >= 0");
+  if (!(p.shear0 >= 0.0) || !std::isfinite(p.shear0)) return fail(SALE_EINVAL, "problem: shear0 must be finite and >= 0");
+  if (p.shear0 > 0.0) {
+    const double fin[] = {p.shear_dp, p.shear_dt, p.e_ref, p.yield0, p.yield_max, p.hard_beta, p.hard_n};
+    for (double v : fin)
+      if (!std::isfinite(v)) return fail(SALE_EINVAL, "problem: strength parameters must be finite");
+    if (!(p.cv > 0.0) || !(p.rho_ref > 0.0) || !std::isfinite(p.cv) || !std::isfinite(p.rho_ref))
+      return fail(SALE_EINVAL, "problem: strength needs cv > 0 and rho_ref > 0");
+    if (p.yield0 < 0.0 || p.yield_max < 0.0 || p.hard_beta < 0.0 || p.hard_n < 0.0)
+      return fail(SALE_EINVAL, "problem: yield0, yield_max, hard_beta, hard_n must be >= 0");
+    if (p.time_order == 2)
+      return fail(SALE_EINVAL, "problem: material strength takes the single-stage step (time_order 1)");
+  }
   return SALE_OK;
 }
 
@@ -625,6 +649,8 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
     return fail(SALE_EINVAL, "sale_state_init: unknown precision %d", precision);
   int rc = validate_problem(*prob);
   if (rc) return rc;
+  if (prob->shear0 > 0.0 && precision != SALE_FP64)
+    return fail(SALE_EINVAL, "sale_state_init: material strength runs on FP64 states");
   if (!mixed_fits(mesh, precision))
     return fail(SALE_EINVAL, "sale_state_init: FP32-mixed states index nodes in 32 bits (at most 2^31 - 1 nodes)");
   rc = check_device_buffer("sale_state_init", device_buf, bytes, sale_state_bytes_for(mesh, prob, precision));
@@ -648,6 +674,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   st->o2 = precision == SALE_FP64 && prob->remap_order == 2;
   st->pc = prob->time_order == 2;
   st->hg = prob->c_hg > 0.0;
+  st->str = precision == SALE_FP64 && prob->shear0 > 0.0;
   st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
@@ -714,6 +741,8 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     return cuda_fail(e, "sale_state_init: upload");
   }
   launch_reset(st->S, st->stream);
+  if (st->sdev && e == cudaSuccess)  // strength: unstressed, no plastic strain
+    e = cudaMemsetAsync(st->sdev, 0, sizeof(double) * 7 * (size_t)st->nc, st->stream);
   if (!mixed) {
     const Fields<double> F = fields_t<double>(st);
     launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->stream);
@@ -823,7 +852,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
 }
 
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
-  if (remap && st->x_is_ref) {
+  if (remap && st->x_is_ref && !st->str) {  // strength runs the general kernels
     launch_ale_cycle(st, dt_override);
     return;
   }
@@ -872,7 +901,7 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
     if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
     for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles of launch_cycle
       const bool remap = remap_every > 0 && (j + 1) % remap_every == 0;
-      if (remap && st->x_is_ref) {
+      if (remap && st->x_is_ref && !st->str) {
         st->upar ^= 1;
         continue;
       }
@@ -1000,6 +1029,11 @@ static void *field_ptr(const sale_state *st, const char *name, bool *node, bool 
   *elem = st->elem;
   if (!strcmp(name, "m")) return st->m;
   if (!strcmp(name, "e")) return st->e;
+  if (st->sdev) {  // strength: deviatoric stress components and plastic strain
+    static const char *const snames[7] = {"sxx", "syy", "szz", "sxy", "syz", "szx", "eps_p"};
+    for (int q = 0; q < 7; ++q)
+      if (!strcmp(name, snames[q])) return st->sdev + (size_t)q * (size_t)st->nc;
+  }
   *writable = false;
   if (!strcmp(name, "rho")) return st->rho;
   if (!strcmp(name, "p")) return st->p;
@@ -1105,7 +1139,7 @@ extern "C" int sale_refresh(sale_state *st) {
   int rc = ready(st, "sale_refresh");
   if (rc) return rc;
   // on the reference mesh the FP64 refresh reads the cached geometry
-  launch_k(st, st->precision == SALE_FP64 ? (st->x_is_ref ? kAleEos : kEos) : kMixEos, kDtPropose);
+  launch_k(st, st->precision == SALE_FP64 ? (st->x_is_ref && !st->str ? kAleEos : kEos) : kMixEos, kDtPropose);
   CUDA_TRY(cudaGetLastError());
   return SALE_OK;
 }
@@ -1301,8 +1335,9 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   for (int i = 0; i < n; ++i) {
     int rc = validate_problem(probs[i]);
     if (rc) return fail(rc, "sale_batch_create: mesh %d: %s", i, sale_last_error());
-    if (probs[i].time_order == 2 || probs[i].c_hg > 0.0)
-      return fail(SALE_EINVAL, "sale_batch_create: mesh %d: batches run the single-stage step without hourglass control",
+    if (probs[i].time_order == 2 || probs[i].c_hg > 0.0 || probs[i].shear0 > 0.0)
+      return fail(SALE_EINVAL,
+                  "sale_batch_create: mesh %d: batches run the single-stage step without hourglass control or strength",
                   i);
   }
   std::vector<size_t> soff((size_t)n);

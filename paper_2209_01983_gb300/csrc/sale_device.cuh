@@ -175,6 +175,86 @@ __device__ __forceinline__ P3 hourglass_corner(const R *fh, long long nc, long l
   return {(double)fh[(3ll * a + 0) * nc + c], (double)fh[(3ll * a + 1) * nc + c], (double)fh[(3ll * a + 2) * nc + c]};
 }
 
+// ---------------------------------------------------------------------------
+// Material strength: the stress module (Steinberg-Guinan shear modulus and
+// yield, Wilkins deviatoric stress update)
+// ---------------------------------------------------------------------------
+
+// Steinberg, Cochran, Guinan (J. Appl. Phys. 51, 1498, 1980): G grows with
+// the pressure scaled by the cube root of eta = rho_ref / rho and falls
+// with the temperature T - T_ref = (e - e_ref) / cv, clamped at 0; the yield
+// stress work-hardens, Y0 (1 + beta eps_p)^n up to Ymax, and follows G / G0.
+__device__ __forceinline__ void steinberg_gy(const Strength &s, double p, double rho, double e, double eps_p,
+                                             double &G, double &Y) {
+  double g = s.shear0 + s.shear_dp * p * cbrt(s.rho_ref / rho) + s.shear_dt * (e - s.e_ref) / s.cv;
+  if (!(g > 0.0)) g = 0.0;
+  double y = s.yield0 * pow(1.0 + s.hard_beta * eps_p, s.hard_n);
+  if (y > s.yield_max) y = s.yield_max;
+  G = g;
+  Y = y * g / s.shear0;
+}
+
+// S_c g for the deviatoric stress of cell c (sdev[q nc + c], q = xx, yy,
+// zz, xy, yz, zx).
+template <typename R>
+__device__ __forceinline__ P3 stress_apply(const R *sd, long long nc, long long c, P3 g) {
+  const double sxx = (double)sd[c], syy = (double)sd[nc + c], szz = (double)sd[2 * nc + c];
+  const double sxy = (double)sd[3 * nc + c], syz = (double)sd[4 * nc + c], szx = (double)sd[5 * nc + c];
+  return {sxx * g.x + sxy * g.y + szx * g.z, sxy * g.x + syy * g.y + syz * g.z, szx * g.x + syz * g.y + szz * g.z};
+}
+
+// Wilkins (1963): with the velocity gradient L[3 i + j] = du_i/dx_j, the
+// strain rate deviator D' and the spin W, the trial stress
+// S* = S + dt (2 G D' + W S - S W) (Jaumann rate); above the von Mises
+// surface sqrt(3/2 S*:S*) = Y it is scaled back onto it (radial return)
+// and the plastic strain grows by (J - Y) / (3 G).  S6 = (xx, yy, zz, xy,
+// yz, zx) in place.
+__device__ __forceinline__ void stress_update(double (&S6)[6], const double (&L)[9], double dt, double G, double Y,
+                                              double &deps) {
+  const double S[3][3] = {{S6[0], S6[3], S6[5]}, {S6[3], S6[1], S6[4]}, {S6[5], S6[4], S6[2]}};
+  double D[3][3], W[3][3], T[3][3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      D[i][j] = 0.5 * (L[3 * i + j] + L[3 * j + i]);
+      W[i][j] = 0.5 * (L[3 * i + j] - L[3 * j + i]);
+    }
+  const double tr = (D[0][0] + D[1][1] + D[2][2]) / 3.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i) D[i][i] -= tr;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+      double ws = 0.0, sw = 0.0;
+#pragma unroll
+      for (int k = 0; k < 3; ++k) {
+        ws += W[i][k] * S[k][j];
+        sw += S[i][k] * W[k][j];
+      }
+      T[i][j] = S[i][j] + dt * (2.0 * G * D[i][j] + ws - sw);
+    }
+  double ss = 0.0;
+#pragma unroll
+  for (int i = 0; i < 3; ++i)
+#pragma unroll
+    for (int j = 0; j < 3; ++j) ss += T[i][j] * T[i][j];
+  const double J = sqrt(1.5 * ss);
+  double scale = 1.0;
+  deps = 0.0;
+  if (J > Y) {
+    scale = Y / J;
+    if (G > 0.0) deps = (J - Y) / (3.0 * G);
+  }
+  S6[0] = scale * T[0][0];
+  S6[1] = scale * T[1][1];
+  S6[2] = scale * T[2][2];
+  S6[3] = scale * 0.5 * (T[0][1] + T[1][0]);
+  S6[4] = scale * 0.5 * (T[1][2] + T[2][1]);
+  S6[5] = scale * 0.5 * (T[2][0] + T[0][2]);
+}
+
 __device__ __forceinline__ double warp_max(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));

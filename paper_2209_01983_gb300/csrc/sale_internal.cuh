@@ -89,6 +89,11 @@ enum DtMode : int {
 };
 
 // Device pointers and constants of one state (passed by value).
+// Steinberg-Guinan parameters (the problem descriptor's strength fields).
+struct Strength {
+  double shear0, shear_dp, shear_dt, cv, e_ref, rho_ref, yield0, yield_max, hard_beta, hard_n;
+};
+
 template <typename R>
 struct Fields {
   // --- read by the FP32-mixed kernels (a batch stages this prefix, up to
@@ -97,6 +102,12 @@ struct Fields {
   long long nc, nn;
   R *u, *v, *w;                // node velocity
   R *ub, *vb, *wb;             // time-centred / remapped node velocity
+  // Material strength (Steinberg-Guinan G and Y, Wilkins deviatoric
+  // stress), FP64 states with shear0 > 0: sdev[q nc + c], q = xx, yy, zz,
+  // xy, yz, zx, then the equivalent plastic strain; sold the same layout,
+  // the copy the cell remap reads its donors from.  Null: no strength.
+  R *sdev, *sold;
+  Strength str;
   R *mn;                       // node mass
   R *dke;                      // kinetic energy lost by the node remap
   R *m, *e;                    // cell mass, specific internal energy

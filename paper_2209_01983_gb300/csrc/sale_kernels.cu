@@ -132,7 +132,13 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
     F.q[c] = (R)q;
     F.cs[c] = (R)cs;
     F.sig[c] = (R)(p + q);
-    dtc = F.cfl * L / sqrt(cs * cs + 2.0 * q / rho);
+    double c2 = cs * cs + 2.0 * q / rho;
+    if (F.sdev) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho)
+      double Gm, Ym;
+      steinberg_gy(F.str, p, rho, e, (double)F.sdev[6 * F.nc + c], Gm, Ym);
+      c2 += 4.0 * Gm / (3.0 * rho);
+    }
+    dtc = F.cfl * L / sqrt(c2);
     if (dtc != dtc) {
       set_status(S, SALE_ENAN);
       dtc = INFINITY;
@@ -159,6 +165,7 @@ __device__ __forceinline__ void add_corner_force(const Fields<R> &F, const R *gx
   const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
   const double sig = (double)F.sig[c];
   P3 cf = sig * g;
+  if (F.sdev) cf = cf - stress_apply(F.sdev, F.nc, c, g);  // the deviatoric part of the cell stress
   if (F.fh) cf = cf + hourglass_corner(F.fh, F.nc, c, 7 - S8);
   f = f + cf;
 }
@@ -311,6 +318,35 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), UB[a]);
     e1 -= h / m * work_hg;
   }
+  if (F.sdev) {
+    // the deviatoric forces' work, then the stress at n+1 from the
+    // time-centred velocity gradient L = (1/V^n) sum_a ubar_a (x) dV/dx_a and
+    // G, Y of the state at n (single-stage step: X is x^n here)
+    double work_s = 0.0, L[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      work_s += dot(stress_apply(F.sdev, F.nc, c, G[a]), UB[a]);
+      const double ua[3] = {UB[a].x, UB[a].y, UB[a].z}, ga[3] = {G[a].x, G[a].y, G[a].z};
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) L[3 * r + q] += ua[r] * ga[q];
+    }
+    e1 += h / m * work_s;
+    const double Vn = (double)F.vol[c];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) L[q] /= Vn;
+    const long long nc = F.nc;
+    double Gm, Ym, deps;
+    steinberg_gy(F.str, (double)F.p[c], (double)F.rho[c], (double)F.e[c], (double)F.sdev[6 * nc + c], Gm, Ym);
+    double S6[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S6[q] = (double)F.sdev[q * nc + c];
+    stress_update(S6, L, h, Gm, Ym, deps);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) F.sdev[q * nc + c] = (R)S6[q];
+    F.sdev[6 * nc + c] = (R)((double)F.sdev[6 * nc + c] + deps);
+  }
   if (pc) load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   else load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
@@ -386,6 +422,8 @@ __global__ void __launch_bounds__(kBlock) k_remap_faces(Fields<R> F, DevScalars 
   face_flux<0>(F, c, i, j, k, F.mux, F.epx);
   face_flux<1>(F, c, i, j, k, F.muy, F.epy);
   face_flux<2>(F, c, i, j, k, F.muz, F.epz);
+  if (F.sdev)  // the cell remap reads the donors' stress from this copy while it writes the new one
+    for (int q = 0; q < 7; ++q) F.sold[q * F.nc + c] = F.sdev[q * F.nc + c];
 }
 
 // Dual mass flux along the mesh edge from node (i,j,k) to its +AX
@@ -507,6 +545,28 @@ __global__ void __launch_bounds__(kBlock) k_remap_cells(Fields<R> F, DevScalars 
   F.m[c] = (R)m1;
   F.e[c] = (R)(ie / m1);
   if (F.im) F.im[c] = (R)(1.0 / m1);
+  if (F.sdev) {
+    // deviatoric stress and plastic strain per unit mass, carried by each
+    // face's mass flux from its donor (mu > 0: the high cell), first-order
+    // donor cell; low faces take mass from this cell, high faces give it
+    const long long nc = F.nc;
+    double ms[7];
+#pragma unroll
+    for (int q = 0; q < 7; ++q) ms[q] = m0 * (double)F.sold[q * nc + c];
+    auto face = [&](double mu, long long lo, long long hi, double sign) {
+      const long long dn = mu > 0.0 ? hi : lo;
+#pragma unroll
+      for (int q = 0; q < 7; ++q) ms[q] += sign * mu * (double)F.sold[q * nc + dn];
+    };
+    if (i > 0) face((double)F.mux[c], c - 1, c, -1.0);
+    if (i + 1 < F.nx) face((double)F.mux[c + 1], c, c + 1, 1.0);
+    if (j > 0) face((double)F.muy[c], c - sy, c, -1.0);
+    if (j + 1 < F.ny) face((double)F.muy[c + sy], c, c + sy, 1.0);
+    if (k > 0) face((double)F.muz[c], c - sz, c, -1.0);
+    if (k + 1 < F.nz) face((double)F.muz[c + sz], c, c + sz, 1.0);
+#pragma unroll
+    for (int q = 0; q < 7; ++q) F.sdev[q * nc + c] = (R)(ms[q] / m1);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -41,7 +41,10 @@ class sale_problem_desc(C.Structure):
                 ("p_blast", C.c_double), ("e_deposit", C.c_double),
                 ("cfl", C.c_double), ("c_q", C.c_double), ("c_l", C.c_double),
                 ("dt_init", C.c_double), ("dt_growth", C.c_double), ("ke_fix", C.c_int),
-                ("remap_order", C.c_int), ("time_order", C.c_int), ("c_hg", C.c_double)]
+                ("remap_order", C.c_int), ("time_order", C.c_int), ("c_hg", C.c_double),
+                ("shear0", C.c_double), ("shear_dp", C.c_double), ("shear_dt", C.c_double), ("cv", C.c_double),
+                ("e_ref", C.c_double), ("rho_ref", C.c_double), ("yield0", C.c_double), ("yield_max", C.c_double),
+                ("hard_beta", C.c_double), ("hard_n", C.c_double)]
 
 
 class sale_diag(C.Structure):
