@@ -163,29 +163,36 @@ MIXED_HG = {
 }
 
 
-# Material strength (FP64, general kernels): the deviatoric stress S (6)
-# and plastic strain per cell.  Node pass: S of the 8 cells, S dV/dx per
-# corner (9 multiply-adds).  Cell pass: S, eps_p read and written, the
+# Material strength (FP64): the deviatoric stress S (6) and plastic strain
+# per cell.  Node pass: S of the 8 cells, S dV/dx per corner (9
+# multiply-adds).  Cell pass: S, eps_p read and the new values written, the
 # deviatoric work (8 x (15 + 5)), the velocity gradient (8 x 9
 # multiply-adds), Steinberg-Guinan G and Y (~20), the Wilkins update (strain
-# rate and spin 18, trial stress 9 x 16, J 18, return 13).  EoS + dt: eps_p,
-# G and 4 G / (3 rho).  Remap: the copy of S, eps_p (faces pass), and their
-# transport with the six face fluxes (cells pass).
+# rate and spin 18, trial stress 9 x 16, J 18, return 13).  Remap: S, eps_p
+# read (own and donors') and written, transported with the six face fluxes;
+# the CFL speed adds G of the new state.  The general kernels also copy S,
+# eps_p in the face pass for the cell remap.
+_STR_CELL = 8 * 20 + 8 * 18 + 20 + 18 + 9 * 16 + 18 + 13
+_STR_REMAP = 7 * (2 + 6 * 2) + 7
 FP64_STRENGTH_EXTRA = {
     "lagrange_nodes": (8 * 6, 8 * 18),
-    "lagrange_cells": (8 * 14, 8 * 20 + 8 * 18 + 20 + 18 + 9 * 16 + 18 + 13),
+    "lagrange_cells": (8 * 14, _STR_CELL),
     "eos_dt": (8 * 1, 25),
     "remap_faces": (8 * 14, 0),
-    "remap_cells": (8 * 14, 7 * (2 + 6 * 2) + 7),
+    "remap_cells": (8 * 14, _STR_REMAP),
+    "ale_nodes": (8 * 6, 8 * 18),
+    "ale_cells": (8 * 14, _STR_CELL),
+    "ale_remap_eos": (8 * 14, _STR_REMAP + 25),
 }
 
 
 def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
           hourglass: bool = False, strength: bool = False):
     if precision == "fp64":
-        if strength:  # the general kernels, with the stress module
+        if strength:  # the same kernels with the stress module
+            base = table(precision, path, jitter, order, time_order, hourglass)
             return {k: (u, b + FP64_STRENGTH_EXTRA.get(k, (0, 0))[0], f + FP64_STRENGTH_EXTRA.get(k, (0, 0))[1])
-                    for k, (u, b, f) in FP64.items()}
+                    for k, (u, b, f) in base.items()}
         if path != "ale":
             return FP64
         t = dict(FP64_ALE_O2 if order == 2 else FP64_ALE)

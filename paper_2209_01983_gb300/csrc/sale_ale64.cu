@@ -148,6 +148,7 @@ __global__ void __launch_bounds__(kBlock) k_geo_init_nodes(Fields<double> F, dou
   }
 }
 
+template <bool STR>
 __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScalars *S, double dt_override) {
   const long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (n >= F.nn || !cycle_active(S)) return;
@@ -161,7 +162,9 @@ __global__ void __launch_bounds__(kBlock) k_ale_nodes(Fields<double> F, DevScala
     const int ci = i - 1 + (s & 1), cj = j - 1 + ((s >> 1) & 1), ck = k - 1 + ((s >> 2) & 1);
     if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) continue;
     const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
-    P3 cf = F.sig[c] * corner_g(Gs, F.nc, c, 7 - s);
+    const P3 g = corner_g(Gs, F.nc, c, 7 - s);
+    P3 cf = F.sig[c] * g;
+    if constexpr (STR) cf = cf - stress_apply(F.sdev, F.nc, c, g);  // the deviatoric part of the cell stress
     if (F.fh) cf = cf + hourglass_corner(F.fh, F.nc, c, 7 - s);
     f = f + cf;
   }
@@ -236,7 +239,8 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   }
 }
 
-__global__ void __launch_bounds__(kBlock, 4) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
+template <bool STR>
+__global__ void __launch_bounds__(kBlock, STR ? 2 : 4) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   const double h = step_dt(S, dt_override);
@@ -261,6 +265,42 @@ __global__ void __launch_bounds__(kBlock, 4) k_ale_cells(Fields<double> F, DevSc
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), ub[a]);
     e1 -= h * im * work_hg;
+  }
+  if constexpr (STR) {
+    // the deviatoric forces' work; the stress at n+1 from the time-centred
+    // velocity gradient L = (1/V_E) sum_a ubar_a (x) dV/dx_a (x^n is the
+    // reference mesh) and G, Y of the state at n, written to the remap's
+    // copy, which the remap + EoS pass transports back into sdev
+    const long long nc = F.nc;
+    double L[9] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const P3 g = corner_g(Gs, nc, c, a);
+      const double ua[3] = {ub[a].x, ub[a].y, ub[a].z}, ga[3] = {g.x, g.y, g.z};
+#pragma unroll
+      for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) L[3 * r + q] += ua[r] * ga[q];
+    }
+    // sum_a (S dV/dx_a) . ubar_a = S : sum_a ubar_a (x) dV/dx_a, the same sum
+    // regrouped (S is symmetric)
+    const double sxx = F.sdev[c], syy = F.sdev[nc + c], szz = F.sdev[2 * nc + c];
+    const double sxy = F.sdev[3 * nc + c], syz = F.sdev[4 * nc + c], szx = F.sdev[5 * nc + c];
+    const double work_s = sxx * L[0] + syy * L[4] + szz * L[8] + sxy * (L[1] + L[3]) + syz * (L[5] + L[7]) +
+                          szx * (L[2] + L[6]);
+    e1 += h * im * work_s;
+    const double iv = F.iVE[c];
+#pragma unroll
+    for (int q = 0; q < 9; ++q) L[q] *= iv;
+    // G and Y of the state at n, from the remap + EoS that ended the last cycle
+    const double Gm = F.sdev[7 * nc + c], Ym = F.sdev[8 * nc + c];
+    double deps, S6[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) S6[q] = F.sdev[q * nc + c];
+    stress_update(S6, L, h, Gm, Ym, deps);
+#pragma unroll
+    for (int q = 0; q < 6; ++q) F.sold[q * nc + c] = S6[q];
+    F.sold[6 * nc + c] = F.sdev[6 * nc + c] + deps;
   }
   F.e[c] = e1;
   // swept volumes of the three low faces, assembled from k_ale_edges: the
@@ -485,6 +525,7 @@ __global__ void __launch_bounds__(kAleTx * kAleTy) k_ale_remap_nodes(Fields<doub
 // 1/V_E, L_E) from its mass, specific energy and node velocities U; writes
 // the derived fields and returns the CFL rate (cs^2 + 2 q / rho) / (cfl L)^2
 // = 1 / dt_c^2.
+template <bool STR = false>
 __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long long c, const P3 (&U)[8], double m,
                                                double e) {
   const double V = F.VE[c];
@@ -508,7 +549,15 @@ __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long lon
   F.p[c] = p;
   F.q[c] = q;
   F.sig[c] = p + q;  // cs is not stored: it is a function of e (sale_copy_field derives it)
-  return (cs2 + 2.0 * q_rho) * F.iL2[c];
+  double c2 = cs2 + 2.0 * q_rho;
+  if constexpr (STR) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho); G, Y kept for the next cell pass
+    double Gm, Ym;
+    steinberg_gy(F.str, p, rho, e, F.sdev[6 * F.nc + c], Gm, Ym);
+    F.sdev[7 * F.nc + c] = Gm;
+    F.sdev[8 * F.nc + c] = Ym;
+    c2 += 4.0 * Gm / (3.0 * rho);
+  }
+  return c2 * F.iL2[c];
 }
 
 __device__ __forceinline__ void ale_cell_velocities(const Fields<double> &F, int i, int j, int k, P3 (&U)[8]) {
@@ -649,6 +698,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
 
 // Cell remap + EoS of cell c; returns its CFL rate 1 / dt_c^2 (0 outside
 // the mesh).
+template <bool STR>
 __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, DevScalars *S, long long c) {
   double rate = 0.0;
   if (c < F.nc) {
@@ -682,7 +732,29 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
     F.m[c] = m1;
     F.im[c] = r;
     F.e[c] = e;
-    rate = ale_eos_cell(F, c, U, m1, e);
+    if constexpr (STR) {
+      // deviatoric stress and plastic strain per unit mass, carried by each
+      // face's mass flux from its donor (mu > 0: the high cell), from the
+      // Lagrangian values the cell pass left in sold
+      const long long nc = F.nc;
+      double ms[7];
+#pragma unroll
+      for (int q = 0; q < 7; ++q) ms[q] = m0 * F.sold[q * nc + c];
+      auto face = [&](double mu, long long lo, long long hi, double sign) {
+        const long long dn = mu > 0.0 ? hi : lo;
+#pragma unroll
+        for (int q = 0; q < 7; ++q) ms[q] += sign * mu * F.sold[q * nc + dn];
+      };
+      if (i > 0) face(F.mux[c], c - 1, c, -1.0);
+      if (i + 1 < F.nx) face(F.mux[c + 1], c, c + 1, 1.0);
+      if (j > 0) face(F.muy[c], c - sy, c, -1.0);
+      if (j + 1 < F.ny) face(F.muy[c + sy], c, c + sy, 1.0);
+      if (k > 0) face(F.muz[c], c - sz, c, -1.0);
+      if (k + 1 < F.nz) face(F.muz[c + sz], c, c + sz, 1.0);
+#pragma unroll
+      for (int q = 0; q < 7; ++q) F.sdev[q * nc + c] = ms[q] * r;
+    }
+    rate = ale_eos_cell<STR>(F, c, U, m1, e);
     if (nan_d(rate)) {
       set_status(S, SALE_ENAN);
       rate = 0.0;
@@ -696,13 +768,14 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
 // largest rate is exact, and dt with it.
 constexpr int kEosCellsPerThread = 4;
 
-__global__ void __launch_bounds__(kBlock, 3) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
+template <bool STR>
+__global__ void __launch_bounds__(kBlock, STR ? 2 : 3) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
   if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
   const long long c0 = blockIdx.x * (long long)(kBlock * kEosCellsPerThread) + threadIdx.x;
   double rate = 0.0;  // CFL rate 1 / dt_c^2
 #pragma unroll 1
   for (int r = 0; r < kEosCellsPerThread; ++r)
-    rate = max_nonneg_d(rate, ale_remap_eos_cell(F, S, c0 + (long long)r * kBlock));  // rates are >= 0, not NaN
+    rate = max_nonneg_d(rate, ale_remap_eos_cell<STR>(F, S, c0 + (long long)r * kBlock));  // rates are >= 0, not NaN
   block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
 }
 
@@ -743,11 +816,17 @@ void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *
 
 void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double dt_override, cudaStream_t st) {
   switch (kid) {
-    case kAleNodes: k_ale_nodes<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAleNodes:
+      if (F.sdev) k_ale_nodes<true><<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_nodes<false><<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override);
+      break;
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleHourglass: k_ale_hourglass<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kAleCells: k_ale_cells<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAleCells:
+      if (F.sdev) k_ale_cells<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_cells<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleSlopes: k_ale_slopes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleFluxes:
@@ -761,10 +840,12 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
       break;
     }
     case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
-    case kAleRemapEos:
-      k_ale_remap_eos<<<grid_ale((F.nc + kEosCellsPerThread - 1) / kEosCellsPerThread), kBlock, 0, st>>>(F, S,
-                                                                                                      dt_override);
+    case kAleRemapEos: {
+      const unsigned g = grid_ale((F.nc + kEosCellsPerThread - 1) / kEosCellsPerThread);
+      if (F.sdev) k_ale_remap_eos<true><<<g, kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_remap_eos<false><<<g, kBlock, 0, st>>>(F, S, dt_override);
       break;
+    }
     default: break;
   }
 }

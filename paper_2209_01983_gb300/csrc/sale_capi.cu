@@ -225,7 +225,7 @@ struct sale_state {
   double *geoIVE, *geoIL2;               //   1 / V_E, 1 / (cfl L_E)^2
   double *geoHG;                         //   hourglass shape vectors (32 per cell; control on)
   double *im, *imn;                      //   1 / m per cell, 1 / mn per node
-  double *sdev, *sold;                   //   strength: stress + plastic strain (7 per cell), remap copy
+  double *sdev, *sold;                   //   strength: stress, plastic strain, G, Y (9 per cell); remap copy (7)
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -319,7 +319,7 @@ static size_t carve(sale_state *st, char *base) {
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
     if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
     if (st->str) {
-      st->sdev = (double *)cv.take(sizeof(double) * 7 * nc);
+      st->sdev = (double *)cv.take(sizeof(double) * 9 * nc);
       st->sold = (double *)cv.take(sizeof(double) * 7 * nc);
     }
   } else {
@@ -427,7 +427,8 @@ static Fields<R> fields_t(const sale_state *st) {
   F.c_hg = st->prob.c_hg;
   F.c_hg32 = (float)st->prob.c_hg;
   F.str = {st->prob.shear0,  st->prob.shear_dp,  st->prob.shear_dt,  st->prob.cv,        st->prob.e_ref,
-           st->prob.rho_ref, st->prob.yield0,    st->prob.yield_max, st->prob.hard_beta, st->prob.hard_n};
+           st->prob.rho_ref, st->prob.yield0,    st->prob.yield_max, st->prob.hard_beta, st->prob.hard_n,
+           st->prob.cv > 0.0 ? 1.0 / st->prob.cv : 0.0, st->prob.shear0 > 0.0 ? 1.0 / st->prob.shear0 : 0.0};
   F.srx = (R *)st->slope[0];
   F.sry = (R *)st->slope[1];
   F.srz = (R *)st->slope[2];
@@ -742,7 +743,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   }
   launch_reset(st->S, st->stream);
   if (st->sdev && e == cudaSuccess)  // strength: unstressed, no plastic strain
-    e = cudaMemsetAsync(st->sdev, 0, sizeof(double) * 7 * (size_t)st->nc, st->stream);
+    e = cudaMemsetAsync(st->sdev, 0, sizeof(double) * 9 * (size_t)st->nc, st->stream);
   if (!mixed) {
     const Fields<double> F = fields_t<double>(st);
     launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->stream);
@@ -852,7 +853,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
 }
 
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
-  if (remap && st->x_is_ref && !st->str) {  // strength runs the general kernels
+  if (remap && st->x_is_ref) {
     launch_ale_cycle(st, dt_override);
     return;
   }
@@ -901,7 +902,7 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
     if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
     for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles of launch_cycle
       const bool remap = remap_every > 0 && (j + 1) % remap_every == 0;
-      if (remap && st->x_is_ref && !st->str) {
+      if (remap && st->x_is_ref) {
         st->upar ^= 1;
         continue;
       }

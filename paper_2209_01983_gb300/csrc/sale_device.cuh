@@ -186,12 +186,12 @@ __device__ __forceinline__ P3 hourglass_corner(const R *fh, long long nc, long l
 // stress work-hardens, Y0 (1 + beta eps_p)^n up to Ymax, and follows G / G0.
 __device__ __forceinline__ void steinberg_gy(const Strength &s, double p, double rho, double e, double eps_p,
                                              double &G, double &Y) {
-  double g = s.shear0 + s.shear_dp * p * cbrt(s.rho_ref / rho) + s.shear_dt * (e - s.e_ref) / s.cv;
+  double g = s.shear0 + s.shear_dp * p * cbrt(s.rho_ref / rho) + s.shear_dt * (e - s.e_ref) * s.inv_cv;
   if (!(g > 0.0)) g = 0.0;
   double y = s.yield0 * pow(1.0 + s.hard_beta * eps_p, s.hard_n);
   if (y > s.yield_max) y = s.yield_max;
   G = g;
-  Y = y * g / s.shear0;
+  Y = y * g * s.inv_shear0;
 }
 
 // S_c g for the deviatoric stress of cell c (sdev[q nc + c], q = xx, yy,
@@ -240,10 +240,10 @@ __device__ __forceinline__ void stress_update(double (&S6)[6], const double (&L)
   for (int i = 0; i < 3; ++i)
 #pragma unroll
     for (int j = 0; j < 3; ++j) ss += T[i][j] * T[i][j];
-  const double J = sqrt(1.5 * ss);
   double scale = 1.0;
   deps = 0.0;
-  if (J > Y) {
+  if (1.5 * ss > Y * Y) {  // J > Y, the square root and division only where the cell yields
+    const double J = sqrt(1.5 * ss);
     scale = Y / J;
     if (G > 0.0) deps = (J - Y) / (3.0 * G);
   }

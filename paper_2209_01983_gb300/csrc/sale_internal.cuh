@@ -92,6 +92,7 @@ enum DtMode : int {
 // Steinberg-Guinan parameters (the problem descriptor's strength fields).
 struct Strength {
   double shear0, shear_dp, shear_dt, cv, e_ref, rho_ref, yield0, yield_max, hard_beta, hard_n;
+  double inv_cv, inv_shear0;  // 1 / cv, 1 / shear0
 };
 
 template <typename R>
@@ -104,8 +105,10 @@ struct Fields {
   R *ub, *vb, *wb;             // time-centred / remapped node velocity
   // Material strength (Steinberg-Guinan G and Y, Wilkins deviatoric
   // stress), FP64 states with shear0 > 0: sdev[q nc + c], q = xx, yy, zz,
-  // xy, yz, zx, then the equivalent plastic strain; sold the same layout,
-  // the copy the cell remap reads its donors from.  Null: no strength.
+  // xy, yz, zx, then the equivalent plastic strain (q = 6), and G, Y of the
+  // current state (q = 7, 8: written by the EoS that ends every cycle, read
+  // by the next cell pass); sold the first seven, the copy the cell remap
+  // reads its donors from.  Null: no strength.
   R *sdev, *sold;
   Strength str;
   R *mn;                       // node mass

@@ -133,9 +133,11 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
     F.cs[c] = (R)cs;
     F.sig[c] = (R)(p + q);
     double c2 = cs * cs + 2.0 * q / rho;
-    if (F.sdev) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho)
+    if (F.sdev) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho); G, Y kept for the next cell pass
       double Gm, Ym;
       steinberg_gy(F.str, p, rho, e, (double)F.sdev[6 * F.nc + c], Gm, Ym);
+      F.sdev[7 * F.nc + c] = (R)Gm;
+      F.sdev[8 * F.nc + c] = (R)Ym;
       c2 += 4.0 * Gm / (3.0 * rho);
     }
     dtc = F.cfl * L / sqrt(c2);
@@ -337,9 +339,9 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
 #pragma unroll
     for (int q = 0; q < 9; ++q) L[q] /= Vn;
     const long long nc = F.nc;
-    double Gm, Ym, deps;
-    steinberg_gy(F.str, (double)F.p[c], (double)F.rho[c], (double)F.e[c], (double)F.sdev[6 * nc + c], Gm, Ym);
-    double S6[6];
+    // G and Y of the state at n, from the EoS that ended the last cycle
+    const double Gm = (double)F.sdev[7 * nc + c], Ym = (double)F.sdev[8 * nc + c];
+    double deps, S6[6];
 #pragma unroll
     for (int q = 0; q < 6; ++q) S6[q] = (double)F.sdev[q * nc + c];
     stress_update(S6, L, h, Gm, Ym, deps);

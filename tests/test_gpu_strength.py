@@ -130,7 +130,7 @@ def test_strength_rules(sale):
     m = sale.Mesh(md)
     base = sale.sale_state_bytes(m._h, sale.SALE_FP64)
     need = sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(pd)), sale.SALE_FP64)
-    assert need >= base + 2 * 7 * 8 * md.ncell  # stress and plastic strain, and their remap copy
+    assert need >= base + (9 + 7) * 8 * md.ncell  # stress, plastic strain, G, Y; the remap copy
     with pytest.raises(sale.SaleError) as ei:
         sale.State(md, pd, precision=sale.SALE_FP32_MIXED)
     assert ei.value.code == sale.SALE_EINVAL
