@@ -728,7 +728,13 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
     // (a NaN mass with the sign bit clear passes here and makes the rate NaN)
     if (!pos_d(m1)) set_status(S, nan_d(m1) ? SALE_ENAN : SALE_ENEGVOL);
     const double r = 1.0 / m1;
-    const double e = ie * r;
+    double e = ie * r;
+    // The second-order remap's limiter divides only where neighbouring
+    // values differ: one residual step (Markstein, IBM J. Res. Dev. 34,
+    // 1990) makes e the correctly rounded ie / m1 in nearly every cell, so
+    // a quiescent region stays bitwise uniform instead of carrying the
+    // product's last-bit noise into the slopes.
+    if (F.remap_order == 2) e = fma(r, fma(-m1, e, ie), e);
     F.m[c] = m1;
     F.im[c] = r;
     F.e[c] = e;
