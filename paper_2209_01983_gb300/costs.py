@@ -57,11 +57,13 @@ FP64_ALE = {
     "ale_density": ("cell", 8 * (3 + 2 + 2), 8),
     # 3 swept volumes, rho_L, e read; 3 mass + 3 energy fluxes + 3 dual-flux parts written
     "ale_fluxes": ("cell", 8 * (3 + 2 + 6 + 3), 15),
-    # 3 dual-flux parts (per cell), u, mn, 0.5|u|^2 read; u', mn', dKE written
-    "ale_remap_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 1 + 1), 6 * 12 + 20),
+    # 3 dual-flux parts (per cell), u, mn, 0.5|u|^2 read; u', mn', 1/mn', dKE
+    # written (the node pass multiplies by 1/mn)
+    "ale_remap_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 1 + 1 + 1), 6 * 12 + 20),
     # 6 fluxes, m, e, dKE, u', G, V_E, L_E, 1/V_E, 1/(cfl L_E)^2 read;
-    # m, e, vol, rho, p, q, sigma written (cs is a function of e, not stored)
-    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 4 + 7), 35 + 48 + 30),
+    # m, 1/m, e, vol, rho, p, q, sigma written (cs is a function of e, not
+    # stored; the cell pass multiplies by 1/m)
+    "ale_remap_eos": ("cell", 8 * (6 + 2 + 1 + 3 + 24 + 4 + 8), 35 + 48 + 30),
 }
 
 

@@ -27,6 +27,6 @@ def test_every_cost_entry_is_a_library_kernel(names):
 
 
 def test_cycle_totals():
-    assert costs.cycle_cost("fp64") == (1592, 627)
+    assert costs.cycle_cost("fp64") == (1608, 627)
     assert costs.cycle_cost("fp32_mixed", jitter=True) == (588, 957)
     assert costs.cycle_cost("fp32_mixed", jitter=False) == (332, 2521)
