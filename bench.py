@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--no-one-by-one", action="store_true",
                     help="batch: skip the comparison with the meshes advanced one by one")
     ap.add_argument("--no-precision", action="store_true", help="default run: skip the precision variant")
+    ap.add_argument("--no-options", action="store_true",
+                    help="default run: skip the scheme-option variants (FP64 cycle with each option)")
+    ap.add_argument("--options-steps", type=int, default=5, help="timed cycles of each scheme-option variant")
     ap.add_argument("--precision-n", type=int, default=128,
                     help="default run: cells per axis of the precision variant (to --t-end)")
     args = ap.parse_args()
@@ -593,12 +596,50 @@ def gpu_arm(args):
         variants[f"batch{args.batch_count}"] = bt
     if not args.no_precision:
         variants["precision"] = measure_precision(args.precision_n, args.t_end, local)
+    if not args.no_options and not args.strength and args.remap_order == 1 and args.time_order == 1 \
+            and args.c_hg == 0 and "fp64" in results:
+        variants["scheme_options"] = measure_options(args, local, results["fp64"])
     if variants:
         line["variants"] = variants
     print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
     return 0
+
+
+# The scheme options of the library, each run alone on the bench mesh (FP64).
+SCHEME_OPTIONS = (("remap_order_2", {"remap_order": 2}), ("predictor_corrector", {"time_order": 2}),
+                  ("hourglass_c_hg_0.05", {"c_hg": 0.05}), ("strength", {"strength": True}))
+
+
+def measure_options(args, local, base):
+    """The FP64 Eulerian cycle on the same mesh with each scheme option (the
+    second-order remap, the predictor-corrector step, hourglass control,
+    material strength), `--options-steps` timed cycles each, against the
+    default cycle of this run."""
+    import argparse as _ap
+
+    import torch
+
+    out = {"steps": args.options_steps, "precision": "fp64",
+           "default_ms_per_step": base["ms"] / args.steps}
+    for name, over in SCHEME_OPTIONS:
+        a = _ap.Namespace(**vars(args))
+        a.steps = args.options_steps
+        for k, v in over.items():
+            setattr(a, k, v)
+        res = measure(a, "fp64", local, lambda: None)
+        ms = res["ms"] / a.steps
+        top = dict(list(res["kernels"].items())[:3])
+        out[name] = {"value": res["md"].ncell / (ms * 1e-3), "unit": UNIT, "ms_per_step": ms,
+                     "vs_default_ms": ms / out["default_ms_per_step"], "gpu_launches": res["gpu_launches"],
+                     "config": workload_config(a, "fp64")["workload"],
+                     "top_kernels_ms_per_launch": {k: v["ms_per_launch"] for k, v in top.items()},
+                     "clocks": res["clocks"], "check": res["check"]}
+        res["st"].close()
+        del res
+        torch.cuda.empty_cache()
+    return out
 
 
 def measure_batch(args, local, steps, unbatched_steps, count):
