@@ -492,7 +492,7 @@ def e2e_rate(args, res, world):
     host = {nm: torch.from_numpy(st.field(nm)).pin_memory() for nm in names}
     h2d = sum(t.numel() * 8 for t in host.values())
     d2h = 8 * 6 + 128  # diagnostics sums + device scalars
-    steps = max(1, min(args.steps, 5))
+    steps = max(1, min(args.steps, 10))
     dd = sale.sale_diag()
 
     def step():
