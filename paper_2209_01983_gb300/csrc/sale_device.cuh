@@ -188,7 +188,9 @@ __device__ __forceinline__ void steinberg_gy(const Strength &s, double p, double
                                              double &G, double &Y) {
   double g = s.shear0 + s.shear_dp * p * cbrt(s.rho_ref / rho) + s.shear_dt * (e - s.e_ref) * s.inv_cv;
   if (!(g > 0.0)) g = 0.0;
-  double y = s.yield0 * pow(1.0 + s.hard_beta * eps_p, s.hard_n);
+  // a cell that never yielded (eps_p exactly 0, which the remap keeps exact
+  // where every donor has it) takes Y0 itself, the value pow(1, n) gives
+  double y = eps_p > 0.0 ? s.yield0 * pow(1.0 + s.hard_beta * eps_p, s.hard_n) : s.yield0;
   if (y > s.yield_max) y = s.yield_max;
   G = g;
   Y = y * g * s.inv_shear0;
