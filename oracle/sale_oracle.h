@@ -123,7 +123,8 @@ int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
                      long long deposit_cell, double deposit_energy);
 /* Overwrite the evolving fields (positions, velocities, node mass, cell
  * mass, energy, time and last dt), then recompute derived fields and the
- * proposed dt.  Used to restart the oracle from an arbitrary state. */
+ * proposed dt.  Used to restart the oracle from an arbitrary state.  The
+ * deviatoric stress and plastic strain (strength) are kept as they are. */
 int oracle_set_state(oracle_state *s, const double *x, const double *y,
                      const double *z, const double *u, const double *v,
                      const double *w, const double *mn, const double *m,
