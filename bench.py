@@ -66,6 +66,8 @@ def parse():
     ap.add_argument("--time-order", type=int, default=1, choices=(1, 2),
                     help="Lagrangian step: 1 single stage, 2 predictor-corrector")
     ap.add_argument("--c-hg", type=float, default=0.0, help="viscous hourglass coefficient (0: none)")
+    ap.add_argument("--remap-every", type=int, default=1,
+                    help="remap after every k-th cycle (0: Lagrangian cycles); FP64 only when not 1")
     ap.add_argument("--strength", action="store_true",
                     help="material strength (Steinberg-Guinan elastic-plastic material, FP64 general kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -290,8 +292,9 @@ def reference_arm(args):
 def workload_config(args, precision):
     order = ("" if args.remap_order == 1 else "-remap2") + ("" if args.time_order == 1 else "-pc") + \
         ("" if args.c_hg == 0 else f"-hg{args.c_hg}") + ("-strength" if args.strength else "")
-    return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-ale-every-cycle{order}",
-            "cells": args.n ** 3, "gamma": 1.4, "remap_every": 1, "remap_order": args.remap_order,
+    mode = {0: "lagrangian", 1: "ale-every-cycle"}.get(args.remap_every, f"remap-every-{args.remap_every}")
+    return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-{mode}{order}",
+            "cells": args.n ** 3, "gamma": 1.4, "remap_every": args.remap_every, "remap_order": args.remap_order,
             "time_order": args.time_order, "c_hg": args.c_hg,
             **({"strength": STRENGTH} if args.strength else {}),
             "precision": precision,
@@ -390,7 +393,7 @@ def measure(args, precision, local, barrier):
         # warm-up part 1: pick the tile shape (ordinary cycles, results unchanged)
         from paper_2209_01983_gb300 import autotune
         tuning = autotune.tune_state(st, cycles=16, repeats=3)
-    st.run_to_time(max_cycles=args.warmup, remap_every=1)
+    st.run_to_time(max_cycles=args.warmup, remap_every=args.remap_every)
 
     # ---- timed region: K full cycles, graph replays on the state's stream
     st.profile(True)
@@ -403,7 +406,7 @@ def measure(args, precision, local, barrier):
     clocks.start()
     time.sleep(0.3)  # let the sampler take a first reading
     ev0.record(st.stream)
-    done = st.run_to_time(max_cycles=args.steps, remap_every=1)
+    done = st.run_to_time(max_cycles=args.steps, remap_every=args.remap_every)
     ev1.record(st.stream)
     ev1.synchronize()
     torch.cuda.synchronize()
@@ -415,7 +418,8 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    table = costs.table(precision, "ale", jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
+    path = "ale" if args.remap_every == 1 else "general"  # only Eulerian-every-cycle runs take the cached kernels
+    table = costs.table(precision, path, jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
                         hourglass=args.c_hg > 0, strength=args.strength)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
@@ -536,7 +540,7 @@ def gpu_arm(args):
             dist.barrier()
 
     precisions = ["fp64", "fp32_mixed"] if args.precision == "both" else [args.precision]
-    if args.strength:  # the stress module runs on FP64 states
+    if args.strength or args.remap_every != 1:  # FP64 states only
         precisions = ["fp64"]
     results = {}
     for prec in precisions:
@@ -597,7 +601,7 @@ def gpu_arm(args):
     if not args.no_precision:
         variants["precision"] = measure_precision(args.precision_n, args.t_end, local)
     if not args.no_options and not args.strength and args.remap_order == 1 and args.time_order == 1 \
-            and args.c_hg == 0 and "fp64" in results:
+            and args.c_hg == 0 and args.remap_every == 1 and "fp64" in results:
         variants["scheme_options"] = measure_options(args, local, results["fp64"])
     if variants:
         line["variants"] = variants

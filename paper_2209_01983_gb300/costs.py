@@ -18,20 +18,29 @@ Formula counts used below (FP64 path):
 
 VOL, GRAD, LEN = 202, 600, 122
 
+# General FP64 kernels (Lagrangian cycles, remap every k > 1 cycles).  The
+# EoS pass evaluates the geometry once per cycle, face by face (HALF_GEOM64
+# below: the corner sums, the face areas and the volume by Euler's
+# relation), and keeps the 24 corner gradients (Gn) for the next step's node
+# and cell passes, which read them instead of rebuilding them.
 # kernel: (unit, bytes per unit FP64, flops per unit)
 FP64 = {
-    # x, u, mn, sigma read; u, ubar, x+ written
-    "lagrange_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 3 + 3 + 3), GRAD + 48 + 20),
-    # x, ubar, x+, m, e, sigma read; e, vol, rho written
-    "lagrange_cells": ("cell", 8 * (3 + 3 + 3 + 3 + 3), GRAD + 40 + 5 + VOL + 1),
+    # x, u, mn, sigma, Gn (24 per cell) read; u, ubar, x+ written; the force
+    # gathered from 8 corners (8 x 3 multiply-adds)
+    "lagrange_nodes": ("node", 8 * (3 + 3 + 1 + 1 + 24 + 3 + 3 + 3), 48 + 20),
+    # Gn, ubar, x+, m, e, sigma read; e, vol, rho written; work from Gn, the
+    # volume at x+ for the remap's donor density
+    "lagrange_cells": ("cell", 8 * (24 + 3 + 3 + 3 + 3), 48 + 5 + VOL + 1),
     # x, x_ref, rho, e read; 3 mass + 3 energy fluxes written
     "remap_faces": ("cell", 8 * (3 + 3 + 2 + 6), 3 * VOL + 6),
     # 3 mass fluxes, u, mn, x_ref read; u', mn', dKE, x written
     "remap_nodes": ("node", 8 * (3 + 3 + 1 + 3 + 3 + 1 + 1 + 3), 125),
     # 6 fluxes, m, e, dKE read; m, e written
     "remap_cells": ("cell", 8 * (6 + 2 + 1 + 2), 35),
-    # x, u, m, e read; vol, rho, p, q, cs, sigma written
-    "eos_dt": ("cell", 8 * (3 + 3 + 2 + 6), VOL + GRAD + 40 + LEN + 33),
+    # x, u, m, e read; vol, rho, p, q, cs, sigma, Gn written; the geometry
+    # face by face, dV/dt (48), EoS, viscosity and the CFL rate (~30)
+    "eos_dt": ("cell", 8 * (3 + 3 + 2 + 6 + 24), 21 + 6 * (12 + 14 + 30 + 9) - 3 * 6 + 4 * 12 + 7 * 5 + 7 + 24
+               + 48 + 30),
 }
 
 # FP64 Eulerian cycle (remap every cycle), cached reference geometry:

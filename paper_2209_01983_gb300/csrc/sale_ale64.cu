@@ -58,42 +58,6 @@ __device__ __forceinline__ double quad_term(P3 p0, P3 p1, P3 p2, P3 p3) {
 }
 constexpr double kInvTwelfth = 1.0 / 12.0;
 
-// Face F's contributions to the corner sums R_a = 24 dV/dx_a of a hex given
-// relative to its node 0 (X[0] = 0), and to max_f |A_f|^2 with the face
-// vector A_f = d02 x d13 (twice the face's vector area).  A corner's fan
-// term, (p_next + 2 p_opposite + p_prev) x (p_prev - p_next) over the
-// face's cycle q0..q3, shares the face's diagonals d02 = q2 - q0 and
-// d13 = q3 - q1 with its neighbours, and opposite corners' terms add up to
-// 2 A_f: t0 = (q1 + q3 + 2 q2) x d13, t1 = d02 x (q0 + q2 + 2 q3),
-// t2 = 2 A_f - t0, t3 = 2 A_f - t1.  The faces through node 0 start at it
-// (q0 = 0).  Every corner's x face (F = 0 or 1) comes first and sets its sum.
-template <int F>
-__device__ __forceinline__ void face_fan(const P3 (&X)[8], P3 (&R)[8], double &a2max) {
-  constexpr int n0 = face_node(F, 0), n1 = face_node(F, 1), n2 = face_node(F, 2), n3 = face_node(F, 3);
-  const P3 q1 = X[n1], q2 = X[n2], q3 = X[n3];
-  const P3 d02 = n0 == 0 ? q2 : q2 - X[n0];
-  const P3 s02 = n0 == 0 ? q2 : X[n0] + q2;
-  const P3 d13 = q3 - q1;
-  const P3 A = cross(d02, d13);
-  const double aa = dot(A, A);
-  a2max = F == 0 ? aa : max_nonneg_d(a2max, aa);
-  const P3 t0 = cross((q1 + q3) + 2.0 * q2, d13);
-  const P3 t1 = cross(d02, s02 + 2.0 * q3);
-  const P3 A2 = 2.0 * A;
-  const P3 t2 = A2 - t0, t3 = A2 - t1;
-  if constexpr (F < 2) {
-    R[n0] = t0;
-    R[n1] = t1;
-    R[n2] = t2;
-    R[n3] = t3;
-  } else {
-    R[n0] = R[n0] + t0;
-    R[n1] = R[n1] + t1;
-    R[n2] = R[n2] + t2;
-    R[n3] = R[n3] + t3;
-  }
-}
-
 }  // namespace
 
 // Reference geometry of every cell: corner gradients, volume, length scale.
@@ -661,18 +625,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
   X[0] = {0.0, 0.0, 0.0};
   P3 R[8];
   double a2max;
-  face_fan<0>(X, R, a2max);
-  face_fan<1>(X, R, a2max);
-  face_fan<2>(X, R, a2max);
-  face_fan<3>(X, R, a2max);
-  face_fan<4>(X, R, a2max);
-  face_fan<5>(X, R, a2max);
-  // V is homogeneous of degree 3 in the node positions, so (Euler)
-  // 3 V = sum_a x_a . dV/dx_a = sum_a x_a . R_a / 24, and x_0 = 0
-  double v72 = dot(X[1], R[1]);
-#pragma unroll
-  for (int a = 2; a < 8; ++a) v72 += dot(X[a], R[a]);
-  const double V = v72 * (1.0 / 72.0);
+  const double V = hex_geometry_rel0(X, R, a2max);
   if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
   double dvdt = 0.0;
 #pragma unroll

@@ -226,6 +226,7 @@ struct sale_state {
   double *geoHG;                         //   hourglass shape vectors (32 per cell; control on)
   double *im, *imn;                      //   1 / m per cell, 1 / mn per node
   double *sdev, *sold;                   //   strength: stress, plastic strain, G, Y (9 per cell); remap copy (7)
+  double *Gn;                            //   corner gradients at the current positions (24 per cell)
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -291,6 +292,7 @@ static size_t carve(sale_state *st, char *base) {
   st->geoG = st->geoVE = st->geoLE = st->geoTE = st->geoIVE = st->geoIL2 = st->geoHG = nullptr;
   st->im = st->imn = nullptr;
   st->sdev = st->sold = nullptr;
+  st->Gn = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -315,6 +317,7 @@ static size_t carve(sale_state *st, char *base) {
     st->kd = (double *)cv.take(sizeof(double) * nn);
     st->im = (double *)cv.take(sizeof(double) * nc);
     st->imn = (double *)cv.take(sizeof(double) * nn);
+    st->Gn = (double *)cv.take(sizeof(double) * 24 * nc);
     if (st->o2)
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
     if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
@@ -388,6 +391,7 @@ static Fields<R> fields_t(const sale_state *st) {
     F.HG = (const R *)st->geoHG;
     F.sdev = (R *)st->sdev;
     F.sold = (R *)st->sold;
+    F.Gn = (R *)st->Gn;
     F.ste = (R *)st->ste;
     F.rE = (const R *)st->relE;
     F.mqx = (R *)st->mq[0];

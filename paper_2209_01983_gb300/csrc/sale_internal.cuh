@@ -137,6 +137,11 @@ struct Fields {
   // gradient folds to constants.
   const float *Gc;
   R *Gh;                       // predictor-corrector: corner gradients at x^{n+1/2}, Gh[(3 a + axis) nc + c]
+  // FP64 states: corner gradients at the current positions, Gn[(3 a + axis)
+  // nc + c], written by the general EoS pass (which runs after every change
+  // of the positions: each cycle, each remap, state creation and refresh)
+  // and read by the next Lagrangian step; null elsewhere
+  R *Gn;
   R *fh;                       // hourglass corner forces of the step, fh[(3 a + axis) nc + c]; null: no control
   double gamma, growth, dt_init;
   float gamma32, cfl32, c_q32, c_l32, c_hg32;  // FP32 copies of the constants

@@ -96,35 +96,61 @@ __global__ void k_reset_scalars(DevScalars *S) {
 // EoS, viscosity, CFL dt
 // ---------------------------------------------------------------------------
 
+// Corner a's gradient from the current-position cache Gn[(3 a + axis) nc + c].
 template <typename R>
-__global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, int mode, double dt_override) {
+__device__ __forceinline__ P3 gn_corner(const R *Gn, long long nc, long long c, int a) {
+  const R *g = Gn + 3ll * a * nc + c;
+  return {(double)g[0], (double)g[nc], (double)g[2 * nc]};
+}
+
+// STR: the state carries material strength (a separate instantiation, so
+// the stress module's registers do not weigh on the plain kernels).
+template <typename R, bool STR>
+__global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_eos_dt(Fields<R> F, DevScalars *S, int mode,
+                                                              double dt_override) {
   const bool active = (mode == kDtAdvance) ? cycle_active(S) : (S->status == 0);
   if (!active) return;  // uniform over the grid: S changes only in the last block
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-  double dtc = INFINITY;
+  double rate = 0.0;  // CFL rate (c / (cfl L))^2; 0 without a cell
   if (c < F.nc) {
     int i, j, k;
     cell_ijk(c, F.nx, F.ny, i, j, k);
-    P3 X[8], U[8], G[8];
+    P3 X[8], Rs[8];
     load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
-    load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
-    shift0(X);
-    const double V = hex_volume_shifted(X);
+    // the geometry once, face by face (volume by Euler's relation), and
+    // the corner gradients kept for the next Lagrangian step
+#pragma unroll
+    for (int a = 1; a < 8; ++a) X[a] = X[a] - X[0];
+    X[0] = {0.0, 0.0, 0.0};
+    double a2max;
+    const double V = hex_geometry_rel0(X, Rs, a2max);
     if (!(V > 0.0)) set_status(S, V != V ? SALE_ENAN : SALE_ENEGVOL);
-    hex_grad_shifted(X, G);
     double dvdt = 0.0;
 #pragma unroll
-    for (int a = 0; a < 8; ++a) dvdt += dot(G[a], U[a]);
-    const double div = dvdt / V;
-    const double L = V / sqrt(hex_max_face_area2(X));
+    for (int a = 0; a < 8; ++a) {
+      const P3 g = kInvSixth24 * Rs[a];
+      if (F.Gn) {
+        F.Gn[(3ll * a + 0) * F.nc + c] = (R)g.x;
+        F.Gn[(3ll * a + 1) * F.nc + c] = (R)g.y;
+        F.Gn[(3ll * a + 2) * F.nc + c] = (R)g.z;
+      }
+      const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+      dvdt += dot(g, P3{(double)F.u[n], (double)F.v[n], (double)F.w[n]});
+    }
+    // with L = V / max_f |A_f / 2|: L div = 2 dvdt / sqrt(max_f |A_f|^2) and
+    // 1 / L^2 = max_f |A_f|^2 / (4 V^2), so neither L nor a division by V is
+    // formed beyond 1 / V
+    const double iv = 1.0 / V;
     const double m = (double)F.m[c], e = (double)F.e[c];
-    const double rho = m / V;
+    const double rho = m * iv;
     const double p = (F.gamma - 1.0) * rho * e;
-    const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
-    double q = 0.0;
-    if (div < 0.0) {
-      const double ld = L * div;
-      q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
+    const double cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
+    const double cs = sqrt(cs2);
+    double q = 0.0, q_rho = 0.0;
+    if (dvdt < 0.0) {  // div < 0 (V > 0)
+      const double ld = 2.0 * dvdt * rsqrt(a2max);
+      q_rho = F.c_q * ld * ld + F.c_l * cs * fabs(ld);
+      q = rho * q_rho;
     }
     F.vol[c] = (R)V;
     F.rho[c] = (R)rho;
@@ -132,21 +158,21 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
     F.q[c] = (R)q;
     F.cs[c] = (R)cs;
     F.sig[c] = (R)(p + q);
-    double c2 = cs * cs + 2.0 * q / rho;
-    if (F.sdev) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho); G, Y kept for the next cell pass
+    double c2 = cs2 + 2.0 * q_rho;
+    if constexpr (STR) {  // longitudinal elastic wave: K / rho + 4 G / (3 rho); G, Y kept for the next cell pass
       double Gm, Ym;
       steinberg_gy(F.str, p, rho, e, (double)F.sdev[6 * F.nc + c], Gm, Ym);
       F.sdev[7 * F.nc + c] = (R)Gm;
       F.sdev[8 * F.nc + c] = (R)Ym;
       c2 += 4.0 * Gm / (3.0 * rho);
     }
-    dtc = F.cfl * L / sqrt(c2);
-    if (dtc != dtc) {
+    rate = c2 * (0.25 * a2max) * (iv * iv) / (F.cfl * F.cfl);
+    if (rate != rate) {
       set_status(S, SALE_ENAN);
-      dtc = INFINITY;
+      rate = 0.0;
     }
   }
-  block_min_dt_and_finalize(F, S, dtc, mode, dt_override);
+  block_min_dt_and_finalize<R, true>(F, S, rate, mode, dt_override);
 }
 
 // ---------------------------------------------------------------------------
@@ -157,14 +183,19 @@ __global__ void __launch_bounds__(kBlock) k_eos_dt(Fields<R> F, DevScalars *S, i
 // the gradient taken at the positions (gx, gy, gz).
 template <int S8, typename R>
 __device__ __forceinline__ void add_corner_force(const Fields<R> &F, const R *gx, const R *gy, const R *gz, int i,
-                                                 int j, int k, P3 &f) {
+                                                 int j, int k, bool cached, P3 &f) {
   const int ci = i - 1 + (S8 & 1), cj = j - 1 + ((S8 >> 1) & 1), ck = k - 1 + ((S8 >> 2) & 1);
   if (ci < 0 || cj < 0 || ck < 0 || ci >= F.nx || cj >= F.ny || ck >= F.nz) return;
-  P3 X[8];
-  load_hex(gx, gy, gz, F.nx, F.ny, ci, cj, ck, X);
-  shift0(X);
-  const P3 g = hex_corner_grad_shifted<7 - S8>(X);
   const long long c = cell_index(F.nx, F.ny, ci, cj, ck);
+  P3 g;
+  if (cached) {  // this node is corner 7 - S8 of the cell; its gradient at x^n from the EoS pass
+    g = gn_corner(F.Gn, F.nc, c, 7 - S8);
+  } else {
+    P3 X[8];
+    load_hex(gx, gy, gz, F.nx, F.ny, ci, cj, ck, X);
+    shift0(X);
+    g = hex_corner_grad_shifted<7 - S8>(X);
+  }
   const double sig = (double)F.sig[c];
   P3 cf = sig * g;
   if (F.sdev) cf = cf - stress_apply(F.sdev, F.nc, c, g);  // the deviatoric part of the cell stress
@@ -184,7 +215,12 @@ __global__ void __launch_bounds__(kBlock) k_hourglass(Fields<R> F, DevScalars *S
   load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
   shift0(X);
-  hex_grad_shifted(X, G);
+  if (F.Gn) {  // the gradients of x^n, kept by the EoS pass
+#pragma unroll
+    for (int a = 0; a < 8; ++a) G[a] = gn_corner(F.Gn, F.nc, c, a);
+  } else {
+    hex_grad_shifted(X, G);
+  }
   // cs from e: the Eulerian kernels do not store it
   const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax((double)F.e[c], 0.0));
   hourglass_store(X, G, U, (double)F.vol[c], (double)F.rho[c], cs, F.c_hg, F.fh, F.nc, c);
@@ -213,10 +249,15 @@ __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalar
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
   P3 X[8], U[8], G[8];
-  load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   load_hex(F.u, F.v, F.w, F.nx, F.ny, i, j, k, U);
-  shift0(X);
-  hex_grad_shifted(X, G);
+  if (F.Gn) {  // the gradients of x^n, kept by the EoS pass
+#pragma unroll
+    for (int a = 0; a < 8; ++a) G[a] = gn_corner(F.Gn, F.nc, c, a);
+  } else {
+    load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+    shift0(X);
+    hex_grad_shifted(X, G);
+  }
   double work = 0.0;
 #pragma unroll
   for (int a = 0; a < 8; ++a) work += dot(G[a], U[a]);
@@ -269,15 +310,16 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScala
   int i, j, k;
   node_ijk(n, F.nx, F.ny, i, j, k);
   const R *gx = pc ? F.xn : F.x, *gy = pc ? F.yn : F.y, *gz = pc ? F.zn : F.z;
+  const bool cached = !pc && F.Gn;  // single stage: the gradients of x^n are kept
   P3 f = {0.0, 0.0, 0.0};
-  add_corner_force<0>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<1>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<2>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<3>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<4>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<5>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<6>(F, gx, gy, gz, i, j, k, f);
-  add_corner_force<7>(F, gx, gy, gz, i, j, k, f);
+  add_corner_force<0>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<1>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<2>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<3>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<4>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<5>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<6>(F, gx, gy, gz, i, j, k, cached, f);
+  add_corner_force<7>(F, gx, gy, gz, i, j, k, cached, f);
   const double mn = (double)F.mn[n];
   const double u0 = (double)F.u[n], v0 = (double)F.v[n], w0 = (double)F.w[n];
   double u1 = u0 + h * f.x / mn, v1 = v0 + h * f.y / mn, w1 = w0 + h * f.z / mn;
@@ -295,8 +337,9 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScala
   oz[n] = (R)((double)F.z[n] + h * wb);
 }
 
-template <typename R>
-__global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScalars *S, double dt_override) {
+template <typename R, bool STR>
+__global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_lagrange_cells(Fields<R> F, DevScalars *S,
+                                                                       double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   const double h = step_dt(S, dt_override);
@@ -304,23 +347,26 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
   cell_ijk(c, F.nx, F.ny, i, j, k);
   const bool pc = F.time_order == 2;  // gradient at x^{n+1/2}, new positions in place
   P3 X[8], UB[8], G[8];
-  if (pc) load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
-  else load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+  double work = 0.0, work_hg = 0.0;
   load_hex(F.ub, F.vb, F.wb, F.nx, F.ny, i, j, k, UB);
-  shift0(X);
-  hex_grad_shifted(X, G);
-  double work = 0.0;
+  if (!pc && F.Gn) {  // the gradients of x^n, kept by the EoS pass
+#pragma unroll
+    for (int a = 0; a < 8; ++a) G[a] = gn_corner(F.Gn, F.nc, c, a);
+  } else {
+    if (pc) load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+    else load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
+    shift0(X);
+    hex_grad_shifted(X, G);
+  }
 #pragma unroll
   for (int a = 0; a < 8; ++a) work += dot(G[a], UB[a]);
-  const double m = (double)F.m[c];
-  double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
-  if (F.fh) {
-    double work_hg = 0.0;
+  if (F.fh)
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), UB[a]);
-    e1 -= h / m * work_hg;
-  }
-  if (F.sdev) {
+  const double m = (double)F.m[c];
+  double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
+  if (F.fh) e1 -= h / m * work_hg;
+  if constexpr (STR) {
     // the deviatoric forces' work, then the stress at n+1 from the
     // time-centred velocity gradient L = (1/V^n) sum_a ubar_a (x) dV/dx_a and
     // G, Y of the state at n (single-stage step: X is x^n here)
@@ -351,6 +397,39 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_cells(Fields<R> F, DevScala
   }
   if (pc) load_hex(F.x, F.y, F.z, F.nx, F.ny, i, j, k, X);
   else load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
+  shift0(X);
+  const double V1 = hex_volume_shifted(X);
+  if (!(V1 > 0.0)) set_status(S, V1 != V1 ? SALE_ENAN : SALE_ENEGVOL);
+  F.e[c] = (R)e1;
+  F.vol[c] = (R)V1;
+  F.rho[c] = (R)(m / V1);
+}
+
+// The Lagrangian cell pass of the common case -- single-stage step, the
+// gradients of x^n kept by the EoS pass, no material strength -- with one
+// corner at a time live: the compatible energy update, then the volume and
+// density at x^{n+1} (the remap's donor density).
+template <typename R>
+__global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F, DevScalars *S,
+                                                                    double dt_override) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  const double h = step_dt(S, dt_override);
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  double work = 0.0, work_hg = 0.0;
+#pragma unroll
+  for (int a = 0; a < 8; ++a) {
+    const long long n = node_index(F.nx, F.ny, i + (a & 1), j + ((a >> 1) & 1), k + ((a >> 2) & 1));
+    const P3 ub = {(double)F.ub[n], (double)F.vb[n], (double)F.wb[n]};
+    work += dot(gn_corner(F.Gn, F.nc, c, a), ub);
+    if (F.fh) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), ub);
+  }
+  const double m = (double)F.m[c];
+  double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
+  if (F.fh) e1 -= h / m * work_hg;
+  P3 X[8];
+  load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
   const double V1 = hex_volume_shifted(X);
   if (!(V1 > 0.0)) set_status(S, V1 != V1 ? SALE_ENAN : SALE_ENEGVOL);
@@ -667,9 +746,16 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
   }
   switch (kid) {
     case kInitNodes: k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F); break;
-    case kEos: k_eos_dt<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override); break;
+    case kEos:
+      if (F.sdev) k_eos_dt<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+      else k_eos_dt<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+      break;
     case kLagNodes: k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
-    case kLagCells: k_lagrange_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kLagCells:
+      if (F.sdev) k_lagrange_cells<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else if (F.Gn && F.time_order != 2) k_lagrange_cells_cached<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else k_lagrange_cells<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      break;
     case kPcPositions: k_pc_positions<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kHourglass: k_hourglass<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
     case kPcPredict: k_pc_predict<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
