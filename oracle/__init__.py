@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes as C
 import math
 import os
+import re
 import subprocess
 
 import numpy as np
@@ -36,6 +37,7 @@ class Params(C.Structure):
         ("shear0", C.c_double), ("shear_dp", C.c_double), ("shear_dt", C.c_double), ("cv", C.c_double),
         ("e_ref", C.c_double), ("rho_ref", C.c_double), ("yield0", C.c_double), ("yield_max", C.c_double),
         ("hard_beta", C.c_double), ("hard_n", C.c_double),
+        ("nmat", C.c_int), ("mat_gamma", C.c_double * 4), ("mat_pinf", C.c_double * 4),
     ]
 
 STRENGTH_FIELDS = ("shear0", "shear_dp", "shear_dt", "cv", "e_ref", "rho_ref", "yield0", "yield_max",
@@ -53,6 +55,7 @@ class _State(C.Structure):
         ("sxx", _dp), ("syy", _dp), ("szz", _dp), ("sxy", _dp), ("syz", _dp), ("szx", _dp), ("eps_p", _dp),
         ("t", C.c_double), ("dt", C.c_double), ("dt_last", C.c_double),
         ("cycle", C.c_longlong), ("status", C.c_int),
+        ("alpha", _dp), ("mm", _dp), ("me", _dp),
     ]
 
 
@@ -88,6 +91,9 @@ def lib():
         L.oracle_create.argtypes = [C.c_int, C.c_int, C.c_int, _dp, _dp, _dp, C.POINTER(Params)]
         L.oracle_destroy.argtypes = [C.POINTER(_State)]
         L.oracle_init_prim.argtypes = [C.POINTER(_State), _dp, _dp, C.c_longlong, C.c_double]
+        L.oracle_init_materials.argtypes = [C.POINTER(_State), _dp, _dp, C.POINTER(C.c_int), C.c_longlong,
+                                            C.c_double]
+        L.oracle_set_materials.argtypes = [C.POINTER(_State), _dp, _dp, _dp]
         L.oracle_set_state.argtypes = [C.POINTER(_State)] + [_dp] * 9 + [C.c_double, C.c_double]
         L.oracle_eos.argtypes = [C.POINTER(_State)]
         L.oracle_cfl_dt.restype = C.c_double
@@ -165,6 +171,9 @@ def params_from(pd, reflect=(1, 1, 1, 1, 1, 1)) -> Params:
     p.c_hg = float(getattr(pd, "c_hg", 0.0))
     for name in STRENGTH_FIELDS:
         setattr(p, name, float(getattr(pd, name, 0.0)))
+    p.nmat = int(getattr(pd, "nmat", 0))
+    for k, (g, pinf) in enumerate(zip(getattr(pd, "mat_gamma", (1.4,) * 4), getattr(pd, "mat_pinf", (0.0,) * 4))):
+        p.mat_gamma[k], p.mat_pinf[k] = float(g), float(pinf)
     return p
 
 
@@ -188,7 +197,12 @@ class Oracle:
         from paper_2209_01983_gb300 import inputs
         o = cls(md.nx, md.ny, md.nz, inputs.mesh_nodes(md), params_from(pd, md.reflect))
         rho0, p0, dep_cell, dep_e = inputs.problem_prim(md, pd)
-        o.check(lib().oracle_init_prim(o._s, _ptr(rho0), _ptr(p0), dep_cell, dep_e))
+        if getattr(pd, "nmat", 0) >= 2:
+            mat = np.ascontiguousarray(inputs.problem_materials(md, pd), dtype=np.int32)
+            o.check(lib().oracle_init_materials(o._s, _ptr(rho0), _ptr(p0), mat.ctypes.data_as(C.POINTER(C.c_int)),
+                                                dep_cell, dep_e))
+        else:
+            o.check(lib().oracle_init_prim(o._s, _ptr(rho0), _ptr(p0), dep_cell, dep_e))
         return o
 
     def __del__(self):
@@ -207,9 +221,26 @@ class Oracle:
         return rc
 
     def field(self, name) -> np.ndarray:
+        """A node or cell field; material fields are alpha<k> (volume
+        fraction), m<k> (mass) and e<k> (specific internal energy) of
+        material k."""
+        mat = re.fullmatch(r"(alpha|m|e)(\d)", name)
+        if mat:
+            k, nc = int(mat.group(2)), self.s.nc
+            if not 0 <= k < max(self.s.prm.nmat, 0) or self.s.prm.nmat < 2:
+                raise KeyError(name)
+            ptr = getattr(self.s, {"alpha": "alpha", "m": "mm", "e": "me"}[mat.group(1)])
+            return np.ctypeslib.as_array(ptr, shape=(self.s.prm.nmat * nc,))[k * nc:(k + 1) * nc].copy()
         n = self.s.nn if name in self.NODE_FIELDS else self.s.nc
         ptr = getattr(self.s, name)
         return np.ctypeslib.as_array(ptr, shape=(n,)).copy()
+
+    def set_materials(self, alpha, m, e):
+        """Per-material fields, one array per material each (see
+        oracle_set_materials); returns the status."""
+        arrs = [np.ascontiguousarray(np.concatenate([np.asarray(a, dtype=np.float64) for a in f]))
+                for f in (alpha, m, e)]
+        return lib().oracle_set_materials(self._s, *[_ptr(a) for a in arrs])
 
     def set_state(self, x, y, z, u, v, w, mn, m, e, t=0.0, dt_last=math.inf):
         arrs = [np.ascontiguousarray(a, dtype=np.float64) for a in (x, y, z, u, v, w, mn, m, e)]

@@ -224,6 +224,14 @@ oracle_state *oracle_create(int nx, int ny, int nz, const double *xn,
     *cell_arrays[i] = alloc_zero(s->nc);
     if (!*cell_arrays[i]) { oracle_destroy(s); return NULL; }
   }
+  if (prm->nmat > ORACLE_MAX_MAT) { oracle_destroy(s); return NULL; }
+  if (prm->nmat >= 2) {
+    double **mat_arrays[] = {&s->alpha, &s->mm, &s->me};
+    for (size_t i = 0; i < 3; ++i) {
+      *mat_arrays[i] = alloc_zero(prm->nmat * s->nc);
+      if (!*mat_arrays[i]) { oracle_destroy(s); return NULL; }
+    }
+  }
   memcpy(s->x, xn, sizeof(double) * s->nn);
   memcpy(s->y, yn, sizeof(double) * s->nn);
   memcpy(s->z, zn, sizeof(double) * s->nn);
@@ -237,7 +245,7 @@ void oracle_destroy(oracle_state *s) {
   if (!s) return;
   double *arrays[] = {s->x, s->y, s->z, s->xr, s->yr, s->zr, s->u, s->v, s->w,
                       s->mn, s->m, s->e, s->vol, s->rho, s->p, s->q, s->cs, s->len,
-                      s->sxx, s->syy, s->szz, s->sxy, s->syz, s->szx, s->eps_p};
+                      s->sxx, s->syy, s->szz, s->sxy, s->syz, s->szx, s->eps_p, s->alpha, s->mm, s->me};
   for (size_t i = 0; i < sizeof(arrays) / sizeof(arrays[0]); ++i) free(arrays[i]);
   free(s);
 }
@@ -329,18 +337,76 @@ static void stress_apply(const oracle_state *s, long long c, const double *g, do
   out[2] = s->szx[c] * g[0] + s->syz[c] * g[1] + s->szz[c] * g[2];
 }
 
-/* EoS (R2), sound speed and artificial viscosity (R3) of one cell with
- * node positions X and velocities U (24 values each), mass m and specific
- * internal energy e.  Returns a status. */
-static int cell_state(const oracle_state *s, const double *X, const double *U, double m, double e, double *V_out,
-                      double *rho_out, double *p_out, double *q_out, double *cs_out, double *L_out) {
+/* ------------------------------------------------------------------ */
+/* Materials (R18)                                                     */
+/* ------------------------------------------------------------------ */
+
+static int mm_on(const oracle_state *s) { return s->prm.nmat >= 2; }
+
+/* Stiffened-gas EoS of material k: p = (g - 1) rho e - g p_inf; its sound
+ * speed c^2 = g (p + p_inf) / rho = g (g - 1) (e - p_inf / rho), floored
+ * at 0 like the single gas's.  p_inf = 0 is the ideal gas. */
+static double mat_pressure(const oracle_state *s, int k, double rho, double e) {
+  const double g = s->prm.mat_gamma[k];
+  return (g - 1.0) * rho * e - g * s->prm.mat_pinf[k];
+}
+
+static double mat_cs2(const oracle_state *s, int k, double rho, double e) {
+  const double g = s->prm.mat_gamma[k];
+  const double c2 = g * (g - 1.0) * (e - s->prm.mat_pinf[k] / rho);
+  return c2 > 0.0 ? c2 : 0.0;
+}
+
+/* Mixed cell c of volume V and mass m: the materials present (alpha_k > 0)
+ * have density rho_k = m_k / (alpha_k V); the cell pressure is
+ * sum_k alpha_k p_k and the squared sound speed the mass-weighted
+ * sum_k m_k c_k^2 / m. */
+static void mixture_eos(const oracle_state *s, long long c, double V, double m, double *p, double *cs2) {
+  double ps = 0.0, cm = 0.0;
+  for (int k = 0; k < s->prm.nmat; ++k) {
+    const long long kc = k * s->nc + c;
+    const double a = s->alpha[kc];
+    if (!(a > 0.0)) continue;
+    const double rk = s->mm[kc] / (a * V);
+    ps += a * mat_pressure(s, k, rk, s->me[kc]);
+    cm += s->mm[kc] * mat_cs2(s, k, rk, s->me[kc]);
+  }
+  *p = ps;
+  *cs2 = cm / m;
+}
+
+/* Cell totals from the materials: m = sum_k m_k, e = sum_k m_k e_k / m. */
+static void mm_totals(oracle_state *s, long long c) {
+  double m = 0.0, ie = 0.0;
+  for (int k = 0; k < s->prm.nmat; ++k) {
+    m += s->mm[k * s->nc + c];
+    ie += s->mm[k * s->nc + c] * s->me[k * s->nc + c];
+  }
+  s->m[c] = m;
+  s->e[c] = ie / m;
+}
+
+/* EoS (R2), sound speed and artificial viscosity (R3) of cell c with node
+ * positions X and velocities U (24 values each), mass m and specific
+ * internal energy e (with materials, the EoS is the mixture's, R18).
+ * Returns a status. */
+static int cell_state(const oracle_state *s, long long c, const double *X, const double *U, double m, double e,
+                      double *V_out, double *rho_out, double *p_out, double *q_out, double *cs_out,
+                      double *L_out) {
   const double g = s->prm.gamma;
   double G[24];
   double V = oracle_hex_volume(X);
   if (!(V > 0.0)) return isnan(V) ? ORACLE_ENAN : ORACLE_ENEGVOL;
   double rho = m / V;
-  double p = (g - 1.0) * rho * e;
-  double cs = sqrt(g * (g - 1.0) * (e > 0.0 ? e : 0.0));
+  double p, cs;
+  if (mm_on(s)) {
+    double cs2;
+    mixture_eos(s, c, V, m, &p, &cs2);
+    cs = sqrt(cs2);
+  } else {
+    p = (g - 1.0) * rho * e;
+    cs = sqrt(g * (g - 1.0) * (e > 0.0 ? e : 0.0));
+  }
   oracle_hex_volume_grad(X, G);
   double dvdt = 0.0;
   for (int a = 0; a < 8; ++a) dvdt += dot3(&G[a * 3], &U[a * 3]);
@@ -371,8 +437,8 @@ int oracle_eos(oracle_state *s) {
         double X[24], U[24];
         gather_hex(s, i, j, k, s->x, s->y, s->z, X);
         gather_hex(s, i, j, k, s->u, s->v, s->w, U);
-        int rc = cell_state(s, X, U, s->m[c], s->e[c], &s->vol[c], &s->rho[c], &s->p[c], &s->q[c], &s->cs[c],
-                            &s->len[c]);
+        int rc = cell_state(s, c, X, U, s->m[c], s->e[c], &s->vol[c], &s->rho[c], &s->p[c], &s->q[c],
+                            &s->cs[c], &s->len[c]);
         if (rc) return s->status = rc;
       }
   return ORACLE_OK;
@@ -407,21 +473,9 @@ static int propose_dt(oracle_state *s) {
   return ORACLE_OK;
 }
 
-int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
-                     long long deposit_cell, double deposit_energy) {
-  const double g = s->prm.gamma;
-  for (int k = 0; k < s->nz; ++k)
-    for (int j = 0; j < s->ny; ++j)
-      for (int i = 0; i < s->nx; ++i) {
-        long long c = cell_id(s, i, j, k);
-        double X[24];
-        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
-        double V = oracle_hex_volume(X);
-        s->m[c] = rho0[c] * V;
-        s->e[c] = p0[c] / ((g - 1.0) * rho0[c]);
-      }
-  if (deposit_cell >= 0 && deposit_cell < s->nc)
-    s->e[deposit_cell] = deposit_energy / s->m[deposit_cell];
+/* The rest of an initial state once m and e are set: u = 0, node masses,
+ * derived fields and the first dt (capped by dt_init). */
+static int init_finish(oracle_state *s) {
   for (long long n = 0; n < s->nn; ++n) s->u[n] = s->v[n] = s->w[n] = 0.0;
   node_masses_from_cells(s);
   s->t = 0.0;
@@ -435,6 +489,90 @@ int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
   s->dt = dt;
   s->dt_last = dt;
   return ORACLE_OK;
+}
+
+int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
+                     long long deposit_cell, double deposit_energy) {
+  if (mm_on(s)) return s->status = ORACLE_EINVAL;  /* materials: oracle_init_materials */
+  const double g = s->prm.gamma;
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double X[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        double V = oracle_hex_volume(X);
+        s->m[c] = rho0[c] * V;
+        s->e[c] = p0[c] / ((g - 1.0) * rho0[c]);
+      }
+  if (deposit_cell >= 0 && deposit_cell < s->nc)
+    s->e[deposit_cell] = deposit_energy / s->m[deposit_cell];
+  return init_finish(s);
+}
+
+/* The materials of the multi-material scheme (R18) take neither strength
+ * nor the second-order options. */
+static int mm_options_ok(const oracle_state *s) {
+  const oracle_params *p = &s->prm;
+  if (p->nmat < 2 || p->nmat > ORACLE_MAX_MAT) return 0;
+  if (strength_on(s) || p->time_order == 2 || p->c_hg > 0.0 || p->remap_order == 2) return 0;
+  for (int k = 0; k < p->nmat; ++k)
+    if (!(p->mat_gamma[k] > 1.0) || !(p->mat_pinf[k] >= 0.0) || isinf(p->mat_gamma[k]) || isinf(p->mat_pinf[k]))
+      return 0;
+  return 1;
+}
+
+int oracle_init_materials(oracle_state *s, const double *rho0, const double *p0, const int *mat,
+                          long long deposit_cell, double deposit_energy) {
+  if (!mm_options_ok(s)) return s->status = ORACLE_EINVAL;
+  const long long nc = s->nc;
+  for (long long c = 0; c < nc; ++c)
+    if (mat[c] < 0 || mat[c] >= s->prm.nmat) return s->status = ORACLE_EINVAL;
+  for (int k = 0; k < s->nz; ++k)
+    for (int j = 0; j < s->ny; ++j)
+      for (int i = 0; i < s->nx; ++i) {
+        long long c = cell_id(s, i, j, k);
+        double X[24];
+        gather_hex(s, i, j, k, s->x, s->y, s->z, X);
+        const int mk = mat[c];
+        const double g = s->prm.mat_gamma[mk];
+        double m = rho0[c] * oracle_hex_volume(X);
+        /* the EoS solved for e at (rho0, p0) */
+        double e = (p0[c] + g * s->prm.mat_pinf[mk]) / ((g - 1.0) * rho0[c]);
+        if (c == deposit_cell) e = deposit_energy / m;
+        for (int q = 0; q < s->prm.nmat; ++q) {
+          s->alpha[q * nc + c] = q == mk ? 1.0 : 0.0;
+          s->mm[q * nc + c] = q == mk ? m : 0.0;
+          s->me[q * nc + c] = q == mk ? e : 0.0;
+        }
+        s->m[c] = m;
+        s->e[c] = e;
+      }
+  return init_finish(s);
+}
+
+int oracle_set_materials(oracle_state *s, const double *alpha, const double *mm, const double *me) {
+  if (!mm_options_ok(s)) return s->status = ORACLE_EINVAL;
+  const long long nc = s->nc;
+  for (long long c = 0; c < nc; ++c) {
+    double asum = 0.0;
+    for (int k = 0; k < s->prm.nmat; ++k) {
+      const long long kc = k * nc + c;
+      if (!(alpha[kc] >= 0.0) || !(mm[kc] >= 0.0) || (alpha[kc] > 0.0) != (mm[kc] > 0.0) || isnan(me[kc]))
+        return s->status = ORACLE_EINVAL;
+      asum += alpha[kc];
+    }
+    if (!(fabs(asum - 1.0) <= 1e-12)) return s->status = ORACLE_EINVAL;
+  }
+  const size_t b = sizeof(double) * (size_t)(s->prm.nmat * nc);
+  memcpy(s->alpha, alpha, b);
+  memcpy(s->mm, mm, b);
+  memcpy(s->me, me, b);
+  for (long long c = 0; c < nc; ++c) mm_totals(s, c);
+  s->status = ORACLE_OK;
+  int rc = oracle_eos(s);
+  if (rc) return rc;
+  return propose_dt(s);
 }
 
 int oracle_set_state(oracle_state *s, const double *x, const double *y,
@@ -517,6 +655,8 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
   const int pc = s->prm.time_order == 2;
   const int str = strength_on(s);
   if (str && pc) return s->status = ORACLE_EINVAL;  /* strength takes the single-stage step */
+  const int mm = mm_on(s);
+  if (mm && !mm_options_ok(s)) return s->status = ORACLE_EINVAL;
   double *fx = alloc_zero(nn), *fy = alloc_zero(nn), *fz = alloc_zero(nn);
   double *ubx = alloc_zero(nn), *uby = alloc_zero(nn), *ubz = alloc_zero(nn);
   double *e_new = alloc_zero(nc), *sig = alloc_zero(nc);
@@ -568,7 +708,7 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
           if (hg) e_half -= 0.5 * dt / s->m[c] * work_hg;
           gather_hex(s, i, j, k, xh, yh, zh, XH);
           double V, rho, p, q, cs, L;
-          int rc = cell_state(s, XH, U, s->m[c], e_half, &V, &rho, &p, &q, &cs, &L);
+          int rc = cell_state(s, c, XH, U, s->m[c], e_half, &V, &rho, &p, &q, &cs, &L);
           if (rc) {
             free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
             free(xh); free(yh); free(zh); free(fh);
@@ -640,6 +780,24 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
           for (int a = 0; a < 8; ++a) work_hg += dot3(&fh[24 * c + a * 3], &UB[a * 3]);
         e_new[c] = s->e[c] - dt / s->m[c] * sigma * work;
         if (hg) e_new[c] -= dt / s->m[c] * work_hg;
+        if (mm) {
+          /* uniform strain (R18): each material takes the cell's volume
+           * change in proportion to its fraction, so material k does the
+           * share alpha_k (p_k + q) of the cell's sigma work; the sum over
+           * k is the cell's work since sum_k alpha_k p_k = p */
+          const double V0 = s->vol[c];
+          double ie = 0.0;
+          for (int kk = 0; kk < s->prm.nmat; ++kk) {
+            const long long kc = kk * nc + c;
+            const double a = s->alpha[kc];
+            if (!(a > 0.0)) continue;
+            const double mk = s->mm[kc];
+            const double pk = mat_pressure(s, kk, mk / (a * V0), s->me[kc]);
+            s->me[kc] -= dt / mk * (a * (pk + s->q[c])) * work;
+            ie += mk * s->me[kc];
+          }
+          e_new[c] = ie / s->m[c];
+        }
         if (str) {
           /* the deviatoric forces' work, then the stress at n+1 from the
            * time-centred velocity gradient and G, Y of the state at n */
@@ -795,6 +953,89 @@ static void advect_strength(const oracle_state *s, double *ms, long long lo, lon
   }
 }
 
+/* Materials (R18): the face's swept volume dv leaves its donor (dv > 0:
+ * the high cell) as each material's share of the donor: volume
+ * alpha_k dv, mass (m_k / V_L) dv -- the material's partial density in
+ * the Lagrangian donor -- and energy that mass times e_k.  mv, mk, me hold
+ * each material's volume, mass and energy at [k * nc + c].  *mu and *ef
+ * get the face's total mass and energy fluxes. */
+static void mm_face(const oracle_state *s, const double *vol_l, long long lo, long long hi, double dv,
+                    double *mv, double *mk, double *me, double *mu, double *ef) {
+  const long long nc = s->nc, dn = dv > 0.0 ? hi : lo;
+  double mu_t = 0.0, ef_t = 0.0;
+  for (int k = 0; k < s->prm.nmat; ++k) {
+    const long long d = k * nc + dn;
+    const double vf = s->alpha[d] * dv;
+    const double mf = s->mm[d] / vol_l[dn] * dv;
+    const double eflux = mf * s->me[d];
+    mv[k * nc + lo] += vf;
+    mv[k * nc + hi] -= vf;
+    mk[k * nc + lo] += mf;
+    mk[k * nc + hi] -= mf;
+    me[k * nc + lo] += eflux;
+    me[k * nc + hi] -= eflux;
+    mu_t += mf;
+    ef_t += eflux;
+  }
+  *mu = mu_t;
+  *ef = ef_t;
+}
+
+/* New material state of cell c after the fluxes (R18).  fix is the
+ * kinetic energy the node remap returns to the cell, shared among the
+ * materials by mass.  Donor-cell upwinding leaves geometric tails of a
+ * material ahead of its front, and a fragment's specific energy is the
+ * ratio of two roundoff-sized numbers: a material whose new volume is
+ * at most ORACLE_ALPHA_MIN of the cell's, or whose mass or volume is not
+ * positive, leaves the cell, its mass and energy going to the remaining
+ * materials in proportion to their masses (the cell's mass and energy
+ * stay as the fluxes left them).  The fractions are the remaining volumes
+ * over their sum. */
+static void mm_cell_update(oracle_state *s, long long c, const double *mv, const double *mk, const double *me,
+                           double fix) {
+  const long long nc = s->nc;
+  const int nm = s->prm.nmat;
+  double m1 = 0.0, vtot = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    m1 += mk[k * nc + c];
+    vtot += mv[k * nc + c];
+  }
+  int keep[ORACLE_MAX_MAT];
+  double mkeep = 0.0, mdrop = 0.0, iedrop = 0.0, vkeep = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    const long long kc = k * nc + c;
+    keep[k] = mk[kc] > 0.0 && mv[kc] > ORACLE_ALPHA_MIN * vtot;
+    const double ie = me[kc] + mk[kc] / m1 * fix;
+    if (keep[k]) {
+      mkeep += mk[kc];
+      vkeep += mv[kc];
+    } else {
+      mdrop += mk[kc];
+      iedrop += ie;
+    }
+  }
+  double msum = 0.0, iesum = 0.0;
+  for (int k = 0; k < nm; ++k) {
+    const long long kc = k * nc + c;
+    if (keep[k]) {
+      const double w = mk[kc] / mkeep;
+      const double mnew = mk[kc] + w * mdrop;
+      const double ie = me[kc] + mk[kc] / m1 * fix + w * iedrop;
+      s->alpha[kc] = mv[kc] / vkeep;
+      s->mm[kc] = mnew;
+      s->me[kc] = ie / mnew;
+      msum += mnew;
+      iesum += ie;
+    } else {
+      s->alpha[kc] = 0.0;
+      s->mm[kc] = 0.0;
+      s->me[kc] = 0.0;
+    }
+  }
+  s->m[c] = msum;
+  s->e[c] = iesum / msum;
+}
+
 int oracle_remap_step(oracle_state *s) {
   if (s->status) return s->status;
   const int nx = s->nx, ny = s->ny, nz = s->nz;
@@ -809,8 +1050,16 @@ int oracle_remap_step(oracle_state *s) {
   double *pz = alloc_zero(nn), *ke = alloc_zero(nn), *dke = alloc_zero(nn);
   const int str = strength_on(s);
   double *ms_new = alloc_zero(str ? 7 * nc : 1);
+  const int mm = mm_on(s);
+  if (mm && !mm_options_ok(s)) {
+    free(dvx); free(dvy); free(dvz); free(mux); free(muy); free(muz); free(rho_l); free(m_new); free(ie_new);
+    free(vol_l); free(mn_new); free(px); free(py); free(pz); free(ke); free(dke); free(ms_new);
+    return s->status = ORACLE_EINVAL;
+  }
+  const long long nmc = mm ? s->prm.nmat * nc : 1;
+  double *mv = alloc_zero(nmc), *mk = alloc_zero(nmc), *me = alloc_zero(nmc);
   double *all[] = {dvx, dvy, dvz, mux, muy, muz, rho_l, m_new, ie_new,
-                   mn_new, px, py, pz, ke, dke, vol_l, ms_new};
+                   mn_new, px, py, pz, ke, dke, vol_l, ms_new, mv, mk, me};
   const size_t nall = sizeof(all) / sizeof(all[0]);
   for (size_t i = 0; i < nall; ++i)
     if (!all[i]) {
@@ -834,6 +1083,13 @@ int oracle_remap_step(oracle_state *s) {
 
   /* 2. Donor-cell mass and energy fluxes.  dV > 0: the swept region lies
    *    in the high-index cell, which donates to the low-index one. */
+  if (mm)
+    for (int k = 0; k < s->prm.nmat; ++k)
+      for (long long c = 0; c < nc; ++c) {
+        mv[k * nc + c] = s->alpha[k * nc + c] * vol_l[c];
+        mk[k * nc + c] = s->mm[k * nc + c];
+        me[k * nc + c] = s->mm[k * nc + c] * s->me[k * nc + c];
+      }
   for (long long c = 0; c < nc; ++c) {
     m_new[c] = s->m[c];
     ie_new[c] = s->m[c] * s->e[c];
@@ -848,7 +1104,8 @@ int oracle_remap_step(oracle_state *s) {
         long long f = i + (long long)(nx + 1) * (j + (long long)ny * k);
         long long lo = cell_id(s, i - 1, j, k), hi = cell_id(s, i, j, k);
         double mu, ef;
-        face_fluxes(s, rho_l, vol_l, i - 1, j, k, 0, dvx[f], &mu, &ef);
+        if (mm) mm_face(s, vol_l, lo, hi, dvx[f], mv, mk, me, &mu, &ef);
+        else face_fluxes(s, rho_l, vol_l, i - 1, j, k, 0, dvx[f], &mu, &ef);
         if (str) advect_strength(s, ms_new, lo, hi, mu, dvx[f]);
         mux[f] = mu;
         m_new[lo] += mu;
@@ -862,7 +1119,8 @@ int oracle_remap_step(oracle_state *s) {
         long long f = i + (long long)nx * (j + (long long)(ny + 1) * k);
         long long lo = cell_id(s, i, j - 1, k), hi = cell_id(s, i, j, k);
         double mu, ef;
-        face_fluxes(s, rho_l, vol_l, i, j - 1, k, 1, dvy[f], &mu, &ef);
+        if (mm) mm_face(s, vol_l, lo, hi, dvy[f], mv, mk, me, &mu, &ef);
+        else face_fluxes(s, rho_l, vol_l, i, j - 1, k, 1, dvy[f], &mu, &ef);
         if (str) advect_strength(s, ms_new, lo, hi, mu, dvy[f]);
         muy[f] = mu;
         m_new[lo] += mu;
@@ -876,7 +1134,8 @@ int oracle_remap_step(oracle_state *s) {
         long long f = i + (long long)nx * (j + (long long)ny * k);
         long long lo = cell_id(s, i, j, k - 1), hi = cell_id(s, i, j, k);
         double mu, ef;
-        face_fluxes(s, rho_l, vol_l, i, j, k - 1, 2, dvz[f], &mu, &ef);
+        if (mm) mm_face(s, vol_l, lo, hi, dvz[f], mv, mk, me, &mu, &ef);
+        else face_fluxes(s, rho_l, vol_l, i, j, k - 1, 2, dvz[f], &mu, &ef);
         if (str) advect_strength(s, ms_new, lo, hi, mu, dvz[f]);
         muz[f] = mu;
         m_new[lo] += mu;
@@ -960,8 +1219,9 @@ int oracle_remap_step(oracle_state *s) {
       }
 
   /* 5. Kinetic-energy fix: each node's lost KE goes in equal shares to
-   *    the internal energy of the cells around it. */
-  if (s->prm.ke_fix)
+   *    the internal energy of the cells around it (with materials, shared
+   *    among the cell's materials in step 6). */
+  if (s->prm.ke_fix && !mm)
     for (int k = 0; k < nz; ++k)
       for (int j = 0; j < ny; ++j)
         for (int i = 0; i < nx; ++i) {
@@ -973,7 +1233,20 @@ int oracle_remap_step(oracle_state *s) {
         }
 
   /* 6. New cell state on the reference mesh. */
-  for (long long c = 0; c < nc; ++c) {
+  if (mm)
+    for (int k = 0; k < nz; ++k)
+      for (int j = 0; j < ny; ++j)
+        for (int i = 0; i < nx; ++i) {
+          long long c = cell_id(s, i, j, k);
+          double fix = 0.0;
+          if (s->prm.ke_fix)
+            for (int a = 0; a < 8; ++a) {
+              int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
+              fix += dke[node_id(s, ni, nj, nk)] / node_cell_count(s, ni, nj, nk);
+            }
+          mm_cell_update(s, c, mv, mk, me, fix);
+        }
+  for (long long c = 0; c < nc && !mm; ++c) {
     s->m[c] = m_new[c];
     s->e[c] = ie_new[c] / m_new[c];
     if (str) {

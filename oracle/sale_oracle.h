@@ -28,7 +28,16 @@
  *     case study (Sec. III-D): deviatoric stress with the Jaumann rate and
  *     von Mises radial return (Wilkins 1963, "Calculation of elastic-plastic
  *     flow"), shear modulus and yield from the Steinberg-Guinan model
- *     (Steinberg, Cochran, Guinan, J. Appl. Phys. 51, 1980).
+ *     (Steinberg, Cochran, Guinan, J. Appl. Phys. 51, 1980);
+ *   - optionally, several materials with their own equations of state (the
+ *     multi-material SALE scheme of Sec. I-D and Table I): per-material
+ *     volume fraction, mass and energy in every cell; stiffened-gas EoS
+ *     (ideal gas when p_inf = 0); mixed cells closed by uniform strain (the
+ *     materials of a cell share its volume change, so the fractions do not
+ *     change in the Lagrangian phase: Benson, "Computational methods in
+ *     Lagrangian and Eulerian hydrocodes", CMAME 99, 1992, Sec. 6), cell
+ *     pressure sum_k alpha_k p_k; donor-cell remap of each material's
+ *     volume, mass and energy.
  *
  * Layout: SoA, x index fastest.  Cell c = i + nx*(j + ny*k); node
  * n = i + (nx+1)*(j + (ny+1)*k).  Local node a = di + 2*dj + 4*dk of cell
@@ -74,7 +83,18 @@ typedef struct oracle_params {
   double yield_max;  /* Ymax                                              */
   double hard_beta;  /* work-hardening coefficient beta                   */
   double hard_n;     /* work-hardening exponent n                         */
+  /* Materials: nmat <= 1 is the single ideal gas of `gamma` above; with
+   * 2 <= nmat <= ORACLE_MAX_MAT every cell holds per-material fractions
+   * and material k has the stiffened-gas EoS (mat_gamma[k], mat_pinf[k]). */
+  int nmat;
+  double mat_gamma[4];
+  double mat_pinf[4];
 } oracle_params;
+
+#define ORACLE_MAX_MAT 4
+/* a material whose volume fraction falls to this or below in a remap
+ * leaves the cell (its mass and energy go to the cell's other materials) */
+#define ORACLE_ALPHA_MIN 1e-8
 
 typedef struct oracle_state {
   int nx, ny, nz;
@@ -91,6 +111,10 @@ typedef struct oracle_state {
   double t, dt, dt_last;   /* time, proposed next dt, last dt used         */
   long long cycle;
   int status;
+  /* materials (nmat >= 2): volume fraction, mass and specific internal
+   * energy of material k in cell c at [k * nc + c]; m and e above are the
+   * cell totals sum_k m_k and sum_k m_k e_k / m */
+  double *alpha, *mm, *me;
 } oracle_state;
 
 /* ---- single-hex geometry; X[a*3+d] = coordinate d of local node a ---- */
@@ -129,6 +153,19 @@ int oracle_set_state(oracle_state *s, const double *x, const double *y,
                      const double *z, const double *u, const double *v,
                      const double *w, const double *mn, const double *m,
                      const double *e, double t, double dt_last);
+/* Multi-material initial state (nmat >= 2): cell c is pure material
+ * mat[c] with primitive rho0, p0, its specific energy from that
+ * material's EoS; the deposit as in oracle_init_prim.  EINVAL for a
+ * material index out of range, an invalid EoS, or an option the
+ * multi-material scheme does not take (strength, predictor-corrector,
+ * hourglass control, second-order remap). */
+int oracle_init_materials(oracle_state *s, const double *rho0, const double *p0, const int *mat,
+                          long long deposit_cell, double deposit_energy);
+/* Overwrite the per-material fields ([k * nc + c] layout), recompute the
+ * cell totals m and e, the derived fields and the proposed dt.  Each cell
+ * needs alpha_k >= 0 summing to 1 (to 1e-12), m_k >= 0, and alpha_k > 0
+ * exactly where m_k > 0; EINVAL otherwise. */
+int oracle_set_materials(oracle_state *s, const double *alpha, const double *mm, const double *me);
 int oracle_eos(oracle_state *s);            /* vol, rho, p, cs, q, len     */
 double oracle_cfl_dt(const oracle_state *s); /* min over cells (uses eos)  */
 

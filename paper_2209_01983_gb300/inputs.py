@@ -106,6 +106,11 @@ class ProblemDesc:
     yield_max: float = 0.0  # Ymax
     hard_beta: float = 0.0  # work-hardening coefficient
     hard_n: float = 0.0     # work-hardening exponent
+    # materials (nmat <= 1: the single ideal gas of `gamma`); with nmat >= 2
+    # material k has the stiffened-gas EoS (mat_gamma[k], mat_pinf[k])
+    nmat: int = 0
+    mat_gamma: tuple = (1.4, 1.4, 1.4, 1.4)
+    mat_pinf: tuple = (0.0, 0.0, 0.0, 0.0)
 
 
 def mesh_nodes(md: MeshDesc):
@@ -166,6 +171,19 @@ def problem_prim(md: MeshDesc, pd: ProblemDesc):
     if pd.kind == PROB_UNIFORM:
         return rho0, p0, -1, 0.0
     raise ValueError(f"unknown problem kind {pd.kind}")
+
+
+def problem_materials(md: MeshDesc, pd: ProblemDesc) -> np.ndarray:
+    """Material of every cell (int32) for nmat >= 2: material 1 where the
+    logical cell centre lo_x + (i + 0.5) * h_x >= x_split (the right state
+    of SOD_X), material 0 elsewhere.  All zeros for nmat <= 1."""
+    if pd.nmat < 2:
+        return np.zeros(md.ncell, dtype=np.int32)
+    hx = (md.hi[0] - md.lo[0]) / md.nx
+    i = np.arange(md.nx, dtype=np.float64)
+    right_i = ~((md.lo[0] + (i + 0.5) * hx) < pd.x_split)
+    right = np.broadcast_to(right_i[None, None, :], (md.nz, md.ny, md.nx)).reshape(-1)
+    return right.astype(np.int32)
 
 
 # ---------------------------------------------------------------------------
