@@ -117,9 +117,32 @@ typedef struct {
  * 4 G / (3 rho), and the remap carries S and the plastic strain eps_p per
  * unit mass with the donor cell's mass flux.  The fields "sxx", "syy",
  * "szz", "sxy", "syz", "szx" and "eps_p" then exist.
+ * Materials, the multi-material scheme of ScalSALE (Sec. I-D, Table I:
+ * "multi-material, multiple EoS"; nmat = 0 or 1: one ideal gas of
+ * `gamma`).  With 2 <= nmat <= SALE_MAX_MAT (FP64 states; single-stage
+ * step, first-order remap, no hourglass control or strength) material k has
+ * the stiffened-gas EoS p = (mat_gamma[k] - 1) rho e - mat_gamma[k]
+ * mat_pinf[k] (mat_pinf[k] = 0: ideal gas; `gamma` is unused) and every
+ * cell holds each material's volume fraction alpha_k, mass m_k and
+ * specific energy e_k.  Initially a cell is pure: material 1 where its
+ * logical centre lo_x + (i + 0.5) h_x >= x_split (the right state of
+ * SOD_X), material 0 elsewhere, its e_k from its own EoS at the cell's
+ * (rho, p).  Mixed cells are closed by uniform strain: the materials share
+ * the cell's volume change in proportion to their fractions, so the
+ * fractions do not change in the Lagrangian step, and material k takes the
+ * share alpha_k (p_k + q) of the cell's compatible work; the cell pressure
+ * is sum_k alpha_k p_k(m_k / (alpha_k V), e_k), its sound speed squared
+ * sum_k m_k c_k^2 / m with c_k^2 = gamma_k (gamma_k - 1) (e_k - p_inf_k /
+ * rho_k) floored at 0.  The remap moves each material's volume
+ * (alpha_k dV), mass ((m_k / V_L) dV) and energy (mass times e_k) out of
+ * the donor of every face, shares the cell's kinetic-energy fix by mass,
+ * and drops a material whose new fraction is at most SALE_MAT_ALPHA_MIN
+ * (its mass and energy go to the cell's other materials by mass).  Fields
+ * "alpha<k>", "m<k>", "e<k>" (k = 0 .. nmat-1) then exist; "m" and "e"
+ * are the cell totals sum_k m_k and sum_k m_k e_k / m.
  * Options other than the defaults may need more device memory: size the
  * buffer with sale_state_bytes_for().  Batches take only the default
- * time_order, c_hg and shear0. */
+ * time_order, c_hg, shear0 and nmat. */
 typedef struct {
   int kind;
   double gamma;
@@ -132,7 +155,12 @@ typedef struct {
   double c_hg;
   double shear0, shear_dp, shear_dt, cv, e_ref, rho_ref;
   double yield0, yield_max, hard_beta, hard_n;
+  int nmat;
+  double mat_gamma[4], mat_pinf[4];
 } sale_problem_desc;
+
+#define SALE_MAX_MAT 4
+#define SALE_MAT_ALPHA_MIN 1e-8
 
 /* Diagnostics (FP64 sums in a fixed reduction order). */
 typedef struct {
@@ -193,15 +221,20 @@ int sale_diagnostics(const sale_state *st, sale_diag *out);
 
 /* Synchronising copy of a field to host FP64.  Names: node fields "x",
  * "y", "z", "u", "v", "w", "mn", "xref", "yref", "zref" (n = nnodes); cell
- * fields "m", "e", "rho", "p", "q", "cs", "vol" (n = ncells).  FP32-mixed
- * fields are widened on the device (hi + lo for the float-float m, e, mn);
- * FP64 "cs" is formed from e as sqrt(gamma (gamma - 1) max(e, 0)), the
- * formula the kernels use. */
+ * fields "m", "e", "rho", "p", "q", "cs", "vol" (n = ncells), and with
+ * materials "alpha<k>", "m<k>", "e<k>".  FP32-mixed fields are widened on
+ * the device (hi + lo for the float-float m, e, mn); FP64 "cs" of a
+ * single-material state is formed from e as sqrt(gamma (gamma - 1)
+ * max(e, 0)), the formula the kernels use. */
 int sale_copy_field(const sale_state *st, const char *name, double *host_out,
                     size_t n);
 /* Overwrite an evolving field from host FP64 (same names as copy_field for
- * "x","y","z","u","v","w","mn","m","e"); call sale_refresh() after the last
- * one to recompute derived fields and dt.  FP32-mixed states split each
+ * "x","y","z","u","v","w","mn","m","e", and with materials "alpha<k>",
+ * "m<k>", "e<k>" in place of "m" and "e"); call sale_refresh() after the
+ * last one to recompute derived fields and dt (with materials, refresh
+ * first forms the cell totals m and e from the material fields; each cell
+ * must have fractions >= 0 summing to 1 and alpha_k > 0 exactly where
+ * m_k > 0, which is not checked).  FP32-mixed states split each
  * value on the device into hi = fl32(x) and, for m, e and mn, lo =
  * fl32(x - hi).  Asynchronous with respect to the host only when host_in is
  * pinned memory (which must then stay unchanged until the state's stream

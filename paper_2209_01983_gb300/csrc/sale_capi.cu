@@ -23,7 +23,7 @@ namespace sale {
 void launch_reset(DevScalars *, cudaStream_t);
 void launch_set_limits(DevScalars *, double, long long, cudaStream_t);
 template <typename R>
-void launch_init_cells(const Fields<R> &, DevScalars *, const double *, const double *, long long, double,
+void launch_init_cells(const Fields<R> &, DevScalars *, const double *, const double *, long long, double, int,
                        cudaStream_t);
 template <typename R>
 void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt_override, double *partial,
@@ -31,6 +31,7 @@ void launch_kernel(int kid, const Fields<R> &, DevScalars *, int mode, double dt
 void launch_geo_init_nodes(const Fields<double> &F, double *rE, cudaStream_t st);
 void launch_geo_init_hg(const Fields<double> &F, double *HG, cudaStream_t st);
 void launch_recip(const double *a, double *r, long long n, cudaStream_t st);
+void launch_mat_totals(const Fields<double> &F, cudaStream_t st);
 void launch_geo_init(const Fields<double> &F, DevScalars *S, double *G, double *VE, double *LE, double *TE,
                      double *iVE, double *iL2, cudaStream_t st);
 void launch_m_init_cells(const Fields<float> &F, DevScalars *S, const double *rho0, const double *p0,
@@ -227,6 +228,7 @@ struct sale_state {
   double *im, *imn;                      //   1 / m per cell, 1 / mn per node
   double *sdev, *sold;                   //   strength: stress, plastic strain, G, Y (9 per cell); remap copy (7)
   double *Gn;                            //   corner gradients at the current positions (24 per cell)
+  double *mat, *mfx;                     //   materials: fraction, mass, energy (3 per material per cell); face fluxes (9)
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -242,6 +244,7 @@ struct sale_state {
   bool pc = false;                       // predictor-corrector scratch carved
   bool hg = false;                       // hourglass scratch carved
   bool str = false;                      // material strength (FP64): deviatoric stress carved
+  int nmat = 0;                          // materials (FP64, >= 2), 0: one ideal gas
   float h32[3];
   int xpar, upar;
   bool x_is_ref;       // current positions are the reference mesh
@@ -293,6 +296,7 @@ static size_t carve(sale_state *st, char *base) {
   st->im = st->imn = nullptr;
   st->sdev = st->sold = nullptr;
   st->Gn = nullptr;
+  st->mat = st->mfx = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -324,6 +328,10 @@ static size_t carve(sale_state *st, char *base) {
     if (st->str) {
       st->sdev = (double *)cv.take(sizeof(double) * 9 * nc);
       st->sold = (double *)cv.take(sizeof(double) * 7 * nc);
+    }
+    if (st->nmat >= 2) {
+      st->mat = (double *)cv.take(sizeof(double) * 3 * (size_t)st->nmat * nc);
+      st->mfx = (double *)cv.take(sizeof(double) * 9 * (size_t)st->nmat * nc);
     }
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
@@ -441,11 +449,18 @@ static Fields<R> fields_t(const sale_state *st) {
   F.sez = (R *)st->slope[5];
   F.ivl = (R *)st->slope[6];
   for (int f = 0; f < 6; ++f) F.reflect[f] = st->reflect[f];
+  F.mat = (R *)st->mat;
+  F.mfx = (R *)st->mfx;
+  F.nmat = st->nmat;
+  for (int k = 0; k < kMaxMat; ++k) {
+    F.mgam[k] = st->prob.mat_gamma[k];
+    F.mpinf[k] = st->prob.mat_pinf[k];
+  }
   return F;
 }
 
 static size_t state_bytes(long long nc, long long nn, int precision, bool jit, bool o2 = false, bool pc = false,
-                          bool hg = false, bool str = false) {
+                          bool hg = false, bool str = false, int nmat = 0) {
   sale_state tmp;
   tmp.nc = nc;
   tmp.nn = nn;
@@ -455,6 +470,7 @@ static size_t state_bytes(long long nc, long long nn, int precision, bool jit, b
   tmp.pc = pc;
   tmp.hg = hg;
   tmp.str = str && precision == SALE_FP64;
+  tmp.nmat = nmat >= 2 && precision == SALE_FP64 ? nmat : 0;
   tmp.elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   return carve(&tmp, nullptr);
 }
@@ -473,7 +489,7 @@ extern "C" size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem
   if (!mesh || !prob || (precision != SALE_FP64 && precision != SALE_FP32_MIXED) || !mixed_fits(mesh, precision))
     return 0;
   return state_bytes(mesh->nc, mesh->nn, precision, mesh->d.jitter > 0.0, prob->remap_order == 2,
-                     prob->time_order == 2, prob->c_hg > 0.0, prob->shear0 > 0.0);
+                     prob->time_order == 2, prob->c_hg > 0.0, prob->shear0 > 0.0, prob->nmat);
 }
 
 static int validate_problem(const sale_problem_desc &p) {
@@ -493,6 +509,17 @@ static int validate_problem(const sale_problem_desc &p) {
   if (p.time_order < 0 || p.time_order > 2) return fail(SALE_EINVAL, "problem: time_order must be 0, 1 or 2");
   if (!(p.c_hg >= 0.0) || !std::isfinite(p.c_hg)) return fail(SALE_EINVAL, "problem: c_hg must be finite and >= 0");
   if (!(p.shear0 >= 0.0) || !std::isfinite(p.shear0)) return fail(SALE_EINVAL, "problem: shear0 must be finite and >= 0");
+  if (p.nmat < 0 || p.nmat > SALE_MAX_MAT) return fail(SALE_EINVAL, "problem: nmat must be in [0, %d]", SALE_MAX_MAT);
+  if (p.nmat >= 2) {
+    for (int k = 0; k < p.nmat; ++k)
+      if (!(p.mat_gamma[k] > 1.0) || !std::isfinite(p.mat_gamma[k]) || !(p.mat_pinf[k] >= 0.0) ||
+          !std::isfinite(p.mat_pinf[k]))
+        return fail(SALE_EINVAL, "problem: material %d needs mat_gamma > 1 and a finite mat_pinf >= 0", k);
+    if (p.time_order == 2 || p.c_hg > 0.0 || p.shear0 > 0.0 || p.remap_order == 2)
+      return fail(SALE_EINVAL,
+                  "problem: materials take the single-stage step and the first-order remap, without hourglass "
+                  "control or strength");
+  }
   if (p.shear0 > 0.0) {
     const double fin[] = {p.shear_dp, p.shear_dt, p.e_ref, p.yield0, p.yield_max, p.hard_beta, p.hard_n};
     for (double v : fin)
@@ -656,6 +683,8 @@ extern "C" int sale_state_init(const sale_mesh *mesh, const sale_problem_desc *p
   if (rc) return rc;
   if (prob->shear0 > 0.0 && precision != SALE_FP64)
     return fail(SALE_EINVAL, "sale_state_init: material strength runs on FP64 states");
+  if (prob->nmat >= 2 && precision != SALE_FP64)
+    return fail(SALE_EINVAL, "sale_state_init: several materials run on FP64 states");
   if (!mixed_fits(mesh, precision))
     return fail(SALE_EINVAL, "sale_state_init: FP32-mixed states index nodes in 32 bits (at most 2^31 - 1 nodes)");
   rc = check_device_buffer("sale_state_init", device_buf, bytes, sale_state_bytes_for(mesh, prob, precision));
@@ -680,6 +709,7 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
   st->pc = prob->time_order == 2;
   st->hg = prob->c_hg > 0.0;
   st->str = precision == SALE_FP64 && prob->shear0 > 0.0;
+  st->nmat = precision == SALE_FP64 && prob->nmat >= 2 ? prob->nmat : 0;
   st->elem = precision == SALE_FP64 ? sizeof(double) : sizeof(float);
   st->stream = (cudaStream_t)cuda_stream;
   st->prob = *prob;
@@ -750,7 +780,11 @@ static int state_init_at(const sale_mesh *mesh, const sale_problem_desc *prob, i
     e = cudaMemsetAsync(st->sdev, 0, sizeof(double) * 9 * (size_t)st->nc, st->stream);
   if (!mixed) {
     const Fields<double> F = fields_t<double>(st);
-    launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, st->stream);
+    // materials: the first cell index whose logical centre is at or past x_split holds material 1
+    int mat_i0 = mesh->d.nx;
+    const double hx = (mesh->d.hi[0] - mesh->d.lo[0]) / mesh->d.nx;
+    for (int i = mesh->d.nx - 1; i >= 0 && !(mesh->d.lo[0] + ((double)i + 0.5) * hx < prob->x_split); --i) mat_i0 = i;
+    launch_init_cells(F, st->S, stage_rho, stage_p, dep_cell, dep_e, mat_i0, st->stream);
     launch_kernel(kInitNodes, F, st->S, 0, 0.0, nullptr, nullptr, st->stream);
     launch_kernel(kEos, F, st->S, kDtInit, 0.0, nullptr, nullptr, st->stream);
     launch_geo_init(F, st->S, st->geoG, st->geoVE, st->geoLE, st->geoTE, st->geoIVE, st->geoIL2, st->stream);
@@ -857,7 +891,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
 }
 
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
-  if (remap && st->x_is_ref) {
+  if (remap && st->x_is_ref && !st->nmat) {  // several materials run the general kernels
     launch_ale_cycle(st, dt_override);
     return;
   }
@@ -906,7 +940,7 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
     if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
     for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles of launch_cycle
       const bool remap = remap_every > 0 && (j + 1) % remap_every == 0;
-      if (remap && st->x_is_ref) {
+      if (remap && st->x_is_ref && !st->nmat) {
         st->upar ^= 1;
         continue;
       }
@@ -1032,8 +1066,18 @@ static void *field_ptr(const sale_state *st, const char *name, bool *node, bool 
   *node = false;
   *writable = true;
   *elem = st->elem;
+  if (st->nmat) {  // materials: fraction, mass, energy of each; the cell totals m, e are derived
+    const char *pre[3] = {"alpha", "m", "e"};
+    for (int q = 0; q < 3; ++q) {
+      const size_t l = strlen(pre[q]);
+      if (!strncmp(name, pre[q], l) && name[l] >= '0' && name[l] < '0' + st->nmat && name[l + 1] == 0)
+        return st->mat + (size_t)(3 * (name[l] - '0') + q) * (size_t)st->nc;
+    }
+    *writable = false;
+  }
   if (!strcmp(name, "m")) return st->m;
   if (!strcmp(name, "e")) return st->e;
+  *writable = true;
   if (st->sdev) {  // strength: deviatoric stress components and plastic strain
     static const char *const snames[7] = {"sxx", "syy", "szz", "sxy", "syz", "szx", "eps_p"};
     for (int q = 0; q < 7; ++q)
@@ -1074,7 +1118,7 @@ extern "C" int sale_copy_field(const sale_state *cst, const char *name, double *
   if (st->precision == SALE_FP32_MIXED && !node && !st->failed &&
       (!strcmp(name, "p") || !strcmp(name, "q") || !strcmp(name, "cs") || !strcmp(name, "vol")))
     dispatch(st, kMixEos, -1, 0.0);  // the mixed cycle stores only rho and p+q
-  const bool cs_from_e = st->precision == SALE_FP64 && !strcmp(name, "cs");
+  const bool cs_from_e = st->precision == SALE_FP64 && !st->nmat && !strcmp(name, "cs");
   if (cs_from_e) {
     // FP64: the sound speed is a function of e, sqrt(gamma (gamma - 1)
     // max(e, 0)), which the Eulerian kernels do not store; the same IEEE
@@ -1144,7 +1188,9 @@ extern "C" int sale_refresh(sale_state *st) {
   int rc = ready(st, "sale_refresh");
   if (rc) return rc;
   // on the reference mesh the FP64 refresh reads the cached geometry
-  launch_k(st, st->precision == SALE_FP64 ? (st->x_is_ref && !st->str ? kAleEos : kEos) : kMixEos, kDtPropose);
+  if (st->nmat) launch_mat_totals(fields_t<double>(st), st->stream);  // m, e from the uploaded materials
+  launch_k(st, st->precision == SALE_FP64 ? (st->x_is_ref && !st->str && !st->nmat ? kAleEos : kEos) : kMixEos,
+           kDtPropose);
   CUDA_TRY(cudaGetLastError());
   return SALE_OK;
 }
@@ -1340,9 +1386,10 @@ extern "C" int sale_batch_create(int n, const sale_mesh_desc *meshes, const sale
   for (int i = 0; i < n; ++i) {
     int rc = validate_problem(probs[i]);
     if (rc) return fail(rc, "sale_batch_create: mesh %d: %s", i, sale_last_error());
-    if (probs[i].time_order == 2 || probs[i].c_hg > 0.0 || probs[i].shear0 > 0.0)
+    if (probs[i].time_order == 2 || probs[i].c_hg > 0.0 || probs[i].shear0 > 0.0 || probs[i].nmat >= 2)
       return fail(SALE_EINVAL,
-                  "sale_batch_create: mesh %d: batches run the single-stage step without hourglass control or strength",
+                  "sale_batch_create: mesh %d: batches run the single-stage step of one material without hourglass "
+                  "control or strength",
                   i);
   }
   std::vector<size_t> soff((size_t)n);

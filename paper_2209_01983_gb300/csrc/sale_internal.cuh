@@ -181,7 +181,19 @@ struct Fields {
   R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
   R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
   int remap_sets_x;            // node remap writes the reference positions to x
+  // Materials (FP64 general path, nmat >= 2; null mat: one ideal gas):
+  // mat[(3 k + q) nc + c] holds material k's volume fraction (q = 0), mass
+  // (q = 1) and specific internal energy (q = 2) in cell c; m and e above
+  // are the cell totals.  mfx[(9 k + 3 axis + q) nc + c] holds the
+  // material's volume (q = 0), mass (1) and energy (2) flux through the
+  // cell's low face along axis, written by the face pass of a remap.
+  R *mat, *mfx;
+  int nmat;
+  double mgam[4], mpinf[4];    // stiffened-gas gamma and p_inf of every material
 };
+
+constexpr int kMaxMat = 4;
+constexpr double kAlphaMin = 1e-8;  // a material at or below this fraction after a remap leaves the cell
 
 // Hourglass patterns of the hex (local node a = di + 2 dj + 4 dk, signs
 // s = 2 d - 1): s_x s_y, s_y s_z, s_z s_x, s_x s_y s_z.

@@ -17,6 +17,11 @@
 //   k_eos_dt          EoS, sound speed, viscosity, p+q, CFL dt (warp-shuffle
 //                     min, one atomicMin per block on the bits of a positive
 //                     double, last block finalises time and dt)
+// With several materials (FP64, nmat >= 2) the EoS pass evaluates the
+// mixture, the cell pass splits the compatible work among the materials
+// (uniform strain) and the face and cell remap passes move each material's
+// volume, mass and energy (separate instantiations: the single-material
+// kernels are unchanged).
 #include <cfloat>
 #include <cmath>
 #include <type_traits>
@@ -31,9 +36,11 @@ namespace sale {
 // ---------------------------------------------------------------------------
 
 // m = rho0 V, e = p0 / ((gamma-1) rho0); the deposit cell gets e = E / m.
+// Materials: cell (i,j,k) is pure material 1 when i >= mat_i0, else 0, its e
+// from that material's stiffened-gas EoS at (rho0, p0).
 template <typename R>
 __global__ void k_init_cells(Fields<R> F, DevScalars *S, const double *rho0, const double *p0,
-                             long long dep_cell, double dep_e) {
+                             long long dep_cell, double dep_e, int mat_i0) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc) return;
   int i, j, k;
@@ -45,10 +52,40 @@ __global__ void k_init_cells(Fields<R> F, DevScalars *S, const double *rho0, con
   if (!(V > 0.0)) set_status(S, SALE_ENEGVOL);
   const double r0 = rho0[c];
   const double m = r0 * V;
-  double e = p0[c] / ((F.gamma - 1.0) * r0);
-  if (c == dep_cell) e = dep_e / m;
+  double e;
+  if (F.mat) {
+    const int km = i >= mat_i0 ? 1 : 0;
+    const double g = F.mgam[km];
+    e = (p0[c] + g * F.mpinf[km]) / ((g - 1.0) * r0);
+    if (c == dep_cell) e = dep_e / m;
+    for (int q = 0; q < F.nmat; ++q) {
+      F.mat[(3ll * q + 0) * F.nc + c] = (R)(q == km ? 1.0 : 0.0);
+      F.mat[(3ll * q + 1) * F.nc + c] = (R)(q == km ? m : 0.0);
+      F.mat[(3ll * q + 2) * F.nc + c] = (R)(q == km ? e : 0.0);
+    }
+  } else {
+    e = p0[c] / ((F.gamma - 1.0) * r0);
+    if (c == dep_cell) e = dep_e / m;
+  }
   F.m[c] = (R)m;
   F.e[c] = (R)e;
+  if (F.im) F.im[c] = (R)(1.0 / m);
+}
+
+// Cell totals from the materials (after a host upload of material fields):
+// m = sum_k m_k, e = sum_k m_k e_k / m.
+template <typename R>
+__global__ void k_mat_totals(Fields<R> F) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc) return;
+  double m = 0.0, ie = 0.0;
+  for (int k = 0; k < F.nmat; ++k) {
+    const double mk = (double)F.mat[(3ll * k + 1) * F.nc + c];
+    m += mk;
+    ie += mk * (double)F.mat[(3ll * k + 2) * F.nc + c];
+  }
+  F.m[c] = (R)m;
+  F.e[c] = (R)(ie / m);
   if (F.im) F.im[c] = (R)(1.0 / m);
 }
 
@@ -96,6 +133,40 @@ __global__ void k_reset_scalars(DevScalars *S) {
 // EoS, viscosity, CFL dt
 // ---------------------------------------------------------------------------
 
+// Stiffened-gas EoS of material k: p = (g - 1) rho e - g p_inf and
+// c^2 = g (g - 1) (e - p_inf / rho), floored at 0 (p_inf = 0: ideal gas).
+template <typename R>
+__device__ __forceinline__ double mat_pressure(const Fields<R> &F, int k, double rho, double e) {
+  const double g = F.mgam[k];
+  return (g - 1.0) * rho * e - g * F.mpinf[k];
+}
+
+template <typename R>
+__device__ __forceinline__ double mat_cs2(const Fields<R> &F, int k, double rho, double e) {
+  const double g = F.mgam[k];
+  const double c2 = g * (g - 1.0) * (e - F.mpinf[k] / rho);
+  return c2 > 0.0 ? c2 : 0.0;
+}
+
+// Mixed cell c of volume V and mass m: materials present (alpha_k > 0) at
+// density m_k / (alpha_k V); p = sum_k alpha_k p_k, c^2 = sum_k m_k c_k^2 / m.
+template <typename R>
+__device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, double V, double m, double &p,
+                                            double &cs2) {
+  double ps = 0.0, cm = 0.0;
+  for (int k = 0; k < F.nmat; ++k) {
+    const long long ia = 3ll * k * F.nc + c;
+    const double a = (double)F.mat[ia];
+    if (!(a > 0.0)) continue;
+    const double mk = (double)F.mat[ia + F.nc], ek = (double)F.mat[ia + 2 * F.nc];
+    const double rk = mk / (a * V);
+    ps += a * mat_pressure(F, k, rk, ek);
+    cm += mk * mat_cs2(F, k, rk, ek);
+  }
+  p = ps;
+  cs2 = cm / m;
+}
+
 // Corner a's gradient from the current-position cache Gn[(3 a + axis) nc + c].
 template <typename R>
 __device__ __forceinline__ P3 gn_corner(const R *Gn, long long nc, long long c, int a) {
@@ -105,7 +176,7 @@ __device__ __forceinline__ P3 gn_corner(const R *Gn, long long nc, long long c, 
 
 // STR: the state carries material strength (a separate instantiation, so
 // the stress module's registers do not weigh on the plain kernels).
-template <typename R, bool STR>
+template <typename R, bool STR, bool MAT>
 __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_eos_dt(Fields<R> F, DevScalars *S, int mode,
                                                               double dt_override) {
   const bool active = (mode == kDtAdvance) ? cycle_active(S) : (S->status == 0);
@@ -143,8 +214,13 @@ __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_eos_dt(Fields<R> F, Dev
     const double iv = 1.0 / V;
     const double m = (double)F.m[c], e = (double)F.e[c];
     const double rho = m * iv;
-    const double p = (F.gamma - 1.0) * rho * e;
-    const double cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
+    double p, cs2;
+    if constexpr (MAT) {
+      mixture_eos(F, c, V, m, p, cs2);
+    } else {
+      p = (F.gamma - 1.0) * rho * e;
+      cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
+    }
     const double cs = sqrt(cs2);
     double q = 0.0, q_rho = 0.0;
     if (dvdt < 0.0) {  // div < 0 (V > 0)
@@ -409,7 +485,9 @@ __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_lagrange_cells(Fields<R
 // gradients of x^n kept by the EoS pass, no material strength -- with one
 // corner at a time live: the compatible energy update, then the volume and
 // density at x^{n+1} (the remap's donor density).
-template <typename R>
+// MAT: several materials; each takes the share alpha_k (p_k + q) of the
+// cell's work (uniform strain: the fractions stay), p_k at the state of x^n.
+template <typename R, bool MAT>
 __global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F, DevScalars *S,
                                                                     double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -428,6 +506,22 @@ __global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F
   const double m = (double)F.m[c];
   double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
   if (F.fh) e1 -= h / m * work_hg;
+  if constexpr (MAT) {
+    const double V0 = (double)F.vol[c], qc = (double)F.q[c];
+    double ie = 0.0;
+    for (int km = 0; km < F.nmat; ++km) {
+      const long long ia = 3ll * km * F.nc + c;
+      const double a = (double)F.mat[ia];
+      if (!(a > 0.0)) continue;
+      const double mk = (double)F.mat[ia + F.nc];
+      double ek = (double)F.mat[ia + 2 * F.nc];
+      const double pk = mat_pressure(F, km, mk / (a * V0), ek);
+      ek -= h / mk * (a * (pk + qc)) * work;
+      F.mat[ia + 2 * F.nc] = (R)ek;
+      ie += mk * ek;
+    }
+    e1 = ie / m;
+  }
   P3 X[8];
   load_hex(F.xn, F.yn, F.zn, F.nx, F.ny, i, j, k, X);
   shift0(X);
@@ -494,12 +588,57 @@ __device__ __forceinline__ void face_flux(const Fields<R> &F, long long c, int i
   ep[c] = (R)(f * e_f);
 }
 
-template <typename R>
+// Materials: the low face along AX moves each material's share of its
+// swept volume dv out of the donor -- volume alpha_k dv, mass (m_k / V_L) dv
+// (the partial density of the Lagrangian donor), energy that mass times
+// e_k -- into mfx; mu and ep get the totals over the materials.
+template <int AX, typename R>
+__device__ __forceinline__ void mat_face_flux(const Fields<R> &F, long long c, int i, int j, int k, R *mu,
+                                              R *ep) {
+  const int idx = AX == 0 ? i : AX == 1 ? j : k;
+  const long long nc = F.nc;
+  if (idx == 0) {
+    mu[c] = (R)0;
+    ep[c] = (R)0;
+    for (int km = 0; km < F.nmat; ++km) {
+      R *o = F.mfx + (9ll * km + 3 * AX) * nc + c;
+      o[0] = o[nc] = o[2 * nc] = (R)0;
+    }
+    return;
+  }
+  const double dv = swept_volume<AX>(F, i, j, k);
+  const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+  const long long dn = dv > 0.0 ? c : c - stride;
+  const double vl = (double)F.vol[dn];
+  double mu_t = 0.0, ef_t = 0.0;
+  for (int km = 0; km < F.nmat; ++km) {
+    const long long ia = 3ll * km * nc + dn;
+    const double vf = (double)F.mat[ia] * dv;
+    const double mf = (double)F.mat[ia + nc] / vl * dv;
+    const double ef = mf * (double)F.mat[ia + 2 * nc];
+    R *o = F.mfx + (9ll * km + 3 * AX) * nc + c;
+    o[0] = (R)vf;
+    o[nc] = (R)mf;
+    o[2 * nc] = (R)ef;
+    mu_t += mf;
+    ef_t += ef;
+  }
+  mu[c] = (R)mu_t;
+  ep[c] = (R)ef_t;
+}
+
+template <typename R, bool MAT>
 __global__ void __launch_bounds__(kBlock) k_remap_faces(Fields<R> F, DevScalars *S) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
+  if constexpr (MAT) {
+    mat_face_flux<0>(F, c, i, j, k, F.mux, F.epx);
+    mat_face_flux<1>(F, c, i, j, k, F.muy, F.epy);
+    mat_face_flux<2>(F, c, i, j, k, F.muz, F.epz);
+    return;
+  }
   face_flux<0>(F, c, i, j, k, F.mux, F.epx);
   face_flux<1>(F, c, i, j, k, F.muy, F.epy);
   face_flux<2>(F, c, i, j, k, F.muz, F.epz);
@@ -598,12 +737,92 @@ __global__ void __launch_bounds__(kBlock) k_remap_nodes(Fields<R> F, DevScalars 
   }
 }
 
+// Materials: each material's volume, mass and energy after the fluxes of
+// the cell's six faces; the kinetic-energy fix shared by mass; a material
+// at or below kAlphaMin of the cell's new volume, or with no positive mass
+// or volume, leaves the cell, its mass and energy going to the remaining
+// materials by mass; fractions = remaining volumes over their sum.
 template <typename R>
+__device__ __forceinline__ void mat_remap_cell(const Fields<R> &F, DevScalars *S, long long c, int i, int j,
+                                               int k) {
+  const long long nc = F.nc, sy = F.nx, sz = (long long)F.nx * F.ny;
+  double fix = 0.0;
+  if (F.ke_fix) {
+#pragma unroll
+    for (int a = 0; a < 8; ++a) {
+      const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
+      const int cnt = ((ni == 0 || ni == F.nx) ? 1 : 2) * ((nj == 0 || nj == F.ny) ? 1 : 2) *
+                      ((nk == 0 || nk == F.nz) ? 1 : 2);
+      fix += (double)F.dke[node_index(F.nx, F.ny, ni, nj, nk)] / (double)cnt;
+    }
+  }
+  const double vl = (double)F.vol[c];
+  double mv[kMaxMat], mk[kMaxMat], me[kMaxMat];
+  double m1 = 0.0, vtot = 0.0;
+  for (int km = 0; km < F.nmat; ++km) {
+    const R *f = F.mfx + 9ll * km * nc;  // f[(3 axis + q) nc + cell]
+    double d[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      double v = -(double)f[q * nc + c] - (double)f[(3 + q) * nc + c] - (double)f[(6 + q) * nc + c];
+      if (i + 1 < F.nx) v += (double)f[q * nc + c + 1];
+      if (j + 1 < F.ny) v += (double)f[(3 + q) * nc + c + sy];
+      if (k + 1 < F.nz) v += (double)f[(6 + q) * nc + c + sz];
+      d[q] = v;
+    }
+    const long long ia = 3ll * km * nc + c;
+    const double m0 = (double)F.mat[ia + nc];
+    mv[km] = (double)F.mat[ia] * vl + d[0];
+    mk[km] = m0 + d[1];
+    me[km] = m0 * (double)F.mat[ia + 2 * nc] + d[2];
+    m1 += mk[km];
+    vtot += mv[km];
+  }
+  bool keep[kMaxMat];
+  double mkeep = 0.0, mdrop = 0.0, iedrop = 0.0, vkeep = 0.0;
+  for (int km = 0; km < F.nmat; ++km) {
+    keep[km] = mk[km] > 0.0 && mv[km] > kAlphaMin * vtot;
+    const double ie = me[km] + mk[km] / m1 * fix;
+    if (keep[km]) {
+      mkeep += mk[km];
+      vkeep += mv[km];
+    } else {
+      mdrop += mk[km];
+      iedrop += ie;
+    }
+  }
+  double msum = 0.0, iesum = 0.0;
+  for (int km = 0; km < F.nmat; ++km) {
+    const long long ia = 3ll * km * nc + c;
+    if (keep[km]) {
+      const double w = mk[km] / mkeep;
+      const double mnew = mk[km] + w * mdrop;
+      const double ie = me[km] + mk[km] / m1 * fix + w * iedrop;
+      F.mat[ia] = (R)(mv[km] / vkeep);
+      F.mat[ia + nc] = (R)mnew;
+      F.mat[ia + 2 * nc] = (R)(ie / mnew);
+      msum += mnew;
+      iesum += ie;
+    } else {
+      F.mat[ia] = F.mat[ia + nc] = F.mat[ia + 2 * nc] = (R)0;
+    }
+  }
+  if (!(msum > 0.0)) set_status(S, msum != msum ? SALE_ENAN : SALE_ENEGVOL);
+  F.m[c] = (R)msum;
+  F.e[c] = (R)(iesum / msum);
+  if (F.im) F.im[c] = (R)(1.0 / msum);
+}
+
+template <typename R, bool MAT>
 __global__ void __launch_bounds__(kBlock) k_remap_cells(Fields<R> F, DevScalars *S) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   int i, j, k;
   cell_ijk(c, F.nx, F.ny, i, j, k);
+  if constexpr (MAT) {
+    mat_remap_cell(F, S, c, i, j, k);
+    return;
+  }
   const long long sy = F.nx, sz = (long long)F.nx * F.ny;
   double dm = -(double)F.mux[c] - (double)F.muy[c] - (double)F.muz[c];
   double de = -(double)F.epx[c] - (double)F.epy[c] - (double)F.epz[c];
@@ -730,8 +949,12 @@ void launch_recip(const double *a, double *r, long long n, cudaStream_t st) {
 
 template <typename R>
 void launch_init_cells(const Fields<R> &F, DevScalars *S, const double *rho0, const double *p0,
-                       long long dep_cell, double dep_e, cudaStream_t st) {
-  k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e);
+                       long long dep_cell, double dep_e, int mat_i0, cudaStream_t st) {
+  k_init_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, rho0, p0, dep_cell, dep_e, mat_i0);
+}
+
+void launch_mat_totals(const Fields<double> &F, cudaStream_t st) {
+  k_mat_totals<double><<<grid_for(F.nc), kBlock, 0, st>>>(F);
 }
 
 void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double dt_override, cudaStream_t st);
@@ -744,24 +967,41 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
     if constexpr (std::is_same<R, double>::value) launch_ale_kernel(kid, F, S, dt_override, st);
     return;
   }
+  // materials run on FP64 states only (the instantiations for float are never launched)
+  constexpr bool kFp64 = std::is_same<R, double>::value;
+  const bool mat = kFp64 && F.mat != nullptr;
   switch (kid) {
     case kInitNodes: k_init_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F); break;
     case kEos:
-      if (F.sdev) k_eos_dt<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
-      else k_eos_dt<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+      if (mat) {
+        if constexpr (kFp64) k_eos_dt<R, false, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+      } else if (F.sdev) k_eos_dt<R, true, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
+      else k_eos_dt<R, false, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, mode, dt_override);
       break;
     case kLagNodes: k_lagrange_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kLagCells:
-      if (F.sdev) k_lagrange_cells<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
-      else if (F.Gn && F.time_order != 2) k_lagrange_cells_cached<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      // materials: a state carries the gradient cache and takes the single-stage step
+      if (mat) {
+        if constexpr (kFp64) k_lagrange_cells_cached<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      } else if (F.sdev) k_lagrange_cells<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else if (F.Gn && F.time_order != 2)
+        k_lagrange_cells_cached<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       else k_lagrange_cells<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       break;
     case kPcPositions: k_pc_positions<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kHourglass: k_hourglass<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
     case kPcPredict: k_pc_predict<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
-    case kRemapFaces: k_remap_faces<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kRemapFaces:
+      if (mat) {
+        if constexpr (kFp64) k_remap_faces<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+      } else k_remap_faces<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+      break;
     case kRemapNodes: k_remap_nodes<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S); break;
-    case kRemapCells: k_remap_cells<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kRemapCells:
+      if (mat) {
+        if constexpr (kFp64) k_remap_cells<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+      } else k_remap_cells<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
+      break;
     case kDiag:
       k_diag_partial<R><<<kDiagBlocks, kBlock, 0, st>>>(F, partial);
       k_diag_final<<<1, kDiagBlocks, 0, st>>>(partial, out);
@@ -771,7 +1011,7 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
 }
 
 template void launch_init_cells<double>(const Fields<double> &, DevScalars *, const double *, const double *,
-                                        long long, double, cudaStream_t);
+                                        long long, double, int, cudaStream_t);
 template void launch_kernel<double>(int, const Fields<double> &, DevScalars *, int, double, double *, double *,
                                     cudaStream_t);
 template void launch_kernel<float>(int, const Fields<float> &, DevScalars *, int, double, double *, double *,

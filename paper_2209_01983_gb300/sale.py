@@ -44,7 +44,8 @@ class sale_problem_desc(C.Structure):
                 ("remap_order", C.c_int), ("time_order", C.c_int), ("c_hg", C.c_double),
                 ("shear0", C.c_double), ("shear_dp", C.c_double), ("shear_dt", C.c_double), ("cv", C.c_double),
                 ("e_ref", C.c_double), ("rho_ref", C.c_double), ("yield0", C.c_double), ("yield_max", C.c_double),
-                ("hard_beta", C.c_double), ("hard_n", C.c_double)]
+                ("hard_beta", C.c_double), ("hard_n", C.c_double),
+                ("nmat", C.c_int), ("mat_gamma", C.c_double * 4), ("mat_pinf", C.c_double * 4)]
 
 
 class sale_diag(C.Structure):
@@ -142,7 +143,11 @@ def problem_desc(pd: inputs.ProblemDesc) -> sale_problem_desc:
     p = sale_problem_desc()
     for name, _ in sale_problem_desc._fields_:
         v = getattr(pd, name)
-        setattr(p, name, int(v) if name in ("kind", "ke_fix", "remap_order", "time_order") else float(v))
+        if name in ("mat_gamma", "mat_pinf"):
+            for k in range(4):
+                getattr(p, name)[k] = float(v[k])
+            continue
+        setattr(p, name, int(v) if name in ("kind", "ke_fix", "remap_order", "time_order", "nmat") else float(v))
     if not math.isfinite(p.dt_init):
         p.dt_init = 0.0
     return p

@@ -96,3 +96,21 @@ def test_state_bytes_for_scheme_options(sale):
     for prec, per_cell in ((sale.SALE_FP64, (24 + 32) * 8), (sale.SALE_FP32_MIXED, 24 * 4)):
         assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(hg)), prec) >= \
             sale.sale_state_bytes(m._h, prec) + per_cell * md.ncell
+
+
+def test_state_bytes_for_materials(sale):
+    import dataclasses
+    md, pd = inputs.sedov_octant(8, jitter=0.1)
+    m = sale.Mesh(md)
+    base = sale.sale_state_bytes(m._h, sale.SALE_FP64)
+    for nmat in (2, 3, 4):
+        pm = dataclasses.replace(pd, nmat=nmat)
+        # fraction, mass, energy of every material; its volume, mass and
+        # energy fluxes through the three low faces
+        got = sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(pm)), sale.SALE_FP64)
+        assert got >= base + (3 + 9) * nmat * 8 * md.ncell
+    # one material is the plain state; FP32-mixed states take no materials
+    assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(dataclasses.replace(pd, nmat=1))),
+                                     sale.SALE_FP64) == base
+    assert sale.sale_state_bytes_for(m._h, C.byref(sale.problem_desc(dataclasses.replace(pd, nmat=2))),
+                                     sale.SALE_FP32_MIXED) == sale.sale_state_bytes(m._h, sale.SALE_FP32_MIXED)
