@@ -45,6 +45,9 @@ UNIT = "cell-updates/s"
 # p = 1e-6); the blast region yields and work-hardens, the rest stays elastic
 STRENGTH = dict(shear0=0.05, shear_dp=0.3, shear_dt=-0.01, cv=1.0, e_ref=0.0, rho_ref=1.0, yield0=2e-3,
                 yield_max=1e-2, hard_beta=20.0, hard_n=0.3)
+# --materials: two materials, the blast's gas (gamma 1.4) and from x = 0.6 on
+# a second ideal gas (gamma 5/3) at the same density and pressure
+MATERIALS = dict(nmat=2, mat_gamma=(1.4, 5.0 / 3.0, 1.4, 1.4), mat_pinf=(0.0, 0.0, 0.0, 0.0), x_split=0.6)
 
 
 def parse():
@@ -70,6 +73,8 @@ def parse():
                     help="remap after every k-th cycle (0: Lagrangian cycles); FP64 only when not 1")
     ap.add_argument("--strength", action="store_true",
                     help="material strength (Steinberg-Guinan elastic-plastic material, FP64 general kernels)")
+    ap.add_argument("--materials", action="store_true",
+                    help="two materials (uniform-strain mixed cells, FP64 general kernels)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-sample-n", type=int, default=64)
     ap.add_argument("--config", default="large", choices=("large", "batch", "precision", "precision-oracle"))
@@ -291,12 +296,14 @@ def reference_arm(args):
 
 def workload_config(args, precision):
     order = ("" if args.remap_order == 1 else "-remap2") + ("" if args.time_order == 1 else "-pc") + \
-        ("" if args.c_hg == 0 else f"-hg{args.c_hg}") + ("-strength" if args.strength else "")
+        ("" if args.c_hg == 0 else f"-hg{args.c_hg}") + ("-strength" if args.strength else "") + \
+        ("-2materials" if args.materials else "")
     mode = {0: "lagrangian", 1: "ale-every-cycle"}.get(args.remap_every, f"remap-every-{args.remap_every}")
     return {"workload": f"sedov-octant-{args.n}^3-jitter{args.jitter}-{mode}{order}",
             "cells": args.n ** 3, "gamma": 1.4, "remap_every": args.remap_every, "remap_order": args.remap_order,
             "time_order": args.time_order, "c_hg": args.c_hg,
             **({"strength": STRENGTH} if args.strength else {}),
+            **({"materials": MATERIALS} if args.materials else {}),
             "precision": precision,
             "l2": "state larger than the 129 MB L2 (no flush)", "parallelism": "replicas"}
 
@@ -382,7 +389,7 @@ def measure(args, precision, local, barrier):
 
     md, pd = inputs.sedov_octant(args.n, jitter=args.jitter)
     pd = dataclasses.replace(pd, remap_order=args.remap_order, time_order=args.time_order, c_hg=args.c_hg,
-                             **(STRENGTH if args.strength else {}))
+                             **(STRENGTH if args.strength else {}), **(MATERIALS if args.materials else {}))
     code = sale.SALE_FP64 if precision == "fp64" else sale.SALE_FP32_MIXED
     st = sale.State(md, pd, precision=code, device=f"cuda:{local}")
     tuning = None
@@ -418,9 +425,10 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    path = "ale" if args.remap_every == 1 else "general"  # only Eulerian-every-cycle runs take the cached kernels
+    # only Eulerian-every-cycle runs of one material take the cached kernels
+    path = "ale" if args.remap_every == 1 and not args.materials else "general"
     table = costs.table(precision, path, jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
-                        hourglass=args.c_hg > 0, strength=args.strength)
+                        hourglass=args.c_hg > 0, strength=args.strength, nmat=2 if args.materials else 0)
     kern = {k: v for k, v in prof.items() if v[1] > 0}
     missing = [k for k in kern if k not in table]
     if missing:
@@ -492,7 +500,7 @@ def e2e_rate(args, res, world):
     from paper_2209_01983_gb300 import sale
 
     st, md = res["st"], res["md"]
-    names = ("u", "v", "w", "mn", "m", "e")
+    names = ("u", "v", "w", "mn") + (("alpha0", "m0", "e0", "alpha1", "m1", "e1") if args.materials else ("m", "e"))
     host = {nm: torch.from_numpy(st.field(nm)).pin_memory() for nm in names}
     h2d = sum(t.numel() * 8 for t in host.values())
     d2h = 8 * 6 + 128  # diagnostics sums + device scalars
@@ -518,7 +526,9 @@ def e2e_rate(args, res, world):
     secs = time.perf_counter() - t0
     return {"value": world * md.ncell * steps / secs, "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "steps": steps, "ms_per_step": [round(t, 2) for t in times],
-            "h2d": "u, v, w, node mass, cell mass, specific energy (FP64, pinned host memory) through sale_set_field",
+            "h2d": "u, v, w, node mass, " + ("each material's fraction, mass and specific energy" if args.materials
+                                              else "cell mass, specific energy")
+                   + " (FP64, pinned host memory) through sale_set_field",
             "d2h": "the step's result as sale_diagnostics: mass, momentum, internal, kinetic and total energy, "
                    "t, dt, cycle and status (the fields stay on the device)"}
 
@@ -540,7 +550,7 @@ def gpu_arm(args):
             dist.barrier()
 
     precisions = ["fp64", "fp32_mixed"] if args.precision == "both" else [args.precision]
-    if args.strength or args.remap_every != 1:  # FP64 states only
+    if args.strength or args.materials or args.remap_every != 1:  # FP64 states only
         precisions = ["fp64"]
     results = {}
     for prec in precisions:
@@ -600,7 +610,8 @@ def gpu_arm(args):
         variants[f"batch{args.batch_count}"] = bt
     if not args.no_precision:
         variants["precision"] = measure_precision(args.precision_n, args.t_end, local)
-    if not args.no_options and not args.strength and args.remap_order == 1 and args.time_order == 1 \
+    if not args.no_options and not args.strength and not args.materials and args.remap_order == 1 \
+            and args.time_order == 1 \
             and args.c_hg == 0 and args.remap_every == 1 and "fp64" in results:
         variants["scheme_options"] = measure_options(args, local, results["fp64"])
     if variants:
@@ -613,14 +624,15 @@ def gpu_arm(args):
 
 # The scheme options of the library, each run alone on the bench mesh (FP64).
 SCHEME_OPTIONS = (("remap_order_2", {"remap_order": 2}), ("predictor_corrector", {"time_order": 2}),
-                  ("hourglass_c_hg_0.05", {"c_hg": 0.05}), ("strength", {"strength": True}))
+                  ("hourglass_c_hg_0.05", {"c_hg": 0.05}), ("strength", {"strength": True}),
+                  ("two_materials", {"materials": True}))
 
 
 def measure_options(args, local, base):
     """The FP64 Eulerian cycle on the same mesh with each scheme option (the
     second-order remap, the predictor-corrector step, hourglass control,
-    material strength), `--options-steps` timed cycles each, against the
-    default cycle of this run."""
+    material strength, two materials), `--options-steps` timed cycles each,
+    against the default cycle of this run."""
     import argparse as _ap
 
     import torch

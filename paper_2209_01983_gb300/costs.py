@@ -197,9 +197,31 @@ FP64_STRENGTH_EXTRA = {
 }
 
 
+# Several materials (FP64 general kernels), per material k: the EoS pass
+# reads alpha_k, m_k, e_k and forms rho_k (2), p_k (5), c_k^2 (6) and the
+# two sums (4); the cell pass reads them and q, forms rho_k, p_k and the
+# work share (13) and writes e_k; the face pass reads them and V_L and
+# writes the volume, mass and energy flux through each low face (6 per
+# face); the cell remap reads the 9 fluxes per material of its own low
+# faces (the high faces' are the neighbours' low faces), alpha_k, m_k, e_k,
+# V_L, dKE, sums them (3 x 6), applies the cutoff and the kinetic-energy
+# share (~18) and writes alpha_k, m_k, e_k and m, e, 1/m.
+def materials_table(base: dict, nmat: int) -> dict:
+    t = dict(base)
+    for k, (db, df) in {"eos_dt": (8 * 3 * nmat, 17 * nmat + 1),
+                        "lagrange_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
+                        "remap_faces": (8 * (3 * nmat + 1 + 9 * nmat), 18 * nmat)}.items():
+        u, b, f = t[k]
+        t[k] = (u, b + db, f + df)
+    t["remap_cells"] = ("cell", 8 * (9 * nmat + 3 * nmat + 2 + 3 * nmat + 3), 36 * nmat + 13)
+    return t
+
+
 def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
-          hourglass: bool = False, strength: bool = False):
+          hourglass: bool = False, strength: bool = False, nmat: int = 0):
     if precision == "fp64":
+        if nmat >= 2:  # the general kernels with materials
+            return materials_table(FP64, nmat)
         if strength:  # the same kernels with the stress module
             base = table(precision, path, jitter, order, time_order, hourglass)
             return {k: (u, b + FP64_STRENGTH_EXTRA.get(k, (0, 0))[0], f + FP64_STRENGTH_EXTRA.get(k, (0, 0))[1])
@@ -225,7 +247,7 @@ def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1
 
 
 def cycle_cost(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
-               hourglass: bool = False, strength: bool = False):
+               hourglass: bool = False, strength: bool = False, nmat: int = 0):
     """(bytes, flops) of one full cycle per cell."""
-    t = table(precision, path, jitter, order, time_order, hourglass, strength)
+    t = table(precision, path, jitter, order, time_order, hourglass, strength, nmat)
     return sum(v[1] for v in t.values()), sum(v[2] for v in t.values())

@@ -24,6 +24,11 @@ def test_every_cost_entry_is_a_library_kernel(names):
         for k, (unit, b, f) in t.items():
             assert unit in ("cell", "node") and b > 0 and f >= 0, k
     assert not sorted(k for k in costs.table("fp64", "general") if k not in names)
+    # several materials: the general kernels, each entry at least its single-material cost
+    for nmat in (2, 3, 4):
+        t, base = costs.table("fp64", "general", nmat=nmat), costs.table("fp64", "general")
+        assert set(t) == set(base)
+        assert all(t[k][1] >= base[k][1] for k in t) and t["remap_cells"][1] > base["remap_cells"][1]
 
 
 def test_cycle_totals():
