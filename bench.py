@@ -425,8 +425,7 @@ def measure(args, precision, local, barrier):
         raise RuntimeError(f"ran {done} of {args.steps} cycles")
     ms = ev0.elapsed_time(ev1)
 
-    # only Eulerian-every-cycle runs of one material take the cached kernels
-    path = "ale" if args.remap_every == 1 and not args.materials else "general"
+    path = "ale" if args.remap_every == 1 else "general"  # only Eulerian-every-cycle runs take the cached kernels
     table = costs.table(precision, path, jitter=args.jitter > 0, order=args.remap_order, time_order=args.time_order,
                         hourglass=args.c_hg > 0, strength=args.strength, nmat=2 if args.materials else 0)
     kern = {k: v for k, v in prof.items() if v[1] > 0}

@@ -206,22 +206,33 @@ FP64_STRENGTH_EXTRA = {
 # faces (the high faces' are the neighbours' low faces), alpha_k, m_k, e_k,
 # V_L, dKE, sums them (3 x 6), applies the cutoff and the kinetic-energy
 # share (~18) and writes alpha_k, m_k, e_k and m, e, 1/m.
-def materials_table(base: dict, nmat: int) -> dict:
+# The Eulerian kernels take the same steps: the cell pass the work split,
+# the flux pass the material fluxes, the remap + EoS pass the material
+# remap (9 fluxes per material instead of the 6 totals, V_L read, the
+# sound speed stored) and the mixture EoS.
+def materials_table(base: dict, nmat: int, path: str = "general") -> dict:
     t = dict(base)
-    for k, (db, df) in {"eos_dt": (8 * 3 * nmat, 17 * nmat + 1),
-                        "lagrange_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
-                        "remap_faces": (8 * (3 * nmat + 1 + 9 * nmat), 18 * nmat)}.items():
+    if path == "ale":
+        extra = {"ale_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
+                 "ale_fluxes": (8 * (12 * nmat + 1), 18 * nmat),
+                 "ale_remap_eos": (8 * (15 * nmat - 6 + 2), 53 * nmat - 21)}
+    else:
+        extra = {"eos_dt": (8 * 3 * nmat, 17 * nmat + 1),
+                 "lagrange_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
+                 "remap_faces": (8 * (3 * nmat + 1 + 9 * nmat), 18 * nmat)}
+    for k, (db, df) in extra.items():
         u, b, f = t[k]
         t[k] = (u, b + db, f + df)
-    t["remap_cells"] = ("cell", 8 * (9 * nmat + 3 * nmat + 2 + 3 * nmat + 3), 36 * nmat + 13)
+    if path != "ale":
+        t["remap_cells"] = ("cell", 8 * (9 * nmat + 3 * nmat + 2 + 3 * nmat + 3), 36 * nmat + 13)
     return t
 
 
 def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
           hourglass: bool = False, strength: bool = False, nmat: int = 0):
     if precision == "fp64":
-        if nmat >= 2:  # the general kernels with materials
-            return materials_table(FP64, nmat)
+        if nmat >= 2:  # the same kernels with materials
+            return materials_table(FP64_ALE if path == "ale" else FP64, nmat, path)
         if strength:  # the same kernels with the stress module
             base = table(precision, path, jitter, order, time_order, hourglass)
             return {k: (u, b + FP64_STRENGTH_EXTRA.get(k, (0, 0))[0], f + FP64_STRENGTH_EXTRA.get(k, (0, 0))[1])

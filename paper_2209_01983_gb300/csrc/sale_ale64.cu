@@ -203,8 +203,12 @@ __global__ void __launch_bounds__(kBlock) k_ale_edges(Fields<double> F, DevScala
   }
 }
 
-template <bool STR>
-__global__ void __launch_bounds__(kBlock, STR ? 2 : 4) k_ale_cells(Fields<double> F, DevScalars *S, double dt_override) {
+// MAT: several materials; each takes the share alpha_k (p_k + q) of the
+// cell's work (uniform strain: the fractions stay), p_k of the state at n on
+// the reference mesh.
+template <bool STR, bool MAT>
+__global__ void __launch_bounds__(kBlock, STR ? 2 : (MAT ? 3 : 4)) k_ale_cells(Fields<double> F, DevScalars *S,
+                                                                            double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
   const double h = step_dt(S, dt_override);
@@ -265,6 +269,23 @@ __global__ void __launch_bounds__(kBlock, STR ? 2 : 4) k_ale_cells(Fields<double
 #pragma unroll
     for (int q = 0; q < 6; ++q) F.sold[q * nc + c] = S6[q];
     F.sold[6 * nc + c] = F.sdev[6 * nc + c] + deps;
+  }
+  if constexpr (MAT) {
+    const long long nc = F.nc;
+    const double V0 = F.VE[c], qc = F.q[c];
+    double ie = 0.0;
+    for (int km = 0; km < F.nmat; ++km) {
+      const long long ia = 3ll * km * nc + c;
+      const double a = F.mat[ia];
+      if (!(a > 0.0)) continue;
+      const double mk = F.mat[ia + nc];
+      double ek = F.mat[ia + 2 * nc];
+      const double pk = mat_pressure(F, km, mk / (a * V0), ek);
+      ek -= h / mk * (a * (pk + qc)) * work;
+      F.mat[ia + 2 * nc] = ek;
+      ie += mk * ek;
+    }
+    e1 = ie * im;
   }
   F.e[c] = e1;
   // swept volumes of the three low faces, assembled from k_ale_edges: the
@@ -344,6 +365,30 @@ __device__ __forceinline__ double ale_donor_flux(const Fields<double> &F, const 
   return f;
 }
 
+// Materials: the donor dn's share of the swept volume v for every material
+// -- volume alpha_k v, mass (m_k / V_L) v, energy that mass times e_k --
+// stored at o + 9 k nc (+ nc, + 2 nc); returns the total mass flux, ef the
+// total energy flux.  One division per face (1 / V_L).
+__device__ __forceinline__ double ale_mat_flux(const Fields<double> &F, long long dn, double v, double &ef,
+                                               double *o) {
+  const long long nc = F.nc;
+  const double sv = v / F.vol[dn];
+  double mu = 0.0, e = 0.0;
+  for (int km = 0; km < F.nmat; ++km) {
+    const long long ia = 3ll * km * nc + dn;
+    const double mf = F.mat[ia + nc] * sv;
+    const double efk = mf * F.mat[ia + 2 * nc];
+    double *ok = o + 9ll * km * nc;
+    ok[0] = F.mat[ia] * v;
+    ok[nc] = mf;
+    ok[2 * nc] = efk;
+    mu += mf;
+    e += efk;
+  }
+  ef = e;
+  return mu;
+}
+
 // Donor-cell fluxes of the low face normal to AX; also the cell's part of
 // the dual-mesh mass flux along AX, (mu_low + mu_high) / 8, mu_high being
 // the low-face flux of the +AX neighbour (0 on the high wall).  The node
@@ -385,6 +430,44 @@ __global__ void __launch_bounds__(kBlock) k_ale_fluxes(Fields<double> F, DevScal
   ale_face_flux<0, O2>(F, c, i, F.nx, F.dvx, F.mux, F.epx, F.mqx);
   ale_face_flux<1, O2>(F, c, j, F.ny, F.dvy, F.muy, F.epy, F.mqy);
   ale_face_flux<2, O2>(F, c, k, F.nz, F.dvz, F.muz, F.epz, F.mqz);
+}
+
+// Materials: every material's fluxes through the three low faces of each
+// cell (mfx), their totals (mu, ep) and the cell's dual-mesh parts (mq),
+// one axis at a time.  The high face enters the dual part only through its
+// total mass flux, the Lagrangian density of its donor times its swept
+// volume.
+__global__ void __launch_bounds__(kBlock) k_ale_mat_fluxes(Fields<double> F, DevScalars *S) {
+  const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  if (c >= F.nc || !cycle_active(S)) return;
+  int i, j, k;
+  cell_ijk(c, F.nx, F.ny, i, j, k);
+  const long long nc = F.nc;
+#pragma unroll 1
+  for (int ax = 0; ax < 3; ++ax) {
+    const int idx = ax == 0 ? i : ax == 1 ? j : k, n_ax = ax == 0 ? F.nx : ax == 1 ? F.ny : F.nz;
+    const long long stride = ax == 0 ? 1 : ax == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
+    const double *dv = ax == 0 ? F.dvx : ax == 1 ? F.dvy : F.dvz;
+    double *o = F.mfx + 3ll * ax * nc + c;
+    double lo = 0.0, ef = 0.0;
+    if (idx == 0) {
+      for (int km = 0; km < F.nmat; ++km) {
+        double *ok = o + 9ll * km * nc;
+        ok[0] = ok[nc] = ok[2 * nc] = 0.0;
+      }
+    } else {
+      const double v = dv[c];
+      lo = ale_mat_flux(F, pos_d(v) ? c : c - stride, v, ef, o);
+    }
+    (ax == 0 ? F.mux : ax == 1 ? F.muy : F.muz)[c] = lo;
+    (ax == 0 ? F.epx : ax == 1 ? F.epy : F.epz)[c] = ef;
+    double hi = 0.0;
+    if (idx + 1 < n_ax) {
+      const double v = dv[c + stride];
+      hi = F.rho[pos_d(v) ? c + stride : c] * v;
+    }
+    (ax == 0 ? F.mqx : ax == 1 ? F.mqy : F.mqz)[c] = (lo + hi) * 0.125;
+  }
 }
 
 // Upwind transport of mass, momentum and kinetic energy into node n across
@@ -489,7 +572,7 @@ __global__ void __launch_bounds__(kAleTx * kAleTy) k_ale_remap_nodes(Fields<doub
 // 1/V_E, L_E) from its mass, specific energy and node velocities U; writes
 // the derived fields and returns the CFL rate (cs^2 + 2 q / rho) / (cfl L)^2
 // = 1 / dt_c^2.
-template <bool STR = false>
+template <bool STR = false, bool MAT = false>
 __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long long c, const P3 (&U)[8], double m,
                                                double e) {
   const double V = F.VE[c];
@@ -500,8 +583,14 @@ __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long lon
   const double div = dvdt * inv_v;
   const double L = F.LE[c];
   const double rho = m * inv_v;
-  const double p = (F.gamma - 1.0) * rho * e;
-  const double cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
+  double p, cs2;
+  if constexpr (MAT) {  // the mixture; its sound speed is not a function of e, so it is stored
+    mixture_eos(F, c, V, m, p, cs2);
+    F.cs[c] = sqrt(cs2);
+  } else {
+    p = (F.gamma - 1.0) * rho * e;
+    cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
+  }
   double q_rho = 0.0;  // q / rho
   if (sign_d(div)) {   // div < 0 (-0 gives q = 0 either way); the sound speed itself only where the cell compresses
     const double ld = L * div;
@@ -651,9 +740,24 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
 
 // Cell remap + EoS of cell c; returns its CFL rate 1 / dt_c^2 (0 outside
 // the mesh).
-template <bool STR>
+template <bool STR, bool MAT>
 __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, DevScalars *S, long long c) {
   double rate = 0.0;
+  if constexpr (MAT) {  // the materials' remap (V_L from the density pass), then the mixture's EoS
+    if (c < F.nc) {
+      int i, j, k;
+      cell_ijk(c, F.nx, F.ny, i, j, k);
+      mat_remap_cell(F, S, c, i, j, k);
+      P3 U[8];
+      ale_cell_velocities(F, i, j, k, U);
+      rate = ale_eos_cell<false, true>(F, c, U, F.m[c], F.e[c]);
+      if (nan_d(rate)) {
+        set_status(S, SALE_ENAN);
+        rate = 0.0;
+      }
+    }
+    return rate;
+  }
   if (c < F.nc) {
     int i, j, k;
     cell_ijk(c, F.nx, F.ny, i, j, k);
@@ -727,14 +831,15 @@ __device__ __forceinline__ double ale_remap_eos_cell(const Fields<double> &F, De
 // largest rate is exact, and dt with it.
 constexpr int kEosCellsPerThread = 4;
 
-template <bool STR>
-__global__ void __launch_bounds__(kBlock, STR ? 2 : 3) k_ale_remap_eos(Fields<double> F, DevScalars *S, double dt_override) {
+template <bool STR, bool MAT>
+__global__ void __launch_bounds__(kBlock, STR || MAT ? 2 : 3) k_ale_remap_eos(Fields<double> F, DevScalars *S,
+                                                                             double dt_override) {
   if (!cycle_active(S)) return;  // uniform over the grid: S changes only in the last block
   const long long c0 = blockIdx.x * (long long)(kBlock * kEosCellsPerThread) + threadIdx.x;
   double rate = 0.0;  // CFL rate 1 / dt_c^2
 #pragma unroll 1
   for (int r = 0; r < kEosCellsPerThread; ++r)
-    rate = max_nonneg_d(rate, ale_remap_eos_cell<STR>(F, S, c0 + (long long)r * kBlock));  // rates are >= 0, not NaN
+    rate = max_nonneg_d(rate, ale_remap_eos_cell<STR, MAT>(F, S, c0 + (long long)r * kBlock));  // rates are >= 0, not NaN
   block_min_dt_and_finalize<double, true>(F, S, rate, kDtAdvance, dt_override);
 }
 
@@ -783,13 +888,15 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
     case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAleHourglass: k_ale_hourglass<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleCells:
-      if (F.sdev) k_ale_cells<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
-      else k_ale_cells<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      if (F.mat) k_ale_cells<false, true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else if (F.sdev) k_ale_cells<true, false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_cells<false, false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       break;
     case kAleDensity: k_ale_density<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleSlopes: k_ale_slopes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
     case kAleFluxes:
-      if (F.remap_order == 2) k_ale_fluxes<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      if (F.mat) k_ale_mat_fluxes<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      else if (F.remap_order == 2) k_ale_fluxes<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
       else k_ale_fluxes<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
       break;
     case kAleRemapNodes: {
@@ -801,8 +908,9 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
     case kAleEos: k_ale_eos<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, kDtPropose); break;
     case kAleRemapEos: {
       const unsigned g = grid_ale((F.nc + kEosCellsPerThread - 1) / kEosCellsPerThread);
-      if (F.sdev) k_ale_remap_eos<true><<<g, kBlock, 0, st>>>(F, S, dt_override);
-      else k_ale_remap_eos<false><<<g, kBlock, 0, st>>>(F, S, dt_override);
+      if (F.mat) k_ale_remap_eos<false, true><<<g, kBlock, 0, st>>>(F, S, dt_override);
+      else if (F.sdev) k_ale_remap_eos<true, false><<<g, kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_remap_eos<false, false><<<g, kBlock, 0, st>>>(F, S, dt_override);
       break;
     }
     default: break;

@@ -891,7 +891,7 @@ static void launch_ale_cycle(sale_state *st, double dt_override) {
 }
 
 static void launch_cycle(sale_state *st, bool remap, double dt_override) {
-  if (remap && st->x_is_ref && !st->nmat) {  // several materials run the general kernels
+  if (remap && st->x_is_ref) {
     launch_ale_cycle(st, dt_override);
     return;
   }
@@ -940,7 +940,7 @@ static int get_graph(sale_state *st, int k, int remap_every, cudaGraphExec_t *ou
     if (st->prof_on) st->pending_graphs.push_back(&st->graph_events[key]);
     for (int j = 0; j < k; ++j) {  // replay the buffer-role toggles of launch_cycle
       const bool remap = remap_every > 0 && (j + 1) % remap_every == 0;
-      if (remap && st->x_is_ref && !st->nmat) {
+      if (remap && st->x_is_ref) {
         st->upar ^= 1;
         continue;
       }

@@ -133,40 +133,6 @@ __global__ void k_reset_scalars(DevScalars *S) {
 // EoS, viscosity, CFL dt
 // ---------------------------------------------------------------------------
 
-// Stiffened-gas EoS of material k: p = (g - 1) rho e - g p_inf and
-// c^2 = g (g - 1) (e - p_inf / rho), floored at 0 (p_inf = 0: ideal gas).
-template <typename R>
-__device__ __forceinline__ double mat_pressure(const Fields<R> &F, int k, double rho, double e) {
-  const double g = F.mgam[k];
-  return (g - 1.0) * rho * e - g * F.mpinf[k];
-}
-
-template <typename R>
-__device__ __forceinline__ double mat_cs2(const Fields<R> &F, int k, double rho, double e) {
-  const double g = F.mgam[k];
-  const double c2 = g * (g - 1.0) * (e - F.mpinf[k] / rho);
-  return c2 > 0.0 ? c2 : 0.0;
-}
-
-// Mixed cell c of volume V and mass m: materials present (alpha_k > 0) at
-// density m_k / (alpha_k V); p = sum_k alpha_k p_k, c^2 = sum_k m_k c_k^2 / m.
-template <typename R>
-__device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, double V, double m, double &p,
-                                            double &cs2) {
-  double ps = 0.0, cm = 0.0;
-  for (int k = 0; k < F.nmat; ++k) {
-    const long long ia = 3ll * k * F.nc + c;
-    const double a = (double)F.mat[ia];
-    if (!(a > 0.0)) continue;
-    const double mk = (double)F.mat[ia + F.nc], ek = (double)F.mat[ia + 2 * F.nc];
-    const double rk = mk / (a * V);
-    ps += a * mat_pressure(F, k, rk, ek);
-    cm += mk * mat_cs2(F, k, rk, ek);
-  }
-  p = ps;
-  cs2 = cm / m;
-}
-
 // Corner a's gradient from the current-position cache Gn[(3 a + axis) nc + c].
 template <typename R>
 __device__ __forceinline__ P3 gn_corner(const R *Gn, long long nc, long long c, int a) {
@@ -609,12 +575,12 @@ __device__ __forceinline__ void mat_face_flux(const Fields<R> &F, long long c, i
   const double dv = swept_volume<AX>(F, i, j, k);
   const long long stride = AX == 0 ? 1 : AX == 1 ? (long long)F.nx : (long long)F.nx * F.ny;
   const long long dn = dv > 0.0 ? c : c - stride;
-  const double vl = (double)F.vol[dn];
+  const double sv = dv / (double)F.vol[dn];
   double mu_t = 0.0, ef_t = 0.0;
   for (int km = 0; km < F.nmat; ++km) {
     const long long ia = 3ll * km * nc + dn;
     const double vf = (double)F.mat[ia] * dv;
-    const double mf = (double)F.mat[ia + nc] / vl * dv;
+    const double mf = (double)F.mat[ia + nc] * sv;
     const double ef = mf * (double)F.mat[ia + 2 * nc];
     R *o = F.mfx + (9ll * km + 3 * AX) * nc + c;
     o[0] = (R)vf;
@@ -735,82 +701,6 @@ __global__ void __launch_bounds__(kBlock) k_remap_nodes(Fields<R> F, DevScalars 
     F.y[n] = (R)F.yr[n];
     F.z[n] = (R)F.zr[n];
   }
-}
-
-// Materials: each material's volume, mass and energy after the fluxes of
-// the cell's six faces; the kinetic-energy fix shared by mass; a material
-// at or below kAlphaMin of the cell's new volume, or with no positive mass
-// or volume, leaves the cell, its mass and energy going to the remaining
-// materials by mass; fractions = remaining volumes over their sum.
-template <typename R>
-__device__ __forceinline__ void mat_remap_cell(const Fields<R> &F, DevScalars *S, long long c, int i, int j,
-                                               int k) {
-  const long long nc = F.nc, sy = F.nx, sz = (long long)F.nx * F.ny;
-  double fix = 0.0;
-  if (F.ke_fix) {
-#pragma unroll
-    for (int a = 0; a < 8; ++a) {
-      const int ni = i + (a & 1), nj = j + ((a >> 1) & 1), nk = k + ((a >> 2) & 1);
-      const int cnt = ((ni == 0 || ni == F.nx) ? 1 : 2) * ((nj == 0 || nj == F.ny) ? 1 : 2) *
-                      ((nk == 0 || nk == F.nz) ? 1 : 2);
-      fix += (double)F.dke[node_index(F.nx, F.ny, ni, nj, nk)] / (double)cnt;
-    }
-  }
-  const double vl = (double)F.vol[c];
-  double mv[kMaxMat], mk[kMaxMat], me[kMaxMat];
-  double m1 = 0.0, vtot = 0.0;
-  for (int km = 0; km < F.nmat; ++km) {
-    const R *f = F.mfx + 9ll * km * nc;  // f[(3 axis + q) nc + cell]
-    double d[3];
-#pragma unroll
-    for (int q = 0; q < 3; ++q) {
-      double v = -(double)f[q * nc + c] - (double)f[(3 + q) * nc + c] - (double)f[(6 + q) * nc + c];
-      if (i + 1 < F.nx) v += (double)f[q * nc + c + 1];
-      if (j + 1 < F.ny) v += (double)f[(3 + q) * nc + c + sy];
-      if (k + 1 < F.nz) v += (double)f[(6 + q) * nc + c + sz];
-      d[q] = v;
-    }
-    const long long ia = 3ll * km * nc + c;
-    const double m0 = (double)F.mat[ia + nc];
-    mv[km] = (double)F.mat[ia] * vl + d[0];
-    mk[km] = m0 + d[1];
-    me[km] = m0 * (double)F.mat[ia + 2 * nc] + d[2];
-    m1 += mk[km];
-    vtot += mv[km];
-  }
-  bool keep[kMaxMat];
-  double mkeep = 0.0, mdrop = 0.0, iedrop = 0.0, vkeep = 0.0;
-  for (int km = 0; km < F.nmat; ++km) {
-    keep[km] = mk[km] > 0.0 && mv[km] > kAlphaMin * vtot;
-    const double ie = me[km] + mk[km] / m1 * fix;
-    if (keep[km]) {
-      mkeep += mk[km];
-      vkeep += mv[km];
-    } else {
-      mdrop += mk[km];
-      iedrop += ie;
-    }
-  }
-  double msum = 0.0, iesum = 0.0;
-  for (int km = 0; km < F.nmat; ++km) {
-    const long long ia = 3ll * km * nc + c;
-    if (keep[km]) {
-      const double w = mk[km] / mkeep;
-      const double mnew = mk[km] + w * mdrop;
-      const double ie = me[km] + mk[km] / m1 * fix + w * iedrop;
-      F.mat[ia] = (R)(mv[km] / vkeep);
-      F.mat[ia + nc] = (R)mnew;
-      F.mat[ia + 2 * nc] = (R)(ie / mnew);
-      msum += mnew;
-      iesum += ie;
-    } else {
-      F.mat[ia] = F.mat[ia + nc] = F.mat[ia + 2 * nc] = (R)0;
-    }
-  }
-  if (!(msum > 0.0)) set_status(S, msum != msum ? SALE_ENAN : SALE_ENEGVOL);
-  F.m[c] = (R)msum;
-  F.e[c] = (R)(iesum / msum);
-  if (F.im) F.im[c] = (R)(1.0 / msum);
 }
 
 template <typename R, bool MAT>

@@ -25,10 +25,10 @@ def test_every_cost_entry_is_a_library_kernel(names):
             assert unit in ("cell", "node") and b > 0 and f >= 0, k
     assert not sorted(k for k in costs.table("fp64", "general") if k not in names)
     # several materials: the general kernels, each entry at least its single-material cost
-    for nmat in (2, 3, 4):
-        t, base = costs.table("fp64", "general", nmat=nmat), costs.table("fp64", "general")
-        assert set(t) == set(base)
-        assert all(t[k][1] >= base[k][1] for k in t) and t["remap_cells"][1] > base["remap_cells"][1]
+    for nmat, path in itertools.product((2, 3, 4), ("general", "ale")):
+        t, base = costs.table("fp64", path, nmat=nmat), costs.table("fp64", path)
+        assert set(t) == set(base) and not sorted(k for k in t if k not in names)
+        assert all(t[k][1] >= base[k][1] for k in t) and sum(v[1] for v in t.values()) > sum(v[1] for v in base.values())
 
 
 def test_cycle_totals():
