@@ -34,8 +34,9 @@
  *     volume fraction, mass and energy in every cell; stiffened-gas EoS
  *     (ideal gas when p_inf = 0); mixed cells closed by uniform strain (the
  *     materials of a cell share its volume change, so the fractions do not
- *     change in the Lagrangian phase: Benson, "Computational methods in
- *     Lagrangian and Eulerian hydrocodes", CMAME 99, 1992, Sec. 6), cell
+ *     change in the Lagrangian phase; one of the closures surveyed by
+ *     Benson, "Computational methods in Lagrangian and Eulerian
+ *     hydrocodes", CMAME 99, 1992), cell
  *     pressure sum_k alpha_k p_k; donor-cell remap of each material's
  *     volume, mass and energy.
  *
