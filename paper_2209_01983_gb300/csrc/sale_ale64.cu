@@ -270,21 +270,10 @@ __global__ void __launch_bounds__(kBlock, STR ? 2 : (MAT ? 3 : 4)) k_ale_cells(F
     for (int q = 0; q < 6; ++q) F.sold[q * nc + c] = S6[q];
     F.sold[6 * nc + c] = F.sdev[6 * nc + c] + deps;
   }
-  if constexpr (MAT) {
-    const long long nc = F.nc;
-    const double V0 = F.VE[c], qc = F.q[c];
+  if constexpr (MAT) {  // x^n is the reference mesh
+    const double qc = F.q[c];
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) {
-      const long long ia = 3ll * km * nc + c;
-      const double a = F.mat[ia];
-      if (!(a > 0.0)) continue;
-      const double mk = F.mat[ia + nc];
-      double ek = F.mat[ia + 2 * nc];
-      const double pk = mat_pressure(F, km, mk / (a * V0), ek);
-      ek -= h / mk * (a * (pk + qc)) * work;
-      F.mat[ia + 2 * nc] = ek;
-      ie += mk * ek;
-    }
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, F.VE[c], F.iVE[c], qc, h, work);
     e1 = ie * im;
   }
   F.e[c] = e1;
@@ -585,7 +574,7 @@ __device__ __forceinline__ double ale_eos_cell(const Fields<double> &F, long lon
   const double rho = m * inv_v;
   double p, cs2;
   if constexpr (MAT) {  // the mixture; its sound speed is not a function of e, so it is stored
-    mixture_eos(F, c, V, m, p, cs2);
+    mixture_eos(F, c, V, inv_v, F.im[c], p, cs2);
     F.cs[c] = sqrt(cs2);
   } else {
     p = (F.gamma - 1.0) * rho * e;

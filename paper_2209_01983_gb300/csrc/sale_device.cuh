@@ -434,42 +434,50 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
 // Materials (several per cell, FP64 states)
 // ---------------------------------------------------------------------------
 
-// Stiffened-gas EoS of material k: p = (g - 1) rho e - g p_inf and
-// c^2 = g (g - 1) (e - p_inf / rho), floored at 0 (p_inf = 0: ideal gas).
+// Material k is a stiffened gas: p = (g - 1) rho e - g p_inf, c^2 = g (g - 1)
+// (e - p_inf / rho) floored at 0 (p_inf = 0: ideal gas).
+// Mixed cell c of volume V (iv = 1/V) and mass m (im = 1/m): materials
+// present (alpha_k > 0) at density rho_k = m_k / (alpha_k V); p = sum_k
+// alpha_k p_k, c^2 = sum_k m_k c_k^2 / m.  Written without a division, in
+// the material's internal energy ie_k = m_k e_k: alpha_k p_k = (g - 1) ie_k / V
+// - g p_inf alpha_k and m_k c_k^2 = g (g - 1) (ie_k - p_inf alpha_k V), floored
+// at 0 (the FP64 pipe bounds these kernels, and a division takes about ten
+// of its instructions).
 template <typename R>
-__device__ __forceinline__ double mat_pressure(const Fields<R> &F, int k, double rho, double e) {
-  const double g = F.mgam[k];
-  return (g - 1.0) * rho * e - g * F.mpinf[k];
-}
-
-template <typename R>
-__device__ __forceinline__ double mat_cs2(const Fields<R> &F, int k, double rho, double e) {
-  const double g = F.mgam[k];
-  const double c2 = g * (g - 1.0) * (e - F.mpinf[k] / rho);
-  return c2 > 0.0 ? c2 : 0.0;
-}
-
-// Mixed cell c of volume V and mass m: materials present (alpha_k > 0) at
-// density m_k / (alpha_k V); p = sum_k alpha_k p_k, c^2 = sum_k m_k c_k^2 / m.
-// One FP64 division per material (the density; p_inf / rho_k only for a
-// stiffened gas) and one per cell: the FP64 pipe bounds these kernels.
-template <typename R>
-__device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, double V, double m, double &p,
-                                            double &cs2) {
+__device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, double V, double iv, double im,
+                                            double &p, double &cs2) {
   double ps = 0.0, cm = 0.0;
   for (int k = 0; k < F.nmat; ++k) {
     const long long ia = 3ll * k * F.nc + c;
     const double a = (double)F.mat[ia];
     if (!(a > 0.0)) continue;
-    const double mk = (double)F.mat[ia + F.nc], ek = (double)F.mat[ia + 2 * F.nc];
-    const double rk = mk / (a * V);
+    const double ie = (double)F.mat[ia + F.nc] * (double)F.mat[ia + 2 * F.nc];
     const double g = F.mgam[k], pinf = F.mpinf[k];
-    ps += a * ((g - 1.0) * rk * ek - g * pinf);
-    double c2 = g * (g - 1.0) * (pinf != 0.0 ? ek - pinf / rk : ek);
-    cm += mk * (c2 > 0.0 ? c2 : 0.0);
+    ps += (g - 1.0) * ie * iv - g * pinf * a;
+    const double mc2 = g * (g - 1.0) * (ie - pinf * a * V);
+    cm += mc2 > 0.0 ? mc2 : 0.0;
   }
   p = ps;
-  cs2 = cm / m;
+  cs2 = cm * im;
+}
+
+// The cell pass's share of the compatible work for material k of cell c
+// (uniform strain): e_k -= dt alpha_k (p_k + q) W / m_k, with W = sum_a
+// dV/dx_a . ubar_a and p_k at the state of x^n (volume V0, iv0 = 1/V0);
+// returns m_k e_k of the new state (0 for an absent material).
+template <typename R>
+__device__ __forceinline__ double mat_work_share(const Fields<R> &F, long long c, int k, double V0, double iv0,
+                                                 double q, double h, double work) {
+  const long long ia = 3ll * k * F.nc + c;
+  const double a = (double)F.mat[ia];
+  if (!(a > 0.0)) return 0.0;
+  const double mk = (double)F.mat[ia + F.nc];
+  double ek = (double)F.mat[ia + 2 * F.nc];
+  const double g = F.mgam[k];
+  const double apk = (g - 1.0) * (mk * ek) * iv0 - g * F.mpinf[k] * a;  // alpha_k p_k
+  ek -= h * (apk + a * q) * work / mk;
+  F.mat[ia + 2 * F.nc] = (R)ek;
+  return mk * ek;
 }
 
 // Materials: each material's volume, mass and energy after the fluxes of
@@ -515,9 +523,11 @@ __device__ __forceinline__ void mat_remap_cell(const Fields<R> &F, DevScalars *S
     m1 += mk[km];
     vtot += mv[km];
   }
-  // the kinetic-energy share goes into me; one reciprocal per sum, one
-  // division per material for its specific energy
-  const double fix_m = fix / m1;
+  // the kinetic-energy share goes into me; one reciprocal per sum (the same
+  // sum when no material leaves), one division per material for its
+  // specific energy
+  const double r1 = 1.0 / m1;
+  const double fix_m = fix * r1;
   bool keep[kMaxMat];
   double mkeep = 0.0, mdrop = 0.0, iedrop = 0.0, vkeep = 0.0;
   for (int km = 0; km < F.nmat; ++km) {
@@ -531,7 +541,7 @@ __device__ __forceinline__ void mat_remap_cell(const Fields<R> &F, DevScalars *S
       iedrop += me[km];
     }
   }
-  const double imkeep = 1.0 / mkeep, ivkeep = 1.0 / vkeep;
+  const double imkeep = mkeep == m1 ? r1 : 1.0 / mkeep, ivkeep = 1.0 / vkeep;
   double msum = 0.0, iesum = 0.0;
   for (int km = 0; km < F.nmat; ++km) {
     const long long ia = 3ll * km * nc + c;
@@ -549,7 +559,7 @@ __device__ __forceinline__ void mat_remap_cell(const Fields<R> &F, DevScalars *S
     }
   }
   if (!(msum > 0.0)) set_status(S, msum != msum ? SALE_ENAN : SALE_ENEGVOL);
-  const double r = 1.0 / msum;
+  const double r = msum == m1 ? r1 : 1.0 / msum;
   F.m[c] = (R)msum;
   F.e[c] = (R)(iesum * r);
   if (F.im) F.im[c] = (R)r;

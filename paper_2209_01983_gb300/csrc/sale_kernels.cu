@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_eos_dt(Fields<R> F, Dev
     const double rho = m * iv;
     double p, cs2;
     if constexpr (MAT) {
-      mixture_eos(F, c, V, m, p, cs2);
+      mixture_eos(F, c, V, iv, (double)F.im[c], p, cs2);
     } else {
       p = (F.gamma - 1.0) * rho * e;
       cs2 = F.gamma * (F.gamma - 1.0) * max0_d(e);
@@ -473,19 +473,9 @@ __global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F
   double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
   if (F.fh) e1 -= h / m * work_hg;
   if constexpr (MAT) {
-    const double V0 = (double)F.vol[c], qc = (double)F.q[c];
+    const double V0 = (double)F.vol[c], qc = (double)F.q[c], iv0 = 1.0 / V0;
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) {
-      const long long ia = 3ll * km * F.nc + c;
-      const double a = (double)F.mat[ia];
-      if (!(a > 0.0)) continue;
-      const double mk = (double)F.mat[ia + F.nc];
-      double ek = (double)F.mat[ia + 2 * F.nc];
-      const double pk = mat_pressure(F, km, mk / (a * V0), ek);
-      ek -= h / mk * (a * (pk + qc)) * work;
-      F.mat[ia + 2 * F.nc] = (R)ek;
-      ie += mk * ek;
-    }
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, iv0, qc, h, work);
     e1 = ie / m;
   }
   P3 X[8];
