@@ -214,6 +214,7 @@ def materials_table(base: dict, nmat: int, path: str = "general") -> dict:
     t = dict(base)
     if path == "ale":
         extra = {"ale_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
+                 "ale_density": (8, 1),  # 1 / V_L written for the flux pass
                  "ale_fluxes": (8 * (12 * nmat + 1), 18 * nmat),
                  "ale_remap_eos": (8 * (15 * nmat - 6 + 2), 53 * nmat - 21)}
     else:

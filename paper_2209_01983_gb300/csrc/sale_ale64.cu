@@ -309,7 +309,7 @@ __global__ void __launch_bounds__(kBlock) k_ale_density(Fields<double> F, DevSca
   if (!pos_d(VL)) set_status(S, nan_d(VL) ? SALE_ENAN : SALE_ENEGVOL);  // a NaN with the sign clear: caught by the EoS
   F.vol[c] = VL;
   F.rho[c] = F.m[c] / VL;
-  if (F.remap_order == 2) F.ivl[c] = 1.0 / VL;  // the six faces' swept fractions multiply by it
+  if (F.ivl) F.ivl[c] = 1.0 / VL;  // second-order remap and materials: the face fluxes multiply by it
 }
 
 // Limited slopes of the Lagrangian density and the specific energy along
@@ -357,11 +357,11 @@ __device__ __forceinline__ double ale_donor_flux(const Fields<double> &F, const 
 // Materials: the donor dn's share of the swept volume v for every material
 // -- volume alpha_k v, mass (m_k / V_L) v, energy that mass times e_k --
 // stored at o + 9 k nc (+ nc, + 2 nc); returns the total mass flux, ef the
-// total energy flux.  One division per face (1 / V_L).
+// total energy flux.  1 / V_L comes from the density pass (no division).
 __device__ __forceinline__ double ale_mat_flux(const Fields<double> &F, long long dn, double v, double &ef,
                                                double *o) {
   const long long nc = F.nc;
-  const double sv = v / F.vol[dn];
+  const double sv = v * F.ivl[dn];
   double mu = 0.0, e = 0.0;
   for (int km = 0; km < F.nmat; ++km) {
     const long long ia = 3ll * km * nc + dn;

@@ -324,6 +324,8 @@ static size_t carve(sale_state *st, char *base) {
     st->Gn = (double *)cv.take(sizeof(double) * 24 * nc);
     if (st->o2)
       for (int d = 0; d < 7; ++d) st->slope[d] = (double *)cv.take(sizeof(double) * nc);
+    else if (st->nmat >= 2)  // materials: 1 / V_L for the flux pass
+      st->slope[6] = (double *)cv.take(sizeof(double) * nc);
     if (st->hg) st->geoHG = (double *)cv.take(sizeof(double) * 32 * nc);
     if (st->str) {
       st->sdev = (double *)cv.take(sizeof(double) * 9 * nc);

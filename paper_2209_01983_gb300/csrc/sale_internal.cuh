@@ -179,7 +179,7 @@ struct Fields {
   R *kd;
   double cfl, c_q, c_l, c_hg;
   R *srx, *sry, *srz, *sex, *sey, *sez;  // FP64 Eulerian path: slopes of rho_L and e along x, y, z
-  R *ivl;                      // FP64 Eulerian path, second-order remap: 1 / V_L
+  R *ivl;                      // FP64 Eulerian path, second-order remap or materials: 1 / V_L (null otherwise)
   int remap_sets_x;            // node remap writes the reference positions to x
   // Materials (FP64 general path, nmat >= 2; null mat: one ideal gas):
   // mat[(3 k + q) nc + c] holds material k's volume fraction (q = 0), mass
