@@ -91,6 +91,31 @@ def test_two_material_sedov_against_oracle(sale, remap_every, cycles):
     assert st.diagnostics()["dt"] == pytest.approx(o.s.dt, rel=1e-10)
 
 
+def test_explicit_steps_then_eulerian_cycles(sale):
+    """Explicit Lagrangian steps with given dt and remaps (general kernels),
+    then Eulerian cycles from the reference mesh (cached-geometry kernels):
+    the two kernel sets hand the material state to each other."""
+    md = inputs.MeshDesc(14, 12, 10, lo=(0.0, 0.0, 0.0), hi=(1.2, 1.2, 1.2), jitter=0.1)
+    _, pd = inputs.sedov_octant(8)
+    pd = mat_problem(pd, (1.4, 3.0), (0.0, 1e-5), x_split=0.2)
+    st = sale.State(md, pd)
+    o = oracle.Oracle.from_problem(md, pd)
+    for it in range(6):
+        dt = 2e-4 * (1 + it)
+        st.lagrange_step(dt)
+        o.check(o.lagrange_step(dt))
+        if it % 2 == 1:
+            st.remap_step()
+            o.check(o.remap_step())
+    compare(st, o)
+    compare_materials(st, o, 2)
+    assert st.run_to_time(max_cycles=20, remap_every=1) == 20
+    rc, n = o.run(max_cycles=20, remap_every=1)
+    assert rc == 0 and n == 20
+    compare(st, o)
+    compare_materials(st, o, 2)
+
+
 def test_three_materials_from_uploaded_fractions(sale):
     """Fractions, masses and energies uploaded through sale_set_field (a
     random mixture of three materials, two of them stiffened, at one
