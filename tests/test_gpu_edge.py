@@ -2,7 +2,7 @@
 slabs and lines (every node on a wall, tiles that are all tail).
 
 FP64 against the oracle at 1e-10 (Lagrange and Eulerian cycles, with and
-without the scheme options); FP32-mixed against FP64 (L1 <= 1e-4); a batch
+without the scheme options, with strength and with two materials); FP32-mixed against FP64 (L1 <= 1e-4); a batch
 of degenerate meshes bitwise against each mesh alone.
 """
 import dataclasses
@@ -46,6 +46,38 @@ def test_fp64_matches_oracle(sale, dims, remap_every, opts):
     rc, n = o.run(max_cycles=25, remap_every=remap_every)
     assert rc == 0 and n == 25
     compare(st, o)
+
+
+STRENGTH = dict(shear0=0.05, shear_dp=0.3, shear_dt=-0.01, cv=1.0, rho_ref=1.0, yield0=2e-3, yield_max=1e-2,
+                hard_beta=20.0, hard_n=0.3)
+
+
+@pytest.mark.parametrize("dims", DIMS)
+@pytest.mark.parametrize("remap_every,kind", [(1, "strength"), (0, "strength"), (1, "materials"), (0, "materials"),
+                                              (3, "materials")])
+def test_fp64_options_on_degenerate_meshes(sale, dims, remap_every, kind):
+    from test_gpu_multimat import compare_materials
+    md, pd = problem(dims)
+    if kind == "strength":
+        pd = dataclasses.replace(pd, **STRENGTH)
+    else:  # material 1 from the middle of the box on (the whole box when it is one cell wide)
+        pd = dataclasses.replace(pd, nmat=2, mat_gamma=(1.4, 3.0, 1.4, 1.4), mat_pinf=(0.0, 1e-6, 0.0, 0.0),
+                                 x_split=0.05 * dims[0])
+    st = sale.State(md, pd)
+    assert st.run_to_time(max_cycles=25, remap_every=remap_every) == 25
+    o = oracle.Oracle.from_problem(md, pd)
+    rc, n = o.run(max_cycles=25, remap_every=remap_every)
+    assert rc == 0 and n == 25
+    compare(st, o)
+    if kind == "materials":
+        compare_materials(st, o, 2)
+    else:  # the stress normwise over its six components, the plastic strain on its own scale
+        comps = ("sxx", "syy", "szz", "sxy", "syz", "szx")
+        scale = max(float(np.max(np.abs(o.field(f)))) for f in comps)
+        for f in comps:
+            assert float(np.max(np.abs(st.field(f) - o.field(f)))) <= 1e-10 * scale, f  # 0 on both: one cell
+        ep = o.field("eps_p")
+        assert float(np.max(np.abs(st.field("eps_p") - ep))) <= 1e-10 * float(np.max(ep))
 
 
 @pytest.mark.parametrize("dims", DIMS)
