@@ -116,29 +116,30 @@ def test_explicit_steps_then_eulerian_cycles(sale):
     compare_materials(st, o, 2)
 
 
-def test_three_materials_from_uploaded_fractions(sale):
+@pytest.mark.parametrize("nmat", [3, 4])
+def test_materials_from_uploaded_fractions(sale, nmat):
     """Fractions, masses and energies uploaded through sale_set_field (a
-    random mixture of three materials, two of them stiffened, at one
+    random mixture of three or four materials, some stiffened, at one
     pressure) drive the following Eulerian cycles exactly as the oracle's
     set_materials does."""
     md = inputs.MeshDesc(14, 12, 10, lo=(0.0, 0.0, 0.0), hi=(1.2, 1.2, 1.2), jitter=0.1)
     _, pd = inputs.sedov_octant(8)
-    gam, pinf, rho = (1.4, 3.0, 2.2), (0.0, 0.2, 0.05), (1.0, 2.0, 4.0)
+    gam, pinf, rho = (1.4, 3.0, 2.2, 5.0 / 3.0)[:nmat], (0.0, 0.2, 0.05, 0.0)[:nmat], (1.0, 2.0, 4.0, 0.5)[:nmat]
     pd = mat_problem(pd, gam, pinf)
     st = sale.State(md, pd)
     o = oracle.Oracle.from_problem(md, pd)
     rng = np.random.default_rng(2209)
-    w = rng.random((3, md.ncell)) * (rng.random((3, md.ncell)) > 0.3) + 1e-3
+    w = rng.random((nmat, md.ncell)) * (rng.random((nmat, md.ncell)) > 0.3) + 1e-3
     alpha = w / w.sum(axis=0)
     vol = o.field("vol")
     # one pressure in every material of a cell: 0.5 in the 3x3x3 corner block, 1e-3 elsewhere
     cell = np.arange(md.ncell)
     i, j, k3 = cell % md.nx, (cell // md.nx) % md.ny, cell // (md.nx * md.ny)
     p = np.where((i < 3) & (j < 3) & (k3 < 3), 0.5, 1e-3)
-    mm = [alpha[k] * rho[k] * vol for k in range(3)]
-    me = [(p + gam[k] * pinf[k]) / ((gam[k] - 1.0) * rho[k]) for k in range(3)]
+    mm = [alpha[k] * rho[k] * vol for k in range(nmat)]
+    me = [(p + gam[k] * pinf[k]) / ((gam[k] - 1.0) * rho[k]) for k in range(nmat)]
     assert o.set_materials(list(alpha), mm, me) == 0
-    for k in range(3):
+    for k in range(nmat):
         st.set_field(f"alpha{k}", alpha[k])
         st.set_field(f"m{k}", mm[k])
         st.set_field(f"e{k}", me[k])
@@ -162,7 +163,7 @@ def test_three_materials_from_uploaded_fractions(sale):
     rc, n = o.run(max_cycles=30, remap_every=1)
     assert rc == 0 and n == 30
     compare(st, o)
-    compare_materials(st, o, 3)
+    compare_materials(st, o, nmat)
 
 
 def test_identical_materials_equal_one_gas_on_the_gpu(sale):
