@@ -511,11 +511,11 @@ int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
 }
 
 /* The materials of the multi-material scheme (R18) take neither strength
- * nor the second-order options. */
+ * nor the second-order options (hourglass control, yes). */
 static int mm_options_ok(const oracle_state *s) {
   const oracle_params *p = &s->prm;
   if (p->nmat < 2 || p->nmat > ORACLE_MAX_MAT) return 0;
-  if (strength_on(s) || p->time_order == 2 || p->c_hg > 0.0 || p->remap_order == 2) return 0;
+  if (strength_on(s) || p->time_order == 2 || p->remap_order == 2) return 0;
   for (int k = 0; k < p->nmat; ++k)
     if (!(p->mat_gamma[k] > 1.0) || !(p->mat_pinf[k] >= 0.0) || isinf(p->mat_gamma[k]) || isinf(p->mat_pinf[k]))
       return 0;
@@ -784,7 +784,9 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
           /* uniform strain (R18): each material takes the cell's volume
            * change in proportion to its fraction, so material k does the
            * share alpha_k (p_k + q) of the cell's sigma work; the sum over
-           * k is the cell's work since sum_k alpha_k p_k = p */
+           * k is the cell's work since sum_k alpha_k p_k = p.  The
+           * hourglass forces' work, a dissipation like q's, is shared by
+           * fraction too. */
           const double V0 = s->vol[c];
           double ie = 0.0;
           for (int kk = 0; kk < s->prm.nmat; ++kk) {
@@ -793,7 +795,7 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
             if (!(a > 0.0)) continue;
             const double mk = s->mm[kc];
             const double pk = mat_pressure(s, kk, mk / (a * V0), s->me[kc]);
-            s->me[kc] -= dt / mk * (a * (pk + s->q[c])) * work;
+            s->me[kc] -= dt / mk * (a * (pk + s->q[c]) * work + (hg ? a * work_hg : 0.0));
             ie += mk * s->me[kc];
           }
           e_new[c] = ie / s->m[c];

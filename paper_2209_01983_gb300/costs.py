@@ -232,8 +232,8 @@ def materials_table(base: dict, nmat: int, path: str = "general") -> dict:
 def table(precision: str, path: str = "ale", jitter: bool = True, order: int = 1, time_order: int = 1,
           hourglass: bool = False, strength: bool = False, nmat: int = 0):
     if precision == "fp64":
-        if nmat >= 2:  # the same kernels with materials
-            return materials_table(FP64_ALE if path == "ale" else FP64, nmat, path)
+        if nmat >= 2:  # the same kernels with materials (and hourglass control when asked)
+            return materials_table(table(precision, path, jitter, order, time_order, hourglass), nmat, path)
         if strength:  # the same kernels with the stress module
             base = table(precision, path, jitter, order, time_order, hourglass)
             return {k: (u, b + FP64_STRENGTH_EXTRA.get(k, (0, 0))[0], f + FP64_STRENGTH_EXTRA.get(k, (0, 0))[1])

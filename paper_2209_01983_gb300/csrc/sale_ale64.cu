@@ -228,8 +228,8 @@ __global__ void __launch_bounds__(kBlock, STR ? 2 : (MAT ? 3 : 4)) k_ale_cells(F
   }
   const double im = F.im[c];
   double e1 = F.e[c] - h * im * F.sig[c] * work;
+  double work_hg = 0.0;
   if (F.fh) {
-    double work_hg = 0.0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), ub[a]);
     e1 -= h * im * work_hg;
@@ -273,7 +273,7 @@ __global__ void __launch_bounds__(kBlock, STR ? 2 : (MAT ? 3 : 4)) k_ale_cells(F
   if constexpr (MAT) {  // x^n is the reference mesh
     const double qc = F.q[c];
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, F.VE[c], F.iVE[c], qc, h, work);
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, F.VE[c], F.iVE[c], qc, h, work, work_hg);
     e1 = ie * im;
   }
   F.e[c] = e1;
@@ -642,6 +642,8 @@ __global__ void __launch_bounds__(kBlock) k_geo_init_hg(Fields<double> F, double
 // n: q_alpha = sum_a gamma_alpha(a) u_a, f_a = -kappa sum_alpha
 // gamma_alpha(a) q_alpha, kappa = c_hg rho cs V^(2/3), with the cached
 // scaled shape vectors (k_geo_init_hg).
+// MAT: several materials, the mixture's sound speed (stored by the EoS) in kappa.
+template <bool MAT>
 __global__ void __launch_bounds__(kBlock, 2) k_ale_hourglass(Fields<double> F, DevScalars *S) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
@@ -657,7 +659,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_hourglass(Fields<double> F, D
 #pragma unroll
     for (int al = 0; al < 4; ++al) q[al] = a == 0 ? hg[(8ll * al) * nc] * u : q[al] + hg[(8ll * al + a) * nc] * u;
   }
-  const double kappa = F.c_hg * F.rho[c] * sqrt(F.gamma * (F.gamma - 1.0) * fmax(F.e[c], 0.0));
+  const double cs = MAT ? F.cs[c] : sqrt(F.gamma * (F.gamma - 1.0) * fmax(F.e[c], 0.0));
+  const double kappa = F.c_hg * F.rho[c] * cs;
 #pragma unroll
   for (int al = 0; al < 4; ++al) q[al] = -kappa * q[al];
 #pragma unroll
@@ -875,7 +878,10 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
       break;
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
-    case kAleHourglass: k_ale_hourglass<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S); break;
+    case kAleHourglass:
+      if (F.mat) k_ale_hourglass<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      else k_ale_hourglass<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
+      break;
     case kAleCells:
       if (F.mat) k_ale_cells<false, true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       else if (F.sdev) k_ale_cells<true, false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);

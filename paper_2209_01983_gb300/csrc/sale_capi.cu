@@ -517,10 +517,9 @@ static int validate_problem(const sale_problem_desc &p) {
       if (!(p.mat_gamma[k] > 1.0) || !std::isfinite(p.mat_gamma[k]) || !(p.mat_pinf[k] >= 0.0) ||
           !std::isfinite(p.mat_pinf[k]))
         return fail(SALE_EINVAL, "problem: material %d needs mat_gamma > 1 and a finite mat_pinf >= 0", k);
-    if (p.time_order == 2 || p.c_hg > 0.0 || p.shear0 > 0.0 || p.remap_order == 2)
-      return fail(SALE_EINVAL,
-                  "problem: materials take the single-stage step and the first-order remap, without hourglass "
-                  "control or strength");
+    if (p.time_order == 2 || p.shear0 > 0.0 || p.remap_order == 2)
+      return fail(SALE_EINVAL, "problem: materials take the single-stage step and the first-order remap, without "
+                               "strength");
   }
   if (p.shear0 > 0.0) {
     const double fin[] = {p.shear_dp, p.shear_dt, p.e_ref, p.yield0, p.yield_max, p.hard_beta, p.hard_n};

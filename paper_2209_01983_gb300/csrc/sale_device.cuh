@@ -462,12 +462,13 @@ __device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, dou
 }
 
 // The cell pass's share of the compatible work for material k of cell c
-// (uniform strain): e_k -= dt alpha_k (p_k + q) W / m_k, with W = sum_a
-// dV/dx_a . ubar_a and p_k at the state of x^n (volume V0, iv0 = 1/V0);
-// returns m_k e_k of the new state (0 for an absent material).
+// (uniform strain): e_k -= dt alpha_k ((p_k + q) W + W_hg) / m_k, with W =
+// sum_a dV/dx_a . ubar_a, W_hg the hourglass forces' work (0 without
+// control) and p_k at the state of x^n (volume V0, iv0 = 1/V0); returns
+// m_k e_k of the new state (0 for an absent material).
 template <typename R>
 __device__ __forceinline__ double mat_work_share(const Fields<R> &F, long long c, int k, double V0, double iv0,
-                                                 double q, double h, double work) {
+                                                 double q, double h, double work, double work_hg) {
   const long long ia = 3ll * k * F.nc + c;
   const double a = (double)F.mat[ia];
   if (!(a > 0.0)) return 0.0;
@@ -475,7 +476,7 @@ __device__ __forceinline__ double mat_work_share(const Fields<R> &F, long long c
   double ek = (double)F.mat[ia + 2 * F.nc];
   const double g = F.mgam[k];
   const double apk = (g - 1.0) * (mk * ek) * iv0 - g * F.mpinf[k] * a;  // alpha_k p_k
-  ek -= h * (apk + a * q) * work / mk;
+  ek -= h * ((apk + a * q) * work + a * work_hg) / mk;
   F.mat[ia + 2 * F.nc] = (R)ek;
   return mk * ek;
 }

@@ -263,8 +263,9 @@ __global__ void __launch_bounds__(kBlock) k_hourglass(Fields<R> F, DevScalars *S
   } else {
     hex_grad_shifted(X, G);
   }
-  // cs from e: the Eulerian kernels do not store it
-  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax((double)F.e[c], 0.0));
+  // cs from e (the Eulerian kernels do not store it); with materials the
+  // mixture's, stored by the EoS
+  const double cs = F.mat ? (double)F.cs[c] : sqrt(F.gamma * (F.gamma - 1.0) * fmax((double)F.e[c], 0.0));
   hourglass_store(X, G, U, (double)F.vol[c], (double)F.rho[c], cs, F.c_hg, F.fh, F.nc, c);
 }
 
@@ -475,7 +476,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F
   if constexpr (MAT) {
     const double V0 = (double)F.vol[c], qc = (double)F.q[c], iv0 = 1.0 / V0;
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, iv0, qc, h, work);
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, iv0, qc, h, work, work_hg);
     e1 = ie / m;
   }
   P3 X[8];

@@ -25,6 +25,7 @@ def test_every_cost_entry_is_a_library_kernel(names):
             assert unit in ("cell", "node") and b > 0 and f >= 0, k
     assert not sorted(k for k in costs.table("fp64", "general") if k not in names)
     # several materials: the general kernels, each entry at least its single-material cost
+    assert "ale_hourglass" in costs.table("fp64", "ale", hourglass=True, nmat=2)
     for nmat, path in itertools.product((2, 3, 4), ("general", "ale")):
         t, base = costs.table("fp64", path, nmat=nmat), costs.table("fp64", path)
         assert set(t) == set(base) and not sorted(k for k in t if k not in names)
