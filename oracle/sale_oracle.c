@@ -360,16 +360,18 @@ static double mat_cs2(const oracle_state *s, int k, double rho, double e) {
 /* Mixed cell c of volume V and mass m: the materials present (alpha_k > 0)
  * have density rho_k = m_k / (alpha_k V); the cell pressure is
  * sum_k alpha_k p_k and the squared sound speed the mass-weighted
- * sum_k m_k c_k^2 / m. */
-static void mixture_eos(const oracle_state *s, long long c, double V, double m, double *p, double *cs2) {
+ * sum_k m_k c_k^2 / m.  me holds the materials' specific energies
+ * ([k * nc + c]: the state's, or the predictor's half-step ones). */
+static void mixture_eos(const oracle_state *s, long long c, double V, double m, const double *me, double *p,
+                        double *cs2) {
   double ps = 0.0, cm = 0.0;
   for (int k = 0; k < s->prm.nmat; ++k) {
     const long long kc = k * s->nc + c;
     const double a = s->alpha[kc];
     if (!(a > 0.0)) continue;
     const double rk = s->mm[kc] / (a * V);
-    ps += a * mat_pressure(s, k, rk, s->me[kc]);
-    cm += s->mm[kc] * mat_cs2(s, k, rk, s->me[kc]);
+    ps += a * mat_pressure(s, k, rk, me[kc]);
+    cm += s->mm[kc] * mat_cs2(s, k, rk, me[kc]);
   }
   *p = ps;
   *cs2 = cm / m;
@@ -388,11 +390,11 @@ static void mm_totals(oracle_state *s, long long c) {
 
 /* EoS (R2), sound speed and artificial viscosity (R3) of cell c with node
  * positions X and velocities U (24 values each), mass m and specific
- * internal energy e (with materials, the EoS is the mixture's, R18).
- * Returns a status. */
+ * internal energy e (with materials, the EoS is the mixture's of the
+ * material energies me, R18).  Returns a status. */
 static int cell_state(const oracle_state *s, long long c, const double *X, const double *U, double m, double e,
-                      double *V_out, double *rho_out, double *p_out, double *q_out, double *cs_out,
-                      double *L_out) {
+                      const double *me, double *V_out, double *rho_out, double *p_out, double *q_out,
+                      double *cs_out, double *L_out) {
   const double g = s->prm.gamma;
   double G[24];
   double V = oracle_hex_volume(X);
@@ -401,7 +403,7 @@ static int cell_state(const oracle_state *s, long long c, const double *X, const
   double p, cs;
   if (mm_on(s)) {
     double cs2;
-    mixture_eos(s, c, V, m, &p, &cs2);
+    mixture_eos(s, c, V, m, me, &p, &cs2);
     cs = sqrt(cs2);
   } else {
     p = (g - 1.0) * rho * e;
@@ -437,7 +439,7 @@ int oracle_eos(oracle_state *s) {
         double X[24], U[24];
         gather_hex(s, i, j, k, s->x, s->y, s->z, X);
         gather_hex(s, i, j, k, s->u, s->v, s->w, U);
-        int rc = cell_state(s, c, X, U, s->m[c], s->e[c], &s->vol[c], &s->rho[c], &s->p[c], &s->q[c],
+        int rc = cell_state(s, c, X, U, s->m[c], s->e[c], s->me, &s->vol[c], &s->rho[c], &s->p[c], &s->q[c],
                             &s->cs[c], &s->len[c]);
         if (rc) return s->status = rc;
       }
@@ -511,11 +513,12 @@ int oracle_init_prim(oracle_state *s, const double *rho0, const double *p0,
 }
 
 /* The materials of the multi-material scheme (R18) take neither strength
- * nor the second-order options (hourglass control, yes). */
+ * nor the second-order remap (the predictor-corrector and hourglass
+ * control, yes). */
 static int mm_options_ok(const oracle_state *s) {
   const oracle_params *p = &s->prm;
   if (p->nmat < 2 || p->nmat > ORACLE_MAX_MAT) return 0;
-  if (strength_on(s) || p->time_order == 2 || p->remap_order == 2) return 0;
+  if (strength_on(s) || p->remap_order == 2) return 0;
   for (int k = 0; k < p->nmat; ++k)
     if (!(p->mat_gamma[k] > 1.0) || !(p->mat_pinf[k] >= 0.0) || isinf(p->mat_gamma[k]) || isinf(p->mat_pinf[k]))
       return 0;
@@ -664,10 +667,14 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
   const int hg = s->prm.c_hg > 0.0;
   double *fh = hg ? alloc_zero(24 * nc) : NULL;
   double *s_new = str ? alloc_zero(7 * nc) : NULL;  /* S (6) and eps_p at n+1 */
+  /* materials with the predictor: half-step specific energies, and each
+   * material's half-step share alpha_k (p_k + q) of the cell's sigma */
+  const int mmpc = mm && pc;
+  double *meh = mmpc ? alloc_zero(s->prm.nmat * nc) : NULL, *share = mmpc ? alloc_zero(s->prm.nmat * nc) : NULL;
   if (!fx || !fy || !fz || !ubx || !uby || !ubz || !e_new || !sig || !xh || !yh || !zh || (hg && !fh) ||
-      (str && !s_new)) {
+      (str && !s_new) || (mmpc && (!meh || !share))) {
     free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-    free(xh); free(yh); free(zh); free(fh); free(s_new);
+    free(xh); free(yh); free(zh); free(fh); free(s_new); free(meh); free(share);
     return s->status = ORACLE_ENOMEM;
   }
 
@@ -706,15 +713,31 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
             for (int a = 0; a < 8; ++a) work_hg += dot3(&fh[24 * c + a * 3], &U[a * 3]);
           double e_half = s->e[c] - 0.5 * dt / s->m[c] * sig[c] * work;
           if (hg) e_half -= 0.5 * dt / s->m[c] * work_hg;
+          if (mmpc)  /* each material's half step, its share of the work as in the corrector below */
+            for (int kk = 0; kk < s->prm.nmat; ++kk) {
+              const long long kc = kk * nc + c;
+              const double a = s->alpha[kc];
+              meh[kc] = 0.0;
+              if (!(a > 0.0)) continue;
+              const double mk = s->mm[kc];
+              const double pk = mat_pressure(s, kk, mk / (a * s->vol[c]), s->me[kc]);
+              meh[kc] = s->me[kc] - 0.5 * dt / mk * (a * (pk + s->q[c]) * work + (hg ? a * work_hg : 0.0));
+            }
           gather_hex(s, i, j, k, xh, yh, zh, XH);
           double V, rho, p, q, cs, L;
-          int rc = cell_state(s, c, XH, U, s->m[c], e_half, &V, &rho, &p, &q, &cs, &L);
+          int rc = cell_state(s, c, XH, U, s->m[c], e_half, meh, &V, &rho, &p, &q, &cs, &L);
           if (rc) {
             free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-            free(xh); free(yh); free(zh); free(fh);
+            free(xh); free(yh); free(zh); free(fh); free(meh); free(share);
             return s->status = rc;
           }
           e_new[c] = p + q;  /* sigma^{n+1/2}, moved into sig below */
+          if (mmpc)
+            for (int kk = 0; kk < s->prm.nmat; ++kk) {
+              const long long kc = kk * nc + c;
+              const double a = s->alpha[kc];
+              share[kc] = a > 0.0 ? a * (mat_pressure(s, kk, s->mm[kc] / (a * V), meh[kc]) + q) : 0.0;
+            }
         }
     memcpy(sig, e_new, sizeof(double) * (size_t)nc);
     gx = xh;
@@ -794,8 +817,9 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
             const double a = s->alpha[kc];
             if (!(a > 0.0)) continue;
             const double mk = s->mm[kc];
-            const double pk = mat_pressure(s, kk, mk / (a * V0), s->me[kc]);
-            s->me[kc] -= dt / mk * (a * (pk + s->q[c]) * work + (hg ? a * work_hg : 0.0));
+            /* the predictor-corrector's share is that of the half step */
+            const double sh = pc ? share[kc] : a * (mat_pressure(s, kk, mk / (a * V0), s->me[kc]) + s->q[c]);
+            s->me[kc] -= dt / mk * (sh * work + (hg ? a * work_hg : 0.0));
             ie += mk * s->me[kc];
           }
           e_new[c] = ie / s->m[c];
@@ -839,7 +863,7 @@ int oracle_lagrange_step(oracle_state *s, double dt) {
       s->eps_p[c] = s_new[7 * c + 6];
     }
   free(fx); free(fy); free(fz); free(ubx); free(uby); free(ubz); free(e_new); free(sig);
-  free(xh); free(yh); free(zh); free(fh); free(s_new);
+  free(xh); free(yh); free(zh); free(fh); free(s_new); free(meh); free(share);
 
   s->t += dt;
   s->dt_last = dt;
