@@ -214,6 +214,8 @@ def materials_table(base: dict, nmat: int, path: str = "general") -> dict:
     t = dict(base)
     if path == "ale":
         extra = {"ale_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
+                 # predictor-corrector: the materials' half step, their shares written
+                 "ale_predict": (8 * 4 * nmat, 20 * nmat),
                  "ale_density": (8, 1),  # 1 / V_L written for the flux pass
                  "ale_fluxes": (8 * (12 * nmat + 1), 18 * nmat),
                  "ale_remap_eos": (8 * (15 * nmat - 6 + 2), 53 * nmat - 21)}
@@ -222,6 +224,8 @@ def materials_table(base: dict, nmat: int, path: str = "general") -> dict:
                  "lagrange_cells": (8 * (4 * nmat + 1), 15 * nmat + 1),
                  "remap_faces": (8 * (3 * nmat + 1 + 9 * nmat), 18 * nmat)}
     for k, (db, df) in extra.items():
+        if k not in t:  # an option's kernel the run does not launch
+            continue
         u, b, f = t[k]
         t[k] = (u, b + db, f + df)
     if path != "ale":

@@ -273,7 +273,8 @@ __global__ void __launch_bounds__(kBlock, STR ? 2 : (MAT ? 3 : 4)) k_ale_cells(F
   if constexpr (MAT) {  // x^n is the reference mesh
     const double qc = F.q[c];
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, F.VE[c], F.iVE[c], qc, h, work, work_hg);
+    for (int km = 0; km < F.nmat; ++km)
+      ie += mat_work_share(F, c, km, F.VE[c], F.iVE[c], qc, h, work, work_hg, F.time_order == 2);
     e1 = ie * im;
   }
   F.e[c] = e1;
@@ -678,6 +679,9 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_hourglass(Fields<double> F, D
 // cached gradient and u^n, then the EoS and viscosity on x_ref + dt/2 u^n.
 // sigma^{n+1/2} replaces sigma; the corner gradients at x^{n+1/2} go to Gh
 // for the corrector's node and cell passes.
+// MAT: several materials (see mat_predict); their half-step shares of
+// sigma are kept for the corrector's cell pass.
+template <bool MAT>
 __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, DevScalars *S, double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
@@ -719,8 +723,16 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
     dvdt += dot(g, P3{F.u[n], F.v[n], F.w[n]});
   }
   const double rho = m / V;
-  const double p = (F.gamma - 1.0) * rho * e;
-  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  double p, cs;
+  double aph[kMaxMat];
+  if constexpr (MAT) {  // x^n is the reference mesh
+    double cs2;
+    mat_predict(F, c, F.iVE[c], F.q[c], 0.5 * h, work, work_hg, V, 1.0 / V, F.im[c], aph, p, cs2);
+    cs = sqrt(cs2);
+  } else {
+    p = (F.gamma - 1.0) * rho * e;
+    cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  }
   // L div = (V / max_f |A_f / 2|) (dvdt / V) = 2 dvdt / sqrt(max_f |A_f|^2)
   double q = 0.0;
   if (dvdt < 0.0) {
@@ -728,6 +740,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_ale_predict(Fields<double> F, Dev
     q = rho * (F.c_q * ld * ld + F.c_l * cs * fabs(ld));
   }
   F.sig[c] = p + q;
+  if constexpr (MAT) mat_store_shares(F, c, aph, q);
 }
 
 // Cell remap + EoS of cell c; returns its CFL rate 1 / dt_c^2 (0 outside
@@ -877,7 +890,10 @@ void launch_ale_kernel(int kid, const Fields<double> &F, DevScalars *S, double d
       else k_ale_nodes<false><<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override);
       break;
     case kAleEdges: k_ale_edges<<<grid_ale(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
-    case kAlePredict: k_ale_predict<<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kAlePredict:
+      if (F.mat) k_ale_predict<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else k_ale_predict<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      break;
     case kAleHourglass:
       if (F.mat) k_ale_hourglass<true><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);
       else k_ale_hourglass<false><<<grid_ale(F.nc), kBlock, 0, st>>>(F, S);

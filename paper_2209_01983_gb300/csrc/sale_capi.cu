@@ -229,6 +229,7 @@ struct sale_state {
   double *sdev, *sold;                   //   strength: stress, plastic strain, G, Y (9 per cell); remap copy (7)
   double *Gn;                            //   corner gradients at the current positions (24 per cell)
   double *mat, *mfx;                     //   materials: fraction, mass, energy (3 per material per cell); face fluxes (9)
+  double *msh;                           //   materials with the predictor-corrector: half-step shares (1 per material)
   double *ste, *mq[3], *kd;              // FP64 path: Eulerian-cycle working arrays
   double *relE;                          // FP64 path: reference offsets to 6 neighbours (18 per node)
   double *slope[7];                      // FP64 path, second-order remap: slopes of rho_L and e along x, y, z; 1/V_L
@@ -296,7 +297,7 @@ static size_t carve(sale_state *st, char *base) {
   st->im = st->imn = nullptr;
   st->sdev = st->sold = nullptr;
   st->Gn = nullptr;
-  st->mat = st->mfx = nullptr;
+  st->mat = st->mfx = st->msh = nullptr;
   st->ste = st->kd = st->mq[0] = st->mq[1] = st->mq[2] = nullptr;
   st->relE = nullptr;
   for (int d = 0; d < 7; ++d) st->slope[d] = nullptr;
@@ -334,6 +335,7 @@ static size_t carve(sale_state *st, char *base) {
     if (st->nmat >= 2) {
       st->mat = (double *)cv.take(sizeof(double) * 3 * (size_t)st->nmat * nc);
       st->mfx = (double *)cv.take(sizeof(double) * 9 * (size_t)st->nmat * nc);
+      if (st->pc) st->msh = (double *)cv.take(sizeof(double) * (size_t)st->nmat * nc);
     }
   } else {
     st->off4 = (float4 *)cv.take(sizeof(float4) * nn);
@@ -453,6 +455,7 @@ static Fields<R> fields_t(const sale_state *st) {
   for (int f = 0; f < 6; ++f) F.reflect[f] = st->reflect[f];
   F.mat = (R *)st->mat;
   F.mfx = (R *)st->mfx;
+  F.msh = (R *)st->msh;
   F.nmat = st->nmat;
   for (int k = 0; k < kMaxMat; ++k) {
     F.mgam[k] = st->prob.mat_gamma[k];
@@ -517,9 +520,8 @@ static int validate_problem(const sale_problem_desc &p) {
       if (!(p.mat_gamma[k] > 1.0) || !std::isfinite(p.mat_gamma[k]) || !(p.mat_pinf[k] >= 0.0) ||
           !std::isfinite(p.mat_pinf[k]))
         return fail(SALE_EINVAL, "problem: material %d needs mat_gamma > 1 and a finite mat_pinf >= 0", k);
-    if (p.time_order == 2 || p.shear0 > 0.0 || p.remap_order == 2)
-      return fail(SALE_EINVAL, "problem: materials take the single-stage step and the first-order remap, without "
-                               "strength");
+    if (p.shear0 > 0.0 || p.remap_order == 2)
+      return fail(SALE_EINVAL, "problem: materials take the first-order remap, without strength");
   }
   if (p.shear0 > 0.0) {
     const double fin[] = {p.shear_dp, p.shear_dt, p.e_ref, p.yield0, p.yield_max, p.hard_beta, p.hard_n};

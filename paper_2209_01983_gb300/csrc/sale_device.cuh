@@ -434,6 +434,43 @@ __device__ __forceinline__ void block_min_dt32_and_finalize(const Fields<R> &F, 
 // Materials (several per cell, FP64 states)
 // ---------------------------------------------------------------------------
 
+// Predictor of the materials (predictor-corrector step): each material's
+// half-step internal energy m_k e_k - dt/2 (alpha_k (p_k + q0) W + alpha_k
+// W_hg), p_k at the state of x^n (volume V0, iv0 = 1/V0, viscosity q0), and
+// the mixture at x^{n+1/2} (volume Vh, ivh = 1/Vh, im = 1/m): p and the
+// mass-weighted c^2 as in mixture_eos; alpha_k p_k of the half step is left
+// in aph[k] (0 for an absent material).
+template <typename R>
+__device__ __forceinline__ void mat_predict(const Fields<R> &F, long long c, double iv0, double q0, double hh,
+                                            double work, double work_hg, double Vh, double ivh, double im,
+                                            double (&aph)[kMaxMat], double &p, double &cs2) {
+  double ps = 0.0, cm = 0.0;
+  for (int k = 0; k < F.nmat; ++k) {
+    const long long ia = 3ll * k * F.nc + c;
+    const double a = (double)F.mat[ia];
+    aph[k] = 0.0;
+    if (!(a > 0.0)) continue;
+    const double ie = (double)F.mat[ia + F.nc] * (double)F.mat[ia + 2 * F.nc];
+    const double g = F.mgam[k], pinf = F.mpinf[k];
+    const double apk = (g - 1.0) * ie * iv0 - g * pinf * a;
+    const double ieh = ie - hh * ((apk + a * q0) * work + a * work_hg);
+    aph[k] = (g - 1.0) * ieh * ivh - g * pinf * a;
+    ps += aph[k];
+    const double mc2 = g * (g - 1.0) * (ieh - pinf * a * Vh);
+    cm += mc2 > 0.0 ? mc2 : 0.0;
+  }
+  p = ps;
+  cs2 = cm * im;
+}
+
+// The predictor's shares alpha_k (p_k + q) of the half step, for the corrector.
+template <typename R>
+__device__ __forceinline__ void mat_store_shares(const Fields<R> &F, long long c, const double (&aph)[kMaxMat],
+                                                 double q) {
+  for (int k = 0; k < F.nmat; ++k)
+    F.msh[k * F.nc + c] = (R)(aph[k] + (double)F.mat[3ll * k * F.nc + c] * q);
+}
+
 // Material k is a stiffened gas: p = (g - 1) rho e - g p_inf, c^2 = g (g - 1)
 // (e - p_inf / rho) floored at 0 (p_inf = 0: ideal gas).
 // Mixed cell c of volume V (iv = 1/V) and mass m (im = 1/m): materials
@@ -462,21 +499,23 @@ __device__ __forceinline__ void mixture_eos(const Fields<R> &F, long long c, dou
 }
 
 // The cell pass's share of the compatible work for material k of cell c
-// (uniform strain): e_k -= dt alpha_k ((p_k + q) W + W_hg) / m_k, with W =
-// sum_a dV/dx_a . ubar_a, W_hg the hourglass forces' work (0 without
-// control) and p_k at the state of x^n (volume V0, iv0 = 1/V0); returns
-// m_k e_k of the new state (0 for an absent material).
+// (uniform strain): e_k -= dt (alpha_k (p_k + q) W + alpha_k W_hg) / m_k,
+// with W = sum_a dV/dx_a . ubar_a, W_hg the hourglass forces' work (0
+// without control) and p_k at the state of x^n (volume V0, iv0 = 1/V0);
+// with the predictor-corrector (pc) alpha_k (p_k + q) is the predictor's,
+// from msh.  Returns m_k e_k of the new state (0 for an absent material).
 template <typename R>
 __device__ __forceinline__ double mat_work_share(const Fields<R> &F, long long c, int k, double V0, double iv0,
-                                                 double q, double h, double work, double work_hg) {
+                                                 double q, double h, double work, double work_hg, bool pc) {
   const long long ia = 3ll * k * F.nc + c;
   const double a = (double)F.mat[ia];
   if (!(a > 0.0)) return 0.0;
   const double mk = (double)F.mat[ia + F.nc];
   double ek = (double)F.mat[ia + 2 * F.nc];
   const double g = F.mgam[k];
-  const double apk = (g - 1.0) * (mk * ek) * iv0 - g * F.mpinf[k] * a;  // alpha_k p_k
-  ek -= h * ((apk + a * q) * work + a * work_hg) / mk;
+  const double sh = pc ? (double)F.msh[k * F.nc + c]
+                       : (g - 1.0) * (mk * ek) * iv0 - g * F.mpinf[k] * a + a * q;  // alpha_k (p_k + q)
+  ek -= h * (sh * work + a * work_hg) / mk;
   F.mat[ia + 2 * F.nc] = (R)ek;
   return mk * ek;
 }

@@ -188,6 +188,7 @@ struct Fields {
   // material's volume (q = 0), mass (1) and energy (2) flux through the
   // cell's low face along axis, written by the face pass of a remap.
   R *mat, *mfx;
+  R *msh;                      // materials with the predictor-corrector: alpha_k (p_k + q) of the half step, msh[k nc + c]
   int nmat;
   double mgam[4], mpinf[4];    // stiffened-gas gamma and p_inf of every material
 };

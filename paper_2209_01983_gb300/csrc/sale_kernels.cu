@@ -284,7 +284,9 @@ __global__ void __launch_bounds__(kBlock) k_pc_positions(Fields<R> F, DevScalars
 // Predictor of every cell: e^{n+1/2} = e^n - dt/(2m) sigma^n sum_a
 // dV/dx_a(x^n).u^n_a, then the EoS and viscosity on x^{n+1/2} with u^n;
 // sigma^{n+1/2} replaces sigma (read only by this cell's thread).
-template <typename R>
+// MAT: several materials, each with its own half-step energy; their
+// half-step shares of sigma are kept for the corrector.
+template <typename R, bool MAT>
 __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalars *S, double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
   if (c >= F.nc || !cycle_active(S)) return;
@@ -306,8 +308,8 @@ __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalar
   for (int a = 0; a < 8; ++a) work += dot(G[a], U[a]);
   const double m = (double)F.m[c];
   double e = (double)F.e[c] - 0.5 * h / m * (double)F.sig[c] * work;
+  double work_hg = 0.0;
   if (F.fh) {
-    double work_hg = 0.0;
 #pragma unroll
     for (int a = 0; a < 8; ++a) work_hg += dot(hourglass_corner(F.fh, F.nc, c, a), U[a]);
     e -= 0.5 * h / m * work_hg;
@@ -321,8 +323,17 @@ __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalar
 #pragma unroll
   for (int a = 0; a < 8; ++a) dvdt += dot(G[a], U[a]);
   const double rho = m / V;
-  const double p = (F.gamma - 1.0) * rho * e;
-  const double cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  double p, cs;
+  double aph[kMaxMat];
+  if constexpr (MAT) {
+    double cs2;
+    mat_predict(F, c, 1.0 / (double)F.vol[c], (double)F.q[c], 0.5 * h, work, work_hg, V, 1.0 / V, (double)F.im[c],
+                aph, p, cs2);
+    cs = sqrt(cs2);
+  } else {
+    p = (F.gamma - 1.0) * rho * e;
+    cs = sqrt(F.gamma * (F.gamma - 1.0) * fmax(e, 0.0));
+  }
   const double div = dvdt / V;
   const double L = V / sqrt(hex_max_face_area2(X));
   double q = 0.0;
@@ -331,6 +342,7 @@ __global__ void __launch_bounds__(kBlock, 2) k_pc_predict(Fields<R> F, DevScalar
     q = rho * (F.c_q * ld * ld + F.c_l * cs * L * fabs(div));
   }
   F.sig[c] = (R)(p + q);
+  if constexpr (MAT) mat_store_shares(F, c, aph, q);
 }
 
 // Lagrangian node pass.  Single stage: corner forces of x^n, new positions
@@ -380,7 +392,9 @@ __global__ void __launch_bounds__(kBlock) k_lagrange_nodes(Fields<R> F, DevScala
   oz[n] = (R)((double)F.z[n] + h * wb);
 }
 
-template <typename R, bool STR>
+// MAT: several materials (the predictor-corrector's corrector: each takes
+// its half-step share of sigma from the predictor).
+template <typename R, bool STR, bool MAT>
 __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_lagrange_cells(Fields<R> F, DevScalars *S,
                                                                        double dt_override) {
   const long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x;
@@ -409,6 +423,12 @@ __global__ void __launch_bounds__(kBlock, STR ? 1 : 2) k_lagrange_cells(Fields<R
   const double m = (double)F.m[c];
   double e1 = (double)F.e[c] - h / m * (double)F.sig[c] * work;
   if (F.fh) e1 -= h / m * work_hg;
+  if constexpr (MAT) {
+    const double V0 = (double)F.vol[c], qc = (double)F.q[c];
+    double ie = 0.0;
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, 1.0 / V0, qc, h, work, work_hg, pc);
+    e1 = ie / m;
+  }
   if constexpr (STR) {
     // the deviatoric forces' work, then the stress at n+1 from the
     // time-centred velocity gradient L = (1/V^n) sum_a ubar_a (x) dV/dx_a and
@@ -476,7 +496,7 @@ __global__ void __launch_bounds__(kBlock, 3) k_lagrange_cells_cached(Fields<R> F
   if constexpr (MAT) {
     const double V0 = (double)F.vol[c], qc = (double)F.q[c], iv0 = 1.0 / V0;
     double ie = 0.0;
-    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, iv0, qc, h, work, work_hg);
+    for (int km = 0; km < F.nmat; ++km) ie += mat_work_share(F, c, km, V0, iv0, qc, h, work, work_hg, false);
     e1 = ie / m;
   }
   P3 X[8];
@@ -863,15 +883,22 @@ void launch_kernel(int kid, const Fields<R> &F, DevScalars *S, int mode, double 
     case kLagCells:
       // materials: a state carries the gradient cache and takes the single-stage step
       if (mat) {
-        if constexpr (kFp64) k_lagrange_cells_cached<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
-      } else if (F.sdev) k_lagrange_cells<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+        if constexpr (kFp64) {
+          if (F.time_order == 2) k_lagrange_cells<R, false, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+          else k_lagrange_cells_cached<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+        }
+      } else if (F.sdev) k_lagrange_cells<R, true, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       else if (F.Gn && F.time_order != 2)
         k_lagrange_cells_cached<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
-      else k_lagrange_cells<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      else k_lagrange_cells<R, false, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
       break;
     case kPcPositions: k_pc_positions<R><<<grid_for(F.nn), kBlock, 0, st>>>(F, S, dt_override); break;
     case kHourglass: k_hourglass<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S); break;
-    case kPcPredict: k_pc_predict<R><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override); break;
+    case kPcPredict:
+      if (mat) {
+        if constexpr (kFp64) k_pc_predict<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      } else k_pc_predict<R, false><<<grid_for(F.nc), kBlock, 0, st>>>(F, S, dt_override);
+      break;
     case kRemapFaces:
       if (mat) {
         if constexpr (kFp64) k_remap_faces<R, true><<<grid_for(F.nc), kBlock, 0, st>>>(F, S);
