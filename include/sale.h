@@ -119,8 +119,8 @@ typedef struct {
  * "szz", "sxy", "syz", "szx" and "eps_p" then exist.
  * Materials, the multi-material scheme of ScalSALE (Sec. I-D, Table I:
  * "multi-material, multiple EoS"; nmat = 0 or 1: one ideal gas of
- * `gamma`).  With 2 <= nmat <= SALE_MAX_MAT (FP64 states; single-stage
- * step, first-order remap, no strength) material k has
+ * `gamma`).  With 2 <= nmat <= SALE_MAX_MAT (FP64 states; first-order
+ * remap, no strength) material k has
  * the stiffened-gas EoS p = (mat_gamma[k] - 1) rho e - mat_gamma[k]
  * mat_pinf[k] (mat_pinf[k] = 0: ideal gas; `gamma` is unused) and every
  * cell holds each material's volume fraction alpha_k, mass m_k and
@@ -139,7 +139,9 @@ typedef struct {
  * and drops a material whose new fraction is at most SALE_MAT_ALPHA_MIN
  * (its mass and energy go to the cell's other materials by mass).  With
  * hourglass control the materials share its work by fraction and its
- * coefficient takes the mixture's sound speed.  Fields
+ * coefficient takes the mixture's sound speed; with the predictor-corrector
+ * each material's half step follows from its share of the predictor's work
+ * and its half-step share alpha_k (p_k + q) enters the corrector.  Fields
  * "alpha<k>", "m<k>", "e<k>" (k = 0 .. nmat-1) then exist; "m" and "e"
  * are the cell totals sum_k m_k and sum_k m_k e_k / m.
  * Options other than the defaults may need more device memory: size the

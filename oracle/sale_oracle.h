@@ -158,8 +158,7 @@ int oracle_set_state(oracle_state *s, const double *x, const double *y,
  * mat[c] with primitive rho0, p0, its specific energy from that
  * material's EoS; the deposit as in oracle_init_prim.  EINVAL for a
  * material index out of range, an invalid EoS, or an option the
- * multi-material scheme does not take (strength, predictor-corrector,
- * second-order remap). */
+ * multi-material scheme does not take (strength, second-order remap). */
 int oracle_init_materials(oracle_state *s, const double *rho0, const double *p0, const int *mat,
                           long long deposit_cell, double deposit_energy);
 /* Overwrite the per-material fields ([k * nc + c] layout), recompute the
