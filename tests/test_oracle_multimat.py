@@ -335,6 +335,45 @@ def test_predictor_corrector_is_second_order_for_each_material():
     assert errs[1] <= 0.35 * errs[0]  # second order: a quarter
 
 
+def test_mixed_column_standing_wave_period():
+    """A small standing wave u = eps sin(pi x) in a column of uniformly
+    mixed cells between walls (no viscosity) oscillates at the uniform-strain
+    mixture's sound speed, c^2 = sum_k m_k c_k^2 / m = sum_k alpha_k rho_k
+    c_k^2 / rho, so the kinetic energy first vanishes at t = L / (2 c).
+    Worked numbers: alpha = (0.4, 0.6), rho = (1, 2), p = 1, gamma = (1.4, 3),
+    p_inf = (0, 2): c_0^2 = 1.4, c_1^2 = 3 (1 + 2) / 2 = 4.5, c^2 = (0.4 1.4 +
+    1.2 4.5) / 1.6 = 3.725, t = 0.5 / 1.93003 = 0.25906.  A volume-weighted
+    c^2 (3.26, t = 0.2769) or Wood's pressure-equilibrium speed (c^2 = 1.774,
+    t = 0.3754) each miss by more than 6%."""
+    nx = 100
+    gam, pinf, rho, p = (1.4, 3.0), (0.0, 2.0), (1.0, 2.0), 1.0
+    md, o = mixed_box(nx, 1, 1, 0.0, gam, pinf, rho, p, c_q=0.0, c_l=0.0, frac=0.4, hi=(1.0, 1.0 / nx, 1.0 / nx))
+    x = o.field("x")
+    zero = np.zeros(md.nnode)
+    assert o.set_state(x, o.field("y"), o.field("z"), 1e-4 * np.sin(math.pi * x), zero, zero, o.field("mn"),
+                       o.field("m"), o.field("e")) == 0
+    ts, ks = [o.s.t], [o.diagnostics()["ke"]]
+    while o.s.t < 0.33:
+        rc, n = o.run(max_cycles=1)
+        assert rc == 0 and n == 1
+        ts.append(o.s.t)
+        ks.append(o.diagnostics()["ke"])
+    ks = np.array(ks)
+    i = int(np.argmin(ks))
+    assert 0 < i < len(ks) - 1
+    t0, t1, t2 = ts[i - 1], ts[i], ts[i + 1]  # the parabola through the samples around the minimum
+    k0, k1, k2 = ks[i - 1], ks[i], ks[i + 1]
+    den = (t0 - t1) * (t0 - t2) * (t1 - t2)
+    A = (t2 * (k1 - k0) + t1 * (k0 - k2) + t0 * (k2 - k1)) / den
+    B = (t2 * t2 * (k0 - k1) + t1 * t1 * (k2 - k0) + t0 * t0 * (k1 - k2)) / den
+    t_min = -B / (2.0 * A)
+    c2 = (0.4 * 1.0 * 1.4 + 0.6 * 2.0 * 4.5) / (0.4 * 1.0 + 0.6 * 2.0)
+    want = 0.5 / math.sqrt(c2)
+    assert abs(want - 0.25906) <= 1e-5
+    assert abs(t_min - want) <= 0.01 * want, (t_min, want)
+    assert ks[i] <= 1e-3 * ks[0]
+
+
 def test_first_dt_closed_forms():
     # unequal spacings: h = min(1/8, 0.6/6, 0.4/5) = 0.08
     hi = (1.0, 0.6, 0.4)
