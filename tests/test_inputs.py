@@ -61,3 +61,21 @@ def test_batch_instances_ranges():
     pr = np.array([p.p_l if p.kind == inputs.PROB_SOD_X else p.p_blast for _, p in inst])
     assert pr.min() >= 10.0 and pr.max() <= 1e4
     assert inputs.batch_instances(4)[3][0] == inst[3][0]
+
+
+def test_problem_materials_follow_the_sod_split():
+    # material 1 is exactly the right state of the shock tube (logical cell
+    # centres at or past x_split); one material: all zeros
+    import dataclasses
+    md, pd = inputs.sod_x(10, 2, 3)
+    none = inputs.problem_materials(md, pd)
+    assert none.dtype == np.int32 and not np.any(none)
+    pm = dataclasses.replace(pd, nmat=2)
+    mat = inputs.problem_materials(md, pm)
+    rho0, _, _, _ = inputs.problem_prim(md, pd)
+    assert np.array_equal(mat == 1, rho0 == pd.rho_r)
+    assert mat.reshape(3, 2, 10)[0, 0].tolist() == [0] * 5 + [1] * 5
+    # a split between two cell centres, and one past the box
+    assert inputs.problem_materials(md, dataclasses.replace(pm, x_split=0.31)).reshape(3, 2, 10)[0, 0].tolist() == \
+        [0] * 3 + [1] * 7
+    assert not np.any(inputs.problem_materials(md, dataclasses.replace(pm, x_split=2.0)))
