@@ -193,8 +193,11 @@ int sale_mesh_nodes(const sale_mesh *mesh, double *xyz, size_t n);
 size_t sale_state_bytes(const sale_mesh *mesh, int precision);
 /* Device bytes for this mesh, problem and precision: includes the scratch
  * of the second-order remap (FP64), of the predictor-corrector step
- * (half-step corner gradients) and of the hourglass control (corner
- * forces) when the problem asks for them. */
+ * (half-step corner gradients), of the hourglass control (corner forces),
+ * of material strength (stress, plastic strain, G, Y and the remap's copy)
+ * and of several materials (each material's fraction, mass and energy, its
+ * face fluxes, 1 / V_L, and with the predictor-corrector its half-step
+ * share of sigma) when the problem asks for them. */
 size_t sale_state_bytes_for(const sale_mesh *mesh, const sale_problem_desc *prob, int precision);
 /* Initialise a state in the caller's device buffer (>= sale_state_bytes_for,
  * 256-byte aligned) on `cuda_stream` (a cudaStream_t; NULL = legacy
